@@ -1,0 +1,513 @@
+/*
+ * isrs_oracle.c -- plain, slow FP64 CPU oracle of the ISRS Gaussian-noise
+ * integral model of arXiv 2401.18022 (App. A, Eqs. gain/pk/phi/slow_vary/
+ * q1..q4/gain_fin/psi_fin; Sec. II Eqs. d, d_slope, d_curve, gamma; Sec. IV
+ * Eq. loss).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg load this library; the product path never
+ * calls it, and it shares no code, header, table or constant generator with
+ * the CUDA library.  Everything is double precision, loops are written in the
+ * order of the paper's definitions, and no blocking, fusion or reordering is
+ * applied beyond tabulating per-z quantities once per z.
+ *
+ * Readings of the paper that this oracle fixes (the paper is silent on them):
+ *  - Riemann grid: G x G midpoints per rectangular "piece" (a channel-pair
+ *    cell clipped to one quadrant), uniform in s = ln(upsilon1) and, per row,
+ *    uniform in upsilon2 between the row's limits; upsilon1 is cut off below
+ *    at eps * upsilon1_max.
+ *  - z-grid: N_M edges with equal power drop per step, z-tilde_m = z_m.
+ *  - Power profile: the closed-form ISRS profile for a linear Raman slope
+ *    (the model the paper builds on, App. A), normalised by the integral of
+ *    the transmitted PSD, with per-channel attenuation.
+ *  - P_NLI,i = G(f_i) B_i and eta_i = P_NLI,i / P_i^3.
+ *
+ * Units: THz, ps, km, W.  phi in rad/km.
+ */
+#define _GNU_SOURCE
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_C_NM_PER_PS 299792.458
+#define ORC_H_PLANCK 6.62607015e-34
+
+/* ---------------------------------------------------------------------- */
+/* Sec. II, Eqs. d, d_slope, d_curve: beta2, beta3, beta4 from D, S, Sdot  */
+/* at the reference wavelength.  lambda [nm], D [ps/nm/km], S [ps/nm^2/km],*/
+/* Sdot [ps/nm^3/km]  ->  beta_k [ps^k/km].                                */
+/* ---------------------------------------------------------------------- */
+void orc_beta_from_dispersion(double lambda_nm, double D, double S, double Sdot,
+                              double *beta /* [3] */)
+{
+    double w = 2.0 * ORC_PI * ORC_C_NM_PER_PS;          /* 2 pi c [nm/ps] */
+    double l = lambda_nm;
+    beta[0] = -D * l * l / w;
+    beta[1] = l * l * l / (w * w) * (2.0 * D + S * l);
+    beta[2] = -l * l * l * l / (w * w * w) * (6.0 * D + 6.0 * S * l + Sdot * l * l);
+}
+
+/* Sec. II, Eq. gamma: gamma = 2 pi n2 / (lambda Aeff)  [1/(W km)].        */
+double orc_gamma(double lambda_nm, double n2_m2_per_W, double aeff_um2)
+{
+    double lam_m = lambda_nm * 1e-9, aeff_m2 = aeff_um2 * 1e-12;
+    return 2.0 * ORC_PI / lam_m * n2_m2_per_W / aeff_m2 * 1e3;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. III-A / App. A (slowly varying power): N_M edges, "log-scale      */
+/* distance intervals" with equal power change per step:                  */
+/*   exp(-a z_e(m)) = 1 - (m / (N_M - 1)) (1 - exp(-a L)).                 */
+/* ---------------------------------------------------------------------- */
+int orc_zgrid(double L, double a, int n_edges, double *z)
+{
+    if (n_edges < 2 || !(L > 0.0)) return -1;
+    double drop = (a > 0.0) ? 1.0 - exp(-a * L) : 0.0;
+    for (int m = 0; m < n_edges; ++m) {
+        double t = (double)m / (double)(n_edges - 1);
+        z[m] = (a > 0.0) ? -log(1.0 - t * drop) / a : t * L;
+    }
+    z[n_edges - 1] = L;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* App. A, Eq. phi: phase mismatch per unit length [rad/km] for offsets    */
+/* f1, f2 from the channel under test, fi = CUT offset from the reference. */
+/* ---------------------------------------------------------------------- */
+double orc_phi(double f1, double f2, double fi, double b2, double b3, double b4)
+{
+    double bracket = b2
+        + ORC_PI * b3 * (f1 + f2 + 2.0 * fi)
+        + (2.0 * ORC_PI * ORC_PI / 3.0) * b4
+          * (f1 * f1 + 1.5 * f1 * f2 + 3.0 * f1 * fi + f2 * f2 + 3.0 * f2 * fi + 3.0 * fi * fi);
+    return -4.0 * ORC_PI * ORC_PI * f1 * f2 * bracket;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Channel plan helpers.  G_Tx is rectangular per channel (Sec. III):      */
+/* G_Tx(F) = P_c / B_c on [f_c - B_c/2, f_c + B_c/2), zero in the gaps.    */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int n;
+    const double *f, *B, *P, *alpha;
+} orc_plan;
+
+/* index of the channel containing F, or -1 (channels sorted, disjoint) */
+static int orc_channel_of(const orc_plan *pl, double F)
+{
+    int lo = 0, hi = pl->n - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        double a = pl->f[mid] - 0.5 * pl->B[mid], b = pl->f[mid] + 0.5 * pl->B[mid];
+        if (F < a) hi = mid - 1;
+        else if (F >= b) lo = mid + 1;
+        else return mid;
+    }
+    return -1;
+}
+
+/* ---------------------------------------------------------------------- */
+/* ISRS power profile, linear Raman slope (App. A; the closed form the     */
+/* model builds on):                                                       */
+/*  rho(z,F) = e^{-alpha_c z} P_tot e^{-kappa(z)(F - f_ref)} / N(z),       */
+/*  kappa(z) = P_tot C_r L_eff(z),  L_eff(z) = (1 - e^{-alpha_R z})/alpha_R,*/
+/*  N(z) = int G_Tx(nu) e^{-kappa(z)(nu - f_ref)} dnu                      */
+/*       = sum_k P_k e^{-kappa (f_k - f_ref)} sinh(kappa B_k/2)/(kappa B_k/2)*/
+/* ln N is accumulated with a max shift so that large tilts stay finite.   */
+/* ---------------------------------------------------------------------- */
+static double orc_sinhc(double x)
+{
+    if (fabs(x) < 1e-4) return 1.0 + x * x / 6.0;
+    return sinh(x) / x;
+}
+
+double orc_leff(double z, double alpha_R)
+{
+    return (alpha_R > 0.0) ? (1.0 - exp(-alpha_R * z)) / alpha_R : z;
+}
+
+static double orc_ptot(const orc_plan *pl)
+{
+    double s = 0.0;
+    for (int k = 0; k < pl->n; ++k) s += pl->P[k];
+    return s;
+}
+
+static double orc_kappa(const orc_plan *pl, double z, double Cr, double alpha_R)
+{
+    return orc_ptot(pl) * Cr * orc_leff(z, alpha_R);
+}
+
+static double orc_lnN(const orc_plan *pl, double kappa, double f_ref)
+{
+    double mx = -INFINITY;
+    for (int k = 0; k < pl->n; ++k) {
+        if (pl->P[k] <= 0.0) continue;
+        double e = log(pl->P[k]) - kappa * (pl->f[k] - f_ref) + log(orc_sinhc(0.5 * kappa * pl->B[k]));
+        if (e > mx) mx = e;
+    }
+    double s = 0.0;
+    for (int k = 0; k < pl->n; ++k) {
+        if (pl->P[k] <= 0.0) continue;
+        double e = log(pl->P[k]) - kappa * (pl->f[k] - f_ref) + log(orc_sinhc(0.5 * kappa * pl->B[k]));
+        s += exp(e - mx);
+    }
+    return mx + log(s);
+}
+
+/* ln rho(z, F) for F inside channel c. */
+static double orc_lnrho_c(const orc_plan *pl, int c, double z, double F, double lnPtot,
+                          double lnN, double kappa, double f_ref)
+{
+    return -pl->alpha[c] * z + lnPtot - lnN - kappa * (F - f_ref);
+}
+
+/* Public: ln rho(z, F) at an arbitrary z (F must lie in a channel, else NaN). */
+double orc_lnrho(int n, const double *f, const double *B, const double *P, const double *alpha,
+                 double f_ref, double Cr, double alpha_R, double z, double F)
+{
+    orc_plan pl = {n, f, B, P, alpha};
+    int c = orc_channel_of(&pl, F);
+    if (c < 0) return NAN;
+    double kappa = orc_kappa(&pl, z, Cr, alpha_R);
+    return orc_lnrho_c(&pl, c, z, F, log(orc_ptot(&pl)), orc_lnN(&pl, kappa, f_ref), kappa, f_ref);
+}
+
+/* ---------------------------------------------------------------------- */
+/* App. A, Eq. slow_vary: the z-sum                                        */
+/*   S = sum_m p_m dz_m sinc(phi dz_m / 2) e^{j phi z_m}                   */
+/* for given per-step powers p_m (single span, L-tilde = 0).               */
+/* ---------------------------------------------------------------------- */
+static double orc_sinc(double x)
+{
+    if (fabs(x) < 1e-4) return 1.0 - x * x / 6.0;
+    return sin(x) / x;
+}
+
+void orc_zsum(int n_steps, const double *z_mid, const double *dz, const double *p, double phi,
+              double *S /* [2] re, im */)
+{
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < n_steps; ++m) {
+        double a = p[m] * dz[m] * orc_sinc(0.5 * phi * dz[m]);
+        re += a * cos(phi * z_mid[m]);
+        im += a * sin(phi * z_mid[m]);
+    }
+    S[0] = re;
+    S[1] = im;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Pieces.  The plane of offsets (f1, f2) of CUT i is split into channel-  */
+/* pair cells (a,b): F_a = f_i + f1 in channel a, F_b = f_i + f2 in        */
+/* channel b.  Each cell is cut at f1 = 0 and f2 = 0 into quadrant pieces  */
+/* (App. A, Eqs. q1a..q4d): |f1| in [x_lo, x_hi], |f2| in [y_lo, y_hi],    */
+/* signs (s1, s2).  cell_set 0: SCI + XCI cells (a == i or b == i);        */
+/* cell_set 1: all cells.                                                  */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int a, b, s1, s2;
+    double xlo, xhi, ylo, yhi;
+} orc_piece;
+
+static int orc_split(double lo, double hi, int *sg, double *plo, double *phi_)
+{
+    int k = 0;
+    if (hi > 0.0) { sg[k] = +1; plo[k] = lo > 0.0 ? lo : 0.0; phi_[k] = hi; ++k; }
+    if (lo < 0.0) { sg[k] = -1; plo[k] = hi < 0.0 ? -hi : 0.0; phi_[k] = -lo; ++k; }
+    return k;
+}
+
+/* Writes the pieces of CUT i into out (if non-NULL); returns their count. */
+int orc_pieces(int n, const double *f, const double *B, int i, int cell_set, orc_piece *out)
+{
+    int cnt = 0;
+    for (int a = 0; a < n; ++a) {
+        for (int b = 0; b < n; ++b) {
+            if (cell_set == 0 && a != i && b != i) continue;
+            int sa[2], sb[2];
+            double xl[2], xh[2], yl[2], yh[2];
+            int na = orc_split(f[a] - 0.5 * B[a] - f[i], f[a] + 0.5 * B[a] - f[i], sa, xl, xh);
+            int nb = orc_split(f[b] - 0.5 * B[b] - f[i], f[b] + 0.5 * B[b] - f[i], sb, yl, yh);
+            for (int u = 0; u < na; ++u)
+                for (int v = 0; v < nb; ++v) {
+                    if (!(xh[u] > xl[u]) || !(yh[v] > yl[v])) continue;
+                    if (out) {
+                        orc_piece *q = &out[cnt];
+                        q->a = a; q->b = b; q->s1 = sa[u]; q->s2 = sb[v];
+                        q->xlo = xl[u]; q->xhi = xh[u]; q->ylo = yl[v]; q->yhi = yh[v];
+                    }
+                    ++cnt;
+                }
+        }
+    }
+    return cnt;
+}
+
+/* Flat export of the piece list for tests: rows of
+ * (a, b, s1, s2, xlo, xhi, ylo, yhi) as doubles. */
+int orc_pieces_flat(int n, const double *f, const double *B, int i, int cell_set, double *out8)
+{
+    int cnt = orc_pieces(n, f, B, i, cell_set, NULL);
+    if (!out8) return cnt;
+    orc_piece *p = (orc_piece *)malloc(sizeof(orc_piece) * (size_t)(cnt > 0 ? cnt : 1));
+    orc_pieces(n, f, B, i, cell_set, p);
+    for (int k = 0; k < cnt; ++k) {
+        double *r = out8 + 8 * k;
+        r[0] = p[k].a; r[1] = p[k].b; r[2] = p[k].s1; r[3] = p[k].s2;
+        r[4] = p[k].xlo; r[5] = p[k].xhi; r[6] = p[k].ylo; r[7] = p[k].yhi;
+    }
+    free(p);
+    return cnt;
+}
+
+/* ---------------------------------------------------------------------- */
+/* The problem: plan, fibre, z-grid tables.                                */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    orc_plan pl;
+    double L, f_ref, b2, b3, b4, Cr, alpha_R, eps;
+    int G, n_steps, cell_set;
+    double lnPtot;
+    double *z_mid, *dz, *kappa, *lnN;   /* per step */
+    /* ones-mode: Psi's PSD product and link factor replaced by 1 (area). */
+    int unit_integrand;
+} orc_problem;
+
+static void orc_problem_tables(orc_problem *pr, int n_edges)
+{
+    pr->n_steps = n_edges - 1;
+    double *ze = (double *)malloc(sizeof(double) * (size_t)n_edges);
+    orc_zgrid(pr->L, pr->alpha_R, n_edges, ze);
+    pr->z_mid = (double *)malloc(sizeof(double) * (size_t)pr->n_steps);
+    pr->dz = (double *)malloc(sizeof(double) * (size_t)pr->n_steps);
+    pr->kappa = (double *)malloc(sizeof(double) * (size_t)pr->n_steps);
+    pr->lnN = (double *)malloc(sizeof(double) * (size_t)pr->n_steps);
+    pr->lnPtot = log(orc_ptot(&pr->pl));
+    for (int m = 0; m < pr->n_steps; ++m) {
+        pr->z_mid[m] = 0.5 * (ze[m] + ze[m + 1]);     /* z-tilde_m = z_m */
+        pr->dz[m] = ze[m + 1] - ze[m];
+        pr->kappa[m] = orc_kappa(&pr->pl, pr->z_mid[m], pr->Cr, pr->alpha_R);
+        pr->lnN[m] = orc_lnN(&pr->pl, pr->kappa[m], pr->f_ref);
+    }
+    free(ze);
+}
+
+static void orc_problem_free(orc_problem *pr)
+{
+    free(pr->z_mid); free(pr->dz); free(pr->kappa); free(pr->lnN);
+}
+
+/* ---------------------------------------------------------------------- */
+/* App. A, Eqs. q1..q4 and psi_fin: Riemann sum of one piece in hyperbolic */
+/* coordinates upsilon1 = |f1||f2|, upsilon2 = ln sqrt(|f1|/|f2|), whose   */
+/* Jacobian is 1; g1 = sqrt(u1) e^{u2}, g2 = sqrt(u1) e^{-u2}.             */
+/* ---------------------------------------------------------------------- */
+static double orc_piece_sum(const orc_problem *pr, int i, const orc_piece *q)
+{
+    const orc_plan *pl = &pr->pl;
+    const int G = pr->G;
+    double fi = pl->f[i];
+    double fi_off = fi - pr->f_ref;
+    double u1_hi = q->xhi * q->yhi;
+    double u1_lo = q->xlo * q->ylo;
+    if (u1_lo < pr->eps * u1_hi) u1_lo = pr->eps * u1_hi;
+    double ds = (log(u1_hi) - log(u1_lo)) / G;
+    double total = 0.0, comp = 0.0;
+    for (int r = 0; r < G; ++r) {
+        double u1 = exp(log(u1_lo) + (r + 0.5) * ds);
+        double ymin = q->ylo, ymax = q->yhi;
+        if (u1 / q->xhi > ymin) ymin = u1 / q->xhi;
+        if (q->xlo > 0.0 && u1 / q->xlo < ymax) ymax = u1 / q->xlo;
+        if (!(ymax > ymin)) continue;
+        double u2_lo = 0.5 * log(u1) - log(ymax);
+        double u2_hi = 0.5 * log(u1) - log(ymin);
+        double du2 = (u2_hi - u2_lo) / G;
+        double w = u1 * ds * du2;                     /* d(u1) = u1 ds */
+        for (int c = 0; c < G; ++c) {
+            double u2 = u2_lo + (c + 0.5) * du2;
+            double g1 = sqrt(u1) * exp(u2), g2 = sqrt(u1) * exp(-u2);
+            double f1 = q->s1 * g1, f2 = q->s2 * g2;
+            double val;
+            if (pr->unit_integrand) {
+                val = 1.0;
+            } else {
+                double Fa = fi + f1, Fb = fi + f2, Fc = fi + f1 + f2;
+                int ca = orc_channel_of(pl, Fa), cb = orc_channel_of(pl, Fb), cc = orc_channel_of(pl, Fc);
+                if (ca < 0 || cb < 0 || cc < 0) continue;
+                /* G_Tx(f1) G_Tx(f2) G_Tx(f1 + f2 - f) */
+                double W = (pl->P[ca] / pl->B[ca]) * (pl->P[cb] / pl->B[cb]) * (pl->P[cc] / pl->B[cc]);
+                if (W == 0.0) continue;
+                double phi = orc_phi(f1, f2, fi_off, pr->b2, pr->b3, pr->b4);
+                double Sre = 0.0, Sim = 0.0;
+                for (int m = 0; m < pr->n_steps; ++m) {
+                    double z = pr->z_mid[m];
+                    /* Eq. pk: p = sqrt(rho(F_a) rho(F_b) rho(F_c) / rho(f)) */
+                    double lra = orc_lnrho_c(pl, ca, z, Fa, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
+                    double lrb = orc_lnrho_c(pl, cb, z, Fb, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
+                    double lrc = orc_lnrho_c(pl, cc, z, Fc, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
+                    double lri = orc_lnrho_c(pl, i, z, fi, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
+                    double p = exp(0.5 * (lra + lrb + lrc - lri));
+                    /* Eq. slow_vary: p dz sinc(phi dz / 2) e^{j phi z_m} */
+                    double amp = p * pr->dz[m] * orc_sinc(0.5 * phi * pr->dz[m]);
+                    double sn, cs;
+                    sincos(phi * z, &sn, &cs);
+                    Sre += amp * cs;
+                    Sim += amp * sn;
+                }
+                val = W * (Sre * Sre + Sim * Sim);
+            }
+            /* Neumaier-compensated accumulation in FP64 */
+            double term = w * val, t = total + term;
+            if (fabs(total) >= fabs(term)) comp += (total - t) + term;
+            else comp += (term - t) + total;
+            total = t;
+        }
+    }
+    return total + comp;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Parallel driver: work items are (CUT, piece); each thread takes the    */
+/* next item from a shared counter; per-CUT sums run in piece order.      */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    const orc_problem *pr;
+    const int *item_cut;
+    const orc_piece *item_piece;
+    double *item_val;
+    long n_items;
+    long next;
+    pthread_mutex_t mu;
+} orc_work;
+
+static void *orc_worker(void *arg)
+{
+    orc_work *wk = (orc_work *)arg;
+    for (;;) {
+        pthread_mutex_lock(&wk->mu);
+        long k = wk->next++;
+        pthread_mutex_unlock(&wk->mu);
+        if (k >= wk->n_items) break;
+        wk->item_val[k] = orc_piece_sum(wk->pr, wk->item_cut[k], &wk->item_piece[k]);
+    }
+    return NULL;
+}
+
+/*
+ * Sigma_i = sum over the CUT's pieces of the Riemann sums, i.e. the frequency
+ * integral of Eq. gain_fin at f = f_i without the 16/27 gamma^2 factor
+ * [W^3 km^2 / THz].
+ *
+ * fibre[7] = {L_km, f_ref_THz, beta2, beta3, beta4, Cr, alpha_R}
+ * quad[3]  = {G, n_edges, cell_set}
+ * piece_out (optional): per-piece sums, in the order of orc_pieces, for each
+ * requested CUT one after another.
+ * unit_integrand != 0 replaces the integrand by 1 (returns covered area).
+ */
+int orc_sigma(int n, const double *f, const double *B, const double *P, const double *alpha,
+              const double *fibre, const int *quad, double eps, const int *cuts, int n_cuts,
+              int n_threads, int unit_integrand, double *sigma_out, double *piece_out)
+{
+    if (n < 1 || n_cuts < 0 || quad[0] < 1 || quad[1] < 2) return -1;
+    orc_problem pr;
+    memset(&pr, 0, sizeof(pr));
+    pr.pl.n = n; pr.pl.f = f; pr.pl.B = B; pr.pl.P = P; pr.pl.alpha = alpha;
+    pr.L = fibre[0]; pr.f_ref = fibre[1]; pr.b2 = fibre[2]; pr.b3 = fibre[3]; pr.b4 = fibre[4];
+    pr.Cr = fibre[5]; pr.alpha_R = fibre[6];
+    pr.G = quad[0]; pr.cell_set = quad[2]; pr.eps = eps; pr.unit_integrand = unit_integrand;
+    orc_problem_tables(&pr, quad[1]);
+
+    long total = 0;
+    int *cnt = (int *)malloc(sizeof(int) * (size_t)(n_cuts > 0 ? n_cuts : 1));
+    for (int k = 0; k < n_cuts; ++k) {
+        cnt[k] = orc_pieces(n, f, B, cuts[k], pr.cell_set, NULL);
+        total += cnt[k];
+    }
+    orc_piece *pieces = (orc_piece *)malloc(sizeof(orc_piece) * (size_t)(total > 0 ? total : 1));
+    int *item_cut = (int *)malloc(sizeof(int) * (size_t)(total > 0 ? total : 1));
+    double *val = (double *)calloc((size_t)(total > 0 ? total : 1), sizeof(double));
+    long off = 0;
+    for (int k = 0; k < n_cuts; ++k) {
+        orc_pieces(n, f, B, cuts[k], pr.cell_set, pieces + off);
+        for (int j = 0; j < cnt[k]; ++j) item_cut[off + j] = cuts[k];
+        off += cnt[k];
+    }
+
+    orc_work wk;
+    wk.pr = &pr; wk.item_cut = item_cut; wk.item_piece = pieces; wk.item_val = val;
+    wk.n_items = total; wk.next = 0;
+    pthread_mutex_init(&wk.mu, NULL);
+    if (n_threads < 1) n_threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, orc_worker, &wk);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&wk.mu);
+    free(th);
+
+    off = 0;
+    for (int k = 0; k < n_cuts; ++k) {
+        double s = 0.0, comp = 0.0;
+        for (int j = 0; j < cnt[k]; ++j) {
+            double term = val[off + j], t = s + term;
+            if (fabs(s) >= fabs(term)) comp += (s - t) + term;
+            else comp += (term - t) + s;
+            s = t;
+            if (piece_out) piece_out[off + j] = term;
+        }
+        sigma_out[k] = s + comp;
+        off += cnt[k];
+    }
+    free(cnt); free(pieces); free(item_cut); free(val);
+    orc_problem_free(&pr);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Eq. gain_fin with P_NLI,i = G(f_i) B_i:                                 */
+/*   eta_i = (16/27) gamma_i^2 B_i Sigma_i / P_i^3   [1/W^2]               */
+/* ---------------------------------------------------------------------- */
+void orc_eta_from_sigma(int n_cuts, const double *sigma, const double *gamma, const double *B,
+                        const double *P, double *eta, double *pnli)
+{
+    for (int k = 0; k < n_cuts; ++k) {
+        double g = 16.0 / 27.0 * gamma[k] * gamma[k] * sigma[k] * B[k];
+        if (pnli) pnli[k] = g;
+        eta[k] = (P[k] > 0.0) ? g / (P[k] * P[k] * P[k]) : NAN;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. IV, Eq. loss: amplifiers restore the launch profile, so           */
+/*   SNR_i = P_i / (eta_i P_i^3 + P_ASE,i),                               */
+/*   P_ASE,i = NF_i h f_i (G_i - 1) B_i,  G_i = 1 / rho(L, f_i),          */
+/* optional transceiver noise 1/SNR += 1/SNR_TRX, and the throughput      */
+/*   T = 2 sum_{i not guard} B_i log2(1 + SNR_i)    [Tb/s with B in THz]. */
+/* ---------------------------------------------------------------------- */
+double orc_snr_throughput(int n, const double *f, const double *B, const double *P,
+                          const double *alpha, const double *fibre, const double *eta,
+                          const double *nf_dB, double snr_trx_dB, const unsigned char *guard,
+                          double *snr, double *pase)
+{
+    orc_plan pl = {n, f, B, P, alpha};
+    double f_ref = fibre[1], Cr = fibre[5], alpha_R = fibre[6], L = fibre[0];
+    double kappa = orc_kappa(&pl, L, Cr, alpha_R);
+    double lnN = orc_lnN(&pl, kappa, f_ref), lnPtot = log(orc_ptot(&pl));
+    double T = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double lr = orc_lnrho_c(&pl, i, L, f[i], lnPtot, lnN, kappa, f_ref);
+        double gain = exp(-lr);
+        double nf = pow(10.0, nf_dB[i] / 10.0);
+        double pa = nf * ORC_H_PLANCK * (f[i] * 1e12) * (gain - 1.0) * (B[i] * 1e12);
+        if (pase) pase[i] = pa;
+        if (P[i] <= 0.0 || (guard && guard[i])) { snr[i] = 0.0; continue; }
+        double s = P[i] / (eta[i] * P[i] * P[i] * P[i] + pa);
+        if (snr_trx_dB > 0.0) s = 1.0 / (1.0 / s + pow(10.0, -snr_trx_dB / 10.0));
+        snr[i] = s;
+        T += 2.0 * B[i] * log2(1.0 + s);
+    }
+    return T;
+}
