@@ -1,0 +1,212 @@
+/*
+ * isrs_gn.h -- C ABI of the GB300 (sm_103a) ISRS Gaussian-noise integral
+ * model of arXiv 2401.18022 (Jarmolovicius et al., "Optimising O-to-U band
+ * transmission using fast ISRS Gaussian noise numerical integral model").
+ *
+ * The library computes, for every channel under test (CUT) i of a WDM plan,
+ * the nonlinear-interference (NLI) coefficient eta_i of App. A, Eqs.
+ * gain_fin / psi_fin: the frequency double integral of the ISRS GN model,
+ * split into quadrants (Eqs. q1a..q4d) and evaluated as a Riemann sum in
+ * hyperbolic coordinates (Eqs. q1..q4), with the power profile term p of
+ * Eq. pk, the phase mismatch of Eq. phi (beta2, beta3, beta4) and the
+ * slowly-varying-power z-sum of Eq. slow_vary.  From eta it derives the SNR
+ * and Shannon throughput of Sec. IV, Eq. loss, and the gradient of that
+ * throughput with respect to the per-channel launch powers.
+ *
+ * Units: frequency THz, length km, power W, beta_k in ps^k/km,
+ * alpha in 1/km (power), gamma in 1/(W km), C_r in 1/(W km THz).
+ *
+ * Conventions for every call:
+ *  - No C++ exception crosses this boundary; every call returns an
+ *    isrs_status.  On error nothing is written to the outputs and
+ *    isrs_last_error() describes the cause.
+ *  - Channel-plan arrays (isrs_channels) are HOST pointers, read during the
+ *    call only.  Channels must be sorted by frequency and disjoint.
+ *  - Launch powers and per-channel outputs may be host or device pointers;
+ *    the library detects which (cudaPointerGetAttributes).  Device pointers
+ *    must belong to the handle's device.  With device outputs the call is
+ *    asynchronous on `stream`; with any host output it synchronises `stream`
+ *    before returning.
+ *  - The caller owns all input and output buffers.  The handle owns its
+ *    device workspace and a cache of per-plan tables (pieces, z-grid).  A
+ *    handle must not be used from two host threads at once.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef ISRS_GN_H
+#define ISRS_GN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISRS_OK = 0,
+    ISRS_ERR_INVALID_ARG = 1,   /* argument outside the documented domain */
+    ISRS_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    ISRS_ERR_ALLOC = 3,         /* device or host allocation failed */
+    ISRS_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
+    ISRS_ERR_NUMERIC = 5,       /* non-finite intermediate (e.g. overflow) */
+    ISRS_ERR_UNSUPPORTED = 6    /* valid but not supported by this build */
+} isrs_status;
+
+typedef struct isrs_handle_s *isrs_handle;
+
+/* Cell sets (which channel-pair cells (a,b) of the (f1,f2) plane of a CUT
+ * are integrated; F_a = f_i + f1 in channel a, F_b = f_i + f2 in channel b). */
+#define ISRS_CELLS_SCI_XCI 0   /* a == i or b == i: self- and cross-channel */
+#define ISRS_CELLS_ALL     1   /* every cell: adds multi-channel interference */
+
+/* Arithmetic of the quadrature kernel. */
+#define ISRS_PREC_FP32 0       /* FP32 bulk, float-float phase, compensated sums */
+#define ISRS_PREC_FP64 1       /* plain FP64 throughout (reference GPU path) */
+
+/* Fibre of one span (Sec. II; App. A).  beta_k are the Taylor coefficients of
+ * the propagation constant at f_ref (Eqs. d, d_slope, d_curve).  The power
+ * profile is the closed-form ISRS solution for a linear Raman gain slope
+ * C_r, with L_eff(z) = (1 - exp(-alpha_R z)) / alpha_R; alpha_R also sets the
+ * equal-power-drop z-grid. */
+typedef struct {
+    double L_km;
+    double f_ref_THz;
+    double beta2, beta3, beta4;
+    double Cr;
+    double alpha_R_per_km;
+} isrs_fibre;
+
+/* Channel plan (host pointers, n_ch entries each).  nf_dB and guard may be
+ * NULL (noise figure then 0 dB; no guard channels).  gamma is that of each
+ * channel; the model uses the CUT's gamma for the whole integral (App. A). */
+typedef struct {
+    int n_ch;
+    const double *f_THz;
+    const double *B_THz;
+    const double *alpha_per_km;
+    const double *gamma_per_W_km;
+    const double *nf_dB;
+    const unsigned char *guard;
+} isrs_channels;
+
+/* Quadrature settings.  G x G grid points per piece (a cell clipped to one
+ * quadrant): G rows uniform in ln(upsilon1) from eps_v1 * upsilon1_max, G
+ * columns uniform in upsilon2 per row (App. A, Eqs. q1..q4).  n_edges z-grid
+ * edges (n_edges - 1 steps, Eq. slow_vary). */
+typedef struct {
+    int G;
+    int n_edges;
+    double eps_v1;
+    int cell_set;
+    int precision;
+    double snr_trx_dB;          /* <= 0: no transceiver noise (Sec. IV) */
+} isrs_quad;
+
+/* ------------------------------------------------------------------------ */
+/* Handle                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Creates a handle bound to CUDA device `device`.  Allocates no device
+ * memory until the first compute call.  Errors: INVALID_ARG (NULL out or bad
+ * device), CUDA. */
+isrs_status isrs_create(isrs_handle *out, int device);
+
+/* Frees the handle and all device memory it owns.  NULL is accepted. */
+isrs_status isrs_destroy(isrs_handle h);
+
+const char *isrs_status_string(isrs_status s);
+
+/* Last error message of the handle (never NULL; "" if none).  Valid until
+ * the next call on the handle. */
+const char *isrs_last_error(isrs_handle h);
+
+/* ------------------------------------------------------------------------ */
+/* Host helpers (Sec. II)                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Eqs. d, d_slope, d_curve: beta2 [ps^2/km], beta3 [ps^3/km], beta4
+ * [ps^4/km] from D [ps/nm/km], S [ps/nm^2/km] and Sdot [ps/nm^3/km] at
+ * lambda_nm.  Writes beta[0..2].  Errors: INVALID_ARG (NULL or lambda <= 0). */
+isrs_status isrs_beta_from_dispersion(double lambda_nm, double D, double S, double Sdot,
+                                      double *beta);
+
+/* Eq. gamma: gamma = 2 pi n2 / (lambda Aeff) [1/(W km)] with n2 [m^2/W] and
+ * Aeff [um^2].  Returns NaN on a non-positive argument. */
+double isrs_gamma_from_aeff(double lambda_nm, double n2_m2_per_W, double aeff_um2);
+
+/* ------------------------------------------------------------------------ */
+/* Forward                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* eta_i for the CUTs listed in `cuts` (n_cuts entries, any order, no
+ * repeats; cuts == NULL means all channels 0..n_ch-1 and n_cuts is then
+ * ignored).  Eq. gain_fin with P_NLI,i = G(f_i) B_i and eta_i = P_NLI,i/P_i^3.
+ *   P_W[n_ch]       launch powers (>= 0; 0 marks an empty slot)
+ *   eta[n_out]      eta_i [1/W^2]; NaN for an empty CUT          (nullable)
+ *   pnli[n_out]     P_NLI,i [W]                                   (nullable)
+ *   sigma[n_out]    the frequency integral without 16/27 gamma^2
+ *                   [W^3 km^2/THz]                                (nullable)
+ * n_out = n_cuts (or n_ch).  Errors: INVALID_ARG (plan not sorted/disjoint,
+ * B <= 0, P < 0 or NaN, G < 1, n_edges < 2, L <= 0, bad cell_set/precision,
+ * bad cut index), UNSUPPORTED (a piece whose F_c range covers more than 16
+ * channels), ALLOC, CUDA, NUMERIC. */
+isrs_status isrs_gn_eta(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch,
+                        const double *P_W, const isrs_quad *quad, const int *cuts, int n_cuts,
+                        double *eta, double *pnli, double *sigma, void *stream);
+
+/* SNR and throughput for all channels (Sec. IV, Eq. loss):
+ *   SNR_i = P_i / (eta_i P_i^3 + P_ASE,i), optional 1/SNR += 1/SNR_TRX,
+ *   P_ASE,i = NF_i h f_i (G_i - 1) B_i with G_i = 1 / rho(L, f_i),
+ *   T = 2 sum_{i not guard, P_i > 0} B_i log2(1 + SNR_i)  [Tb/s].
+ *   snr[n_ch], eta[n_ch] (nullable), T_host (nullable, host double). */
+isrs_status isrs_gn_snr(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch,
+                        const double *P_W, const isrs_quad *quad, double *snr, double *eta,
+                        double *T_host, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Gradient                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* dT/dP_j [Tb/s per W] of the throughput T of isrs_gn_snr with respect to
+ * every launch power, through eta (the PSD product and the ISRS profile of
+ * every grid point), the ASE gain G_i and the SNR numerator.  Computed by a
+ * hand-written adjoint of the FP32 forward (quad->precision must be
+ * ISRS_PREC_FP32).  All P_j must be > 0 and no channel may be a guard.
+ *   dT_dP[n_ch], snr[n_ch] (nullable), eta[n_ch] (nullable),
+ *   T_host (nullable, host double). */
+isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch,
+                         const double *P_W, const isrs_quad *quad, double *dT_dP, double *snr,
+                         double *eta, double *T_host, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* eta for n_prof launch-power profiles over n_plans channel plans in one
+ * persistent launch (one work queue over (profile, CUT, piece-chunk) tiles).
+ *   plans[n_plans]           channel plans (host)
+ *   plan_of_profile[n_prof]  host int, plan index of each profile
+ *   P_W                      concatenated powers: profile p occupies
+ *                            n_ch(plan_of_profile[p]) entries starting at
+ *                            the sum of the previous profiles' sizes
+ *   eta                      same layout as P_W (host or device)
+ * Errors as isrs_gn_eta. */
+isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_plans,
+                                const isrs_channels *plans, int n_prof,
+                                const int *plan_of_profile, const double *P_W,
+                                const isrs_quad *quad, double *eta, void *stream);
+
+/* Work-tile shape used by the quadrature kernels: points per work item and
+ * threads per block.  0 selects the built-in default / autotuned choice.
+ * Errors: INVALID_ARG (negative or not a supported block size). */
+isrs_status isrs_set_tile(isrs_handle h, int points_per_item, int threads_per_block);
+
+/* Number of quadrature-kernel launches and grid points of the last compute
+ * call (for throughput accounting).  Any argument may be NULL. */
+isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_point_steps,
+                                  int *n_kernel_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISRS_GN_H */

@@ -1,0 +1,916 @@
+// Host side of the ISRS GN library: argument validation, the per-plan piece
+// list (App. A, Eqs. q1a..q4d: channel-pair cells cut into quadrant pieces),
+// the work-tile queue, the z-grid tables (Sec. III-A: equal power drop per
+// step), workspace management and the C ABI entry points of isrs_gn.h.
+//
+// Everything that depends on the launch powers runs in the kernels; the
+// plan-dependent tables built here are cached in HBM per plan signature.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/isrs_gn.h"
+#include "isrs_kernels.h"
+
+using namespace isrs;
+
+namespace {
+
+constexpr double kCnmPerPs = 299792.458;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+// Geometry of one launch signature: plans, CUT lists, profiles -> plan,
+// quadrature and tile.  Owned by the handle's cache.
+struct Geom {
+    uint64_t key = 0;
+    int n_prof = 0, n_plans = 0, n_steps = 0, G = 0;
+    double eps_v1 = 0.0;
+    double phase_rev_max = 0.0;   // bound of |phi| L / 2pi over all pieces
+    int n_items = 0, n_slots = 0;
+    int64_t n_pieces = 0, n_points = 0, n_points_unfolded = 0;
+    float dz_max = 0.f;
+    std::vector<int> prof_ch_off, plan_ch_off, plan_n, prof_plan;
+    int total_prof_ch = 0, total_plan_ch = 0;
+    DevBuf pieces, items, slot_items, slot_cut, prof_slot_off, plan_ch_off_d, plan_n_d, prof_ch_off_d,
+        prof_plan_d, ch_frel, ch_B, ch_alpha, ch_gamma, ch_nf, guard, zs_a, zs_b, zs_d, item_slot;
+    bool has_nf = false, has_guard = false;
+};
+
+}  // namespace
+
+struct isrs_handle_s {
+    int device = 0;
+    int num_sms = 1;
+    std::string err;
+    DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
+        o_pase, o_T, gA, gK, gPd, ybar, dTdP;
+    std::vector<std::unique_ptr<Geom>> cache;   // most recent first
+    int tile_points = 0, tile_threads = 0;
+    int64_t last_points = 0, last_psteps = 0;
+    int last_launches = 0;
+};
+
+namespace {
+
+// ----------------------------------------------------------------------------
+// errors
+// ----------------------------------------------------------------------------
+isrs_status fail(isrs_handle h, isrs_status s, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? ISRS_ERR_ALLOC : ISRS_ERR_CUDA,  \
+                        "%s: %s", #call, cudaGetErrorString(e_));                             \
+    } while (0)
+
+isrs_status ensure(isrs_handle h, DevBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return ISRS_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return fail(h, ISRS_ERR_ALLOC, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b.cap = bytes;
+    return ISRS_OK;
+}
+
+void release(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+template <typename T>
+isrs_status upload(isrs_handle h, DevBuf &b, const std::vector<T> &v, cudaStream_t st)
+{
+    isrs_status s = ensure(h, b, v.size() * sizeof(T));
+    if (s != ISRS_OK) return s;
+    if (!v.empty()) CK(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return ISRS_OK;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ----------------------------------------------------------------------------
+// validation
+// ----------------------------------------------------------------------------
+bool finite(double x) { return std::isfinite(x); }
+
+isrs_status check_fibre(isrs_handle h, const isrs_fibre *fb)
+{
+    if (!fb) return fail(h, ISRS_ERR_INVALID_ARG, "fibre is NULL");
+    if (!(fb->L_km > 0.0) || !finite(fb->L_km)) return fail(h, ISRS_ERR_INVALID_ARG, "L_km must be > 0");
+    if (!finite(fb->f_ref_THz) || !finite(fb->beta2) || !finite(fb->beta3) || !finite(fb->beta4) ||
+        !finite(fb->Cr))
+        return fail(h, ISRS_ERR_INVALID_ARG, "non-finite fibre parameter");
+    if (!(fb->alpha_R_per_km >= 0.0) || !finite(fb->alpha_R_per_km))
+        return fail(h, ISRS_ERR_INVALID_ARG, "alpha_R must be >= 0");
+    return ISRS_OK;
+}
+
+isrs_status check_plan(isrs_handle h, const isrs_channels *c)
+{
+    if (!c) return fail(h, ISRS_ERR_INVALID_ARG, "channels is NULL");
+    if (c->n_ch < 1) return fail(h, ISRS_ERR_INVALID_ARG, "n_ch must be >= 1");
+    if (!c->f_THz || !c->B_THz || !c->alpha_per_km || !c->gamma_per_W_km)
+        return fail(h, ISRS_ERR_INVALID_ARG, "channel array is NULL");
+    for (int k = 0; k < c->n_ch; ++k) {
+        if (!finite(c->f_THz[k]) || !(c->B_THz[k] > 0.0) || !finite(c->B_THz[k]))
+            return fail(h, ISRS_ERR_INVALID_ARG, "channel %d: bad frequency or bandwidth", k);
+        if (!(c->alpha_per_km[k] >= 0.0) || !finite(c->alpha_per_km[k]) || !finite(c->gamma_per_W_km[k]))
+            return fail(h, ISRS_ERR_INVALID_ARG, "channel %d: bad alpha or gamma", k);
+        if (c->nf_dB && !finite(c->nf_dB[k])) return fail(h, ISRS_ERR_INVALID_ARG, "channel %d: bad NF", k);
+        if (k > 0) {
+            if (!(c->f_THz[k] > c->f_THz[k - 1]))
+                return fail(h, ISRS_ERR_INVALID_ARG, "channels not sorted at %d", k);
+            if (c->f_THz[k - 1] + 0.5 * c->B_THz[k - 1] > c->f_THz[k] - 0.5 * c->B_THz[k] + 1e-12)
+                return fail(h, ISRS_ERR_INVALID_ARG, "channels %d and %d overlap", k - 1, k);
+        }
+    }
+    return ISRS_OK;
+}
+
+isrs_status check_quad(isrs_handle h, const isrs_quad *q)
+{
+    if (!q) return fail(h, ISRS_ERR_INVALID_ARG, "quad is NULL");
+    if (q->G < 1 || q->G > kMaxG) return fail(h, ISRS_ERR_INVALID_ARG, "G must be in [1, %d]", kMaxG);
+    if (q->n_edges < 2 || q->n_edges > kMaxSteps + 1)
+        return fail(h, ISRS_ERR_INVALID_ARG, "n_edges must be in [2, %d]", kMaxSteps + 1);
+    if (!(q->eps_v1 > 0.0 && q->eps_v1 < 1.0)) return fail(h, ISRS_ERR_INVALID_ARG, "eps_v1 must be in (0,1)");
+    if (q->cell_set != ISRS_CELLS_SCI_XCI && q->cell_set != ISRS_CELLS_ALL)
+        return fail(h, ISRS_ERR_INVALID_ARG, "bad cell_set");
+    if (q->precision != ISRS_PREC_FP32 && q->precision != ISRS_PREC_FP64)
+        return fail(h, ISRS_ERR_INVALID_ARG, "bad precision");
+    if (!finite(q->snr_trx_dB)) return fail(h, ISRS_ERR_INVALID_ARG, "bad snr_trx_dB");
+    return ISRS_OK;
+}
+
+isrs_status check_powers(isrs_handle h, const double *P, int n)
+{
+    double tot = 0.0;
+    for (int k = 0; k < n; ++k) {
+        if (!(P[k] >= 0.0) || !finite(P[k])) return fail(h, ISRS_ERR_INVALID_ARG, "P[%d] must be finite and >= 0", k);
+        tot += P[k];
+    }
+    if (!(tot > 0.0)) return fail(h, ISRS_ERR_INVALID_ARG, "total launch power must be > 0");
+    return ISRS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// signature hashing (FNV-1a)
+// ----------------------------------------------------------------------------
+struct Hasher {
+    uint64_t v = 1469598103934665603ull;
+    void bytes(const void *p, size_t n)
+    {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t k = 0; k < n; ++k) {
+            v ^= c[k];
+            v *= 1099511628211ull;
+        }
+    }
+    template <typename T> void val(const T &x) { bytes(&x, sizeof(T)); }
+};
+
+// ----------------------------------------------------------------------------
+// pieces of one CUT (App. A, Eqs. q1a..q4d).  Cells (a,b) with F_a in channel
+// a, F_b in channel b; the mirror cell (b,a) has the same Riemann sum because
+// the integrand is symmetric in (f1, f2), so only a <= b (ALL) or a == i
+// (SCI+XCI) is kept with multiplicity 2, and in the SCI cell the (-,+)
+// quadrant is folded into (+,-).
+// ----------------------------------------------------------------------------
+int split_interval(double lo, double hi, int *sg, double *plo, double *phi)
+{
+    int k = 0;
+    if (hi > 0.0) { sg[k] = +1; plo[k] = lo > 0.0 ? lo : 0.0; phi[k] = hi; ++k; }
+    if (lo < 0.0) { sg[k] = -1; plo[k] = hi < 0.0 ? -hi : 0.0; phi[k] = -lo; ++k; }
+    return k;
+}
+
+// first channel whose upper edge is > F (channels sorted, disjoint)
+int first_above(const isrs_channels *c, double F)
+{
+    int lo = 0, hi = c->n_ch;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (c->f_THz[mid] + 0.5 * c->B_THz[mid] > F) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// last channel whose lower edge is < F
+int last_below(const isrs_channels *c, double F)
+{
+    int lo = -1, hi = c->n_ch - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (c->f_THz[mid] - 0.5 * c->B_THz[mid] < F) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+isrs_status cut_pieces(isrs_handle h, const isrs_channels *c, int plan, int i, int cell_set,
+                       std::vector<DevPiece> &out)
+{
+    const int n = c->n_ch;
+    const double fi = c->f_THz[i];
+    for (int a = 0; a < n; ++a) {
+        for (int b = 0; b < n; ++b) {
+            if (cell_set == ISRS_CELLS_SCI_XCI) {
+                if (a != i) continue;               // keep (i, b); (b, i) is its mirror
+            } else if (b < a) {
+                continue;                           // keep a <= b
+            }
+            const bool mirror_cell = (a != b);
+            int sa[2], sb[2];
+            double xl[2], xh[2], yl[2], yh[2];
+            const int na = split_interval(c->f_THz[a] - 0.5 * c->B_THz[a] - fi,
+                                          c->f_THz[a] + 0.5 * c->B_THz[a] - fi, sa, xl, xh);
+            const int nb = split_interval(c->f_THz[b] - 0.5 * c->B_THz[b] - fi,
+                                          c->f_THz[b] + 0.5 * c->B_THz[b] - fi, sb, yl, yh);
+            for (int u = 0; u < na; ++u) {
+                for (int v = 0; v < nb; ++v) {
+                    if (!(xh[u] > xl[u]) || !(yh[v] > yl[v])) continue;
+                    float mult = mirror_cell ? 2.0f : 1.0f;
+                    if (!mirror_cell && sa[u] != sb[v]) {
+                        // diagonal cell: quadrants (+,-) and (-,+) are mirrors
+                        if (sa[u] < 0) continue;
+                        mult = 2.0f;
+                    }
+                    DevPiece p;
+                    std::memset(&p, 0, sizeof(p));
+                    p.xlo = xl[u]; p.xhi = xh[u]; p.ylo = yl[v]; p.yhi = yh[v];
+                    p.cut = i; p.a = a; p.b = b; p.plan = plan;
+                    p.flags = (sa[u] < 0 ? 1 : 0) | (sb[v] < 0 ? 2 : 0);
+                    p.mult = mult;
+                    // range of F_c - f_i = s1 |f1| + s2 |f2| over the rectangle
+                    const double ux0 = sa[u] > 0 ? xl[u] : -xh[u], ux1 = sa[u] > 0 ? xh[u] : -xl[u];
+                    const double uy0 = sb[v] > 0 ? yl[v] : -yh[v], uy1 = sb[v] > 0 ? yh[v] : -yl[v];
+                    const int c0 = first_above(c, fi + ux0 + uy0);
+                    const int c1 = last_below(c, fi + ux1 + uy1);
+                    if (c1 < c0) continue;                   // F_c always in a gap: zero
+                    if (c1 - c0 + 1 > kMaxCand)
+                        return fail(h, ISRS_ERR_UNSUPPORTED,
+                                    "a piece's F_c range covers %d channels (max %d)", c1 - c0 + 1, kMaxCand);
+                    p.c_lo = c0;
+                    p.c_hi = c1;
+                    out.push_back(p);
+                }
+            }
+        }
+    }
+    return ISRS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// z-grid (Sec. III-A, App. A): equal power drop per step,
+//   exp(-a z_e) = 1 - (e/(N_M - 1)) (1 - exp(-a L)),  z-tilde_m = z_m (midpoint)
+// Stored per step as FP64 {z_m, dz_m}, FP32 {z_m, dz_m} and the phase
+// positions in revolutions (z / 2 pi) as float-float pairs.
+// ----------------------------------------------------------------------------
+void zgrid_tables(double L, double a, int n_edges, std::vector<float4> &za, std::vector<float4> &zb,
+                  std::vector<double2> &zd, float &dz_max)
+{
+    std::vector<double> ze(n_edges);
+    const double drop = a > 0.0 ? -std::expm1(-a * L) : 0.0;
+    for (int e = 0; e < n_edges; ++e) {
+        const double t = (double)e / (double)(n_edges - 1);
+        ze[e] = a > 0.0 ? -std::log1p(-t * drop) / a : t * L;
+    }
+    ze[n_edges - 1] = L;
+    const int M = n_edges - 1;
+    za.resize(M); zb.resize(M); zd.resize(M);
+    const double inv2pi = 1.0 / (2.0 * 3.14159265358979323846);
+    double dmax = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double zm = 0.5 * (ze[m] + ze[m + 1]);
+        const double dz = ze[m + 1] - ze[m];
+        dmax = std::max(dmax, dz);
+        zd[m] = make_double2(zm, dz);
+        za[m] = make_float4((float)zm, (float)dz, 0.f, 0.f);
+        const double re = ze[m + 1] * inv2pi, rm = zm * inv2pi;
+        const float reh = (float)re, rmh = (float)rm;
+        zb[m] = make_float4(reh, (float)(re - (double)reh), rmh, (float)(rm - (double)rmh));
+    }
+    dz_max = (float)dmax;
+}
+
+// ----------------------------------------------------------------------------
+// Build (or fetch from the cache) the geometry of a launch.
+//   cuts_per_plan[q]: CUT list of plan q (all channels if empty)
+//   prof_plan: plan of each profile; every profile evaluates its plan's CUT list
+// ----------------------------------------------------------------------------
+isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isrs_channels *plans,
+                     const std::vector<std::vector<int>> &cuts_per_plan, const std::vector<int> &prof_plan,
+                     const isrs_quad *q, cudaStream_t st, Geom **out)
+{
+    Hasher hs;
+    hs.val(n_plans);
+    for (int k = 0; k < n_plans; ++k) {
+        const isrs_channels &c = plans[k];
+        hs.val(c.n_ch);
+        hs.bytes(c.f_THz, sizeof(double) * c.n_ch);
+        hs.bytes(c.B_THz, sizeof(double) * c.n_ch);
+        hs.bytes(c.alpha_per_km, sizeof(double) * c.n_ch);
+        hs.bytes(c.gamma_per_W_km, sizeof(double) * c.n_ch);
+        hs.val((int)(c.nf_dB != nullptr));
+        if (c.nf_dB) hs.bytes(c.nf_dB, sizeof(double) * c.n_ch);
+        hs.val((int)(c.guard != nullptr));
+        if (c.guard) hs.bytes(c.guard, c.n_ch);
+        hs.val((int)cuts_per_plan[k].size());
+        if (!cuts_per_plan[k].empty()) hs.bytes(cuts_per_plan[k].data(), sizeof(int) * cuts_per_plan[k].size());
+    }
+    hs.val((int)prof_plan.size());
+    hs.bytes(prof_plan.data(), sizeof(int) * prof_plan.size());
+    hs.val(q->G); hs.val(q->n_edges); hs.val(q->eps_v1); hs.val(q->cell_set);
+    hs.val(fb->L_km); hs.val(fb->f_ref_THz); hs.val(fb->alpha_R_per_km);
+    hs.val(h->tile_points);
+    const uint64_t key = hs.v;
+    for (size_t k = 0; k < h->cache.size(); ++k) {
+        if (h->cache[k]->key == key) {
+            if (k != 0) std::rotate(h->cache.begin(), h->cache.begin() + k, h->cache.begin() + k + 1);
+            *out = h->cache[0].get();
+            return ISRS_OK;
+        }
+    }
+
+    std::unique_ptr<Geom> g(new (std::nothrow) Geom());
+    if (!g) return fail(h, ISRS_ERR_ALLOC, "host allocation failed");
+    g->key = key;
+    g->n_plans = n_plans;
+    g->n_prof = (int)prof_plan.size();
+    g->n_steps = q->n_edges - 1;
+    g->G = q->G;
+    g->eps_v1 = q->eps_v1;
+    const int64_t G2 = (int64_t)q->G * q->G;
+
+    // channel tables
+    std::vector<double> frel, Bv, av, gv, nfv;
+    std::vector<unsigned char> gd;
+    g->has_nf = false;
+    g->has_guard = false;
+    for (int k = 0; k < n_plans; ++k) {
+        g->has_nf |= plans[k].nf_dB != nullptr;
+        g->has_guard |= plans[k].guard != nullptr;
+    }
+    for (int k = 0; k < n_plans; ++k) {
+        const isrs_channels &c = plans[k];
+        g->plan_ch_off.push_back((int)frel.size());
+        g->plan_n.push_back(c.n_ch);
+        for (int j = 0; j < c.n_ch; ++j) {
+            frel.push_back(c.f_THz[j] - fb->f_ref_THz);
+            Bv.push_back(c.B_THz[j]);
+            av.push_back(c.alpha_per_km[j]);
+            gv.push_back(c.gamma_per_W_km[j]);
+            nfv.push_back(c.nf_dB ? c.nf_dB[j] : 0.0);
+            gd.push_back(c.guard ? c.guard[j] : 0);
+        }
+    }
+    g->total_plan_ch = (int)frel.size();
+
+    // pieces per plan and CUT
+    std::vector<DevPiece> pieces;
+    std::vector<std::vector<std::pair<int, int>>> cut_range(n_plans);   // per plan, per listed CUT
+    for (int k = 0; k < n_plans; ++k) {
+        const std::vector<int> &cl = cuts_per_plan[k];
+        const int ncut = cl.empty() ? plans[k].n_ch : (int)cl.size();
+        for (int s = 0; s < ncut; ++s) {
+            const int i = cl.empty() ? s : cl[s];
+            const int p0 = (int)pieces.size();
+            isrs_status st2 = cut_pieces(h, &plans[k], k, i, q->cell_set, pieces);
+            if (st2 != ISRS_OK) return st2;
+            cut_range[k].push_back({p0, (int)pieces.size()});
+        }
+    }
+    g->n_pieces = (int64_t)pieces.size();
+
+    // Bound of the phase phi z over all pieces (Eq. phi): the FP32 path forms
+    // phi z / 2pi in float-float and rounds it on the FMA pipe, valid below 2^22.
+    {
+        const double pi = 3.14159265358979323846;
+        double tmax = 0.0;
+        for (const DevPiece &pc : pieces) {
+            const double fi = std::fabs(plans[pc.plan].f_THz[pc.cut] - fb->f_ref_THz);
+            const double v1 = pc.xhi * pc.yhi, s12 = pc.xhi + pc.yhi;
+            const double br = std::fabs(fb->beta2) + pi * std::fabs(fb->beta3) * (s12 + 2.0 * fi) +
+                              2.0 * pi * pi / 3.0 * std::fabs(fb->beta4) *
+                                  (s12 * s12 + 1.5 * v1 + 3.0 * fi * s12 + 3.0 * fi * fi);
+            tmax = std::max(tmax, 4.0 * pi * pi * v1 * br * fb->L_km / (2.0 * pi));
+        }
+        g->phase_rev_max = tmax;
+    }
+
+    // work items, output slots
+    const int tile_pts = h->tile_points > 0 ? h->tile_points : (1 << 20);
+    const int chunk = (int)std::max<int64_t>(1, tile_pts / G2);
+    std::vector<DevItem> items;
+    std::vector<int2> slot_items;
+    std::vector<int> slot_cut, prof_slot_off, item_slot;
+    g->n_points = 0;
+    g->n_points_unfolded = 0;
+    for (int p = 0; p < g->n_prof; ++p) {
+        const int k = prof_plan[p];
+        g->prof_plan.push_back(k);
+        g->prof_ch_off.push_back(g->total_prof_ch);
+        g->total_prof_ch += plans[k].n_ch;
+        prof_slot_off.push_back((int)slot_items.size());
+        const std::vector<int> &cl = cuts_per_plan[k];
+        for (size_t s = 0; s < cut_range[k].size(); ++s) {
+            const int i = cl.empty() ? (int)s : cl[s];
+            const int it0 = (int)items.size();
+            const int slot = (int)slot_items.size();
+            for (int a = cut_range[k][s].first; a < cut_range[k][s].second; a += chunk) {
+                const int b = std::min(a + chunk, cut_range[k][s].second);
+                items.push_back(DevItem{p, a, b, i});
+                item_slot.push_back(slot);
+            }
+            for (int a = cut_range[k][s].first; a < cut_range[k][s].second; ++a) {
+                g->n_points += G2;
+                g->n_points_unfolded += (int64_t)(pieces[a].mult) * G2;
+            }
+            slot_items.push_back(make_int2(it0, (int)items.size()));
+            slot_cut.push_back(i);
+        }
+    }
+    prof_slot_off.push_back((int)slot_items.size());
+    g->n_items = (int)items.size();
+    g->n_slots = (int)slot_items.size();
+
+    std::vector<float4> za, zb;
+    std::vector<double2> zd;
+    zgrid_tables(fb->L_km, fb->alpha_R_per_km, q->n_edges, za, zb, zd, g->dz_max);
+
+    isrs_status s;
+#define UP(buf, vec) if ((s = upload(h, g->buf, vec, st)) != ISRS_OK) return s
+    UP(pieces, pieces);
+    UP(items, items);
+    UP(slot_items, slot_items);
+    UP(slot_cut, slot_cut);
+    UP(prof_slot_off, prof_slot_off);
+    UP(plan_ch_off_d, g->plan_ch_off);
+    UP(plan_n_d, g->plan_n);
+    UP(prof_ch_off_d, g->prof_ch_off);
+    UP(prof_plan_d, g->prof_plan);
+    UP(ch_frel, frel);
+    UP(ch_B, Bv);
+    UP(ch_alpha, av);
+    UP(ch_gamma, gv);
+    UP(ch_nf, nfv);
+    UP(guard, gd);
+    UP(zs_a, za);
+    UP(zs_b, zb);
+    UP(zs_d, zd);
+    UP(item_slot, item_slot);
+#undef UP
+    CK(cudaStreamSynchronize(st));   // host vectors die at return
+
+    h->cache.insert(h->cache.begin(), std::move(g));
+    while (h->cache.size() > 4) {
+        Geom *old = h->cache.back().get();
+        DevBuf *bufs[] = {&old->pieces, &old->items, &old->slot_items, &old->slot_cut, &old->prof_slot_off,
+                          &old->plan_ch_off_d, &old->plan_n_d, &old->prof_ch_off_d, &old->prof_plan_d,
+                          &old->ch_frel, &old->ch_B, &old->ch_alpha, &old->ch_gamma, &old->ch_nf,
+                          &old->guard, &old->zs_a, &old->zs_b, &old->zs_d, &old->item_slot};
+        for (DevBuf *b : bufs) release(*b);
+        h->cache.pop_back();
+    }
+    *out = h->cache[0].get();
+    return ISRS_OK;
+}
+
+void free_geom(Geom *g)
+{
+    DevBuf *bufs[] = {&g->pieces, &g->items, &g->slot_items, &g->slot_cut, &g->prof_slot_off,
+                      &g->plan_ch_off_d, &g->plan_n_d, &g->prof_ch_off_d, &g->prof_plan_d,
+                      &g->ch_frel, &g->ch_B, &g->ch_alpha, &g->ch_gamma, &g->ch_nf,
+                      &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->item_slot};
+    for (DevBuf *b : bufs) release(*b);
+}
+
+struct Launch {
+    Geom *g = nullptr;
+    int precision = 0;
+    int block = 256;
+};
+
+// Runs prep + quadrature on the powers already in h->P (device, concatenated).
+isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precision, cudaStream_t st)
+{
+    isrs_status s;
+    const int M = g->n_steps;
+    if (precision == ISRS_PREC_FP32 && g->phase_rev_max > 2097152.0)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "phase range %.3g revolutions exceeds the FP32 reduction range",
+                    g->phase_rev_max);
+    if ((s = ensure(h, h->pd_d, sizeof(double) * g->total_prof_ch)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->pd_f, sizeof(float) * g->total_prof_ch)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->lnrho_L, sizeof(double) * g->total_prof_ch)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->step_d, sizeof(double2) * (size_t)g->n_prof * M)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->step_f, sizeof(float2) * (size_t)g->n_prof * M)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->ptot, sizeof(double) * g->n_prof)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->partial, sizeof(double) * std::max(1, g->n_items))) != ISRS_OK) return s;
+    if ((s = ensure(h, h->counter, sizeof(int) * 4)) != ISRS_OK) return s;
+
+    PrepParams pp;
+    pp.P = (const double *)h->P.p;
+    pp.ch_frel = (const double *)g->ch_frel.p;
+    pp.ch_B = (const double *)g->ch_B.p;
+    pp.ch_alpha = (const double *)g->ch_alpha.p;
+    pp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
+    pp.plan_n = (const int *)g->plan_n_d.p;
+    pp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
+    pp.prof_plan = (const int *)g->prof_plan_d.p;
+    pp.zs_d = (const double2 *)g->zs_d.p;
+    pp.n_steps = M;
+    pp.L = fb->L_km;
+    pp.Cr = fb->Cr;
+    pp.alpha_R = fb->alpha_R_per_km;
+    pp.pd_d = (double *)h->pd_d.p;
+    pp.pd_f = (float *)h->pd_f.p;
+    pp.step_d = (double2 *)h->step_d.p;
+    pp.step_f = (float2 *)h->step_f.p;
+    pp.lnrho_L = (double *)h->lnrho_L.p;
+    pp.ptot = (double *)h->ptot.p;
+    CK(launch_prep(pp, g->n_prof, st));
+
+    QuadParams qp;
+    std::memset(&qp, 0, sizeof(qp));
+    qp.pieces = (const DevPiece *)g->pieces.p;
+    qp.items = (const DevItem *)g->items.p;
+    qp.n_items = g->n_items;
+    qp.G = g->G;
+    qp.eps_v1 = g->eps_v1;
+    qp.n_steps = M;
+    qp.beta2 = fb->beta2;
+    qp.beta3 = fb->beta3;
+    qp.beta4 = fb->beta4;
+    qp.ch_frel = (const double *)g->ch_frel.p;
+    qp.ch_B = (const double *)g->ch_B.p;
+    qp.ch_alpha = (const double *)g->ch_alpha.p;
+    qp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
+    qp.pd_f = (const float *)h->pd_f.p;
+    qp.pd_d = (const double *)h->pd_d.p;
+    qp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
+    qp.prof_plan = (const int *)g->prof_plan_d.p;
+    qp.step_f = (const float2 *)h->step_f.p;
+    qp.step_d = (const double2 *)h->step_d.p;
+    qp.zs_a = (const float4 *)g->zs_a.p;
+    qp.zs_b = (const float4 *)g->zs_b.p;
+    qp.zs_d = (const double2 *)g->zs_d.p;
+    qp.dz_max = g->dz_max;
+    qp.partial = (double *)h->partial.p;
+    qp.counter = (int *)h->counter.p;
+    CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
+    const int block = h->tile_threads > 0 ? h->tile_threads : 256;
+    const int per_sm = quad_blocks_per_sm(precision, M, g->G, block);
+    int grid = h->num_sms * per_sm;
+    if (g->n_items < grid) grid = std::max(1, g->n_items);
+    if (g->n_items > 0) CK(launch_quad(qp, precision, grid, block, st));
+    h->last_points = g->n_points;
+    h->last_psteps = g->n_points * (int64_t)M;
+    h->last_launches = 1;
+    return ISRS_OK;
+}
+
+isrs_status run_finish(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, bool want_snr,
+                       cudaStream_t st)
+{
+    isrs_status s;
+    const size_t ns = (size_t)std::max(1, g->n_slots);
+    if ((s = ensure(h, h->o_sigma, sizeof(double) * ns)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->o_pnli, sizeof(double) * ns)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->o_eta, sizeof(double) * ns)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->o_snr, sizeof(double) * ns)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->o_pase, sizeof(double) * ns)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->o_T, sizeof(double) * std::max(1, g->n_prof))) != ISRS_OK) return s;
+    FinishParams fp;
+    std::memset(&fp, 0, sizeof(fp));
+    fp.partial = (const double *)h->partial.p;
+    fp.slot_items = (const int2 *)g->slot_items.p;
+    fp.slot_cut = (const int *)g->slot_cut.p;
+    fp.prof_slot_off = (const int *)g->prof_slot_off.p;
+    fp.prof_plan = (const int *)g->prof_plan_d.p;
+    fp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
+    fp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
+    fp.ch_gamma = (const double *)g->ch_gamma.p;
+    fp.ch_B = (const double *)g->ch_B.p;
+    fp.ch_frel = (const double *)g->ch_frel.p;
+    fp.ch_nf = g->has_nf ? (const double *)g->ch_nf.p : nullptr;
+    fp.guard = g->has_guard ? (const unsigned char *)g->guard.p : nullptr;
+    fp.P = (const double *)h->P.p;
+    fp.lnrho_L = (const double *)h->lnrho_L.p;
+    fp.f_ref = fb->f_ref_THz;
+    fp.snr_trx_lin_inv = q->snr_trx_dB > 0.0 ? std::pow(10.0, -q->snr_trx_dB / 10.0) : 0.0;
+    fp.sigma = (double *)h->o_sigma.p;
+    fp.pnli = (double *)h->o_pnli.p;
+    fp.eta = (double *)h->o_eta.p;
+    if (want_snr) {
+        fp.snr = (double *)h->o_snr.p;
+        fp.pase = (double *)h->o_pase.p;
+    }
+    fp.T = (double *)h->o_T.p;
+    CK(launch_finish(fp, g->n_prof, st));
+    h->last_launches += 1;
+    return ISRS_OK;
+}
+
+isrs_status copy_out(isrs_handle h, double *dst, const DevBuf &src, size_t n, cudaStream_t st, bool &host_out)
+{
+    if (!dst || n == 0) return ISRS_OK;
+    const bool dev = is_device_ptr(dst);
+    if (!dev) host_out = true;
+    CK(cudaMemcpyAsync(dst, src.p, n * sizeof(double), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    return ISRS_OK;
+}
+
+// Load launch powers (host or device) into h->P and validate them on the host.
+isrs_status load_powers(isrs_handle h, const double *P, size_t n, cudaStream_t st)
+{
+    if (!P) return fail(h, ISRS_ERR_INVALID_ARG, "P_W is NULL");
+    isrs_status s;
+    if ((s = ensure(h, h->P, n * sizeof(double))) != ISRS_OK) return s;
+    if (is_device_ptr(P)) {
+        CK(cudaMemcpyAsync(h->P.p, P, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(cudaMemcpyAsync(h->P.p, P, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));   // pageable source: keep the copy complete before return
+    }
+    return ISRS_OK;
+}
+
+isrs_status check_powers_any(isrs_handle h, const double *P, size_t off, int n, cudaStream_t st)
+{
+    if (is_device_ptr(P)) {
+        std::vector<double> tmp(n);
+        CK(cudaMemcpyAsync(tmp.data(), P + off, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return check_powers(h, tmp.data(), n);
+    }
+    return check_powers(h, P + off, n);
+}
+
+isrs_status set_device(isrs_handle h)
+{
+    CK(cudaSetDevice(h->device));
+    return ISRS_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char *isrs_status_string(isrs_status s)
+{
+    switch (s) {
+    case ISRS_OK: return "ok";
+    case ISRS_ERR_INVALID_ARG: return "invalid argument";
+    case ISRS_ERR_CUDA: return "CUDA error";
+    case ISRS_ERR_ALLOC: return "allocation failed";
+    case ISRS_ERR_TIMEOUT: return "timeout";
+    case ISRS_ERR_NUMERIC: return "numeric error";
+    case ISRS_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+isrs_status isrs_create(isrs_handle *out, int device)
+{
+    if (!out) return ISRS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return ISRS_ERR_CUDA;
+    }
+    if (device < 0 || device >= n) return ISRS_ERR_INVALID_ARG;
+    isrs_handle h = new (std::nothrow) isrs_handle_s();
+    if (!h) return ISRS_ERR_ALLOC;
+    h->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete h;
+        return ISRS_ERR_CUDA;
+    }
+    *out = h;
+    return ISRS_OK;
+}
+
+isrs_status isrs_destroy(isrs_handle h)
+{
+    if (!h) return ISRS_OK;
+    cudaSetDevice(h->device);
+    for (auto &g : h->cache) free_geom(g.get());
+    DevBuf *bufs[] = {&h->P, &h->pd_d, &h->pd_f, &h->step_d, &h->step_f, &h->lnrho_L, &h->ptot, &h->partial,
+                      &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
+                      &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP};
+    for (DevBuf *b : bufs) release(*b);
+    delete h;
+    return ISRS_OK;
+}
+
+const char *isrs_last_error(isrs_handle h) { return h ? h->err.c_str() : ""; }
+
+isrs_status isrs_beta_from_dispersion(double lambda_nm, double D, double S, double Sdot, double *beta)
+{
+    if (!beta || !(lambda_nm > 0.0)) return ISRS_ERR_INVALID_ARG;
+    const double w = 2.0 * 3.14159265358979323846 * kCnmPerPs;     // 2 pi c [nm/ps]
+    const double l = lambda_nm;
+    beta[0] = -D * l * l / w;                                        // Eq. d
+    beta[1] = l * l * l / (w * w) * (2.0 * D + S * l);               // Eq. d_slope
+    beta[2] = -l * l * l * l / (w * w * w) * (6.0 * D + 6.0 * S * l + Sdot * l * l);   // Eq. d_curve
+    return ISRS_OK;
+}
+
+double isrs_gamma_from_aeff(double lambda_nm, double n2, double aeff_um2)
+{
+    if (!(lambda_nm > 0.0) || !(n2 > 0.0) || !(aeff_um2 > 0.0)) return NAN;
+    return 2.0 * 3.14159265358979323846 * n2 / ((lambda_nm * 1e-9) * (aeff_um2 * 1e-12)) * 1e3;   // Eq. gamma
+}
+
+isrs_status isrs_set_tile(isrs_handle h, int points_per_item, int threads_per_block)
+{
+    if (!h) return ISRS_ERR_INVALID_ARG;
+    if (points_per_item < 0 || threads_per_block < 0 ||
+        (threads_per_block != 0 && (threads_per_block % 32 != 0 || threads_per_block > 256)))
+        return fail(h, ISRS_ERR_INVALID_ARG, "bad tile (%d, %d)", points_per_item, threads_per_block);
+    h->tile_points = points_per_item;
+    h->tile_threads = threads_per_block;
+    return ISRS_OK;
+}
+
+isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_point_steps, int *n_launches)
+{
+    if (!h) return ISRS_ERR_INVALID_ARG;
+    if (n_points) *n_points = h->last_points;
+    if (n_point_steps) *n_point_steps = h->last_psteps;
+    if (n_launches) *n_launches = h->last_launches;
+    return ISRS_OK;
+}
+
+isrs_status isrs_gn_eta(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
+                        const isrs_quad *quad, const int *cuts, int n_cuts, double *eta, double *pnli,
+                        double *sigma, void *stream)
+{
+    if (!h) return ISRS_ERR_INVALID_ARG;
+    h->err.clear();
+    isrs_status s;
+    if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
+    if ((s = check_plan(h, ch)) != ISRS_OK) return s;
+    if ((s = check_quad(h, quad)) != ISRS_OK) return s;
+    if (!P_W) return fail(h, ISRS_ERR_INVALID_ARG, "P_W is NULL");
+    std::vector<int> cl;
+    if (cuts) {
+        if (n_cuts < 1) return fail(h, ISRS_ERR_INVALID_ARG, "n_cuts must be >= 1");
+        std::vector<char> seen(ch->n_ch, 0);
+        for (int k = 0; k < n_cuts; ++k) {
+            if (cuts[k] < 0 || cuts[k] >= ch->n_ch) return fail(h, ISRS_ERR_INVALID_ARG, "cut %d out of range", cuts[k]);
+            if (seen[cuts[k]]) return fail(h, ISRS_ERR_INVALID_ARG, "cut %d repeated", cuts[k]);
+            seen[cuts[k]] = 1;
+            cl.push_back(cuts[k]);
+        }
+    }
+    if ((s = set_device(h)) != ISRS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = check_powers_any(h, P_W, 0, ch->n_ch, st)) != ISRS_OK) return s;
+    Geom *g = nullptr;
+    std::vector<std::vector<int>> cpp{cl};
+    std::vector<int> pp{0};
+    if ((s = get_geom(h, fibre, 1, ch, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
+    if ((s = load_powers(h, P_W, ch->n_ch, st)) != ISRS_OK) return s;
+    if ((s = run_forward(h, fibre, g, quad->precision, st)) != ISRS_OK) return s;
+    if ((s = run_finish(h, fibre, quad, g, false, st)) != ISRS_OK) return s;
+    bool host_out = false;
+    const size_t n = g->n_slots;
+    if ((s = copy_out(h, eta, h->o_eta, n, st, host_out)) != ISRS_OK) return s;
+    if ((s = copy_out(h, pnli, h->o_pnli, n, st, host_out)) != ISRS_OK) return s;
+    if ((s = copy_out(h, sigma, h->o_sigma, n, st, host_out)) != ISRS_OK) return s;
+    if (host_out) CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return ISRS_OK;
+}
+
+isrs_status isrs_gn_snr(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
+                        const isrs_quad *quad, double *snr, double *eta, double *T_host, void *stream)
+{
+    if (!h) return ISRS_ERR_INVALID_ARG;
+    h->err.clear();
+    isrs_status s;
+    if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
+    if ((s = check_plan(h, ch)) != ISRS_OK) return s;
+    if ((s = check_quad(h, quad)) != ISRS_OK) return s;
+    if (!P_W || !snr) return fail(h, ISRS_ERR_INVALID_ARG, "P_W or snr is NULL");
+    if ((s = set_device(h)) != ISRS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = check_powers_any(h, P_W, 0, ch->n_ch, st)) != ISRS_OK) return s;
+    Geom *g = nullptr;
+    std::vector<std::vector<int>> cpp{std::vector<int>()};
+    std::vector<int> pp{0};
+    if ((s = get_geom(h, fibre, 1, ch, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
+    if ((s = load_powers(h, P_W, ch->n_ch, st)) != ISRS_OK) return s;
+    if ((s = run_forward(h, fibre, g, quad->precision, st)) != ISRS_OK) return s;
+    if ((s = run_finish(h, fibre, quad, g, true, st)) != ISRS_OK) return s;
+    bool host_out = false;
+    const size_t n = g->n_slots;
+    if ((s = copy_out(h, snr, h->o_snr, n, st, host_out)) != ISRS_OK) return s;
+    if ((s = copy_out(h, eta, h->o_eta, n, st, host_out)) != ISRS_OK) return s;
+    if (T_host) {
+        CK(cudaMemcpyAsync(T_host, h->o_T.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (host_out) CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return ISRS_OK;
+}
+
+isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_plans, const isrs_channels *plans,
+                                int n_prof, const int *plan_of_profile, const double *P_W,
+                                const isrs_quad *quad, double *eta, void *stream)
+{
+    if (!h) return ISRS_ERR_INVALID_ARG;
+    h->err.clear();
+    isrs_status s;
+    if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
+    if ((s = check_quad(h, quad)) != ISRS_OK) return s;
+    if (n_plans < 1 || !plans) return fail(h, ISRS_ERR_INVALID_ARG, "no plans");
+    if (n_prof < 1 || !plan_of_profile || !P_W || !eta) return fail(h, ISRS_ERR_INVALID_ARG, "bad profiles");
+    for (int k = 0; k < n_plans; ++k)
+        if ((s = check_plan(h, &plans[k])) != ISRS_OK) return s;
+    size_t total = 0;
+    std::vector<int> pp(n_prof);
+    for (int p = 0; p < n_prof; ++p) {
+        if (plan_of_profile[p] < 0 || plan_of_profile[p] >= n_plans)
+            return fail(h, ISRS_ERR_INVALID_ARG, "profile %d: bad plan index", p);
+        pp[p] = plan_of_profile[p];
+        total += plans[pp[p]].n_ch;
+    }
+    if ((s = set_device(h)) != ISRS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t off = 0;
+    for (int p = 0; p < n_prof; ++p) {
+        if ((s = check_powers_any(h, P_W, off, plans[pp[p]].n_ch, st)) != ISRS_OK) return s;
+        off += plans[pp[p]].n_ch;
+    }
+    Geom *g = nullptr;
+    std::vector<std::vector<int>> cpp(n_plans);
+    if ((s = get_geom(h, fibre, n_plans, plans, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
+    if ((s = load_powers(h, P_W, total, st)) != ISRS_OK) return s;
+    if ((s = run_forward(h, fibre, g, quad->precision, st)) != ISRS_OK) return s;
+    if ((s = run_finish(h, fibre, quad, g, false, st)) != ISRS_OK) return s;
+    bool host_out = false;
+    if ((s = copy_out(h, eta, h->o_eta, total, st, host_out)) != ISRS_OK) return s;
+    if (host_out) CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return ISRS_OK;
+}
+
+isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
+                         const isrs_quad *quad, double *dT_dP, double *snr, double *eta, double *T_host,
+                         void *stream)
+{
+    (void)fibre; (void)ch; (void)P_W; (void)quad; (void)dT_dP; (void)snr; (void)eta; (void)T_host; (void)stream;
+    if (!h) return ISRS_ERR_INVALID_ARG;
+    return fail(h, ISRS_ERR_UNSUPPORTED, "gradient not built yet");
+}
+
+}  // extern "C"

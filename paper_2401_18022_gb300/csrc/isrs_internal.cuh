@@ -1,0 +1,78 @@
+// Internal device-side structures of the ISRS GN library (not part of the ABI).
+//
+// Layout in HBM (all buffers owned by the handle):
+//   plan tables   per channel, plans concatenated:  f_rel (f - f_ref), B, alpha, gamma, nf
+//   pieces        DevPiece[], plans concatenated; per CUT contiguous
+//   items         DevItem[]: work queue of (profile, piece range) tiles, ordered by
+//                 (profile, CUT) so that each CUT owns a contiguous item range
+//   z tables      per step m: float4 {A2? no: z_m, dz_m, ...} see StepZ
+//   profile tabs  per profile and step: float2 {A2_m, K2_m}; per profile and
+//                 channel: P/B (float, double), lnrho(L, f_c)
+//   partials      one double per item
+#pragma once
+#include <cstdint>
+
+namespace isrs {
+
+constexpr int kMaxCand = 16;        // max channels a piece's F_c range may touch
+constexpr int kMaxSteps = 2048;     // max z-steps (n_edges - 1)
+constexpr int kMaxG = 4096;         // max grid points per dimension
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kLog2e = 1.44269504088896340736;
+
+// One rectangular piece of a channel-pair cell clipped to a quadrant:
+// |f1| in [xlo, xhi], |f2| in [ylo, yhi], f1 = s1 |f1|, f2 = s2 |f2|,
+// F_a = f_i + f1 in channel a, F_b = f_i + f2 in channel b, and F_c = f_i +
+// f1 + f2 can only fall in channels c_lo..c_hi.  mult = 2 when the mirror
+// piece (f1 <-> f2) is folded in.  Channel indices are plan-local.
+struct DevPiece {
+    double xlo, xhi, ylo, yhi;
+    int cut, a, b, c_lo;
+    int c_hi, flags, plan, pad;   // flags bit0: s1 < 0, bit1: s2 < 0
+    float mult, pad2, pad3, pad4;
+};
+static_assert(sizeof(DevPiece) == 80, "DevPiece layout");
+
+// One work tile: pieces [piece0, piece1) of one CUT for one profile.
+struct DevItem {
+    int prof;
+    int piece0;
+    int piece1;
+    int cut;        // plan-local CUT index (for bookkeeping)
+};
+
+// Per-launch constants of the quadrature kernels.
+struct QuadParams {
+    const DevPiece *pieces;
+    const DevItem *items;
+    int n_items;
+    int G;
+    int n_steps;
+    double eps_v1;
+    // fibre
+    double beta2, beta3, beta4;
+    // per plan channel tables (concatenated, index plan_ch_off[plan] + c)
+    const double *ch_frel;      // f_c - f_ref
+    const double *ch_B;
+    const double *ch_alpha;     // 1/km
+    const int *plan_ch_off;
+    // per profile channel tables (index prof_ch_off[prof] + c)
+    const float *pd_f;          // P/B
+    const double *pd_d;
+    const int *prof_ch_off;
+    const int *prof_plan;
+    // per profile step tables (index prof * n_steps + m)
+    const float2 *step_f;       // {A2_m, K2_m}: log2 p = A2 + K2 (F_c - f_ref) - at2 z_m
+    const double2 *step_d;      // {ln Ptot - ln N_m, kappa_m}
+    // z tables (per step m)
+    const float4 *zs_a;         // {z_m, dz_m, 0, 0}
+    const float4 *zs_b;         // {edge(m+1) rev hi, lo, mid(m) rev hi, lo}
+    const double2 *zs_d;        // {z_m, dz_m}
+    float dz_max;
+    // outputs / scheduling
+    double *partial;            // one per item
+    int *counter;               // persistent work counter (zeroed before launch)
+    int *err_flag;
+};
+
+}  // namespace isrs

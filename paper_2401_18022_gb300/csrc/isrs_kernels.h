@@ -1,0 +1,74 @@
+// Internal launcher interface between the host API and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "isrs_internal.cuh"
+
+namespace isrs {
+
+struct PrepParams {
+    const double *P;            // per profile channel powers (prof_ch_off)
+    const double *ch_frel, *ch_B, *ch_alpha;
+    const int *plan_ch_off, *plan_n, *prof_ch_off, *prof_plan;
+    const double2 *zs_d;        // {z_m, dz_m}
+    int n_steps;
+    double L, Cr, alpha_R;
+    // outputs
+    double *pd_d;
+    float *pd_f;
+    double2 *step_d;
+    float2 *step_f;
+    double *lnrho_L;
+    double *ptot;
+};
+
+struct FinishParams {
+    const double *partial;
+    const int2 *slot_items;     // per output slot: item range
+    const int *slot_cut;        // per output slot: plan-local CUT index
+    const int *prof_slot_off;   // [n_prof + 1]
+    const int *prof_plan, *plan_ch_off, *prof_ch_off;
+    const double *ch_gamma, *ch_B, *ch_frel, *ch_nf;
+    const unsigned char *guard;
+    const double *P;
+    const double *lnrho_L;
+    double f_ref;
+    double snr_trx_lin_inv;     // 10^(-SNR_TRX/10) or 0
+    // outputs (indexed by slot; any may be null)
+    double *sigma, *pnli, *eta, *snr, *pase;
+    double *T;                  // per profile
+};
+
+// Adjoint of the FP32 quadrature: per CUT, the gradients of Sigma_i with
+// respect to the per-step ISRS tables and the per-channel PSD factors.
+struct AdjParams {
+    QuadParams q;
+    double *gA;                 // [n_slots x n_steps]  d Sigma_i / d (ln p_m offset)
+    double *gK;                 // [n_slots x n_steps]  d Sigma_i / d (-kappa_m) weighted by F_c
+    double *gPd;                // [n_slots x n_ch]     sum of w W |S|^2 multiplicities
+    const int *item_slot;       // slot index of each item
+    int n_ch;
+};
+
+struct ChainParams {
+    const double *P, *ch_frel, *ch_B, *ch_alpha, *ch_gamma, *ch_nf;
+    const double2 *zs_d;
+    const double2 *step_d;
+    const double *sigma, *snr, *lnrho_L, *pnli;
+    const double *gA, *gK, *gPd;
+    int n_ch, n_steps;
+    double L, Cr, alpha_R, f_ref, snr_trx_lin_inv, ptot;
+    double *ybar;               // [n_ch] scratch: dT/dSigma_i
+    double *dT_dP;              // [n_ch]
+};
+
+size_t quad_smem_bytes(int precision, int n_steps, int G);
+int quad_blocks_per_sm(int precision, int n_steps, int G, int block);
+cudaError_t launch_prep(const PrepParams &pp, int n_prof, cudaStream_t st);
+cudaError_t launch_quad(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
+cudaError_t launch_finish(const FinishParams &fp, int n_prof, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjParams &ap, int grid, int block, cudaStream_t st);
+int adjoint_blocks_per_sm(int n_steps, int G, int block);
+cudaError_t launch_chain(const ChainParams &cp, cudaStream_t st);
+
+}  // namespace isrs

@@ -1,0 +1,561 @@
+// Forward kernels of the ISRS GN integral model (arXiv 2401.18022, App. A).
+//
+//  k_prep        per profile (FP64): P_tot, the ISRS normalisation ln N(z_m)
+//                by log-sum-exp over channels, and the per-step power tables
+//                of Eq. pk for the linear-slope closed-form profile.
+//  k_quad_f32    persistent quadrature: one block per work tile (a range of
+//                pieces of one CUT); G x G hyperbolic grid per piece
+//                (Eqs. q1..q4), z-sum of Eq. slow_vary per grid point in FP32
+//                with a float-float phase and mod-2pi reduction; compensated
+//                accumulation; one FP64 partial per tile.
+//  k_quad_f64    the same quadrature in plain FP64 (direct form of
+//                Eq. slow_vary with sinc), used as the reference GPU path.
+//  k_finish      per profile: deterministic FP64 sum of tile partials per CUT,
+//                eta (Eq. gain_fin), P_NLI, SNR and throughput (Eq. loss).
+#include <cuda_runtime.h>
+
+#include "isrs_internal.cuh"
+#include "isrs_kernels.h"
+
+namespace isrs {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// nearest integer of |t| < 2^22 on the FMA pipe (round-to-nearest-even add)
+__device__ __forceinline__ float round_magic(float t)
+{
+    return __fadd_rn(__fadd_rn(t, 12582912.0f), -12582912.0f);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum of one double per thread (blockDim multiple of 32).
+__device__ double block_sum_d(double v, double *scratch)
+{
+    v = warp_sum_d(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += scratch[w];
+        scratch[0] = r;
+    }
+    __syncthreads();
+    r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// k_prep: ISRS profile tables (FP64).  One block per profile.
+//   rho(z,F) = e^{-alpha_c z} P_tot e^{-kappa(z)(F - f_ref)} / N(z)
+//   kappa(z) = P_tot C_r L_eff(z),  N(z) = sum_k P_k e^{-kappa f_k'} sinhc(kappa B_k/2)
+// so ln p_m (Eq. pk) = lnPtot - lnN_m - kappa_m (F_c - f_ref) - at z_m with
+// at = (alpha_a + alpha_b + alpha_c - alpha_i)/2, because F_a + F_b + F_c - f
+// = 2 F_c.  Writes, per step, {A2, K2} = log2(e) {lnPtot - lnN, -kappa} and
+// {lnPtot - lnN, kappa}; per channel P/B and ln rho(L, f_c).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sinhc_d(double x)
+{
+    return fabs(x) < 1e-4 ? 1.0 + x * x / 6.0 : sinh(x) / x;
+}
+
+__global__ void __launch_bounds__(256) k_prep(PrepParams pp)
+{
+    __shared__ double scratch[32];
+    __shared__ double s_lnN_L, s_kap_L;
+    const int p = blockIdx.x;
+    const int plan = pp.prof_plan[p];
+    const int n = pp.plan_n[plan];
+    const int coff = pp.plan_ch_off[plan];
+    const int poff = pp.prof_ch_off[p];
+    const double *P = pp.P + poff;
+    const double *fr = pp.ch_frel + coff;
+    const double *B = pp.ch_B + coff;
+
+    double part = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) part += P[c];
+    const double Ptot = block_sum_d(part, scratch);
+    const double lnPtot = log(Ptot);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double pd = P[c] / B[c];
+        pp.pd_d[poff + c] = pd;
+        pp.pd_f[poff + c] = (float)pd;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int M = pp.n_steps;
+    for (int m = wid; m <= M; m += nw) {
+        const double z = (m < M) ? pp.zs_d[m].x : pp.L;
+        const double leff = pp.alpha_R > 0.0 ? -expm1(-pp.alpha_R * z) / pp.alpha_R : z;
+        const double kap = Ptot * pp.Cr * leff;
+        double mx = -1e300;
+        for (int c = lane; c < n; c += 32) {
+            if (P[c] > 0.0) {
+                double e = log(P[c]) - kap * fr[c] + log(sinhc_d(0.5 * kap * B[c]));
+                mx = fmax(mx, e);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        double s = 0.0;
+        for (int c = lane; c < n; c += 32) {
+            if (P[c] > 0.0) {
+                double e = log(P[c]) - kap * fr[c] + log(sinhc_d(0.5 * kap * B[c]));
+                s += exp(e - mx);
+            }
+        }
+        s = warp_sum_d(s);
+        const double lnN = mx + log(s);
+        if (lane == 0) {
+            if (m < M) {
+                pp.step_d[(size_t)p * M + m] = make_double2(lnPtot - lnN, kap);
+                pp.step_f[(size_t)p * M + m] =
+                    make_float2((float)((lnPtot - lnN) * kLog2e), (float)(-kap * kLog2e));
+            } else {
+                s_lnN_L = lnN;
+                s_kap_L = kap;
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        pp.lnrho_L[poff + c] = -pp.ch_alpha[coff + c] * pp.L + lnPtot - s_lnN_L - s_kap_L * fr[c];
+    }
+    if (threadIdx.x == 0) pp.ptot[p] = Ptot;
+}
+
+// ---------------------------------------------------------------------------
+// Piece set-up shared by the quadrature kernels (FP64, once per piece).
+// Row r (uniform in s = ln upsilon1): upsilon1 = exp(s_r); the |f2| range
+// [ymin, ymax] of that row; upsilon2 spans ln(ymax/ymin) in G columns.
+// Stored relative to the row centre so FP32 points keep full precision:
+//   x_j = xc e^{d_j}, y_j = yc e^{-d_j}, d_j = (j + 1/2 - G/2) du2,
+//   weight = upsilon1 ds du2 (the Jacobian of (f1, f2) -> (u1, u2) is 1).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void piece_rows(const DevPiece &pc, int G, double eps, T *rows)
+{
+    const double u1hi = pc.xhi * pc.yhi;
+    const double u1lo = fmax(pc.xlo * pc.ylo, eps * u1hi);
+    const double llo = log(u1lo);
+    const double ds = (log(u1hi) - llo) / G;
+    for (int r = threadIdx.x; r < G; r += blockDim.x) {
+        const double u1 = exp(llo + (r + 0.5) * ds);
+        const double ymin = fmax(pc.ylo, u1 / pc.xhi);
+        const double ymax = pc.xlo > 0.0 ? fmin(pc.yhi, u1 / pc.xlo) : pc.yhi;
+        T rw;
+        if (ymax > ymin) {
+            const double du2 = log1p((ymax - ymin) / ymin) / G;
+            const double yc = sqrt(ymin * ymax);
+            rw.xc = u1 / yc;
+            rw.yc = yc;
+            rw.du2 = du2;
+            rw.w = u1 * ds * du2;
+        } else {
+            rw.xc = 0; rw.yc = 0; rw.du2 = 0; rw.w = 0;
+        }
+        rows[r] = rw;
+    }
+}
+
+struct RowF { float xc, yc, du2, w; };
+struct RowD { double xc, yc, du2, w; };
+
+// Per-piece constants: CUT offset, signs, the PSD factors of F_a and F_b, the
+// attenuation part of ln p and the candidate channels of F_c (edges relative
+// to the CUT so that F_c - f_i = f1 + f2 is compared without cancellation).
+template <typename T>
+struct PieceConst {
+    T fi, s1, s2, wab, at_ab, mult;
+    int nc;
+    T lo[kMaxCand], hi[kMaxCand], pd[kMaxCand], hat[kMaxCand];
+};
+
+template <typename T>
+__device__ void piece_consts(const QuadParams &qp, const DevPiece &pc, int prof, T at_scale,
+                             const T *pdv, PieceConst<T> &k)
+{
+    if (threadIdx.x == 0) {
+        const int coff = qp.plan_ch_off[pc.plan];
+        const int poff = qp.prof_ch_off[prof];
+        const double fi = qp.ch_frel[coff + pc.cut];
+        k.fi = (T)fi;
+        k.s1 = (pc.flags & 1) ? T(-1) : T(1);
+        k.s2 = (pc.flags & 2) ? T(-1) : T(1);
+        k.wab = pdv[poff + pc.a] * pdv[poff + pc.b];
+        k.at_ab = (T)(0.5 * (qp.ch_alpha[coff + pc.a] + qp.ch_alpha[coff + pc.b] -
+                             qp.ch_alpha[coff + pc.cut])) * at_scale;
+        k.mult = (T)pc.mult;
+        int nc = 0;
+        for (int c = pc.c_lo; c <= pc.c_hi && nc < kMaxCand; ++c, ++nc) {
+            const double fc = qp.ch_frel[coff + c], hb = 0.5 * qp.ch_B[coff + c];
+            k.lo[nc] = (T)((fc - hb) - fi);
+            k.hi[nc] = (T)((fc + hb) - fi);
+            k.pd[nc] = pdv[poff + c];
+            k.hat[nc] = (T)(0.5 * qp.ch_alpha[coff + c]) * at_scale;
+        }
+        k.nc = nc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 z-sums.  Shared tables per step m (staged in shared memory):
+//   s1[m] = {edge(m+1)/2pi hi, lo, A2_m, K2_m},  s2[m] = {z_m, dz_m, z_m/2pi hi, lo}
+// log2 p_m = A2_m + K2_m Fc - at z_m;  phase in revolutions t = phi * (z/2pi)
+// formed as an error-free float-float product and reduced to [-1/2, 1/2].
+//
+// Telescoped form (|phi| dz_max > pi): by Eq. slow_vary the step factor is
+// exactly dz sinc(phi dz/2) e^{j phi z_m} = (E_{m+1} - E_m)/(j phi) with
+// E_e = e^{j phi z_e}, so one complex exponential per edge suffices and
+// |S|^2 = |sum_m p_m (E_{m+1} - E_m)|^2 / phi^2.
+// Direct form (|phi| dz_max <= pi): the sinc is a short even polynomial of
+// x = phi dz/2 (|x| <= pi/2, truncation < 4e-8) and avoids the cancellation of
+// E_{m+1} - E_m at small phase steps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void phasor_rev(float phi, float hi, float lo, float &sn, float &cs)
+{
+    const float th = phi * hi;
+    float tl = fmaf(phi, hi, -th);
+    tl = fmaf(phi, lo, tl);
+    const float k = round_magic(th);
+    const float fr = __fadd_rn(th, -k) + tl;
+    __sincosf(fr * 6.283185307179586f, &sn, &cs);
+}
+
+__device__ __forceinline__ float zsum_tele_f(float phi, float Fc, float at, const float4 *s1,
+                                             const float4 *s2, int M)
+{
+    float Er = 1.0f, Ei = 0.0f, Sr = 0.0f, Si = 0.0f;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 a = s1[m];
+        const float zm = s2[m].x;
+        float sn, cs;
+        phasor_rev(phi, a.x, a.y, sn, cs);
+        float lp = fmaf(a.w, Fc, a.z);
+        lp = fmaf(-at, zm, lp);
+        const float p = ex2_approx(lp);
+        Sr = fmaf(p, cs - Er, Sr);
+        Si = fmaf(p, sn - Ei, Si);
+        Er = cs;
+        Ei = sn;
+    }
+    return (Sr * Sr + Si * Si) / (phi * phi);
+}
+
+__device__ __forceinline__ float zsum_direct_f(float phi, float Fc, float at, const float4 *s1,
+                                               const float4 *s2, int M)
+{
+    float Sr = 0.0f, Si = 0.0f;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 a = s1[m];
+        const float4 b = s2[m];
+        float sn, cs;
+        phasor_rev(phi, b.z, b.w, sn, cs);
+        const float x = 0.5f * phi * b.y;
+        const float x2 = x * x;
+        float sc = fmaf(x2, -2.5052108e-8f, 2.7557319e-6f);   // -1/11!, 1/9!
+        sc = fmaf(x2, sc, -1.9841270e-4f);                     // -1/7!
+        sc = fmaf(x2, sc, 8.3333333e-3f);                      // 1/5!
+        sc = fmaf(x2, sc, -1.6666667e-1f);                     // -1/3!
+        sc = fmaf(x2, sc, 1.0f);
+        float lp = fmaf(a.w, Fc, a.z);
+        lp = fmaf(-at, b.x, lp);
+        const float amp = ex2_approx(lp) * b.y * sc;
+        Sr = fmaf(amp, cs, Sr);
+        Si = fmaf(amp, sn, Si);
+    }
+    return Sr * Sr + Si * Si;
+}
+
+// ---------------------------------------------------------------------------
+// k_quad_f32: persistent FP32 quadrature.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
+{
+    extern __shared__ float4 smem_f4[];
+    const int M = qp.n_steps, G = qp.G;
+    float4 *s1 = smem_f4;                 // [M]
+    float4 *s2 = s1 + M;                  // [M]
+    RowF *rows = reinterpret_cast<RowF *>(s2 + M);   // [G]
+    __shared__ PieceConst<float> kc;
+    __shared__ double scratch[32];
+    __shared__ int s_item;
+
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float4 zb = qp.zs_b[m];
+        const float4 za = qp.zs_a[m];
+        s1[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
+        s2[m] = make_float4(za.x, za.y, zb.z, zb.w);
+    }
+    const float c3 = (float)(kPi * qp.beta3);
+    const float c4 = (float)(2.0 * kPi * kPi / 3.0 * qp.beta4);
+    const float b2 = (float)qp.beta2;
+    const float m4pi2 = (float)(-4.0 * kPi * kPi);
+    const float phi_direct = 3.14159265f / qp.dz_max;
+    const float log2e = (float)kLog2e;
+    int cur_prof = -1;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(qp.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= qp.n_items) break;
+        const DevItem item = qp.items[it];
+        if (item.prof != cur_prof) {
+            const float2 *st = qp.step_f + (size_t)item.prof * M;
+            for (int m = threadIdx.x; m < M; m += blockDim.x) {
+                const float2 v = st[m];
+                s1[m].z = v.x;
+                s1[m].w = v.y;
+            }
+            cur_prof = item.prof;
+        }
+        double acc = 0.0;
+        for (int k = item.piece0; k < item.piece1; ++k) {
+            const DevPiece pc = qp.pieces[k];
+            piece_rows<RowF>(pc, G, qp.eps_v1, rows);
+            piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
+            __syncthreads();
+            const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2;
+            const float three_fi2 = 3.0f * fi * fi;
+            float sum = 0.0f, comp = 0.0f;
+            const int npts = G * G;
+            for (int q = threadIdx.x; q < npts; q += blockDim.x) {
+                const int r = q / G;
+                const int j = q - r * G;
+                const RowF rw = rows[r];
+                if (rw.w == 0.0f) continue;
+                const float d = ((float)j + 0.5f - 0.5f * (float)G) * rw.du2;
+                const float e = expf(d);
+                const float f1 = s1g * (rw.xc * e);
+                const float f2 = s2g * (rw.yc / e);
+                const float u = f1 + f2;                    // F_c - f_i
+                int ci = -1;
+                for (int c = 0; c < kc.nc; ++c) {
+                    if (u >= kc.lo[c] && u < kc.hi[c]) { ci = c; break; }
+                }
+                if (ci < 0) continue;                       // F_c in a gap
+                const float W = kc.wab * kc.pd[ci];
+                const float at = kc.at_ab + kc.hat[ci];
+                const float Fc = fi + u;                    // F_c - f_ref
+                // Eq. phi
+                const float br = b2 + c3 * (u + 2.0f * fi) +
+                                 c4 * (f1 * f1 + 1.5f * f1 * f2 + 3.0f * fi * u + f2 * f2 + three_fi2);
+                const float phi = m4pi2 * f1 * f2 * br;
+                float S2;
+                if (fabsf(phi) > phi_direct) S2 = zsum_tele_f(phi, Fc, at, s1, s2, M);
+                else S2 = zsum_direct_f(phi, Fc, at, s1, s2, M);
+                // compensated accumulation over this thread's points
+                const float y = rw.w * W * S2 - comp;
+                const float t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+            }
+            acc += (double)kc.mult * ((double)sum - (double)comp);
+            __syncthreads();
+        }
+        const double tot = block_sum_d(acc, scratch);
+        if (threadIdx.x == 0) qp.partial[it] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_quad_f64: the same quadrature in plain FP64 (direct form, libm functions).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sinc_d(double x)
+{
+    return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x;
+}
+
+__global__ void __launch_bounds__(256) k_quad_f64(QuadParams qp)
+{
+    extern __shared__ double2 smem_d2[];
+    const int M = qp.n_steps, G = qp.G;
+    double2 *sz = smem_d2;                 // [M] {z_m, dz_m}
+    double2 *st = sz + M;                  // [M] {lnPtot - lnN, kappa}
+    RowD *rows = reinterpret_cast<RowD *>(st + M);
+    __shared__ PieceConst<double> kc;
+    __shared__ double scratch[32];
+    __shared__ int s_item;
+
+    for (int m = threadIdx.x; m < M; m += blockDim.x) sz[m] = qp.zs_d[m];
+    const double c3 = kPi * qp.beta3;
+    const double c4 = 2.0 * kPi * kPi / 3.0 * qp.beta4;
+    int cur_prof = -1;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(qp.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= qp.n_items) break;
+        const DevItem item = qp.items[it];
+        if (item.prof != cur_prof) {
+            for (int m = threadIdx.x; m < M; m += blockDim.x) st[m] = qp.step_d[(size_t)item.prof * M + m];
+            cur_prof = item.prof;
+        }
+        double acc = 0.0;
+        for (int k = item.piece0; k < item.piece1; ++k) {
+            const DevPiece pc = qp.pieces[k];
+            piece_rows<RowD>(pc, G, qp.eps_v1, rows);
+            piece_consts<double>(qp, pc, item.prof, 1.0, qp.pd_d, kc);
+            __syncthreads();
+            const double fi = kc.fi;
+            double sum = 0.0;
+            const int npts = G * G;
+            for (int q = threadIdx.x; q < npts; q += blockDim.x) {
+                const int r = q / G;
+                const int j = q - r * G;
+                const RowD rw = rows[r];
+                if (rw.w == 0.0) continue;
+                const double d = ((double)j + 0.5 - 0.5 * (double)G) * rw.du2;
+                const double f1 = kc.s1 * (rw.xc * exp(d));
+                const double f2 = kc.s2 * (rw.yc * exp(-d));
+                const double u = f1 + f2;
+                int ci = -1;
+                for (int c = 0; c < kc.nc; ++c) {
+                    if (u >= kc.lo[c] && u < kc.hi[c]) { ci = c; break; }
+                }
+                if (ci < 0) continue;
+                const double W = kc.wab * kc.pd[ci];
+                const double at = kc.at_ab + kc.hat[ci];
+                const double Fc = fi + u;
+                const double br = qp.beta2 + c3 * (u + 2.0 * fi) +
+                                  c4 * (f1 * f1 + 1.5 * f1 * f2 + 3.0 * fi * u + f2 * f2 + 3.0 * fi * fi);
+                const double phi = -4.0 * kPi * kPi * f1 * f2 * br;
+                double Sr = 0.0, Si = 0.0;
+                for (int m = 0; m < M; ++m) {
+                    const double2 zz = sz[m];
+                    const double2 tt = st[m];
+                    const double p = exp(tt.x - tt.y * Fc - at * zz.x);
+                    const double amp = p * zz.y * sinc_d(0.5 * phi * zz.y);
+                    double sn, cs;
+                    sincos(phi * zz.x, &sn, &cs);
+                    Sr += amp * cs;
+                    Si += amp * sn;
+                }
+                sum += rw.w * W * (Sr * Sr + Si * Si);
+            }
+            acc += kc.mult * sum;
+            __syncthreads();
+        }
+        const double tot = block_sum_d(acc, scratch);
+        if (threadIdx.x == 0) qp.partial[it] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_finish: per profile, Sigma_i = ordered sum of the CUT's tile partials;
+// eta_i = (16/27) gamma_i^2 B_i Sigma_i / P_i^3 (Eq. gain_fin, P_NLI = G B);
+// SNR_i = P_i / (P_NLI,i + P_ASE,i) with P_ASE,i = NF h f (1/rho(L,f) - 1) B
+// and optional transceiver noise; T = 2 sum B log2(1 + SNR) (Eq. loss).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_finish(FinishParams fp)
+{
+    __shared__ double scratch[32];
+    const int p = blockIdx.x;
+    const int plan = fp.prof_plan[p];
+    const int coff = fp.plan_ch_off[plan];
+    const int poff = fp.prof_ch_off[p];
+    const int s0 = fp.prof_slot_off[p], s1 = fp.prof_slot_off[p + 1];
+    double tpart = 0.0;
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const int2 rg = fp.slot_items[s];
+        const int i = fp.slot_cut[s];
+        double sig = 0.0;
+        for (int it = rg.x; it < rg.y; ++it) sig += fp.partial[it];
+        const double g = fp.ch_gamma[coff + i];
+        const double B = fp.ch_B[coff + i];
+        const double P = fp.P[poff + i];
+        const double pnli = 16.0 / 27.0 * g * g * B * sig;
+        const double eta = P > 0.0 ? pnli / (P * P * P) : __longlong_as_double(0x7ff8000000000000LL);
+        if (fp.sigma) fp.sigma[s] = sig;
+        if (fp.pnli) fp.pnli[s] = pnli;
+        if (fp.eta) fp.eta[s] = eta;
+        if (fp.snr) {
+            const double nf = fp.ch_nf ? pow(10.0, fp.ch_nf[coff + i] / 10.0) : 1.0;
+            const double f_abs = fp.ch_frel[coff + i] + fp.f_ref;
+            const double gain = exp(-fp.lnrho_L[poff + i]);
+            const double pase = nf * 6.62607015e-34 * (f_abs * 1e12) * (gain - 1.0) * (B * 1e12);
+            const bool off = !(P > 0.0) || (fp.guard && fp.guard[coff + i]);
+            double snr = 0.0;
+            if (!off) {
+                snr = P / (pnli + pase);
+                if (fp.snr_trx_lin_inv > 0.0) snr = 1.0 / (1.0 / snr + fp.snr_trx_lin_inv);
+                tpart += 2.0 * B * log2(1.0 + snr);
+            }
+            fp.snr[s] = snr;
+            if (fp.pase) fp.pase[s] = pase;
+        }
+    }
+    const double T = block_sum_d(tpart, scratch);
+    if (threadIdx.x == 0 && fp.T) fp.T[p] = T;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+size_t quad_smem_bytes(int precision, int n_steps, int G)
+{
+    if (precision == 0) return (size_t)n_steps * 2 * sizeof(float4) + (size_t)G * sizeof(RowF);
+    return (size_t)n_steps * 2 * sizeof(double2) + (size_t)G * sizeof(RowD);
+}
+
+cudaError_t launch_prep(const PrepParams &pp, int n_prof, cudaStream_t st)
+{
+    k_prep<<<n_prof, 256, 0, st>>>(pp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quad(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st)
+{
+    const size_t smem = quad_smem_bytes(precision, qp.n_steps, qp.G);
+    if (precision == 0) {
+        cudaFuncSetAttribute(k_quad_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_quad_f32<<<grid, block, smem, st>>>(qp);
+    } else {
+        cudaFuncSetAttribute(k_quad_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_quad_f64<<<grid, block, smem, st>>>(qp);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const FinishParams &fp, int n_prof, cudaStream_t st)
+{
+    k_finish<<<n_prof, 256, 0, st>>>(fp);
+    return cudaGetLastError();
+}
+
+int quad_blocks_per_sm(int precision, int n_steps, int G, int block)
+{
+    int nb = 0;
+    const size_t smem = quad_smem_bytes(precision, n_steps, G);
+    if (precision == 0) {
+        cudaFuncSetAttribute(k_quad_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_quad_f32, block, smem);
+    } else {
+        cudaFuncSetAttribute(k_quad_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_quad_f64, block, smem);
+    }
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace isrs

@@ -1,0 +1,60 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads
+and exports every function declared in include/isrs_gn.h; host helpers agree
+with the paper's Sec. II formulas through an independent route."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"^\s*(?:isrs_status|double|const char \*)\s*\*?\s*(isrs_\w+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_18022_gb300 import _capi
+    return _capi.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lib.isrs_status_string(s)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    h = ctypes.c_void_p()
+    st = lib.isrs_create(ctypes.byref(h), 0)
+    assert st in (1, 2) and not h.value
+
+
+def test_host_beta_helper_matches_oracle(lib, orc):
+    """Both implement Eqs. d..d_curve independently; they must agree."""
+    from paper_2401_18022_gb300 import _capi
+    for lam, D, S, Sd in [(1550.1, 17.0, 0.057, 0.0), (1310.0, 0.0, 0.09, -2.06e-4)]:
+        out = np.zeros(3)
+        assert lib.isrs_beta_from_dispersion(lam, D, S, Sd, out.ctypes.data_as(_capi.c_double_p)) == 0
+        assert np.allclose(out, orc.beta_from_dispersion(lam, D, S, Sd), rtol=1e-14, atol=0)
+    assert lib.isrs_beta_from_dispersion(-1.0, 1, 1, 1, out.ctypes.data_as(_capi.c_double_p)) == 1
+    g = lib.isrs_gamma_from_aeff(1550.0, 2.6e-20, 80.0)
+    assert g == pytest.approx(orc.gamma(1550.0, 2.6e-20, 80.0), rel=1e-14)
+    assert np.isnan(lib.isrs_gamma_from_aeff(0.0, 2.6e-20, 80.0))

@@ -1,0 +1,158 @@
+"""GPU parity of the forward path against the FP64 oracle, through the C ABI.
+
+Tolerances:
+  * FP64 GPU path: same algorithm in the same precision; differences come
+    from summation order and libm ulps, and from grid points that sit within
+    ~1e-15 THz of a channel edge (classified differently).  rtol 1e-9.
+  * FP32 path: points are located with FP32 coordinates (relative error
+    ~1e-7, i.e. kHz to MHz at tens of THz), so points within that distance of
+    an F_c channel edge may switch sides; the phase is float-float with error
+    ~1e-6 rad and the z-sum terms carry ~1e-6 relative error.  Together this
+    bounds |d eta / eta| well below 2e-4 (0.0009 dB); the target stated for
+    the method, 0.01 dB of SNR per channel, allows 2.3e-3.
+"""
+import numpy as np
+import pytest
+
+from paper_2401_18022_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL_F64 = 1e-9
+RTOL_F32 = 2e-4
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2401_18022_gb300 import api
+    return api.Engine(0)
+
+
+def _oracle_sigma(orc, wl, cuts=None, P=None):
+    return orc.sigma(wl, P=P, cuts=cuts)
+
+
+@pytest.mark.parametrize("cell_set", [W.CELLS_ALL, W.CELLS_SCI_XCI])
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_tiny_all_cuts(eng, orc, cell_set, prec, rtol):
+    wl = W.tiny(G=64, cell_set=cell_set)
+    ref = _oracle_sigma(orc, wl)
+    got = eng.eta(wl, precision=prec)
+    np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)
+    e_ref, pn_ref = orc.eta(wl, ref)
+    np.testing.assert_allclose(got["eta"], e_ref, rtol=rtol)
+    np.testing.assert_allclose(got["pnli"], pn_ref, rtol=rtol)
+
+
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_oband_zero_dispersion_subset(eng, orc, prec, rtol):
+    """41-ch O-band at lambda0 (beta2 = 0, beta3/beta4 only), all cells incl. MCI,
+    ragged G (not a multiple of the block), several CUTs across the band."""
+    wl = W.oband(G=27, n_edges=41)
+    cuts = [0, 7, 20, 33, 40]
+    ref = _oracle_sigma(orc, wl, cuts=cuts)
+    got = eng.eta(wl, cuts=cuts, precision=prec)
+    np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)
+
+
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_uwb_sampled_cuts_small_grid(eng, orc, prec, rtol):
+    """589-ch UWB plan, SCI+XCI, G = 16: edge, centre and near-edge CUTs."""
+    wl = W.uwb(G=16)
+    cuts = [0, 1, 150, 294, 451, 587, 588]
+    ref = _oracle_sigma(orc, wl, cuts=cuts)
+    got = eng.eta(wl, cuts=cuts, precision=prec)
+    np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)
+
+
+def test_snr_and_throughput(eng, orc):
+    wl = W.tiny(G=48).with_(snr_trx_dB=20.0)
+    r = orc.evaluate(wl)
+    got = eng.snr(wl, precision=0)
+    snr_db_err = np.abs(10 * np.log10(got["snr"]) - 10 * np.log10(r["snr"]))
+    assert snr_db_err.max() < 1e-3
+    assert got["T"] == pytest.approx(r["T"], rel=1e-5)
+    got64 = eng.snr(wl, precision=1)
+    np.testing.assert_allclose(got64["snr"], r["snr"], rtol=1e-9)
+    assert got64["T"] == pytest.approx(r["T"], rel=1e-11)
+
+
+def test_device_tensors_and_stream(eng, orc):
+    import torch
+    wl = W.tiny(G=32)
+    P = torch.tensor(wl.P_W, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        got = eng.eta(wl, P=P, precision=1)
+    s.synchronize()
+    assert got["eta"].is_cuda
+    ref = orc.sigma(wl)
+    np.testing.assert_allclose(got["sigma"].cpu().numpy(), ref, rtol=RTOL_F64)
+
+
+def test_empty_slot_and_single_channel(eng, orc):
+    wl = W.tiny(G=32)
+    P = wl.P_W.copy()
+    P[3] = 0.0
+    ref = orc.sigma(wl, P=P)
+    got = eng.eta(wl, P=P, precision=1)
+    np.testing.assert_allclose(got["sigma"], ref, rtol=RTOL_F64)
+    assert np.isnan(got["eta"][3]) and np.all(np.isfinite(np.delete(got["eta"], 3)))
+    r = orc.evaluate(wl, P=P)
+    s = eng.snr(wl, P=P, precision=1)
+    assert s["snr"][3] == 0.0
+    assert s["T"] == pytest.approx(r["T"], rel=1e-11)
+    one = W.tiny(G=40).with_(f_THz=np.array([193.4]), B_THz=np.array([0.096]), P_W=np.array([1e-3]),
+                              alpha_per_km=np.array([0.046]), lambda_nm=np.array([1550.1]),
+                              aeff_um2=np.array([80.0]), nf_dB=np.array([5.0]))
+    np.testing.assert_allclose(eng.eta(one, precision=0)["sigma"], orc.sigma(one), rtol=RTOL_F32)
+
+
+def test_invalid_arguments_write_nothing(eng):
+    from paper_2401_18022_gb300._capi import IsrsError
+    wl = W.tiny(G=8)
+    bad = [wl.with_(f_THz=wl.f_THz[::-1].copy()),                       # unsorted
+           wl.with_(B_THz=np.full(5, 0.2)),                               # overlapping
+           wl.with_(G=0), wl.with_(n_edges=1), wl.with_(L_km=0.0),
+           wl.with_(eps_v1=0.0), wl.with_(cell_set=3)]
+    for b in bad:
+        with pytest.raises(IsrsError) as ei:
+            eng.eta(b)
+        assert ei.value.status == 1
+    with pytest.raises(IsrsError):
+        eng.eta(wl, P=-wl.P_W)
+    with pytest.raises(IsrsError):
+        eng.eta(wl, P=np.zeros(5))
+    with pytest.raises(IsrsError):
+        eng.eta(wl, cuts=[0, 0])
+    with pytest.raises(IsrsError):
+        eng.eta(wl, cuts=[7])
+
+
+def test_batched_equals_single_profile_launches(eng):
+    """Each profile of a batched launch equals its own single-profile launch
+    bit for bit: the tile partials do not depend on which block computes them
+    and are summed in a fixed order."""
+    bw = W.batched(n_prof=6, G=8, n_edges=17, sizes=(41, 20, 9))
+    eta_b = eng.eta_batched(bw)
+    off = 0
+    for p in range(6):
+        wl = bw.plans[bw.plan_of_profile[p]]
+        n = wl.n_ch
+        single = eng.eta(wl, P=bw.P_W[p])["eta"]
+        np.testing.assert_array_equal(eta_b[off:off + n], single)
+        off += n
+
+
+def test_batched_matches_oracle(eng, orc):
+    bw = W.batched(n_prof=3, G=12, n_edges=17, sizes=(30, 11, 5))
+    eta_b = eng.eta_batched(bw, precision=1)
+    off = 0
+    for p in range(3):
+        wl = bw.plans[bw.plan_of_profile[p]]
+        ref, _ = orc.eta(wl, orc.sigma(wl, P=bw.P_W[p]), P=bw.P_W[p])
+        np.testing.assert_allclose(eta_b[off:off + wl.n_ch], ref, rtol=RTOL_F64)
+        off += wl.n_ch
