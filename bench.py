@@ -1,0 +1,351 @@
+"""Benchmark of the ISRS GN hot path on the 589-channel O-to-U band system.
+
+One step = one full pass of the hot path on the 589 x 96 GBaud, 1260-1675 nm,
+80 km workload (G = 256 per piece, 113 z-edges, SCI + XCI cells): ISRS
+profile tables, the hyperbolic Riemann sum for every CUT, eta, SNR and
+throughput, and (once the adjoint is built) the gradient of the throughput
+with respect to all 589 launch powers.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "589-ch SNR eval time & grid-pts/s; SNR+gradient time vs plain FP64 at 0.01 dB"
+UNIT = "grid-pts/s"
+SFU_PER_CLK_PER_SM = 16          # MUFU (sin, cos, ex2, rcp) issue rate per SM per clock
+FP32_PER_CLK_PER_SM = 128
+N_SMS = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _workload(G: int, rank: int = 0):
+    from paper_2401_18022_gb300 import workloads as W
+    wl = W.uwb(G=G)
+    if rank > 0:
+        # weak scaling: each rank evaluates its own independent launch-power profile
+        rng = np.random.default_rng(100 + rank)
+        wl = wl.with_(P_W=W.dbm_to_w(1.0 + rng.uniform(-0.5, 0.5, wl.n_ch)))
+    return wl
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(G: int, budget_core_s: float = 20.0):
+    """Time the FP64 oracle as it stands on a bounded sample of the workload:
+    every k-th piece of the centre CUT, k chosen for ~budget_core_s of CPU work."""
+    import oracle
+    wl = _workload(G)
+    cut = wl.n_ch // 2
+    oracle.build()
+    threads = os.cpu_count() or 1
+    probe = oracle.time_sample(wl, [cut], 512, threads=threads)
+    per_pt_core = probe["seconds"] * threads / max(1, probe["points"])
+    n_pieces = probe["pieces_total"]
+    want_pts = budget_core_s / max(per_pt_core, 1e-12)
+    stride = int(max(1, min(n_pieces, round(n_pieces * G * G / max(want_pts, 1.0)))))
+    r = oracle.time_sample(wl, [cut], stride, threads=threads)
+    return {"value": r["points"] / r["seconds"], "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 CPU oracle, CUT {cut} of the 589-ch plan, G={G}, every {stride}th of its "
+                      f"{n_pieces} pieces ({r['pieces']} pieces, {r['points']} grid points, "
+                      f"{r['point_steps']} point-steps) in {r['seconds']:.2f} s on {threads} threads",
+            "seconds": r["seconds"], "points": r["points"]}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    wl = _workload(args.G)
+    oracle.build()
+    threads = os.cpu_count() or 1
+    cut = wl.n_ch // 2
+    n_pieces = len(oracle.pieces(wl.f_THz, wl.B_THz, cut, wl.cell_set))
+    stride = max(1, n_pieces // 24)        # ~24 pieces (~1.6e6 points) per step
+    for _ in range(args.warmup):
+        oracle.time_sample(wl, [cut], stride * 4, threads=threads)
+    secs, pts = 0.0, 0
+    for _ in range(args.steps):
+        r = oracle.time_sample(wl, [cut], stride, threads=threads)
+        secs += r["seconds"]
+        pts += r["points"]
+    value = pts / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "uwb-589ch-80km-G256-N113-sci_xci (bounded sample per step)",
+                       "n_ch": wl.n_ch, "G": wl.G, "n_edges": wl.n_edges, "cells": "sci_xci",
+                       "l2": "CPU run"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"every {stride}th of the {n_pieces} pieces of CUT {cut} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2401_18022_gb300 import api
+    eng = api.Engine(local)
+    wl = _workload(args.G, rank)
+    dev = torch.device("cuda", local)
+    P = torch.tensor(wl.P_W, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+    use_grad = args.mode == "grad"
+
+    def step():
+        if use_grad:
+            return eng.grad(wl, P=P)
+        return eng.snr(wl, P=P)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    info = eng.last_launch_info()
+    launches_per_step = info["launches"]
+
+    clk = Clocks(local)
+    clk.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    quad_ms = []
+    for k in range(args.steps):
+        flush.zero_()                                  # L2 flushed between timed iterations
+        starts[k].record(stream)
+        out = step()
+        ends[k].record(stream)
+        quad_ms.append(eng.last_kernel_ms(0))          # events around the quadrature launch
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+
+    # grid points of the method's Riemann grid (mirror cells counted, as in the oracle)
+    from paper_2401_18022_gb300 import workloads as W
+    import oracle  # noqa: F401  (only for the CPU baseline below)
+    n_eval = info["points"]
+    n_grid = _unfolded_points(wl)
+    value = world * n_grid * args.steps / t_total
+
+    # roofline of the dominant kernel (k_quad_f32): 3 SFU evaluations per
+    # evaluated point-step (sin, cos of the edge phasor, ex2 of the power term)
+    quad_ms = float(np.mean(quad_ms))
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sfu_peak = N_SMS * SFU_PER_CLK_PER_SM * sm_max * 1e6 / 1e12       # Tops/s
+    fwd_psteps = _fwd_point_steps(eng, wl, P) if use_grad else info["point_steps"]
+    achieved = 3.0 * fwd_psteps / (quad_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Tops/s (SFU)",
+            "frac": achieved / sfu_peak, "traffic": None,
+            "kernel": "k_quad_f32", "kernel_ms": quad_ms,
+            "peak_source": f"152 SMs x 16 SFU/clk x {sm_max:.0f} MHz (max SM clock)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "uwb-589ch-80km-G256-N113-sci_xci" + ("+grad" if use_grad else ""),
+                       "n_ch": wl.n_ch, "G": wl.G, "n_edges": wl.n_edges, "cells": "sci_xci",
+                       "profile": "R1 closed-form ISRS, flat 1 dBm/ch",
+                       "l2": "flushed (256 MB write) between timed iterations",
+                       "grid_points_per_step": n_grid, "evaluated_points_per_step": n_eval,
+                       "step": "isrs_gn_grad (SNR + dT/dP)" if use_grad else "isrs_gn_snr (eta, SNR, T)"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks, "roofline": roof, "wall_s": wall}
+    if rank == 0 and not args.quick:
+        line["e2e"] = _e2e(eng, wl, args, world, n_grid)
+        line["fp64_path"] = _fp64_path(eng, wl, P, args)
+        line["cpu_baseline"] = cpu_baseline(args.G) if world == 1 else None
+        line["T_Tbps"] = float(out["T"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _unfolded_points(wl):
+    """Grid points of the Riemann sum as defined (every piece of every CUT,
+    mirror cells included): G^2 x (4 + 2 (N-1)) per CUT for SCI + XCI."""
+    n = wl.n_ch
+    per_cut = 4 + 2 * (n - 1) if wl.cell_set == 0 else None
+    if per_cut is None:
+        raise ValueError("bench counts SCI+XCI grids only")
+    return n * per_cut * wl.G * wl.G
+
+
+def _fwd_point_steps(eng, wl, P):
+    eng.eta(wl, P=P)
+    return eng.last_launch_info()["point_steps"]
+
+
+def _e2e(eng, wl, args, world, n_grid):
+    """Same metric through the C ABI with host buffers: H2D of the launch
+    powers and D2H of SNR, eta and T inside the timed region."""
+    import torch
+    P_host = np.ascontiguousarray(wl.P_W)
+    k = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        r = eng.grad(wl, P=P_host) if args.mode == "grad" else eng.snr(wl, P=P_host)
+    dt = time.perf_counter() - t0
+    n_out = 3 if args.mode == "grad" else 2
+    return {"value": world * n_grid * k / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * wl.n_ch,
+            "d2h_bytes_per_step": 8 * wl.n_ch * n_out + 8, "steps": k, "seconds": dt,
+            "T_Tbps": float(r["T"])}
+
+
+def _fp64_path(eng, wl, P, args):
+    """The plain FP64 GPU path on a subset of CUTs (it is ~165x slower on
+    GB300's FP64 units): time per CUT extrapolated to 589 CUTs, and the
+    FP32-vs-FP64 eta/SNR error on those CUTs."""
+    import torch
+    cuts = [0, wl.n_ch // 2, wl.n_ch - 1]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r64 = eng.eta(wl, P=P, cuts=cuts, precision=1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    r32 = eng.eta(wl, P=P, cuts=cuts, precision=0)
+    e64 = r64["eta"].cpu().numpy()
+    e32 = r32["eta"].cpu().numpy()
+    err_db = float(np.max(np.abs(10 * np.log10(e32 / e64))))
+    per_cut = dt / len(cuts)
+    return {"cuts": cuts, "seconds_for_cuts": dt, "extrapolated_589ch_s": per_cut * wl.n_ch,
+            "max_eta_err_dB_fp32_vs_fp64": err_db, "note": "extrapolated linearly (equal work per CUT)"}
+
+
+def profile_case(kind: str) -> int:
+    """One small launch for kernel captures: the 589-ch plan at G = 64 for 8
+    CUTs spread over the band (about 9.4e6 points, tens of milliseconds)."""
+    import torch
+    from paper_2401_18022_gb300 import api
+    eng = api.Engine(0)
+    wl = _workload(64)
+    P = torch.tensor(wl.P_W, dtype=torch.float64, device="cuda")
+    cuts = [int(c) for c in np.linspace(0, wl.n_ch - 1, 8)]
+    if kind == "adjoint":
+        eng.grad(wl.with_(G=16), P=P)
+    else:
+        eng.eta(wl, P=P, cuts=cuts, precision=1 if kind == "quad64" else 0)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": kind, **eng.last_launch_info()}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--G", type=int, default=256)
+    ap.add_argument("--mode", default="snr", choices=["snr", "grad"])
+    ap.add_argument("--quick", action="store_true", help="skip e2e, FP64 and CPU legs")
+    ap.add_argument("--profile-case", default=None, choices=["quad", "quad64", "adjoint"],
+                    help="run one small launch of a kernel (for ncu captures) and exit")
+    args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

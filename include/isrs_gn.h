@@ -206,6 +206,13 @@ isrs_status isrs_set_tile(isrs_handle h, int points_per_item, int threads_per_bl
 isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_point_steps,
                                   int *n_kernel_launches);
 
+/* Duration [ms] of the last quadrature (which = 0) or adjoint (which = 1)
+ * kernel launch of this handle, from CUDA events recorded on the launch
+ * stream immediately around it (not recorded while the stream is being
+ * captured into a graph).  Waits for that launch to finish.
+ * Errors: INVALID_ARG (bad which, or no such launch recorded yet), CUDA. */
+isrs_status isrs_last_kernel_ms(isrs_handle h, int which, float *ms);
+
 #ifdef __cplusplus
 }
 #endif

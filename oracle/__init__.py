@@ -62,6 +62,9 @@ def _load():
         lib.orc_sigma.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _I, ctypes.c_double, _I,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
         lib.orc_sigma.restype = ctypes.c_int
+        lib.orc_sigma_sampled.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _I, ctypes.c_double, _I,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.orc_sigma_sampled.restype = ctypes.c_int
         lib.orc_eta_from_sigma.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D]
         lib.orc_snr_throughput.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _D,
                                            ctypes.c_double, ctypes.POINTER(ctypes.c_ubyte), _D, _D]
@@ -178,6 +181,34 @@ def sigma(wl, P=None, cuts: Optional[Sequence[int]] = None, threads: Optional[in
     if return_pieces:
         return out, pout[:n_pieces]
     return out
+
+
+def time_sample(wl, cuts, stride: int, threads: Optional[int] = None) -> dict:
+    """Time the oracle on every stride-th piece of the given CUTs (a bounded
+    sample of a workload).  Returns the wall time and the grid points and
+    point-steps the sample evaluated."""
+    import time
+    f, B = _f64(wl.f_THz), _f64(wl.B_THz)
+    P, alpha = _f64(wl.P_W), _f64(wl.alpha_per_km)
+    fib = _f64(fibre_params(wl))
+    quad = np.array([wl.G, wl.n_edges, wl.cell_set], dtype=np.int32)
+    cuts = np.ascontiguousarray(np.asarray(cuts, dtype=np.int32))
+    threads = threads or os.cpu_count() or 1
+    n_pieces = sum(_load().orc_pieces_flat(len(f), _dp(f), _dp(B), int(c), int(wl.cell_set), None)
+                   for c in cuts)
+    pout = np.zeros(max(n_pieces, 1))
+    out = np.zeros(len(cuts))
+    t0 = time.perf_counter()
+    rc = _load().orc_sigma_sampled(len(f), _dp(f), _dp(B), _dp(P), _dp(alpha), _dp(fib),
+                                   quad.ctypes.data_as(_I), float(wl.eps_v1), cuts.ctypes.data_as(_I),
+                                   len(cuts), int(threads), 0, int(stride), _dp(out), _dp(pout))
+    dt = time.perf_counter() - t0
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    n_eval = len(range(0, n_pieces, max(1, int(stride))))
+    pts = n_eval * wl.G * wl.G
+    return {"seconds": dt, "points": pts, "point_steps": pts * (wl.n_edges - 1), "threads": threads,
+            "pieces": n_eval, "pieces_total": n_pieces}
 
 
 def eta(wl, sigma_: np.ndarray, cuts=None, P=None):

@@ -380,6 +380,7 @@ typedef struct {
     const orc_piece *item_piece;
     double *item_val;
     long n_items;
+    long stride;
     long next;
     pthread_mutex_t mu;
 } orc_work;
@@ -389,7 +390,8 @@ static void *orc_worker(void *arg)
     orc_work *wk = (orc_work *)arg;
     for (;;) {
         pthread_mutex_lock(&wk->mu);
-        long k = wk->next++;
+        long k = wk->next;
+        wk->next += wk->stride;
         pthread_mutex_unlock(&wk->mu);
         if (k >= wk->n_items) break;
         wk->item_val[k] = orc_piece_sum(wk->pr, wk->item_cut[k], &wk->item_piece[k]);
@@ -407,10 +409,13 @@ static void *orc_worker(void *arg)
  * piece_out (optional): per-piece sums, in the order of orc_pieces, for each
  * requested CUT one after another.
  * unit_integrand != 0 replaces the integrand by 1 (returns covered area).
+ * item_stride > 1 evaluates only every item_stride-th piece (the others are
+ * left at zero): a bounded sample used to time the oracle, not a result.
  */
-int orc_sigma(int n, const double *f, const double *B, const double *P, const double *alpha,
-              const double *fibre, const int *quad, double eps, const int *cuts, int n_cuts,
-              int n_threads, int unit_integrand, double *sigma_out, double *piece_out)
+int orc_sigma_sampled(int n, const double *f, const double *B, const double *P, const double *alpha,
+                      const double *fibre, const int *quad, double eps, const int *cuts, int n_cuts,
+                      int n_threads, int unit_integrand, int item_stride, double *sigma_out,
+                      double *piece_out)
 {
     if (n < 1 || n_cuts < 0 || quad[0] < 1 || quad[1] < 2) return -1;
     orc_problem pr;
@@ -439,7 +444,7 @@ int orc_sigma(int n, const double *f, const double *B, const double *P, const do
 
     orc_work wk;
     wk.pr = &pr; wk.item_cut = item_cut; wk.item_piece = pieces; wk.item_val = val;
-    wk.n_items = total; wk.next = 0;
+    wk.n_items = total; wk.next = 0; wk.stride = item_stride > 1 ? item_stride : 1;
     pthread_mutex_init(&wk.mu, NULL);
     if (n_threads < 1) n_threads = 1;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
@@ -510,4 +515,12 @@ double orc_snr_throughput(int n, const double *f, const double *B, const double 
         T += 2.0 * B[i] * log2(1.0 + s);
     }
     return T;
+}
+
+int orc_sigma(int n, const double *f, const double *B, const double *P, const double *alpha,
+              const double *fibre, const int *quad, double eps, const int *cuts, int n_cuts,
+              int n_threads, int unit_integrand, double *sigma_out, double *piece_out)
+{
+    return orc_sigma_sampled(n, f, B, P, alpha, fibre, quad, eps, cuts, n_cuts, n_threads,
+                             unit_integrand, 1, sigma_out, piece_out);
 }

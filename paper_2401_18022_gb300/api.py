@@ -112,6 +112,13 @@ class Engine:
         check(self.lib.isrs_last_launch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"points": a.value, "point_steps": b.value, "launches": c.value}
 
+    def last_kernel_ms(self, which: int = 0) -> float:
+        """Duration of the last quadrature (0) or adjoint (1) kernel, from
+        CUDA events recorded on its launch stream."""
+        ms = ctypes.c_float()
+        check(self.lib.isrs_last_kernel_ms(self.h, int(which), ctypes.byref(ms)), self.h)
+        return ms.value
+
     # ---- calls -----------------------------------------------------------
     def eta(self, wl, P=None, cuts: Optional[Sequence[int]] = None, precision: int = PREC_FP32,
             want_sigma: bool = True):

@@ -60,6 +60,8 @@ struct isrs_handle_s {
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
     int last_launches = 0;
+    cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [quad, adjoint][start, end]
+    bool ev_valid[2] = {false, false};
 };
 
 namespace {
@@ -128,6 +130,22 @@ bool is_device_ptr(const void *p)
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Records event `pos` (0 start, 1 end) of kernel class `which` on the stream,
+// unless the stream is being captured.
+isrs_status mark(isrs_handle h, int which, int pos, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        h->ev_valid[which] = false;
+        return ISRS_OK;
+    }
+    if (!h->ev[which][pos]) CK(cudaEventCreate(&h->ev[which][pos]));
+    CK(cudaEventRecord(h->ev[which][pos], st));
+    if (pos == 1) h->ev_valid[which] = true;
+    return ISRS_OK;
 }
 
 // ----------------------------------------------------------------------------
@@ -603,7 +621,9 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     const int per_sm = quad_blocks_per_sm(precision, M, g->G, block);
     int grid = h->num_sms * per_sm;
     if (g->n_items < grid) grid = std::max(1, g->n_items);
+    if ((s = mark(h, 0, 0, st)) != ISRS_OK) return s;
     if (g->n_items > 0) CK(launch_quad(qp, precision, grid, block, st));
+    if ((s = mark(h, 0, 1, st)) != ISRS_OK) return s;
     h->last_points = g->n_points;
     h->last_psteps = g->n_points * (int64_t)M;
     h->last_launches = 1;
@@ -745,6 +765,9 @@ isrs_status isrs_destroy(isrs_handle h)
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
                       &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP};
     for (DevBuf *b : bufs) release(*b);
+    for (int w = 0; w < 2; ++w)
+        for (int k = 0; k < 2; ++k)
+            if (h->ev[w][k]) cudaEventDestroy(h->ev[w][k]);
     delete h;
     return ISRS_OK;
 }
@@ -785,6 +808,16 @@ isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_p
     if (n_points) *n_points = h->last_points;
     if (n_point_steps) *n_point_steps = h->last_psteps;
     if (n_launches) *n_launches = h->last_launches;
+    return ISRS_OK;
+}
+
+isrs_status isrs_last_kernel_ms(isrs_handle h, int which, float *ms)
+{
+    if (!h || !ms || which < 0 || which > 1) return ISRS_ERR_INVALID_ARG;
+    if (!h->ev_valid[which]) return fail(h, ISRS_ERR_INVALID_ARG, "no launch recorded");
+    CK(cudaSetDevice(h->device));
+    CK(cudaEventSynchronize(h->ev[which][1]));
+    CK(cudaEventElapsedTime(ms, h->ev[which][0], h->ev[which][1]));
     return ISRS_OK;
 }
 
