@@ -115,7 +115,7 @@ def cpu_baseline(G: int, budget_core_s: float = 20.0):
     cut = wl.n_ch // 2
     oracle.build()
     threads = os.cpu_count() or 1
-    probe = oracle.time_sample(wl, [cut], 512, threads=threads)
+    probe = oracle.time_sample(wl, [cut], 64, threads=threads)
     per_pt_core = probe["seconds"] * threads / max(1, probe["points"])
     n_pieces = probe["pieces_total"]
     want_pts = budget_core_s / max(per_pt_core, 1e-12)
@@ -311,16 +311,19 @@ def _fp64_path(eng, wl, P, args):
 
 
 def profile_case(kind: str) -> int:
-    """One small launch for kernel captures: the 589-ch plan at G = 64 for 8
-    CUTs spread over the band (about 9.4e6 points, tens of milliseconds)."""
+    """One launch for kernel captures: the 589-ch plan at the bench's G = 256
+    for 16 CUTs spread over the band (1.2e9 points, ~1.2e3 work tiles, about
+    0.1 s), so every SM is busy as in the full run."""
     import torch
     from paper_2401_18022_gb300 import api
     eng = api.Engine(0)
-    wl = _workload(64)
+    wl = _workload(256)
     P = torch.tensor(wl.P_W, dtype=torch.float64, device="cuda")
-    cuts = [int(c) for c in np.linspace(0, wl.n_ch - 1, 8)]
+    cuts = [int(c) for c in np.linspace(0, wl.n_ch - 1, 16)]
     if kind == "adjoint":
         eng.grad(wl.with_(G=16), P=P)
+    elif kind == "quad64":                 # FP64 is ~200x slower: 4 CUTs at G = 64
+        eng.eta(wl.with_(G=64), P=P, cuts=cuts[::4], precision=1)
     else:
         eng.eta(wl, P=P, cuts=cuts, precision=1 if kind == "quad64" else 0)
     torch.cuda.synchronize()

@@ -344,10 +344,11 @@ void zgrid_tables(double L, double a, int n_edges, std::vector<float4> &za, std:
         const double dz = ze[m + 1] - ze[m];
         dmax = std::max(dmax, dz);
         zd[m] = make_double2(zm, dz);
-        za[m] = make_float4((float)zm, (float)dz, 0.f, 0.f);
+        // {z_m, z_m^2 + dz_m^2/12 (second moment incl. the sinc term), log2 dz_m, dz_m}
+        za[m] = make_float4((float)zm, (float)(zm * zm + dz * dz / 12.0), (float)std::log2(dz), (float)dz);
         const double re = ze[m + 1] * inv2pi, rm = zm * inv2pi;
-        const float reh = (float)re, rmh = (float)rm;
-        zb[m] = make_float4(reh, (float)(re - (double)reh), rmh, (float)(rm - (double)rmh));
+        const float reh = (float)re;
+        zb[m] = make_float4(reh, (float)(re - (double)reh), (float)rm, 0.f);
     }
     dz_max = (float)dmax;
 }
@@ -614,6 +615,7 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     qp.zs_b = (const float4 *)g->zs_b.p;
     qp.zs_d = (const double2 *)g->zs_d.p;
     qp.dz_max = g->dz_max;
+    qp.L = (float)fb->L_km;
     qp.partial = (double *)h->partial.p;
     qp.counter = (int *)h->counter.p;
     CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));

@@ -65,10 +65,11 @@ struct QuadParams {
     const float2 *step_f;       // {A2_m, K2_m}: log2 p = A2 + K2 (F_c - f_ref) - at2 z_m
     const double2 *step_d;      // {ln Ptot - ln N_m, kappa_m}
     // z tables (per step m)
-    const float4 *zs_a;         // {z_m, dz_m, 0, 0}
-    const float4 *zs_b;         // {edge(m+1) rev hi, lo, mid(m) rev hi, lo}
+    const float4 *zs_a;         // {z_m, z_m^2 + dz_m^2/12, log2 dz_m, dz_m}
+    const float4 *zs_b;         // {z_{m+1}/2pi hi, lo (float-float), z_m/2pi, 0}
     const double2 *zs_d;        // {z_m, dz_m}
     float dz_max;
+    float L;                    // span length [km]
     // outputs / scheduling
     double *partial;            // one per item
     int *counter;               // persistent work counter (zeroed before launch)

@@ -214,40 +214,96 @@ __device__ void piece_consts(const QuadParams &qp, const DevPiece &pc, int prof,
 }
 
 // ---------------------------------------------------------------------------
-// FP32 z-sums.  Shared tables per step m (staged in shared memory):
-//   s1[m] = {edge(m+1)/2pi hi, lo, A2_m, K2_m},  s2[m] = {z_m, dz_m, z_m/2pi hi, lo}
-// log2 p_m = A2_m + K2_m Fc - at z_m;  phase in revolutions t = phi * (z/2pi)
-// formed as an error-free float-float product and reduced to [-1/2, 1/2].
+// FP32 z-sums.  Per-step tables staged in shared memory:
+//   sT[m] = {A2_m + log2 dz_m, K2_m, z_m, c_m = z_m^2 + dz_m^2/12}
+//   sD[m] = {z_m / 2pi, dz_m}
+//   sE[m] = {z_{m+1}/2pi hi, lo (float-float), A2_m, K2_m}
+// with log2 p_m = A2_m + K2_m Fc - at z_m (Eq. pk for the closed-form
+// profile).  The phase is carried in revolutions (z / 2pi).
 //
-// Telescoped form (|phi| dz_max > pi): by Eq. slow_vary the step factor is
-// exactly dz sinc(phi dz/2) e^{j phi z_m} = (E_{m+1} - E_m)/(j phi) with
-// E_e = e^{j phi z_e}, so one complex exponential per edge suffices and
-// |S|^2 = |sum_m p_m (E_{m+1} - E_m)|^2 / phi^2.
-// Direct form (|phi| dz_max <= pi): the sinc is a short even polynomial of
-// x = phi dz/2 (|x| <= pi/2, truncation < 4e-8) and avoids the cancellation of
-// E_{m+1} - E_m at small phase steps.
+// Three exact-to-FP32 evaluations of S = sum_m p_m dz_m sinc(phi dz_m/2)
+// e^{j phi z_m} (Eq. slow_vary), chosen per grid point by |phi|:
+//  * small (|phi| L <= 0.02): second-order expansion in phi,
+//      |S|^2 = M0^2 - phi^2 (M0 M2 - M1^2) + O((phi L)^4),
+//    M0 = sum p dz, M1 = sum p dz z, M2 = sum p dz (z^2 + dz^2/12); the
+//    truncation is below 1e-9 relative (one exp per step, no phasor).
+//  * direct (|phi| dz_max <= pi): the formula as written, sinc by its even
+//    Taylor polynomial in x = phi dz/2 (|x| <= pi/2, truncation < 4e-8),
+//    phase phi z/2pi < L/(2 dz_max) revolutions formed in FP32.
+//  * telescoped (otherwise): dz sinc(phi dz/2) e^{j phi z_m} equals
+//    (E_{m+1} - E_m)/(j phi) with E_e = e^{j phi z_e}, so one complex
+//    exponential per edge suffices; the phase phi z_e / 2pi (up to ~1e5
+//    revolutions) is an error-free float-float product reduced to [-1/2, 1/2].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void phasor_rev(float phi, float hi, float lo, float &sn, float &cs)
+__device__ __forceinline__ void sincos_rev(float t, float &sn, float &cs)
+{
+    const float fr = __fadd_rn(t, -round_magic(t));
+    __sincosf(fr * 6.283185307179586f, &sn, &cs);
+}
+
+__device__ __forceinline__ void phasor_rev_ff(float phi, float hi, float lo, float &sn, float &cs)
 {
     const float th = phi * hi;
     float tl = fmaf(phi, hi, -th);
     tl = fmaf(phi, lo, tl);
-    const float k = round_magic(th);
-    const float fr = __fadd_rn(th, -k) + tl;
+    const float fr = __fadd_rn(th, -round_magic(th)) + tl;
     __sincosf(fr * 6.283185307179586f, &sn, &cs);
 }
 
-__device__ __forceinline__ float zsum_tele_f(float phi, float Fc, float at, const float4 *s1,
-                                             const float4 *s2, int M)
+__device__ __forceinline__ float zsum_small_f(float phi, float Fc, float at, const float4 *sT, int M)
+{
+    float M0 = 0.0f, M1 = 0.0f, M2 = 0.0f;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 a = sT[m];
+        float lp = fmaf(a.y, Fc, a.x);
+        lp = fmaf(-at, a.z, lp);
+        const float w = ex2_approx(lp);          // p_m dz_m
+        M0 += w;
+        M1 = fmaf(w, a.z, M1);
+        M2 = fmaf(w, a.w, M2);
+    }
+    return fmaf(-phi * phi, fmaf(M0, M2, -M1 * M1), M0 * M0);
+}
+
+__device__ __forceinline__ float zsum_direct_f(float phi, float Fc, float at, const float4 *sT,
+                                               const float2 *sD, int M)
+{
+    float Sr = 0.0f, Si = 0.0f;
+    const float hphi = 0.5f * phi;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 a = sT[m];
+        const float2 d = sD[m];
+        float sn, cs;
+        sincos_rev(phi * d.x, sn, cs);
+        const float x = hphi * d.y;
+        const float x2 = x * x;
+        float sc = fmaf(x2, -2.5052108e-8f, 2.7557319e-6f);   // -1/11!, 1/9!
+        sc = fmaf(x2, sc, -1.9841270e-4f);                     // -1/7!
+        sc = fmaf(x2, sc, 8.3333333e-3f);                      // 1/5!
+        sc = fmaf(x2, sc, -1.6666667e-1f);                     // -1/3!
+        sc = fmaf(x2, sc, 1.0f);
+        float lp = fmaf(a.y, Fc, a.x);
+        lp = fmaf(-at, a.z, lp);
+        const float amp = ex2_approx(lp) * sc;   // p_m dz_m sinc
+        Sr = fmaf(amp, cs, Sr);
+        Si = fmaf(amp, sn, Si);
+    }
+    return Sr * Sr + Si * Si;
+}
+
+__device__ __forceinline__ float zsum_tele_f(float phi, float Fc, float at, const float4 *sT,
+                                             const float4 *sE, int M)
 {
     float Er = 1.0f, Ei = 0.0f, Sr = 0.0f, Si = 0.0f;
 #pragma unroll 4
     for (int m = 0; m < M; ++m) {
-        const float4 a = s1[m];
-        const float zm = s2[m].x;
+        const float4 e = sE[m];
+        const float zm = sT[m].z;
         float sn, cs;
-        phasor_rev(phi, a.x, a.y, sn, cs);
-        float lp = fmaf(a.w, Fc, a.z);
+        phasor_rev_ff(phi, e.x, e.y, sn, cs);
+        float lp = fmaf(e.w, Fc, e.z);
         lp = fmaf(-at, zm, lp);
         const float p = ex2_approx(lp);
         Sr = fmaf(p, cs - Er, Sr);
@@ -258,32 +314,6 @@ __device__ __forceinline__ float zsum_tele_f(float phi, float Fc, float at, cons
     return (Sr * Sr + Si * Si) / (phi * phi);
 }
 
-__device__ __forceinline__ float zsum_direct_f(float phi, float Fc, float at, const float4 *s1,
-                                               const float4 *s2, int M)
-{
-    float Sr = 0.0f, Si = 0.0f;
-#pragma unroll 4
-    for (int m = 0; m < M; ++m) {
-        const float4 a = s1[m];
-        const float4 b = s2[m];
-        float sn, cs;
-        phasor_rev(phi, b.z, b.w, sn, cs);
-        const float x = 0.5f * phi * b.y;
-        const float x2 = x * x;
-        float sc = fmaf(x2, -2.5052108e-8f, 2.7557319e-6f);   // -1/11!, 1/9!
-        sc = fmaf(x2, sc, -1.9841270e-4f);                     // -1/7!
-        sc = fmaf(x2, sc, 8.3333333e-3f);                      // 1/5!
-        sc = fmaf(x2, sc, -1.6666667e-1f);                     // -1/3!
-        sc = fmaf(x2, sc, 1.0f);
-        float lp = fmaf(a.w, Fc, a.z);
-        lp = fmaf(-at, b.x, lp);
-        const float amp = ex2_approx(lp) * b.y * sc;
-        Sr = fmaf(amp, cs, Sr);
-        Si = fmaf(amp, sn, Si);
-    }
-    return Sr * Sr + Si * Si;
-}
-
 // ---------------------------------------------------------------------------
 // k_quad_f32: persistent FP32 quadrature.
 // ---------------------------------------------------------------------------
@@ -291,25 +321,29 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
 {
     extern __shared__ float4 smem_f4[];
     const int M = qp.n_steps, G = qp.G;
-    float4 *s1 = smem_f4;                 // [M]
-    float4 *s2 = s1 + M;                  // [M]
-    RowF *rows = reinterpret_cast<RowF *>(s2 + M);   // [G]
+    float4 *sT = smem_f4;                              // [M]
+    float4 *sE = sT + M;                               // [M]
+    float2 *sD = reinterpret_cast<float2 *>(sE + M);   // [M]
+    RowF *rows = reinterpret_cast<RowF *>(sD + M + (M & 1));   // [G], 16-byte aligned
     __shared__ PieceConst<float> kc;
     __shared__ double scratch[32];
     __shared__ int s_item;
 
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const float4 zb = qp.zs_b[m];
-        const float4 za = qp.zs_a[m];
-        s1[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
-        s2[m] = make_float4(za.x, za.y, zb.z, zb.w);
+        const float4 za = qp.zs_a[m];   // {z_m, c_m, log2 dz_m, dz_m}
+        const float4 zb = qp.zs_b[m];   // {edge(m+1)/2pi hi, lo, z_m/2pi, 0}
+        sT[m] = make_float4(0.0f, 0.0f, za.x, za.y);
+        sE[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
+        sD[m] = make_float2(zb.z, za.w);
     }
     const float c3 = (float)(kPi * qp.beta3);
     const float c4 = (float)(2.0 * kPi * kPi / 3.0 * qp.beta4);
     const float b2 = (float)qp.beta2;
     const float m4pi2 = (float)(-4.0 * kPi * kPi);
     const float phi_direct = 3.14159265f / qp.dz_max;
+    const float phi_small = 0.02f / qp.L;
     const float log2e = (float)kLog2e;
+    const float invG = 1.0f / (float)G;
     int cur_prof = -1;
 
     for (;;) {
@@ -323,8 +357,10 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
             const float2 *st = qp.step_f + (size_t)item.prof * M;
             for (int m = threadIdx.x; m < M; m += blockDim.x) {
                 const float2 v = st[m];
-                s1[m].z = v.x;
-                s1[m].w = v.y;
+                sT[m].x = v.x + qp.zs_a[m].z;
+                sT[m].y = v.y;
+                sE[m].z = v.x;
+                sE[m].w = v.y;
             }
             cur_prof = item.prof;
         }
@@ -339,14 +375,15 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
             float sum = 0.0f, comp = 0.0f;
             const int npts = G * G;
             for (int q = threadIdx.x; q < npts; q += blockDim.x) {
-                const int r = q / G;
+                // row r = floor(q / G): (q + 1/2)/G is at least 1/(2G) from an integer
+                const int r = (int)(((float)q + 0.5f) * invG);
                 const int j = q - r * G;
                 const RowF rw = rows[r];
                 if (rw.w == 0.0f) continue;
                 const float d = ((float)j + 0.5f - 0.5f * (float)G) * rw.du2;
                 const float e = expf(d);
                 const float f1 = s1g * (rw.xc * e);
-                const float f2 = s2g * (rw.yc / e);
+                const float f2 = s2g * (rw.yc * __frcp_rn(e));
                 const float u = f1 + f2;                    // F_c - f_i
                 int ci = -1;
                 for (int c = 0; c < kc.nc; ++c) {
@@ -360,9 +397,11 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
                 const float br = b2 + c3 * (u + 2.0f * fi) +
                                  c4 * (f1 * f1 + 1.5f * f1 * f2 + 3.0f * fi * u + f2 * f2 + three_fi2);
                 const float phi = m4pi2 * f1 * f2 * br;
+                const float aphi = fabsf(phi);
                 float S2;
-                if (fabsf(phi) > phi_direct) S2 = zsum_tele_f(phi, Fc, at, s1, s2, M);
-                else S2 = zsum_direct_f(phi, Fc, at, s1, s2, M);
+                if (aphi <= phi_small) S2 = zsum_small_f(phi, Fc, at, sT, M);
+                else if (aphi <= phi_direct) S2 = zsum_direct_f(phi, Fc, at, sT, sD, M);
+                else S2 = zsum_tele_f(phi, Fc, at, sT, sE, M);
                 // compensated accumulation over this thread's points
                 const float y = rw.w * W * S2 - comp;
                 const float t = sum + y;
@@ -515,7 +554,9 @@ __global__ void __launch_bounds__(256) k_finish(FinishParams fp)
 // ---------------------------------------------------------------------------
 size_t quad_smem_bytes(int precision, int n_steps, int G)
 {
-    if (precision == 0) return (size_t)n_steps * 2 * sizeof(float4) + (size_t)G * sizeof(RowF);
+    if (precision == 0)
+        return (size_t)n_steps * (2 * sizeof(float4) + sizeof(float2)) + ((n_steps & 1) ? sizeof(float2) : 0) +
+               (size_t)G * sizeof(RowF);
     return (size_t)n_steps * 2 * sizeof(double2) + (size_t)G * sizeof(RowD);
 }
 
