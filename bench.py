@@ -202,7 +202,7 @@ def run_gpu(args):
         starts[k].record(stream)
         out = step()
         ends[k].record(stream)
-        quad_ms.append(eng.last_kernel_ms(0))          # events around the quadrature launch
+        quad_ms.append(eng.last_kernel_ms(1 if use_grad else 0))   # events around the dominant kernel
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
     if world > 1:
@@ -222,17 +222,28 @@ def run_gpu(args):
     n_grid = _unfolded_points(wl)
     value = world * n_grid * args.steps / t_total
 
-    # roofline of the dominant kernel (k_quad_f32): 3 SFU evaluations per
-    # evaluated point-step (sin, cos of the edge phasor, ex2 of the power term)
+    # roofline of the dominant kernel (k_quad_f32).  Algorithmic SFU work per
+    # point-step by the z-sum form the point took: small-phase expansion 1
+    # (the exp of Eq. pk), direct 3 (sin, cos, exp), telescoped 3 (sin, cos of
+    # the edge phasor, exp); the path counts come from the kernel itself.
     quad_ms = float(np.mean(quad_ms))
+    if use_grad:
+        _fwd_point_steps(eng, wl, P)
+    paths = eng.last_path_counts()
+    n_steps = wl.n_edges - 1
+    sfu_ops = n_steps * (1 * paths["small"] + 3 * paths["direct"] + 3 * paths["telescoped"])
+    if use_grad:
+        sfu_ops *= 2          # the fused adjoint evaluates every z-sum twice (S, then dS/d ln p)
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sfu_peak = N_SMS * SFU_PER_CLK_PER_SM * sm_max * 1e6 / 1e12       # Tops/s
-    fwd_psteps = _fwd_point_steps(eng, wl, P) if use_grad else info["point_steps"]
-    achieved = 3.0 * fwd_psteps / (quad_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Tops/s (SFU)",
+    achieved = sfu_ops / (quad_ms / 1e3) / 1e12
+    tot_pts = max(1, sum(paths.values()))
+    roof = {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Tops/s (SFU: sin, cos, ex2)",
             "frac": achieved / sfu_peak, "traffic": None,
-            "kernel": "k_quad_f32", "kernel_ms": quad_ms,
+            "kernel": "k_quad_adj" if use_grad else "k_quad_f32", "kernel_ms": quad_ms,
+            "sfu_ops_per_launch": sfu_ops,
+            "path_fraction": {k: v / tot_pts for k, v in paths.items()},
             "peak_source": f"152 SMs x 16 SFU/clk x {sm_max:.0f} MHz (max SM clock)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -246,6 +257,8 @@ def run_gpu(args):
                        "step": "isrs_gn_grad (SNR + dT/dP)" if use_grad else "isrs_gn_snr (eta, SNR, T)"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks, "roofline": roof, "wall_s": wall}
+    if rank == 0 and use_grad:
+        line["snr_eval"] = _snr_eval(eng, wl, P, dev, n_grid)
     if rank == 0 and not args.quick:
         line["e2e"] = _e2e(eng, wl, args, world, n_grid)
         line["fp64_path"] = _fp64_path(eng, wl, P, args)
@@ -256,6 +269,25 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
+    """The forward-only 589-ch SNR evaluation (isrs_gn_snr), timed with CUDA
+    events on the launching stream."""
+    import torch
+    st = torch.cuda.current_stream(dev)
+    eng.snr(wl, P=P)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        eng.snr(wl, P=P)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms))
+    return {"ms": t, "grid_pts_per_s": n_grid / (t / 1e3), "kernel": "k_quad_f32",
+            "kernel_ms": eng.last_kernel_ms(0)}
 
 
 def _unfolded_points(wl):
@@ -338,7 +370,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--G", type=int, default=256)
-    ap.add_argument("--mode", default="snr", choices=["snr", "grad"])
+    ap.add_argument("--mode", default="grad", choices=["snr", "grad"],
+                    help="grad: SNR + dT/dP (all hot-path steps); snr: forward only")
     ap.add_argument("--quick", action="store_true", help="skip e2e, FP64 and CPU legs")
     ap.add_argument("--profile-case", default=None, choices=["quad", "quad64", "adjoint"],
                     help="run one small launch of a kernel (for ncu captures) and exit")

@@ -213,6 +213,12 @@ isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_p
  * Errors: INVALID_ARG (bad which, or no such launch recorded yet), CUDA. */
 isrs_status isrs_last_kernel_ms(isrs_handle h, int which, float *ms);
 
+/* Grid points of the last FP32 quadrature launch by the form its z-sum took
+ * (App. A, Eq. slow_vary): counts[0] second-order small-phase expansion,
+ * counts[1] direct form, counts[2] telescoped form.  Synchronises the
+ * device.  Errors: INVALID_ARG (NULL, or no launch yet), CUDA. */
+isrs_status isrs_last_path_counts(isrs_handle h, int64_t *counts);
+
 #ifdef __cplusplus
 }
 #endif

@@ -119,6 +119,12 @@ class Engine:
         check(self.lib.isrs_last_kernel_ms(self.h, int(which), ctypes.byref(ms)), self.h)
         return ms.value
 
+    def last_path_counts(self):
+        """Grid points of the last FP32 launch per z-sum form."""
+        c = (ctypes.c_int64 * 3)()
+        check(self.lib.isrs_last_path_counts(self.h, c), self.h)
+        return {"small": c[0], "direct": c[1], "telescoped": c[2]}
+
     # ---- calls -----------------------------------------------------------
     def eta(self, wl, P=None, cuts: Optional[Sequence[int]] = None, precision: int = PREC_FP32,
             want_sigma: bool = True):

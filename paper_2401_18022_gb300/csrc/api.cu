@@ -54,6 +54,7 @@ struct isrs_handle_s {
     int device = 0;
     int num_sms = 1;
     std::string err;
+    DevBuf paths;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
         o_pase, o_T, gA, gK, gPd, ybar, dTdP;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
@@ -552,7 +553,11 @@ struct Launch {
 };
 
 // Runs prep + quadrature on the powers already in h->P (device, concatenated).
-isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precision, cudaStream_t st)
+// Runs prep + quadrature on the powers already in h->P.  With adjoint set, the
+// fused forward + adjoint kernel also fills the step buckets and the PSD
+// buckets (single profile, FP32).
+isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precision, cudaStream_t st,
+                        bool adjoint = false)
 {
     isrs_status s;
     const int M = g->n_steps;
@@ -619,16 +624,38 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     qp.partial = (double *)h->partial.p;
     qp.counter = (int *)h->counter.p;
     CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
+    if ((s = ensure(h, h->paths, sizeof(unsigned long long) * 4)) != ISRS_OK) return s;
+    CK(cudaMemsetAsync(h->paths.p, 0, sizeof(unsigned long long) * 4, st));
+    qp.path_count = (unsigned long long *)h->paths.p;
     const int block = h->tile_threads > 0 ? h->tile_threads : 256;
-    const int per_sm = quad_blocks_per_sm(precision, M, g->G, block);
-    int grid = h->num_sms * per_sm;
-    if (g->n_items < grid) grid = std::max(1, g->n_items);
-    if ((s = mark(h, 0, 0, st)) != ISRS_OK) return s;
-    if (g->n_items > 0) CK(launch_quad(qp, precision, grid, block, st));
-    if ((s = mark(h, 0, 1, st)) != ISRS_OK) return s;
+    if (adjoint) {
+        const int n_ch = g->plan_n[0];
+        if ((s = ensure(h, h->gA, sizeof(double2) * (size_t)std::max(1, g->n_items) * M)) != ISRS_OK) return s;
+        if ((s = ensure(h, h->gPd, sizeof(double) * (size_t)g->n_slots * n_ch)) != ISRS_OK) return s;
+        CK(cudaMemsetAsync(h->gPd.p, 0, sizeof(double) * (size_t)g->n_slots * n_ch, st));
+        AdjParams ap;
+        ap.q = qp;
+        ap.item_R = (double2 *)h->gA.p;
+        ap.V = (double *)h->gPd.p;
+        ap.item_slot = (const int *)g->item_slot.p;
+        ap.n_ch = n_ch;
+        const int per_sm = adjoint_blocks_per_sm(M, g->G, block);
+        int grid = h->num_sms * per_sm;
+        if (g->n_items < grid) grid = std::max(1, g->n_items);
+        if ((s = mark(h, 1, 0, st)) != ISRS_OK) return s;
+        if (g->n_items > 0) CK(launch_adjoint(ap, grid, block, st));
+        if ((s = mark(h, 1, 1, st)) != ISRS_OK) return s;
+    } else {
+        const int per_sm = quad_blocks_per_sm(precision, M, g->G, block);
+        int grid = h->num_sms * per_sm;
+        if (g->n_items < grid) grid = std::max(1, g->n_items);
+        if ((s = mark(h, 0, 0, st)) != ISRS_OK) return s;
+        if (g->n_items > 0) CK(launch_quad(qp, precision, grid, block, st));
+        if ((s = mark(h, 0, 1, st)) != ISRS_OK) return s;
+    }
     h->last_points = g->n_points;
     h->last_psteps = g->n_points * (int64_t)M;
-    h->last_launches = 1;
+    h->last_launches = 2;   // prep + quadrature
     return ISRS_OK;
 }
 
@@ -767,6 +794,7 @@ isrs_status isrs_destroy(isrs_handle h)
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
                       &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP};
     for (DevBuf *b : bufs) release(*b);
+    release(h->paths);
     for (int w = 0; w < 2; ++w)
         for (int k = 0; k < 2; ++k)
             if (h->ev[w][k]) cudaEventDestroy(h->ev[w][k]);
@@ -820,6 +848,17 @@ isrs_status isrs_last_kernel_ms(isrs_handle h, int which, float *ms)
     CK(cudaSetDevice(h->device));
     CK(cudaEventSynchronize(h->ev[which][1]));
     CK(cudaEventElapsedTime(ms, h->ev[which][0], h->ev[which][1]));
+    return ISRS_OK;
+}
+
+isrs_status isrs_last_path_counts(isrs_handle h, int64_t *counts)
+{
+    if (!h || !counts) return ISRS_ERR_INVALID_ARG;
+    if (!h->paths.p) return fail(h, ISRS_ERR_INVALID_ARG, "no launch recorded");
+    unsigned long long c[4] = {0, 0, 0, 0};
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpy(c, h->paths.p, sizeof(c), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 3; ++k) counts[k] = (int64_t)c[k];
     return ISRS_OK;
 }
 
@@ -943,9 +982,87 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
                          const isrs_quad *quad, double *dT_dP, double *snr, double *eta, double *T_host,
                          void *stream)
 {
-    (void)fibre; (void)ch; (void)P_W; (void)quad; (void)dT_dP; (void)snr; (void)eta; (void)T_host; (void)stream;
     if (!h) return ISRS_ERR_INVALID_ARG;
-    return fail(h, ISRS_ERR_UNSUPPORTED, "gradient not built yet");
+    h->err.clear();
+    isrs_status s;
+    if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
+    if ((s = check_plan(h, ch)) != ISRS_OK) return s;
+    if ((s = check_quad(h, quad)) != ISRS_OK) return s;
+    if (!P_W || !dT_dP) return fail(h, ISRS_ERR_INVALID_ARG, "P_W or dT_dP is NULL");
+    if (quad->precision != ISRS_PREC_FP32)
+        return fail(h, ISRS_ERR_INVALID_ARG, "the gradient is the adjoint of the FP32 path");
+    if (quad->n_edges - 1 > 128) return fail(h, ISRS_ERR_UNSUPPORTED, "gradient supports at most 128 z-steps");
+    if (ch->guard)
+        for (int k = 0; k < ch->n_ch; ++k)
+            if (ch->guard[k]) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs every channel lit (guard %d)", k);
+    if ((s = set_device(h)) != ISRS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        std::vector<double> hp(ch->n_ch);
+        if (is_device_ptr(P_W)) {
+            CK(cudaMemcpyAsync(hp.data(), P_W, sizeof(double) * ch->n_ch, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        } else {
+            std::memcpy(hp.data(), P_W, sizeof(double) * ch->n_ch);
+        }
+        if ((s = check_powers(h, hp.data(), ch->n_ch)) != ISRS_OK) return s;
+        for (int k = 0; k < ch->n_ch; ++k)
+            if (!(hp[k] > 0.0)) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs P[%d] > 0", k);
+    }
+    Geom *g = nullptr;
+    std::vector<std::vector<int>> cpp{std::vector<int>()};
+    std::vector<int> pp{0};
+    if ((s = get_geom(h, fibre, 1, ch, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
+    if ((s = load_powers(h, P_W, ch->n_ch, st)) != ISRS_OK) return s;
+    if ((s = run_forward(h, fibre, g, ISRS_PREC_FP32, st, true)) != ISRS_OK) return s;
+    if ((s = run_finish(h, fibre, quad, g, true, st)) != ISRS_OK) return s;
+    const int n = ch->n_ch, M = g->n_steps;
+    if ((s = ensure(h, h->ybar, sizeof(double) * 2 * n)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->gK, sizeof(double2) * M)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->dTdP, sizeof(double) * n)) != ISRS_OK) return s;
+    ChainParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.P = (const double *)h->P.p;
+    cp.ch_frel = (const double *)g->ch_frel.p;
+    cp.ch_B = (const double *)g->ch_B.p;
+    cp.ch_gamma = (const double *)g->ch_gamma.p;
+    cp.ch_nf = g->has_nf ? (const double *)g->ch_nf.p : nullptr;
+    cp.zs_d = (const double2 *)g->zs_d.p;
+    cp.step_d = (const double2 *)h->step_d.p;
+    cp.snr = (const double *)h->o_snr.p;
+    cp.pnli = (const double *)h->o_pnli.p;
+    cp.pase = (const double *)h->o_pase.p;
+    cp.lnrho_L = (const double *)h->lnrho_L.p;
+    cp.item_R = (const double2 *)h->gA.p;
+    cp.V = (const double *)h->gPd.p;
+    cp.item_slot = (const int *)g->item_slot.p;
+    cp.slot_cut = (const int *)g->slot_cut.p;
+    cp.n_items = g->n_items;
+    cp.n_slots = g->n_slots;
+    cp.n_ch = n;
+    cp.n_steps = M;
+    cp.L = fibre->L_km;
+    cp.Cr = fibre->Cr;
+    cp.alpha_R = fibre->alpha_R_per_km;
+    cp.f_ref = fibre->f_ref_THz;
+    cp.snr_trx_lin_inv = quad->snr_trx_dB > 0.0 ? std::pow(10.0, -quad->snr_trx_dB / 10.0) : 0.0;
+    cp.ybar = (double *)h->ybar.p;
+    cp.aase = (double *)h->ybar.p + n;
+    cp.Rb = (double2 *)h->gK.p;
+    cp.dT_dP = (double *)h->dTdP.p;
+    CK(launch_chain(cp, st));
+    h->last_launches += 3;
+    bool host_out = false;
+    if ((s = copy_out(h, dT_dP, h->dTdP, n, st, host_out)) != ISRS_OK) return s;
+    if ((s = copy_out(h, snr, h->o_snr, n, st, host_out)) != ISRS_OK) return s;
+    if ((s = copy_out(h, eta, h->o_eta, n, st, host_out)) != ISRS_OK) return s;
+    if (T_host) {
+        CK(cudaMemcpyAsync(T_host, h->o_T.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (host_out) CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return ISRS_OK;
 }
 
 }  // extern "C"

@@ -74,6 +74,7 @@ struct QuadParams {
     double *partial;            // one per item
     int *counter;               // persistent work counter (zeroed before launch)
     int *err_flag;
+    unsigned long long *path_count;   // [3] grid points per z-sum form (small, direct, telescoped)
 };
 
 }  // namespace isrs

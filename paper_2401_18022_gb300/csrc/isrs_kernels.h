@@ -39,26 +39,30 @@ struct FinishParams {
     double *T;                  // per profile
 };
 
-// Adjoint of the FP32 quadrature: per CUT, the gradients of Sigma_i with
-// respect to the per-step ISRS tables and the per-channel PSD factors.
+// Adjoint of the FP32 quadrature (single profile): per work tile the step
+// buckets {R_m, R'_m} and per (CUT slot, channel) the PSD buckets V.
 struct AdjParams {
     QuadParams q;
-    double *gA;                 // [n_slots x n_steps]  d Sigma_i / d (ln p_m offset)
-    double *gK;                 // [n_slots x n_steps]  d Sigma_i / d (-kappa_m) weighted by F_c
-    double *gPd;                // [n_slots x n_ch]     sum of w W |S|^2 multiplicities
-    const int *item_slot;       // slot index of each item
+    double2 *item_R;            // [n_items x n_steps]
+    double *V;                  // [n_slots x n_ch], zeroed before launch
+    const int *item_slot;       // output slot of each item
     int n_ch;
 };
 
+// Chain rule from the buckets to dT/dP_j (FP64, single profile).
 struct ChainParams {
-    const double *P, *ch_frel, *ch_B, *ch_alpha, *ch_gamma, *ch_nf;
-    const double2 *zs_d;
-    const double2 *step_d;
-    const double *sigma, *snr, *lnrho_L, *pnli;
-    const double *gA, *gK, *gPd;
-    int n_ch, n_steps;
-    double L, Cr, alpha_R, f_ref, snr_trx_lin_inv, ptot;
-    double *ybar;               // [n_ch] scratch: dT/dSigma_i
+    const double *P, *ch_frel, *ch_B, *ch_gamma, *ch_nf;
+    const double2 *zs_d;        // {z_m, dz_m}
+    const double2 *step_d;      // {lnPtot - lnN_m, kappa_m}
+    const double *snr, *pnli, *pase, *lnrho_L;
+    const double2 *item_R;
+    const double *V;
+    const int *item_slot, *slot_cut;
+    int n_items, n_slots, n_ch, n_steps;
+    double L, Cr, alpha_R, f_ref, snr_trx_lin_inv;
+    double *ybar;               // [n_slots] dT/dSigma_i
+    double *aase;               // [n_slots] dT/dASE_i * dASE_i/d ln G_i
+    double2 *Rb;                // [n_steps] sum_i ybar_i {R_im, R'_im}
     double *dT_dP;              // [n_ch]
 };
 
@@ -67,8 +71,9 @@ int quad_blocks_per_sm(int precision, int n_steps, int G, int block);
 cudaError_t launch_prep(const PrepParams &pp, int n_prof, cudaStream_t st);
 cudaError_t launch_quad(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
 cudaError_t launch_finish(const FinishParams &fp, int n_prof, cudaStream_t st);
-cudaError_t launch_adjoint(const AdjParams &ap, int grid, int block, cudaStream_t st);
+size_t adjoint_smem_bytes(int n_steps, int G, int block);
 int adjoint_blocks_per_sm(int n_steps, int G, int block);
+cudaError_t launch_adjoint(const AdjParams &ap, int grid, int block, cudaStream_t st);
 cudaError_t launch_chain(const ChainParams &cp, cudaStream_t st);
 
 }  // namespace isrs

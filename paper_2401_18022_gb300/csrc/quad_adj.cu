@@ -1,0 +1,571 @@
+// Adjoint of the FP32 quadrature: the gradient of the throughput T (Sec. IV,
+// Eq. loss) with respect to every launch power P_j, through eta (App. A,
+// Eqs. gain_fin, psi_fin, pk, slow_vary), the ASE gain and the SNR numerator.
+//
+// With the closed-form linear-slope profile, per grid point and step
+//   ln p_m = A_m - kappa_m (F_c - f_ref) - at z_m,   A_m = ln P_tot - ln N(z_m),
+// so the powers enter |S|^2 only through (A_m, kappa_m), shared by every point,
+// and through the PSD product W = P_a P_b P_c / (B_a B_b B_c).  For CUT i:
+//   dSigma_i/dP_j = V_ij / P_j + sum_m R_im dA_m/dP_j - sum_m R'_im dkappa_m/dP_j
+// with the buckets
+//   R_im  = sum_points w W d|S|^2/d ln p_m,
+//   R'_im = sum_points w W (F_c - f_ref) d|S|^2/d ln p_m,
+//   V_ij  = sum_points w W |S|^2 (number of j among the point's a, b, c).
+//
+// k_quad_adj evaluates the forward sum and these buckets in one pass over the
+// grid.  Pass 1 (one grid point per lane) forms S as the forward kernel does.
+// Pass 2 turns the warp around: every lane owns a block of K consecutive
+// steps (their tables live in registers) and the warp walks its 32 points,
+// broadcasting each point's state by shuffles, so bucket sums over points
+// need neither atomics nor shared-memory traffic per step.
+#include <cuda_runtime.h>
+
+#include "isrs_internal.cuh"
+#include "isrs_kernels.h"
+#include "quad_common.cuh"
+
+namespace isrs {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPathSmall = 0, kPathDirect = 1, kPathTele = 2;
+
+// Pass-1 z-sums that keep the quantities the derivative needs.
+//   small:  M0, M1, M2 with |S|^2 = M0^2 - phi^2 (M0 M2 - M1^2)
+//   direct: S
+//   tele:   U = sum_m p_m (E_{m+1} - E_m) with |S|^2 = |U|^2 / phi^2
+__device__ __forceinline__ void zsum_small_m(float phi, float Fc, float at, const float4 *sT, int M,
+                                             float &M0, float &M1, float &M2)
+{
+    M0 = 0.0f; M1 = 0.0f; M2 = 0.0f;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 a = sT[m];
+        float lp = fmaf(a.y, Fc, a.x);
+        lp = fmaf(-at, a.z, lp);
+        const float w = ex2_approx(lp);
+        M0 += w;
+        M1 = fmaf(w, a.z, M1);
+        M2 = fmaf(w, a.w, M2);
+    }
+}
+
+__device__ __forceinline__ float sinc_poly(float x)
+{
+    const float x2 = x * x;
+    float sc = fmaf(x2, -2.5052108e-8f, 2.7557319e-6f);
+    sc = fmaf(x2, sc, -1.9841270e-4f);
+    sc = fmaf(x2, sc, 8.3333333e-3f);
+    sc = fmaf(x2, sc, -1.6666667e-1f);
+    return fmaf(x2, sc, 1.0f);
+}
+
+__device__ __forceinline__ void zsum_direct_c(float phi, float Fc, float at, const float4 *sT,
+                                              const float2 *sD, int M, float &Sr, float &Si)
+{
+    Sr = 0.0f; Si = 0.0f;
+    const float hphi = 0.5f * phi;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 a = sT[m];
+        const float2 d = sD[m];
+        float sn, cs;
+        sincos_rev(phi * d.x, sn, cs);
+        float lp = fmaf(a.y, Fc, a.x);
+        lp = fmaf(-at, a.z, lp);
+        const float amp = ex2_approx(lp) * sinc_poly(hphi * d.y);
+        Sr = fmaf(amp, cs, Sr);
+        Si = fmaf(amp, sn, Si);
+    }
+}
+
+__device__ __forceinline__ void zsum_tele_c(float phi, float Fc, float at, const float4 *sT,
+                                            const float4 *sE, int M, float &Ur, float &Ui)
+{
+    float Er = 1.0f, Ei = 0.0f;
+    Ur = 0.0f; Ui = 0.0f;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 e = sE[m];
+        const float zm = sT[m].z;
+        float sn, cs;
+        phasor_rev_ff(phi, e.x, e.y, sn, cs);
+        float lp = fmaf(e.w, Fc, e.z);
+        lp = fmaf(-at, zm, lp);
+        const float p = ex2_approx(lp);
+        Ur = fmaf(p, cs - Er, Ur);
+        Ui = fmaf(p, sn - Ei, Ui);
+        Er = cs;
+        Ei = sn;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// k_quad_adj<K>: fused forward + adjoint, persistent over work tiles of one
+// profile.  Lane l owns steps [K l, K l + K) in pass 2.
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
+{
+    const QuadParams &qp = ap.q;
+    extern __shared__ float4 smem_f4[];
+    const int M = qp.n_steps, G = qp.G;
+    const int nw = blockDim.x >> 5;
+    float4 *sT = smem_f4;
+    float4 *sE = sT + M;
+    float2 *sD = reinterpret_cast<float2 *>(sE + M);
+    RowF *rows = reinterpret_cast<RowF *>(sD + M + (M & 1));
+    double2 *sR = reinterpret_cast<double2 *>(rows + G);      // [nw][M]
+    __shared__ PieceConst<float> kc;
+    __shared__ float sVc[kMaxCand];
+    __shared__ double scratch[32];
+    __shared__ int s_item;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float4 za = qp.zs_a[m];
+        const float4 zb = qp.zs_b[m];
+        sT[m] = make_float4(0.0f, 0.0f, za.x, za.y);
+        sE[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
+        sD[m] = make_float2(zb.z, za.w);
+    }
+    for (int t = threadIdx.x; t < nw * M; t += blockDim.x) sR[t] = make_double2(0.0, 0.0);
+    if (threadIdx.x < kMaxCand) sVc[threadIdx.x] = 0.0f;
+
+    const float c3 = (float)(kPi * qp.beta3);
+    const float c4 = (float)(2.0 * kPi * kPi / 3.0 * qp.beta4);
+    const float b2 = (float)qp.beta2;
+    const float m4pi2 = (float)(-4.0 * kPi * kPi);
+    const float phi_direct = 3.14159265f / qp.dz_max;
+    const float phi_small = 0.02f / qp.L;
+    const float log2e = (float)kLog2e;
+    const float invG = 1.0f / (float)G;
+    const int m0 = lane * K;
+
+    // owned step tables (registers), loaded when the profile is staged
+    float oA2d[K], oA2[K], oK2[K], oz[K], oc[K], omr[K], odz[K], oeh[K], oel[K];
+    float e0h = 0.0f, e0l = 0.0f;
+    float R[K], Rp[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { R[k] = 0.0f; Rp[k] = 0.0f; }
+    int cur_prof = -1;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(qp.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= qp.n_items) break;
+        const DevItem item = qp.items[it];
+        const int slot = ap.item_slot[it];
+        if (item.prof != cur_prof) {
+            const float2 *st = qp.step_f + (size_t)item.prof * M;
+            for (int m = threadIdx.x; m < M; m += blockDim.x) {
+                const float2 v = st[m];
+                sT[m].x = v.x + qp.zs_a[m].z;
+                sT[m].y = v.y;
+                sE[m].z = v.x;
+                sE[m].w = v.y;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int m = m0 + k;
+                const bool ok = m < M;
+                const float4 a = ok ? sT[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 e = ok ? sE[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float2 d = ok ? sD[m] : make_float2(0.f, 0.f);
+                oA2d[k] = a.x; oK2[k] = a.y; oz[k] = a.z; oc[k] = a.w;
+                oeh[k] = e.x; oel[k] = e.y; oA2[k] = e.z;
+                omr[k] = d.x; odz[k] = d.y;
+            }
+            if (m0 > 0 && m0 < M) { e0h = sE[m0 - 1].x; e0l = sE[m0 - 1].y; }
+            cur_prof = item.prof;
+        }
+        double acc = 0.0;
+        for (int kp = item.piece0; kp < item.piece1; ++kp) {
+            const DevPiece pc = qp.pieces[kp];
+            piece_rows<RowF>(pc, G, qp.eps_v1, rows);
+            piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
+            __syncthreads();
+            const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2, mult = kc.mult;
+            const float three_fi2 = 3.0f * fi * fi;
+            float sum = 0.0f, comp = 0.0f;
+            float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f, v3 = 0.0f;
+            const int npts = G * G;
+            int batches = 0;
+            for (int qb = warp * 32; qb < npts; qb += blockDim.x) {
+                // ---- pass 1: this lane's grid point
+                const int q = qb + lane;
+                float phi = 0.0f, Fc = 0.0f, at = 0.0f, cpt = 0.0f, q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
+                int path = 0;
+                if (q < npts) {
+                    const int r = (int)(((float)q + 0.5f) * invG);
+                    const int j = q - r * G;
+                    const RowF rw = rows[r];
+                    if (rw.w != 0.0f) {
+                        const float d = ((float)j + 0.5f - 0.5f * (float)G) * rw.du2;
+                        const float e = expf(d);
+                        const float f1 = s1g * (rw.xc * e);
+                        const float f2 = s2g * (rw.yc * __frcp_rn(e));
+                        const float u = f1 + f2;
+                        int ci = -1;
+                        for (int c = 0; c < kc.nc; ++c) {
+                            if (u >= kc.lo[c] && u < kc.hi[c]) { ci = c; break; }
+                        }
+                        if (ci >= 0) {
+                            const float W = kc.wab * kc.pd[ci];
+                            at = kc.at_ab + kc.hat[ci];
+                            Fc = fi + u;
+                            const float br = b2 + c3 * (u + 2.0f * fi) +
+                                             c4 * (f1 * f1 + 1.5f * f1 * f2 + 3.0f * fi * u + f2 * f2 + three_fi2);
+                            phi = m4pi2 * f1 * f2 * br;
+                            const float aphi = fabsf(phi);
+                            float S2;
+                            if (aphi <= phi_small) {
+                                path = kPathSmall;
+                                zsum_small_m(phi, Fc, at, sT, M, q0, q1, q2);
+                                S2 = fmaf(-phi * phi, fmaf(q0, q2, -q1 * q1), q0 * q0);
+                            } else if (aphi <= phi_direct) {
+                                path = kPathDirect;
+                                zsum_direct_c(phi, Fc, at, sT, sD, M, q0, q1);
+                                S2 = q0 * q0 + q1 * q1;
+                            } else {
+                                path = kPathTele;
+                                zsum_tele_c(phi, Fc, at, sT, sE, M, q0, q1);
+                                S2 = (q0 * q0 + q1 * q1) / (phi * phi);
+                            }
+                            const float val = rw.w * W * S2;
+                            const float y = val - comp;
+                            const float t = sum + y;
+                            comp = (t - sum) - y;
+                            sum = t;
+                            if (ci == 0) v0 += val;
+                            else if (ci == 1) v1 += val;
+                            else if (ci == 2) v2 += val;
+                            else if (ci == 3) v3 += val;
+                            else atomicAdd(&sVc[ci], val);
+                            cpt = mult * rw.w * W;
+                        }
+                    }
+                }
+                __syncwarp();
+                // ---- pass 2: the warp's 32 points, each lane on its own steps
+                for (int p = 0; p < 32; ++p) {
+                    const float cp = __shfl_sync(kFull, cpt, p);
+                    if (cp == 0.0f) continue;
+                    const float ph = __shfl_sync(kFull, phi, p);
+                    const float fc = __shfl_sync(kFull, Fc, p);
+                    const float a_t = __shfl_sync(kFull, at, p);
+                    const float p0 = __shfl_sync(kFull, q0, p);
+                    const float p1 = __shfl_sync(kFull, q1, p);
+                    const float p2 = __shfl_sync(kFull, q2, p);
+                    const int pth = __shfl_sync(kFull, path, p);
+                    const float cF = cp * fc;
+                    if (pth == kPathSmall) {
+                        // d|S|^2/d ln p_m = w_m (2 M0 - phi^2 (M2 + M0 c_m - 2 M1 z_m))
+                        const float ph2 = ph * ph;
+                        const float al0 = 2.0f * p0 - ph2 * p2, al1 = -ph2 * p0, al2 = 2.0f * ph2 * p1;
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            if (m0 + k < M) {
+                                float lp = fmaf(oK2[k], fc, oA2d[k]);
+                                lp = fmaf(-a_t, oz[k], lp);
+                                const float w = ex2_approx(lp);
+                                const float rr = w * fmaf(al2, oz[k], fmaf(al1, oc[k], al0));
+                                R[k] = fmaf(cp, rr, R[k]);
+                                Rp[k] = fmaf(cF, rr, Rp[k]);
+                            }
+                        }
+                    } else if (pth == kPathDirect) {
+                        // d|S|^2/d ln p_m = 2 Re(conj(S) p_m dz_m sinc e^{j phi z_m})
+                        const float hph = 0.5f * ph;
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            if (m0 + k < M) {
+                                float sn, cs;
+                                sincos_rev(ph * omr[k], sn, cs);
+                                float lp = fmaf(oK2[k], fc, oA2d[k]);
+                                lp = fmaf(-a_t, oz[k], lp);
+                                const float amp = ex2_approx(lp) * sinc_poly(hph * odz[k]);
+                                const float rr = 2.0f * amp * fmaf(p0, cs, p1 * sn);
+                                R[k] = fmaf(cp, rr, R[k]);
+                                Rp[k] = fmaf(cF, rr, Rp[k]);
+                            }
+                        }
+                    } else {
+                        // d|S|^2/d ln p_m = 2 Re(conj(U) p_m (E_{m+1} - E_m)) / phi^2
+                        float Er, Ei;
+                        phasor_rev_ff(ph, e0h, e0l, Ei, Er);
+                        const float g = 2.0f / (ph * ph);
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            if (m0 + k < M) {
+                                float sn, cs;
+                                phasor_rev_ff(ph, oeh[k], oel[k], sn, cs);
+                                float lp = fmaf(oK2[k], fc, oA2[k]);
+                                lp = fmaf(-a_t, oz[k], lp);
+                                const float pm = ex2_approx(lp);
+                                const float rr = g * pm * fmaf(p0, cs - Er, p1 * (sn - Ei));
+                                R[k] = fmaf(cp, rr, R[k]);
+                                Rp[k] = fmaf(cF, rr, Rp[k]);
+                                Er = cs;
+                                Ei = sn;
+                            }
+                        }
+                    }
+                }
+                // FP32 lane buckets are moved to the warp's FP64 buckets every 8 batches
+                if (++batches == 8) {
+                    batches = 0;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        if (m0 + k < M) {
+                            double2 &b = sR[warp * M + m0 + k];
+                            b.x += (double)R[k];
+                            b.y += (double)Rp[k];
+                        }
+                        R[k] = 0.0f;
+                        Rp[k] = 0.0f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (m0 + k < M) {
+                    double2 &b = sR[warp * M + m0 + k];
+                    b.x += (double)R[k];
+                    b.y += (double)Rp[k];
+                }
+                R[k] = 0.0f;
+                Rp[k] = 0.0f;
+            }
+            // piece totals: the forward sum and the PSD buckets V_ij
+            const double ptot = block_sum_d((double)sum - (double)comp, scratch);
+            const double t0 = block_sum_d((double)v0, scratch);
+            const double t1 = block_sum_d((double)v1, scratch);
+            const double t2 = block_sum_d((double)v2, scratch);
+            const double t3 = block_sum_d((double)v3, scratch);
+            acc += (double)mult * ptot;
+            if (threadIdx.x == 0) {
+                double *Vrow = ap.V + (size_t)slot * ap.n_ch;
+                atomicAdd(&Vrow[pc.a], (double)mult * ptot);
+                atomicAdd(&Vrow[pc.b], (double)mult * ptot);
+                for (int c = 0; c < kc.nc; ++c) {
+                    const double vc = c == 0 ? t0 : c == 1 ? t1 : c == 2 ? t2 : c == 3 ? t3 : (double)sVc[c];
+                    if (vc != 0.0) atomicAdd(&Vrow[pc.c_lo + c], (double)mult * vc);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < kMaxCand) sVc[threadIdx.x] = 0.0f;
+        }
+        // tile outputs: the forward partial and the step buckets
+        if (threadIdx.x == 0) qp.partial[it] = acc;
+        __syncthreads();
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            double rx = 0.0, ry = 0.0;
+            for (int w = 0; w < nw; ++w) {
+                rx += sR[w * M + m].x;
+                ry += sR[w * M + m].y;
+                sR[w * M + m] = make_double2(0.0, 0.0);
+            }
+            ap.item_R[(size_t)it * M + m] = make_double2(rx, ry);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Chain rule (FP64).  Notation: s_i = SNR_i = P_i / N_i (optionally with
+// 1/SNR += t), N_i = P_NLI,i + P_ASE,i, P_NLI,i = K_i Sigma_i with
+// K_i = (16/27) gamma_i^2 B_i, P_ASE,i = NF h f B (G_i - 1), G_i = 1/rho(L,f_i),
+// T = 2 sum_i B_i log2(1 + s_i).  Then ds/dN = -s^2/P and ds/dP|_N = s^2 N/P^2.
+// For the closed-form profile at any z (kappa = P_tot C_r L_eff(z)):
+//   d ln rho(z,F)/dP_j = 1/P_tot - h_j(kappa)/N(z) - C_r L_eff(z) (F - Fbar(z)),
+//   h_j(kappa) = e^{-kappa f_j'} sinhc(kappa B_j/2),  Fbar = tilted mean frequency.
+// ---------------------------------------------------------------------------
+constexpr int kMaxAdjSteps = 128;
+constexpr double kHPlanck = 6.62607015e-34;
+
+__global__ void __launch_bounds__(256) k_ybar(ChainParams cp)
+{
+    for (int s = threadIdx.x + blockIdx.x * blockDim.x; s < cp.n_slots; s += blockDim.x * gridDim.x) {
+        const int i = cp.slot_cut[s];
+        const double P = cp.P[i], B = cp.ch_B[i], g = cp.ch_gamma[i], snr = cp.snr[s];
+        const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
+        const double dsdN = -snr * snr / P;
+        const double nf = cp.ch_nf ? pow(10.0, cp.ch_nf[i] / 10.0) : 1.0;
+        const double hfb = nf * kHPlanck * ((cp.ch_frel[i] + cp.f_ref) * 1e12) * (B * 1e12);
+        cp.ybar[s] = dTds * dsdN * (16.0 / 27.0) * g * g * B;
+        cp.aase[s] = dTds * dsdN * (cp.pase[s] + hfb);    // dT/dASE * dASE/d ln G
+    }
+}
+
+// Rb[m] = sum over tiles of ybar(slot of tile) * {R_m, R'_m}; one block per m.
+__global__ void __launch_bounds__(256) k_adj_reduce(ChainParams cp)
+{
+    __shared__ double scratch[32];
+    const int m = blockIdx.x;
+    double rx = 0.0, ry = 0.0;
+    for (int it = threadIdx.x; it < cp.n_items; it += blockDim.x) {
+        const double y = cp.ybar[cp.item_slot[it]];
+        const double2 v = cp.item_R[(size_t)it * cp.n_steps + m];
+        rx += y * v.x;
+        ry += y * v.y;
+    }
+    rx = block_sum_d(rx, scratch);
+    ry = block_sum_d(ry, scratch);
+    if (threadIdx.x == 0) cp.Rb[m] = make_double2(rx, ry);
+}
+
+__device__ __forceinline__ double sinhc_ad(double x)
+{
+    return fabs(x) < 1e-4 ? 1.0 + x * x / 6.0 : sinh(x) / x;
+}
+
+// sinhc'(y) / sinhc(y) = coth(y) - 1/y
+__device__ __forceinline__ double dlog_sinhc(double y)
+{
+    return fabs(y) < 1e-3 ? y / 3.0 - y * y * y / 45.0 : 1.0 / tanh(y) - 1.0 / y;
+}
+
+__global__ void __launch_bounds__(256) k_chain(ChainParams cp)
+{
+    __shared__ double s_lnN[kMaxAdjSteps + 1], s_kap[kMaxAdjSteps + 1], s_Le[kMaxAdjSteps + 1],
+        s_Fb[kMaxAdjSteps + 1];
+    __shared__ double scratch[32];
+    __shared__ double s_const[4];
+    const int n = cp.n_ch, M = cp.n_steps;
+    double part = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) part += cp.P[c];
+    const double Ptot = block_sum_d(part, scratch);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // per step m (and z = L at index M): ln N, kappa, L_eff and the tilted mean Fbar - f_ref
+    for (int m = wid; m <= M; m += nw) {
+        const double z = m < M ? cp.zs_d[m].x : cp.L;
+        const double Le = cp.alpha_R > 0.0 ? -expm1(-cp.alpha_R * z) / cp.alpha_R : z;
+        const double kap = Ptot * cp.Cr * Le;
+        double mx = -1e300;
+        for (int c = lane; c < n; c += 32)
+            mx = fmax(mx, log(cp.P[c]) - kap * cp.ch_frel[c] + log(sinhc_ad(0.5 * kap * cp.ch_B[c])));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        double s0 = 0.0, s1 = 0.0;
+        for (int c = lane; c < n; c += 32) {
+            const double a = 0.5 * cp.ch_B[c];
+            const double w = exp(log(cp.P[c]) - kap * cp.ch_frel[c] + log(sinhc_ad(kap * a)) - mx);
+            s0 += w;
+            s1 += w * (cp.ch_frel[c] - a * dlog_sinhc(kap * a));
+        }
+        s0 = warp_sum_d(s0);
+        s1 = warp_sum_d(s1);
+        if (lane == 0) {
+            s_lnN[m] = mx + log(s0);
+            s_kap[m] = kap;
+            s_Le[m] = Le;
+            s_Fb[m] = s1 / s0;
+        }
+    }
+    __syncthreads();
+    // j-independent sums
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) a1 += cp.Rb[m].y * s_Le[m];
+    for (int s = threadIdx.x; s < cp.n_slots; s += blockDim.x) {
+        a2 += cp.aase[s];
+        a3 += cp.aase[s] * (cp.ch_frel[cp.slot_cut[s]] - s_Fb[M]);
+    }
+    a1 = block_sum_d(a1, scratch);
+    a2 = block_sum_d(a2, scratch);
+    a3 = block_sum_d(a3, scratch);
+    if (threadIdx.x == 0) {
+        s_const[0] = -cp.Cr * a1;                     // R' term
+        s_const[1] = a2;                              // sum of aase
+        s_const[2] = cp.Cr * s_Le[M] * a3;            // ASE tilt term
+    }
+    __syncthreads();
+    const double invPt = 1.0 / Ptot;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double fj = cp.ch_frel[j], hB = 0.5 * cp.ch_B[j];
+        double g = s_const[0];
+        for (int m = 0; m < M; ++m) {
+            const double hN = exp(-s_kap[m] * fj + log(sinhc_ad(s_kap[m] * hB)) - s_lnN[m]);
+            g += cp.Rb[m].x * (invPt - hN + cp.Cr * s_Le[m] * s_Fb[m]);
+        }
+        double v = 0.0;
+        for (int s = 0; s < cp.n_slots; ++s) v += cp.ybar[s] * cp.V[(size_t)s * n + j];
+        g += v / cp.P[j];
+        const double hNL = exp(-s_kap[M] * fj + log(sinhc_ad(s_kap[M] * hB)) - s_lnN[M]);
+        g += -s_const[1] * (invPt - hNL) + s_const[2];
+        // SNR numerator (slot j: the gradient call evaluates every channel)
+        const double snr = cp.snr[j], P = cp.P[j], B = cp.ch_B[j];
+        const double N = cp.pnli[j] + cp.pase[j];
+        const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
+        g += dTds * snr * snr * N / (P * P);
+        cp.dT_dP[j] = g;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+size_t adjoint_smem_bytes(int n_steps, int G, int block)
+{
+    return (size_t)n_steps * (2 * sizeof(float4) + sizeof(float2)) + ((n_steps & 1) ? sizeof(float2) : 0) +
+           (size_t)G * sizeof(RowF) + (size_t)(block / 32) * n_steps * sizeof(double2);
+}
+
+template <int K>
+static void *adj_fn()
+{
+    return (void *)k_quad_adj<K>;
+}
+
+static void *adj_kernel_for(int n_steps)
+{
+    const int K = (n_steps + 31) / 32;
+    switch (K) {
+    case 1: return adj_fn<1>();
+    case 2: return adj_fn<2>();
+    case 3: return adj_fn<3>();
+    case 4: return adj_fn<4>();
+    }
+    return nullptr;
+}
+
+int adjoint_blocks_per_sm(int n_steps, int G, int block)
+{
+    void *fn = adj_kernel_for(n_steps);
+    if (!fn) return 0;
+    const size_t smem = adjoint_smem_bytes(n_steps, G, block);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem);
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_adjoint(const AdjParams &ap, int grid, int block, cudaStream_t st)
+{
+    void *fn = adj_kernel_for(ap.q.n_steps);
+    if (!fn) return cudaErrorInvalidValue;
+    const size_t smem = adjoint_smem_bytes(ap.q.n_steps, ap.q.G, block);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    AdjParams a = ap;
+    void *args[] = {&a};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st);
+}
+
+cudaError_t launch_chain(const ChainParams &cp, cudaStream_t st)
+{
+    if (cp.n_steps > kMaxAdjSteps) return cudaErrorInvalidValue;
+    k_ybar<<<1, 256, 0, st>>>(cp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adj_reduce<<<cp.n_steps, 256, 0, st>>>(cp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_chain<<<1, 256, 0, st>>>(cp);
+    return cudaGetLastError();
+}
+
+}  // namespace isrs

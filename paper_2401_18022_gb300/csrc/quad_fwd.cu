@@ -16,50 +16,9 @@
 
 #include "isrs_internal.cuh"
 #include "isrs_kernels.h"
+#include "quad_common.cuh"
 
 namespace isrs {
-
-// ---------------------------------------------------------------------------
-// small helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// nearest integer of |t| < 2^22 on the FMA pipe (round-to-nearest-even add)
-__device__ __forceinline__ float round_magic(float t)
-{
-    return __fadd_rn(__fadd_rn(t, 12582912.0f), -12582912.0f);
-}
-
-__device__ __forceinline__ double warp_sum_d(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Deterministic block sum of one double per thread (blockDim multiple of 32).
-__device__ double block_sum_d(double v, double *scratch)
-{
-    v = warp_sum_d(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) scratch[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += scratch[w];
-        scratch[0] = r;
-    }
-    __syncthreads();
-    r = scratch[0];
-    __syncthreads();
-    return r;
-}
 
 // ---------------------------------------------------------------------------
 // k_prep: ISRS profile tables (FP64).  One block per profile.
@@ -140,80 +99,6 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams pp)
 }
 
 // ---------------------------------------------------------------------------
-// Piece set-up shared by the quadrature kernels (FP64, once per piece).
-// Row r (uniform in s = ln upsilon1): upsilon1 = exp(s_r); the |f2| range
-// [ymin, ymax] of that row; upsilon2 spans ln(ymax/ymin) in G columns.
-// Stored relative to the row centre so FP32 points keep full precision:
-//   x_j = xc e^{d_j}, y_j = yc e^{-d_j}, d_j = (j + 1/2 - G/2) du2,
-//   weight = upsilon1 ds du2 (the Jacobian of (f1, f2) -> (u1, u2) is 1).
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ void piece_rows(const DevPiece &pc, int G, double eps, T *rows)
-{
-    const double u1hi = pc.xhi * pc.yhi;
-    const double u1lo = fmax(pc.xlo * pc.ylo, eps * u1hi);
-    const double llo = log(u1lo);
-    const double ds = (log(u1hi) - llo) / G;
-    for (int r = threadIdx.x; r < G; r += blockDim.x) {
-        const double u1 = exp(llo + (r + 0.5) * ds);
-        const double ymin = fmax(pc.ylo, u1 / pc.xhi);
-        const double ymax = pc.xlo > 0.0 ? fmin(pc.yhi, u1 / pc.xlo) : pc.yhi;
-        T rw;
-        if (ymax > ymin) {
-            const double du2 = log1p((ymax - ymin) / ymin) / G;
-            const double yc = sqrt(ymin * ymax);
-            rw.xc = u1 / yc;
-            rw.yc = yc;
-            rw.du2 = du2;
-            rw.w = u1 * ds * du2;
-        } else {
-            rw.xc = 0; rw.yc = 0; rw.du2 = 0; rw.w = 0;
-        }
-        rows[r] = rw;
-    }
-}
-
-struct RowF { float xc, yc, du2, w; };
-struct RowD { double xc, yc, du2, w; };
-
-// Per-piece constants: CUT offset, signs, the PSD factors of F_a and F_b, the
-// attenuation part of ln p and the candidate channels of F_c (edges relative
-// to the CUT so that F_c - f_i = f1 + f2 is compared without cancellation).
-template <typename T>
-struct PieceConst {
-    T fi, s1, s2, wab, at_ab, mult;
-    int nc;
-    T lo[kMaxCand], hi[kMaxCand], pd[kMaxCand], hat[kMaxCand];
-};
-
-template <typename T>
-__device__ void piece_consts(const QuadParams &qp, const DevPiece &pc, int prof, T at_scale,
-                             const T *pdv, PieceConst<T> &k)
-{
-    if (threadIdx.x == 0) {
-        const int coff = qp.plan_ch_off[pc.plan];
-        const int poff = qp.prof_ch_off[prof];
-        const double fi = qp.ch_frel[coff + pc.cut];
-        k.fi = (T)fi;
-        k.s1 = (pc.flags & 1) ? T(-1) : T(1);
-        k.s2 = (pc.flags & 2) ? T(-1) : T(1);
-        k.wab = pdv[poff + pc.a] * pdv[poff + pc.b];
-        k.at_ab = (T)(0.5 * (qp.ch_alpha[coff + pc.a] + qp.ch_alpha[coff + pc.b] -
-                             qp.ch_alpha[coff + pc.cut])) * at_scale;
-        k.mult = (T)pc.mult;
-        int nc = 0;
-        for (int c = pc.c_lo; c <= pc.c_hi && nc < kMaxCand; ++c, ++nc) {
-            const double fc = qp.ch_frel[coff + c], hb = 0.5 * qp.ch_B[coff + c];
-            k.lo[nc] = (T)((fc - hb) - fi);
-            k.hi[nc] = (T)((fc + hb) - fi);
-            k.pd[nc] = pdv[poff + c];
-            k.hat[nc] = (T)(0.5 * qp.ch_alpha[coff + c]) * at_scale;
-        }
-        k.nc = nc;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // FP32 z-sums.  Per-step tables staged in shared memory:
 //   sT[m] = {A2_m + log2 dz_m, K2_m, z_m, c_m = z_m^2 + dz_m^2/12}
 //   sD[m] = {z_m / 2pi, dz_m}
@@ -235,21 +120,6 @@ __device__ void piece_consts(const QuadParams &qp, const DevPiece &pc, int prof,
 //    exponential per edge suffices; the phase phi z_e / 2pi (up to ~1e5
 //    revolutions) is an error-free float-float product reduced to [-1/2, 1/2].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void sincos_rev(float t, float &sn, float &cs)
-{
-    const float fr = __fadd_rn(t, -round_magic(t));
-    __sincosf(fr * 6.283185307179586f, &sn, &cs);
-}
-
-__device__ __forceinline__ void phasor_rev_ff(float phi, float hi, float lo, float &sn, float &cs)
-{
-    const float th = phi * hi;
-    float tl = fmaf(phi, hi, -th);
-    tl = fmaf(phi, lo, tl);
-    const float fr = __fadd_rn(th, -round_magic(th)) + tl;
-    __sincosf(fr * 6.283185307179586f, &sn, &cs);
-}
-
 __device__ __forceinline__ float zsum_small_f(float phi, float Fc, float at, const float4 *sT, int M)
 {
     float M0 = 0.0f, M1 = 0.0f, M2 = 0.0f;
@@ -344,6 +214,7 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
     const float phi_small = 0.02f / qp.L;
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
+    unsigned n_small = 0, n_direct = 0, n_tele = 0;
     int cur_prof = -1;
 
     for (;;) {
@@ -399,9 +270,16 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
                 const float phi = m4pi2 * f1 * f2 * br;
                 const float aphi = fabsf(phi);
                 float S2;
-                if (aphi <= phi_small) S2 = zsum_small_f(phi, Fc, at, sT, M);
-                else if (aphi <= phi_direct) S2 = zsum_direct_f(phi, Fc, at, sT, sD, M);
-                else S2 = zsum_tele_f(phi, Fc, at, sT, sE, M);
+                if (aphi <= phi_small) {
+                    S2 = zsum_small_f(phi, Fc, at, sT, M);
+                    ++n_small;
+                } else if (aphi <= phi_direct) {
+                    S2 = zsum_direct_f(phi, Fc, at, sT, sD, M);
+                    ++n_direct;
+                } else {
+                    S2 = zsum_tele_f(phi, Fc, at, sT, sE, M);
+                    ++n_tele;
+                }
                 // compensated accumulation over this thread's points
                 const float y = rw.w * W * S2 - comp;
                 const float t = sum + y;
@@ -413,6 +291,20 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
         }
         const double tot = block_sum_d(acc, scratch);
         if (threadIdx.x == 0) qp.partial[it] = tot;
+    }
+    if (qp.path_count) {
+        unsigned long long c0 = n_small, c1 = n_direct, c2 = n_tele;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&qp.path_count[0], c0);
+            atomicAdd(&qp.path_count[1], c1);
+            atomicAdd(&qp.path_count[2], c2);
+        }
     }
 }
 
