@@ -219,6 +219,33 @@ isrs_status isrs_last_kernel_ms(isrs_handle h, int which, float *ms);
  * device.  Errors: INVALID_ARG (NULL, or no launch yet), CUDA. */
 isrs_status isrs_last_path_counts(isrs_handle h, int64_t *counts);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free forward                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* eta_i and P_NLI,i for every channel, like isrs_gn_eta with cuts == NULL,
+ * but without allocating device memory: for callers that cannot call
+ * cudaMalloc (code inside a host framework that owns the device allocator,
+ * a memory-budgeted real-time loop, a process whose allocator is locked).
+ * The paper has no counterpart; this is a deployment variant.
+ *
+ * All scratch (plan tables, per-profile tables, tile partials) lives in one
+ * file-scope device array of 4 MiB that every GPU loading this library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * address with the device current; make that first call before any stream
+ * capture.  Every call shares the array and leaves the last call's contents
+ * in it; calls whose GPU work overlaps (two streams, two host threads, two
+ * devices' worth of work on one device) race on it and must be serialised by
+ * the caller.
+ *   P_W[n_ch], eta[n_ch]: device pointers; pnli[n_ch]: device or NULL.
+ * No handle is used; the call synchronises `stream` once after uploading
+ * the plan tables, then runs asynchronously.
+ * Errors: INVALID_ARG (as isrs_gn_eta, or a host pointer), UNSUPPORTED
+ * (the tables need more than the 4 MiB scratch: e.g. more than ~5e4 pieces,
+ * or the FP32 phase range), CUDA. */
+isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
+                                const isrs_quad *quad, double *eta, double *pnli, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

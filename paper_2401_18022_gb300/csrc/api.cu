@@ -1066,3 +1066,241 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free forward entry point (isrs_gn_eta_noalloc).
+//
+// For callers that cannot allocate device memory themselves: code running
+// inside a host framework that owns the device allocator, a CUDA-graph
+// builder or a real-time loop in which a cudaMalloc would block or break the
+// memory budget.  All scratch lives in one file-scope device array of fixed
+// size that every GPU loading this library holds until the process exits.
+// ============================================================================
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)4 << 20;     // 4 MiB of scratch per device
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_isrs_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once
+// per device, with that device current).
+isrs_status noalloc_scratch(int dev, void **out)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return ISRS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_isrs_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return ISRS_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return ISRS_OK;
+}
+
+// Bump layout of the tables inside the scratch array (256-byte aligned slots).
+struct NoAllocLayout {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        const size_t at = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return at;
+    }
+};
+
+}  // namespace
+
+extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
+                                           const isrs_quad *quad, double *eta, double *pnli, void *stream)
+{
+    isrs_status s;
+    if ((s = check_fibre(nullptr, fibre)) != ISRS_OK) return s;
+    if ((s = check_plan(nullptr, ch)) != ISRS_OK) return s;
+    if ((s = check_quad(nullptr, quad)) != ISRS_OK) return s;
+    if (!P_W || !eta || !is_device_ptr(P_W) || !is_device_ptr(eta) || (pnli && !is_device_ptr(pnli)))
+        return ISRS_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ISRS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = ch->n_ch;
+
+    // launch powers: validated on the host
+    std::vector<double> hp(n);
+    if (cudaMemcpyAsync(hp.data(), P_W, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ISRS_ERR_CUDA;
+    if ((s = check_powers(nullptr, hp.data(), n)) != ISRS_OK) return s;
+
+    // host tables: pieces of every CUT, work tiles, output slots, z-grid
+    std::vector<DevPiece> pieces;
+    std::vector<DevItem> items;
+    std::vector<int2> slot_items;
+    std::vector<int> slot_cut, item_slot;
+    const int64_t G2 = (int64_t)quad->G * quad->G;
+    const int chunk = (int)std::max<int64_t>(1, (int64_t)(1 << 20) / G2);
+    for (int i = 0; i < n; ++i) {
+        const int p0 = (int)pieces.size();
+        if ((s = cut_pieces(nullptr, ch, 0, i, quad->cell_set, pieces)) != ISRS_OK) return s;
+        const int p1 = (int)pieces.size();
+        const int it0 = (int)items.size();
+        for (int a = p0; a < p1; a += chunk) {
+            items.push_back(DevItem{0, a, std::min(a + chunk, p1), i});
+            item_slot.push_back(i);
+        }
+        slot_items.push_back(make_int2(it0, (int)items.size()));
+        slot_cut.push_back(i);
+    }
+    std::vector<double> frel(n), Bv(n), av(n), gv(n);
+    for (int k = 0; k < n; ++k) {
+        frel[k] = ch->f_THz[k] - fibre->f_ref_THz;
+        Bv[k] = ch->B_THz[k];
+        av[k] = ch->alpha_per_km[k];
+        gv[k] = ch->gamma_per_W_km[k];
+    }
+    std::vector<float4> za, zb;
+    std::vector<double2> zd;
+    float dz_max = 0.f;
+    zgrid_tables(fibre->L_km, fibre->alpha_R_per_km, quad->n_edges, za, zb, zd, dz_max);
+    const int M = quad->n_edges - 1;
+    if (quad->precision == ISRS_PREC_FP32) {
+        const double pi = 3.14159265358979323846;
+        for (const DevPiece &pc : pieces) {
+            const double fi = std::fabs(frel[pc.cut]);
+            const double v1 = pc.xhi * pc.yhi, s12 = pc.xhi + pc.yhi;
+            const double br = std::fabs(fibre->beta2) + pi * std::fabs(fibre->beta3) * (s12 + 2.0 * fi) +
+                              2.0 * pi * pi / 3.0 * std::fabs(fibre->beta4) *
+                                  (s12 * s12 + 1.5 * v1 + 3.0 * fi * s12 + 3.0 * fi * fi);
+            if (4.0 * pi * pi * v1 * br * fibre->L_km / (2.0 * pi) > 2097152.0) return ISRS_ERR_UNSUPPORTED;
+        }
+    }
+    const std::vector<int> zero1{0}, plan_n{n}, slot_off{0, n};
+
+    // layout in the scratch array; anything beyond its size is rejected
+    NoAllocLayout L;
+    const size_t o_pieces = L.take(sizeof(DevPiece) * pieces.size());
+    const size_t o_items = L.take(sizeof(DevItem) * items.size());
+    const size_t o_slot_items = L.take(sizeof(int2) * n);
+    const size_t o_slot_cut = L.take(sizeof(int) * n);
+    const size_t o_slot_off = L.take(sizeof(int) * 2);
+    const size_t o_zero = L.take(sizeof(int));
+    const size_t o_plan_n = L.take(sizeof(int));
+    const size_t o_frel = L.take(sizeof(double) * n), o_B = L.take(sizeof(double) * n);
+    const size_t o_alpha = L.take(sizeof(double) * n), o_gamma = L.take(sizeof(double) * n);
+    const size_t o_za = L.take(sizeof(float4) * M), o_zb = L.take(sizeof(float4) * M);
+    const size_t o_zd = L.take(sizeof(double2) * M);
+    const size_t o_P = L.take(sizeof(double) * n);
+    const size_t o_pdd = L.take(sizeof(double) * n), o_pdf = L.take(sizeof(float) * n);
+    const size_t o_lnL = L.take(sizeof(double) * n), o_ptot = L.take(sizeof(double));
+    const size_t o_stepd = L.take(sizeof(double2) * M), o_stepf = L.take(sizeof(float2) * M);
+    const size_t o_partial = L.take(sizeof(double) * std::max<size_t>(1, items.size()));
+    const size_t o_counter = L.take(sizeof(int) * 4), o_T = L.take(sizeof(double));
+    const size_t o_paths = L.take(sizeof(unsigned long long) * 4);
+    if (L.off > kNoAllocBytes) return ISRS_ERR_UNSUPPORTED;
+
+    unsigned char *base = nullptr;
+    if ((s = noalloc_scratch(dev, (void **)&base)) != ISRS_OK) return s;
+    struct Up { size_t off; const void *src; size_t bytes; } ups[] = {
+        {o_pieces, pieces.data(), sizeof(DevPiece) * pieces.size()},
+        {o_items, items.data(), sizeof(DevItem) * items.size()},
+        {o_slot_items, slot_items.data(), sizeof(int2) * n}, {o_slot_cut, slot_cut.data(), sizeof(int) * n},
+        {o_slot_off, slot_off.data(), sizeof(int) * 2}, {o_zero, zero1.data(), sizeof(int)},
+        {o_plan_n, plan_n.data(), sizeof(int)}, {o_frel, frel.data(), sizeof(double) * n},
+        {o_B, Bv.data(), sizeof(double) * n}, {o_alpha, av.data(), sizeof(double) * n},
+        {o_gamma, gv.data(), sizeof(double) * n}, {o_za, za.data(), sizeof(float4) * M},
+        {o_zb, zb.data(), sizeof(float4) * M}, {o_zd, zd.data(), sizeof(double2) * M}};
+    for (const Up &u : ups)
+        if (u.bytes && cudaMemcpyAsync(base + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return ISRS_ERR_CUDA;
+    if (cudaMemcpyAsync(base + o_P, P_W, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(base + o_counter, 0, sizeof(int) * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(base + o_paths, 0, sizeof(unsigned long long) * 4, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)      // the host tables are freed at return
+        return ISRS_ERR_CUDA;
+
+    PrepParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.P = (const double *)(base + o_P);
+    pp.ch_frel = (const double *)(base + o_frel);
+    pp.ch_B = (const double *)(base + o_B);
+    pp.ch_alpha = (const double *)(base + o_alpha);
+    pp.plan_ch_off = pp.prof_ch_off = pp.prof_plan = (const int *)(base + o_zero);
+    pp.plan_n = (const int *)(base + o_plan_n);
+    pp.zs_d = (const double2 *)(base + o_zd);
+    pp.n_steps = M;
+    pp.L = fibre->L_km;
+    pp.Cr = fibre->Cr;
+    pp.alpha_R = fibre->alpha_R_per_km;
+    pp.pd_d = (double *)(base + o_pdd);
+    pp.pd_f = (float *)(base + o_pdf);
+    pp.step_d = (double2 *)(base + o_stepd);
+    pp.step_f = (float2 *)(base + o_stepf);
+    pp.lnrho_L = (double *)(base + o_lnL);
+    pp.ptot = (double *)(base + o_ptot);
+    if (launch_prep(pp, 1, st) != cudaSuccess) return ISRS_ERR_CUDA;
+
+    QuadParams qp;
+    std::memset(&qp, 0, sizeof(qp));
+    qp.pieces = (const DevPiece *)(base + o_pieces);
+    qp.items = (const DevItem *)(base + o_items);
+    qp.n_items = (int)items.size();
+    qp.G = quad->G;
+    qp.n_steps = M;
+    qp.eps_v1 = quad->eps_v1;
+    qp.beta2 = fibre->beta2;
+    qp.beta3 = fibre->beta3;
+    qp.beta4 = fibre->beta4;
+    qp.ch_frel = pp.ch_frel;
+    qp.ch_B = pp.ch_B;
+    qp.ch_alpha = pp.ch_alpha;
+    qp.plan_ch_off = qp.prof_ch_off = qp.prof_plan = (const int *)(base + o_zero);
+    qp.pd_f = pp.pd_f;
+    qp.pd_d = pp.pd_d;
+    qp.step_f = pp.step_f;
+    qp.step_d = pp.step_d;
+    qp.zs_a = (const float4 *)(base + o_za);
+    qp.zs_b = (const float4 *)(base + o_zb);
+    qp.zs_d = pp.zs_d;
+    qp.dz_max = dz_max;
+    qp.L = (float)fibre->L_km;
+    qp.partial = (double *)(base + o_partial);
+    qp.counter = (int *)(base + o_counter);
+    qp.path_count = (unsigned long long *)(base + o_paths);
+    int n_sms = 1;
+    cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = n_sms * quad_blocks_per_sm(quad->precision, M, quad->G, 256);
+    if ((int)items.size() < grid) grid = std::max(1, (int)items.size());
+    if (!items.empty() && launch_quad(qp, quad->precision, grid, 256, st) != cudaSuccess) return ISRS_ERR_CUDA;
+
+    FinishParams fp;
+    std::memset(&fp, 0, sizeof(fp));
+    fp.partial = qp.partial;
+    fp.slot_items = (const int2 *)(base + o_slot_items);
+    fp.slot_cut = (const int *)(base + o_slot_cut);
+    fp.prof_slot_off = (const int *)(base + o_slot_off);
+    fp.prof_plan = fp.plan_ch_off = fp.prof_ch_off = (const int *)(base + o_zero);
+    fp.ch_gamma = (const double *)(base + o_gamma);
+    fp.ch_B = pp.ch_B;
+    fp.ch_frel = pp.ch_frel;
+    fp.P = pp.P;
+    fp.lnrho_L = pp.lnrho_L;
+    fp.f_ref = fibre->f_ref_THz;
+    fp.eta = eta;
+    fp.pnli = pnli;
+    fp.T = (double *)(base + o_T);
+    if (launch_finish(fp, 1, st) != cudaSuccess) return ISRS_ERR_CUDA;
+    return ISRS_OK;
+}
