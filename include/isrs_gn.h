@@ -213,6 +213,12 @@ isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_p
  * Errors: INVALID_ARG (bad which, or no such launch recorded yet), CUDA. */
 isrs_status isrs_last_kernel_ms(isrs_handle h, int which, float *ms);
 
+/* 1 if the last isrs_gn_eta_batched call replayed its captured CUDA graph
+ * (prep, quadrature and finish captured once per launch signature), 0 if it
+ * ran the kernels directly (first call of a signature, or capture not
+ * possible).  Errors: INVALID_ARG (NULL). */
+isrs_status isrs_last_graph_replay(isrs_handle h, int *replayed);
+
 /* Grid points of the last FP32 quadrature launch by the form its z-sum took
  * (App. A, Eq. slow_vary): counts[0] second-order small-phase expansion,
  * counts[1] direct form, counts[2] telescoped form.  Synchronises the

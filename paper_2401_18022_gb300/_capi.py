@@ -74,6 +74,8 @@ def load(build_if_missing: bool = True):
                                         vp, P(Quad), vp, vp]
     lib.isrs_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.isrs_last_launch_info.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), c_int_p]
+    lib.isrs_last_graph_replay.argtypes = [vp, c_int_p]
+    lib.isrs_last_graph_replay.restype = ctypes.c_int
     lib.isrs_last_path_counts.argtypes = [vp, P(ctypes.c_int64)]
     lib.isrs_last_path_counts.restype = ctypes.c_int
     lib.isrs_last_kernel_ms.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]

@@ -119,6 +119,12 @@ class Engine:
         check(self.lib.isrs_last_kernel_ms(self.h, int(which), ctypes.byref(ms)), self.h)
         return ms.value
 
+    def last_graph_replay(self) -> bool:
+        """Whether the last batched call replayed its captured CUDA graph."""
+        v = ctypes.c_int()
+        check(self.lib.isrs_last_graph_replay(self.h, ctypes.byref(v)), self.h)
+        return bool(v.value)
+
     def last_path_counts(self):
         """Grid points of the last FP32 launch per z-sum form."""
         c = (ctypes.c_int64 * 3)()

@@ -46,6 +46,10 @@ struct Geom {
     DevBuf pieces, items, slot_items, slot_cut, prof_slot_off, plan_ch_off_d, plan_n_d, prof_ch_off_d,
         prof_plan_d, ch_frel, ch_B, ch_alpha, ch_gamma, ch_nf, guard, zs_a, zs_b, zs_d, item_slot;
     bool has_nf = false, has_guard = false;
+    // replayable graph of the batched launch (prep -> quadrature -> finish)
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey = 0;                 // fibre, precision and tile the graph was captured with
+    std::vector<void *> gptrs;         // workspace pointers baked into the graph
 };
 
 }  // namespace
@@ -61,6 +65,8 @@ struct isrs_handle_s {
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
     int last_launches = 0;
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
+    bool last_graph = false;             // the last batched call replayed a graph
     cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [quad, adjoint][start, end]
     bool ev_valid[2] = {false, false};
 };
@@ -526,6 +532,7 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     h->cache.insert(h->cache.begin(), std::move(g));
     while (h->cache.size() > 4) {
         Geom *old = h->cache.back().get();
+        if (old->gexec) cudaGraphExecDestroy(old->gexec);
         DevBuf *bufs[] = {&old->pieces, &old->items, &old->slot_items, &old->slot_cut, &old->prof_slot_off,
                           &old->plan_ch_off_d, &old->plan_n_d, &old->prof_ch_off_d, &old->prof_plan_d,
                           &old->ch_frel, &old->ch_B, &old->ch_alpha, &old->ch_gamma, &old->ch_nf,
@@ -539,6 +546,8 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
 
 void free_geom(Geom *g)
 {
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
     DevBuf *bufs[] = {&g->pieces, &g->items, &g->slot_items, &g->slot_cut, &g->prof_slot_off,
                       &g->plan_ch_off_d, &g->plan_n_d, &g->prof_ch_off_d, &g->prof_plan_d,
                       &g->ch_frel, &g->ch_B, &g->ch_alpha, &g->ch_gamma, &g->ch_nf,
@@ -742,6 +751,65 @@ isrs_status set_device(isrs_handle h)
     return ISRS_OK;
 }
 
+// The batched launch as a replayable CUDA graph.  The first call for a launch
+// signature runs directly (which also sizes every workspace buffer) and then
+// captures the same sequence on a private stream; later calls replay it on
+// the caller's stream.  The graph is re-captured whenever the fibre,
+// precision, tile or any workspace pointer it baked in has changed.
+std::vector<void *> workspace_ptrs(isrs_handle h)
+{
+    return {h->P.p, h->pd_d.p, h->pd_f.p, h->lnrho_L.p, h->step_d.p, h->step_f.p, h->ptot.p, h->partial.p,
+            h->counter.p, h->paths.p, h->o_sigma.p, h->o_pnli.p, h->o_eta.p, h->o_snr.p, h->o_pase.p, h->o_T.p};
+}
+
+isrs_status run_batched_graph(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
+{
+    isrs_status s;
+    Hasher hs;
+    hs.val(*fb);
+    hs.val(q->precision);
+    hs.val(h->tile_threads);
+    const uint64_t key = hs.v;
+    if (g->gexec && g->gkey == key && g->gptrs == workspace_ptrs(h)) {
+        CK(cudaGraphLaunch(g->gexec, st));
+        h->last_graph = true;
+        h->last_points = g->n_points;
+        h->last_psteps = g->n_points * (int64_t)g->n_steps;
+        h->last_launches = 3;
+        return ISRS_OK;
+    }
+    if ((s = run_forward(h, fb, g, q->precision, st)) != ISRS_OK) return s;
+    if ((s = run_finish(h, fb, q, g, false, st)) != ISRS_OK) return s;
+    h->last_graph = false;
+    if (g->gexec) {
+        cudaGraphExecDestroy(g->gexec);
+        g->gexec = nullptr;
+    }
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const int saved = h->last_launches;
+    const int64_t sp = h->last_points, ss = h->last_psteps;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        isrs_status s1 = run_forward(h, fb, g, q->precision, h->cap_stream);
+        isrs_status s2 = s1 == ISRS_OK ? run_finish(h, fb, q, g, false, h->cap_stream) : s1;
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (s2 == ISRS_OK && e == cudaSuccess && graph &&
+            cudaGraphInstantiate(&g->gexec, graph, 0) == cudaSuccess) {
+            g->gkey = key;
+            g->gptrs = workspace_ptrs(h);
+        } else {
+            g->gexec = nullptr;          // capture not possible: keep running directly
+        }
+        if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+    h->err.clear();
+    h->last_launches = saved;
+    h->last_points = sp;
+    h->last_psteps = ss;
+    return ISRS_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -798,6 +866,7 @@ isrs_status isrs_destroy(isrs_handle h)
     for (int w = 0; w < 2; ++w)
         for (int k = 0; k < 2; ++k)
             if (h->ev[w][k]) cudaEventDestroy(h->ev[w][k]);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
     return ISRS_OK;
 }
@@ -838,6 +907,13 @@ isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_p
     if (n_points) *n_points = h->last_points;
     if (n_point_steps) *n_point_steps = h->last_psteps;
     if (n_launches) *n_launches = h->last_launches;
+    return ISRS_OK;
+}
+
+isrs_status isrs_last_graph_replay(isrs_handle h, int *replayed)
+{
+    if (!h || !replayed) return ISRS_ERR_INVALID_ARG;
+    *replayed = h->last_graph ? 1 : 0;
     return ISRS_OK;
 }
 
@@ -969,8 +1045,7 @@ isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_pl
     std::vector<std::vector<int>> cpp(n_plans);
     if ((s = get_geom(h, fibre, n_plans, plans, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
     if ((s = load_powers(h, P_W, total, st)) != ISRS_OK) return s;
-    if ((s = run_forward(h, fibre, g, quad->precision, st)) != ISRS_OK) return s;
-    if ((s = run_finish(h, fibre, quad, g, false, st)) != ISRS_OK) return s;
+    if ((s = run_batched_graph(h, fibre, quad, g, st)) != ISRS_OK) return s;
     bool host_out = false;
     if ((s = copy_out(h, eta, h->o_eta, total, st, host_out)) != ISRS_OK) return s;
     if (host_out) CK(cudaStreamSynchronize(st));

@@ -61,20 +61,20 @@ __device__ __forceinline__ float sinc_poly(float x)
     return fmaf(x2, sc, 1.0f);
 }
 
-__device__ __forceinline__ void zsum_direct_c(float phi, float Fc, float at, const float4 *sT,
-                                              const float2 *sD, int M, float &Sr, float &Si)
+__device__ __forceinline__ void zsum_direct_c(float phi, float Fc, float at, const float4 *sR, int M,
+                                              float &Sr, float &Si)
 {
     Sr = 0.0f; Si = 0.0f;
     const float hphi = 0.5f * phi;
+    const float phir = phi * 0.15915494309189535f;
 #pragma unroll 4
     for (int m = 0; m < M; ++m) {
-        const float4 a = sT[m];
-        const float2 d = sD[m];
+        const float4 a = sR[m];
         float sn, cs;
-        sincos_rev(phi * d.x, sn, cs);
+        sincos_rev(phir * a.z, sn, cs);
         float lp = fmaf(a.y, Fc, a.x);
         lp = fmaf(-at, a.z, lp);
-        const float amp = ex2_approx(lp) * sinc_poly(hphi * d.y);
+        const float amp = ex2_approx(lp) * sinc_poly(hphi * a.w);
         Sr = fmaf(amp, cs, Sr);
         Si = fmaf(amp, sn, Si);
     }
@@ -107,18 +107,23 @@ __device__ __forceinline__ void zsum_tele_c(float phi, float Fc, float at, const
 // k_quad_adj<K>: fused forward + adjoint, persistent over work tiles of one
 // profile.  Lane l owns steps [K l, K l + K) in pass 2.
 // ---------------------------------------------------------------------------
+#ifndef ISRS_ADJ_MIN_BLOCKS
+#define ISRS_ADJ_MIN_BLOCKS 2   // resident blocks per SM the register budget is sized for
+#endif
+
 template <int K>
-__global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
+__global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams ap)
 {
     const QuadParams &qp = ap.q;
     extern __shared__ float4 smem_f4[];
     const int M = qp.n_steps, G = qp.G;
     const int nw = blockDim.x >> 5;
-    float4 *sT = smem_f4;
-    float4 *sE = sT + M;
-    float2 *sD = reinterpret_cast<float2 *>(sE + M);
-    RowF *rows = reinterpret_cast<RowF *>(sD + M + (M & 1));
-    double2 *sR = reinterpret_cast<double2 *>(rows + G);      // [nw][M]
+    float4 *sT = smem_f4;                                     // {A2 + log2 dz, K2, z, z^2 + dz^2/12}
+    float4 *sE = sT + M;                                      // {edge/2pi hi, lo, A2, K2}
+    float4 *sR = sE + M;                                      // {A2 + log2 dz, K2, z, dz}
+    RowF *rows = reinterpret_cast<RowF *>(sR + M);
+    // per-warp FP64 step buckets, lane-contiguous: [warp][k][lane] for step lane*K + k
+    double2 *sB = reinterpret_cast<double2 *>(rows + G);
     __shared__ PieceConst<float> kc;
     __shared__ float sVc[kMaxCand];
     __shared__ double scratch[32];
@@ -130,9 +135,9 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
         const float4 zb = qp.zs_b[m];
         sT[m] = make_float4(0.0f, 0.0f, za.x, za.y);
         sE[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
-        sD[m] = make_float2(zb.z, za.w);
+        sR[m] = make_float4(0.0f, 0.0f, za.x, za.w);
     }
-    for (int t = threadIdx.x; t < nw * M; t += blockDim.x) sR[t] = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < nw * K * 32; t += blockDim.x) sB[t] = make_double2(0.0, 0.0);
     if (threadIdx.x < kMaxCand) sVc[threadIdx.x] = 0.0f;
 
     const float c3 = (float)(kPi * qp.beta3);
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
     const int m0 = lane * K;
 
     // owned step tables (registers), loaded when the profile is staged
-    float oA2d[K], oA2[K], oK2[K], oz[K], oc[K], omr[K], odz[K], oeh[K], oel[K];
+    float oA2d[K], oA2[K], oK2[K], oz[K], oc[K], odz[K], oeh[K], oel[K];
     float e0h = 0.0f, e0l = 0.0f;
     float R[K], Rp[K];
 #pragma unroll
@@ -165,10 +170,13 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
             const float2 *st = qp.step_f + (size_t)item.prof * M;
             for (int m = threadIdx.x; m < M; m += blockDim.x) {
                 const float2 v = st[m];
-                sT[m].x = v.x + qp.zs_a[m].z;
+                const float a2d = v.x + qp.zs_a[m].z;
+                sT[m].x = a2d;
                 sT[m].y = v.y;
                 sE[m].z = v.x;
                 sE[m].w = v.y;
+                sR[m].x = a2d;
+                sR[m].y = v.y;
             }
             __syncthreads();
 #pragma unroll
@@ -177,10 +185,9 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
                 const bool ok = m < M;
                 const float4 a = ok ? sT[m] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float4 e = ok ? sE[m] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float2 d = ok ? sD[m] : make_float2(0.f, 0.f);
                 oA2d[k] = a.x; oK2[k] = a.y; oz[k] = a.z; oc[k] = a.w;
                 oeh[k] = e.x; oel[k] = e.y; oA2[k] = e.z;
-                omr[k] = d.x; odz[k] = d.y;
+                odz[k] = ok ? sR[m].w : 0.0f;
             }
             if (m0 > 0 && m0 < M) { e0h = sE[m0 - 1].x; e0l = sE[m0 - 1].y; }
             cur_prof = item.prof;
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
                                 S2 = fmaf(-phi * phi, fmaf(q0, q2, -q1 * q1), q0 * q0);
                             } else if (aphi <= phi_direct) {
                                 path = kPathDirect;
-                                zsum_direct_c(phi, Fc, at, sT, sD, M, q0, q1);
+                                zsum_direct_c(phi, Fc, at, sR, M, q0, q1);
                                 S2 = q0 * q0 + q1 * q1;
                             } else {
                                 path = kPathTele;
@@ -283,11 +290,12 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
                     } else if (pth == kPathDirect) {
                         // d|S|^2/d ln p_m = 2 Re(conj(S) p_m dz_m sinc e^{j phi z_m})
                         const float hph = 0.5f * ph;
+                        const float phr = ph * 0.15915494309189535f;
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
                             if (m0 + k < M) {
                                 float sn, cs;
-                                sincos_rev(ph * omr[k], sn, cs);
+                                sincos_rev(phr * oz[k], sn, cs);
                                 float lp = fmaf(oK2[k], fc, oA2d[k]);
                                 lp = fmaf(-a_t, oz[k], lp);
                                 const float amp = ex2_approx(lp) * sinc_poly(hph * odz[k]);
@@ -323,11 +331,9 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
                     batches = 0;
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        if (m0 + k < M) {
-                            double2 &b = sR[warp * M + m0 + k];
-                            b.x += (double)R[k];
-                            b.y += (double)Rp[k];
-                        }
+                        double2 &b = sB[(warp * K + k) * 32 + lane];
+                        b.x += (double)R[k];
+                        b.y += (double)Rp[k];
                         R[k] = 0.0f;
                         Rp[k] = 0.0f;
                     }
@@ -335,11 +341,9 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                if (m0 + k < M) {
-                    double2 &b = sR[warp * M + m0 + k];
-                    b.x += (double)R[k];
-                    b.y += (double)Rp[k];
-                }
+                double2 &b = sB[(warp * K + k) * 32 + lane];
+                b.x += (double)R[k];
+                b.y += (double)Rp[k];
                 R[k] = 0.0f;
                 Rp[k] = 0.0f;
             }
@@ -366,11 +370,13 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj(AdjParams ap)
         if (threadIdx.x == 0) qp.partial[it] = acc;
         __syncthreads();
         for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            const int ln = m / K, kk = m - ln * K;
             double rx = 0.0, ry = 0.0;
             for (int w = 0; w < nw; ++w) {
-                rx += sR[w * M + m].x;
-                ry += sR[w * M + m].y;
-                sR[w * M + m] = make_double2(0.0, 0.0);
+                double2 &b = sB[(w * K + kk) * 32 + ln];
+                rx += b.x;
+                ry += b.y;
+                b = make_double2(0.0, 0.0);
             }
             ap.item_R[(size_t)it * M + m] = make_double2(rx, ry);
         }
@@ -512,8 +518,9 @@ __global__ void __launch_bounds__(256) k_chain(ChainParams cp)
 // ---------------------------------------------------------------------------
 size_t adjoint_smem_bytes(int n_steps, int G, int block)
 {
-    return (size_t)n_steps * (2 * sizeof(float4) + sizeof(float2)) + ((n_steps & 1) ? sizeof(float2) : 0) +
-           (size_t)G * sizeof(RowF) + (size_t)(block / 32) * n_steps * sizeof(double2);
+    const int K = (n_steps + 31) / 32;
+    return (size_t)n_steps * 3 * sizeof(float4) + (size_t)G * sizeof(RowF) +
+           (size_t)(block / 32) * K * 32 * sizeof(double2);
 }
 
 template <int K>

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams pp)
 // ---------------------------------------------------------------------------
 // FP32 z-sums.  Per-step tables staged in shared memory:
 //   sT[m] = {A2_m + log2 dz_m, K2_m, z_m, c_m = z_m^2 + dz_m^2/12}
-//   sD[m] = {z_m / 2pi, dz_m}
+//   sR[m] = {A2_m + log2 dz_m, K2_m, z_m, dz_m}
 //   sE[m] = {z_{m+1}/2pi hi, lo (float-float), A2_m, K2_m}
 // with log2 p_m = A2_m + K2_m Fc - at z_m (Eq. pk for the closed-form
 // profile).  The phase is carried in revolutions (z / 2pi).
@@ -136,18 +136,18 @@ __device__ __forceinline__ float zsum_small_f(float phi, float Fc, float at, con
     return fmaf(-phi * phi, fmaf(M0, M2, -M1 * M1), M0 * M0);
 }
 
-__device__ __forceinline__ float zsum_direct_f(float phi, float Fc, float at, const float4 *sT,
-                                               const float2 *sD, int M)
+__device__ __forceinline__ float zsum_direct_f(float phi, float Fc, float at, const float4 *sR, int M)
 {
+    // sR[m] = {A2_m + log2 dz_m, K2_m, z_m, dz_m}; phase in revolutions phi/2pi * z_m
     float Sr = 0.0f, Si = 0.0f;
     const float hphi = 0.5f * phi;
+    const float phir = phi * 0.15915494309189535f;
 #pragma unroll 4
     for (int m = 0; m < M; ++m) {
-        const float4 a = sT[m];
-        const float2 d = sD[m];
+        const float4 a = sR[m];
         float sn, cs;
-        sincos_rev(phi * d.x, sn, cs);
-        const float x = hphi * d.y;
+        sincos_rev(phir * a.z, sn, cs);
+        const float x = hphi * a.w;
         const float x2 = x * x;
         float sc = fmaf(x2, -2.5052108e-8f, 2.7557319e-6f);   // -1/11!, 1/9!
         sc = fmaf(x2, sc, -1.9841270e-4f);                     // -1/7!
@@ -191,10 +191,10 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
 {
     extern __shared__ float4 smem_f4[];
     const int M = qp.n_steps, G = qp.G;
-    float4 *sT = smem_f4;                              // [M]
-    float4 *sE = sT + M;                               // [M]
-    float2 *sD = reinterpret_cast<float2 *>(sE + M);   // [M]
-    RowF *rows = reinterpret_cast<RowF *>(sD + M + (M & 1));   // [G], 16-byte aligned
+    float4 *sT = smem_f4;                              // [M] {A2 + log2 dz, K2, z, z^2 + dz^2/12}
+    float4 *sE = sT + M;                               // [M] {edge/2pi hi, lo, A2, K2}
+    float4 *sR = sE + M;                               // [M] {A2 + log2 dz, K2, z, dz}
+    RowF *rows = reinterpret_cast<RowF *>(sR + M);     // [G]
     __shared__ PieceConst<float> kc;
     __shared__ double scratch[32];
     __shared__ int s_item;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
         const float4 zb = qp.zs_b[m];   // {edge(m+1)/2pi hi, lo, z_m/2pi, 0}
         sT[m] = make_float4(0.0f, 0.0f, za.x, za.y);
         sE[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
-        sD[m] = make_float2(zb.z, za.w);
+        sR[m] = make_float4(0.0f, 0.0f, za.x, za.w);
     }
     const float c3 = (float)(kPi * qp.beta3);
     const float c4 = (float)(2.0 * kPi * kPi / 3.0 * qp.beta4);
@@ -228,10 +228,13 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
             const float2 *st = qp.step_f + (size_t)item.prof * M;
             for (int m = threadIdx.x; m < M; m += blockDim.x) {
                 const float2 v = st[m];
-                sT[m].x = v.x + qp.zs_a[m].z;
+                const float a2d = v.x + qp.zs_a[m].z;
+                sT[m].x = a2d;
                 sT[m].y = v.y;
                 sE[m].z = v.x;
                 sE[m].w = v.y;
+                sR[m].x = a2d;
+                sR[m].y = v.y;
             }
             cur_prof = item.prof;
         }
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
                     S2 = zsum_small_f(phi, Fc, at, sT, M);
                     ++n_small;
                 } else if (aphi <= phi_direct) {
-                    S2 = zsum_direct_f(phi, Fc, at, sT, sD, M);
+                    S2 = zsum_direct_f(phi, Fc, at, sR, M);
                     ++n_direct;
                 } else {
                     S2 = zsum_tele_f(phi, Fc, at, sT, sE, M);
@@ -446,9 +449,7 @@ __global__ void __launch_bounds__(256) k_finish(FinishParams fp)
 // ---------------------------------------------------------------------------
 size_t quad_smem_bytes(int precision, int n_steps, int G)
 {
-    if (precision == 0)
-        return (size_t)n_steps * (2 * sizeof(float4) + sizeof(float2)) + ((n_steps & 1) ? sizeof(float2) : 0) +
-               (size_t)G * sizeof(RowF);
+    if (precision == 0) return (size_t)n_steps * 3 * sizeof(float4) + (size_t)G * sizeof(RowF);
     return (size_t)n_steps * 2 * sizeof(double2) + (size_t)G * sizeof(RowD);
 }
 

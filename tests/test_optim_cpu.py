@@ -1,0 +1,69 @@
+"""Host logic of the launch-power optimiser, with a fake engine on the CPU:
+projection onto the dBm bounds, Armijo backtracking, checkpoint and resume."""
+import numpy as np
+import pytest
+
+
+class FakeEngine:
+    """T(P) = sum_j w_j log2(1 + P_j / (a_j + b_j P_j^3)): per-channel optimum inside or
+    outside the bounds depending on (a, b)."""
+    device = 0
+
+    def __init__(self, n=7, seed=0):
+        import torch
+        self.torch_device = torch.device("cpu")
+        rng = np.random.default_rng(seed)
+        self.a = rng.uniform(1e-6, 1e-5, n)
+        self.b = rng.uniform(5.0, 50.0, n)
+        self.b[0] = 1e-3      # optimum far above the upper bound -> pinned at +5 dBm
+        self.w = rng.uniform(0.5, 2.0, n)
+        self.calls = {"grad": 0, "snr": 0}
+
+    def _T(self, P):
+        return float(np.sum(self.w * np.log2(1 + P / (self.a + self.b * P ** 3))))
+
+    def snr(self, wl, P, precision=0):
+        self.calls["snr"] += 1
+        return {"T": self._T(P.numpy())}
+
+    def grad(self, wl, P):
+        import torch
+        self.calls["grad"] += 1
+        P = P.numpy()
+        N = self.a + self.b * P ** 3
+        s = P / N
+        dsdP = (N - P * 3 * self.b * P ** 2) / N ** 2
+        g = self.w / (np.log(2) * (1 + s)) * dsdP
+        return {"T": self._T(P), "dT_dP": torch.tensor(g)}
+
+
+class _WL:
+    def __init__(self, n):
+        self.P_W = np.full(n, 1e-3)
+
+
+def test_ascent_increases_T_and_respects_bounds():
+    from paper_2401_18022_gb300 import optim
+    eng = FakeEngine()
+    res = optim.ascent(eng, _WL(7), iters=40)
+    Ts = [h["T"] for h in res["history"]]
+    assert all(b >= a - 1e-12 for a, b in zip(Ts, Ts[1:]))
+    assert Ts[-1] > res["history"][0]["T_before"]
+    assert np.all(res["x_dbm"] <= 5.0 + 1e-12) and np.all(res["x_dbm"] >= -5.0 - 1e-12)
+    assert res["x_dbm"][0] == pytest.approx(5.0)
+    # projected gradient (components not pushing into an active bound) has shrunk
+    g = eng.grad(None, __import__("torch").tensor(res["P_W"]))["dT_dP"].numpy()
+    gx = g * res["P_W"] * np.log(10) / 10
+    x = res["x_dbm"]
+    free = ~(((x >= 5.0) & (gx > 0)) | ((x <= -5.0) & (gx < 0)))
+    assert np.max(np.abs(gx[free])) < 0.05 * res["history"][0]["grad_inf_per_dB"]
+
+
+def test_ascent_checkpoint_resume_matches_uninterrupted(tmp_path):
+    from paper_2401_18022_gb300 import optim
+    ck = str(tmp_path / "state.json")
+    full = optim.ascent(FakeEngine(), _WL(7), iters=12)
+    optim.ascent(FakeEngine(), _WL(7), iters=6, ckpt=ck, ckpt_every=3)
+    resumed = optim.ascent(FakeEngine(), _WL(7), iters=12, ckpt=ck, resume=True)
+    np.testing.assert_allclose(resumed["x_dbm"], full["x_dbm"], rtol=0, atol=1e-12)
+    assert len(resumed["history"]) == 12
