@@ -39,13 +39,11 @@ def _peaks():
 
 
 def _workload(G: int, rank: int = 0):
-    from paper_2401_18022_gb300 import workloads as W
+    """The 589-ch system; under torchrun each rank evaluates its own
+    independent launch-power profile (weak scaling)."""
+    from paper_2401_18022_gb300 import dist as D, workloads as W
     wl = W.uwb(G=G)
-    if rank > 0:
-        # weak scaling: each rank evaluates its own independent launch-power profile
-        rng = np.random.default_rng(100 + rank)
-        wl = wl.with_(P_W=W.dbm_to_w(1.0 + rng.uniform(-0.5, 0.5, wl.n_ch)))
-    return wl
+    return wl.with_(P_W=D.rank_powers(wl, rank))
 
 
 class Clocks:
@@ -211,9 +209,8 @@ def run_gpu(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_total = sum(step_ms) / 1e3
     if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
+        from paper_2401_18022_gb300 import dist as D
+        t_total = D.max_over_ranks(t_total)
 
     # grid points of the method's Riemann grid (mirror cells counted, as in the oracle)
     from paper_2401_18022_gb300 import workloads as W
@@ -342,6 +339,46 @@ def _fp64_path(eng, wl, P, args):
             "max_eta_err_dB_fp32_vs_fp64": err_db, "note": "extrapolated linearly (equal work per CUT)"}
 
 
+def run_batched(args) -> int:
+    """512 launch-power profiles over the 589/295/147-channel plans (G = 64)
+    in one persistent, graph-replayed launch with autotuned tiles."""
+    import torch
+    from paper_2401_18022_gb300 import api, autotune, workloads as W
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    eng = api.Engine(local)
+    bw = W.batched(n_prof=512, G=64)
+    tile = autotune.tune(eng, bw)
+    dev = torch.device("cuda", local)
+    P = torch.tensor(np.concatenate(bw.P_W), dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        eng.eta_batched(bw, P)
+    torch.cuda.synchronize(dev)
+    ms, replays = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        eng.eta_batched(bw, P)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+        replays.append(eng.last_graph_replay())
+    n_grid = sum(_unfolded_points(bw.plans[k]) for k in bw.plan_of_profile)
+    t = sum(ms) / 1e3
+    line = {"metric": METRIC, "value": n_grid * args.steps / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched-512-profiles-589/295/147ch-G64-N113-sci_xci",
+                       "grid_points_per_step": n_grid, "tile": {k: tile[k] for k in ("points_per_item", "threads")},
+                       "graph_replayed_steps": int(sum(replays)), "l2": "flushed between timed iterations"},
+            "gpu_launches": 3 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def profile_case(kind: str) -> int:
     """One launch for kernel captures: the 589-ch plan at the bench's G = 256
     for 16 CUTs spread over the band (1.2e9 points, ~1.2e3 work tiles, about
@@ -373,6 +410,8 @@ def main():
     ap.add_argument("--mode", default="grad", choices=["snr", "grad"],
                     help="grad: SNR + dT/dP (all hot-path steps); snr: forward only")
     ap.add_argument("--quick", action="store_true", help="skip e2e, FP64 and CPU legs")
+    ap.add_argument("--workload", default="uwb", choices=["uwb", "batched"],
+                    help="uwb: the 589-ch system (default); batched: 512 profiles over 3 plans")
     ap.add_argument("--profile-case", default=None, choices=["quad", "quad64", "adjoint"],
                     help="run one small launch of a kernel (for ncu captures) and exit")
     args = ap.parse_args()
@@ -380,6 +419,8 @@ def main():
         return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_gpu(args)
 
 
