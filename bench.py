@@ -219,18 +219,20 @@ def run_gpu(args):
     n_grid = _unfolded_points(wl)
     value = world * n_grid * args.steps / t_total
 
-    # roofline of the dominant kernel (k_quad_f32).  Algorithmic SFU work per
-    # point-step by the z-sum form the point took: small-phase expansion 1
-    # (the exp of Eq. pk), direct 3 (sin, cos, exp), telescoped 3 (sin, cos of
-    # the edge phasor, exp); the path counts come from the kernel itself.
+    # roofline of the dominant kernel.  Algorithmic SFU work per point-step by
+    # the z-sum form the point took: direct 3 (sin, cos, exp), telescoped 3
+    # (sin, cos of the edge phasor, exp), small-phase 0 (its moments are
+    # contracted once per piece and channel: ~nc x 112 exps per 65,536 points).
+    # The fused adjoint repeats the direct/telescoped work in pass 2 and
+    # evaluates the small-phase step terms there (1 exp per step).
     quad_ms = float(np.mean(quad_ms))
     if use_grad:
         _fwd_point_steps(eng, wl, P)
     paths = eng.last_path_counts()
     n_steps = wl.n_edges - 1
-    sfu_ops = n_steps * (1 * paths["small"] + 3 * paths["direct"] + 3 * paths["telescoped"])
+    sfu_ops = n_steps * 3 * (paths["direct"] + paths["telescoped"])
     if use_grad:
-        sfu_ops *= 2          # the fused adjoint evaluates every z-sum twice (S, then dS/d ln p)
+        sfu_ops = 2 * sfu_ops + n_steps * paths["small"]
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sfu_peak = N_SMS * SFU_PER_CLK_PER_SM * sm_max * 1e6 / 1e12       # Tops/s

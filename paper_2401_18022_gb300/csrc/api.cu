@@ -58,7 +58,7 @@ struct isrs_handle_s {
     int device = 0;
     int num_sms = 1;
     std::string err;
-    DevBuf paths;
+    DevBuf paths, kapL;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
         o_pase, o_T, gA, gK, gPd, ybar, dTdP;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
@@ -579,6 +579,7 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     if ((s = ensure(h, h->step_d, sizeof(double2) * (size_t)g->n_prof * M)) != ISRS_OK) return s;
     if ((s = ensure(h, h->step_f, sizeof(float2) * (size_t)g->n_prof * M)) != ISRS_OK) return s;
     if ((s = ensure(h, h->ptot, sizeof(double) * g->n_prof)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->kapL, sizeof(double) * g->n_prof)) != ISRS_OK) return s;
     if ((s = ensure(h, h->partial, sizeof(double) * std::max(1, g->n_items))) != ISRS_OK) return s;
     if ((s = ensure(h, h->counter, sizeof(int) * 4)) != ISRS_OK) return s;
 
@@ -602,6 +603,7 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     pp.step_f = (float2 *)h->step_f.p;
     pp.lnrho_L = (double *)h->lnrho_L.p;
     pp.ptot = (double *)h->ptot.p;
+    pp.kap_L = (double *)h->kapL.p;
     CK(launch_prep(pp, g->n_prof, st));
 
     QuadParams qp;
@@ -629,6 +631,7 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     qp.zs_b = (const float4 *)g->zs_b.p;
     qp.zs_d = (const double2 *)g->zs_d.p;
     qp.dz_max = g->dz_max;
+    qp.kap_L = (const double *)h->kapL.p;
     qp.L = (float)fb->L_km;
     qp.partial = (double *)h->partial.p;
     qp.counter = (int *)h->counter.p;
@@ -759,7 +762,7 @@ isrs_status set_device(isrs_handle h)
 std::vector<void *> workspace_ptrs(isrs_handle h)
 {
     return {h->P.p, h->pd_d.p, h->pd_f.p, h->lnrho_L.p, h->step_d.p, h->step_f.p, h->ptot.p, h->partial.p,
-            h->counter.p, h->paths.p, h->o_sigma.p, h->o_pnli.p, h->o_eta.p, h->o_snr.p, h->o_pase.p, h->o_T.p};
+            h->counter.p, h->paths.p, h->kapL.p, h->o_sigma.p, h->o_pnli.p, h->o_eta.p, h->o_snr.p, h->o_pase.p, h->o_T.p};
 }
 
 isrs_status run_batched_graph(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
@@ -863,6 +866,7 @@ isrs_status isrs_destroy(isrs_handle h)
                       &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP};
     for (DevBuf *b : bufs) release(*b);
     release(h->paths);
+    release(h->kapL);
     for (int w = 0; w < 2; ++w)
         for (int k = 0; k < 2; ++k)
             if (h->ev[w][k]) cudaEventDestroy(h->ev[w][k]);

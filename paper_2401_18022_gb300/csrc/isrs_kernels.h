@@ -20,6 +20,7 @@ struct PrepParams {
     float2 *step_f;
     double *lnrho_L;
     double *ptot;
+    double *kap_L;              // kappa(L) per profile (the largest ISRS exponent slope)
 };
 
 struct FinishParams {

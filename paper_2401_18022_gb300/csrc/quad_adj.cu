@@ -105,11 +105,19 @@ __device__ __forceinline__ void zsum_tele_c(float phi, float Fc, float at, const
 
 // ---------------------------------------------------------------------------
 // k_quad_adj<K>: fused forward + adjoint, persistent over work tiles of one
-// profile.  Lane l owns steps [K l, K l + K) in pass 2.
+// profile.  Pass 1: lane = grid point.  Pass 2: lane l owns steps
+// [K l, K l + K); the warp walks its 32 points, whose state pass 1 staged in
+// shared memory (two broadcast 128-bit loads per point).  The owned step
+// tables and the lane buckets live in registers only during pass 2 (a
+// lane-contiguous shared copy of the tables; FP32 shared bucket accumulators
+// folded into FP64 every 8 batches), so pass 1 runs at forward-like register
+// pressure.
 // ---------------------------------------------------------------------------
 #ifndef ISRS_ADJ_MIN_BLOCKS
 #define ISRS_ADJ_MIN_BLOCKS 2   // resident blocks per SM the register budget is sized for
 #endif
+
+constexpr int kOwnFields = 8;   // A2d, A2, K2, z, c, dz, edge hi, edge lo
 
 template <int K>
 __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams ap)
@@ -121,11 +129,15 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     float4 *sT = smem_f4;                                     // {A2 + log2 dz, K2, z, z^2 + dz^2/12}
     float4 *sE = sT + M;                                      // {edge/2pi hi, lo, A2, K2}
     float4 *sR = sE + M;                                      // {A2 + log2 dz, K2, z, dz}
-    RowF *rows = reinterpret_cast<RowF *>(sR + M);
-    // per-warp FP64 step buckets, lane-contiguous: [warp][k][lane] for step lane*K + k
-    double2 *sB = reinterpret_cast<double2 *>(rows + G);
+    RowF *rows = reinterpret_cast<RowF *>(sR + M);            // [G]
+    float4 *sPs = reinterpret_cast<float4 *>(rows + G);       // [nw][32][2] staged point states
+    double2 *sB = reinterpret_cast<double2 *>(sPs + nw * 64); // [nw][K][32] FP64 step buckets
+    float2 *sF = reinterpret_cast<float2 *>(sB + nw * K * 32);    // [nw][K][32] FP32 step buckets
+    float *sO = reinterpret_cast<float *>(sF + nw * K * 32);      // [kOwnFields][K][32] owned tables
     __shared__ PieceConst<float> kc;
+    __shared__ ChebTab ct;
     __shared__ float sVc[kMaxCand];
+    __shared__ float sE0[2][32];                              // first edge of each lane's block
     __shared__ double scratch[32];
     __shared__ int s_item;
 
@@ -137,7 +149,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
         sE[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
         sR[m] = make_float4(0.0f, 0.0f, za.x, za.w);
     }
-    for (int t = threadIdx.x; t < nw * K * 32; t += blockDim.x) sB[t] = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < nw * K * 32; t += blockDim.x) {
+        sB[t] = make_double2(0.0, 0.0);
+        sF[t] = make_float2(0.0f, 0.0f);
+    }
     if (threadIdx.x < kMaxCand) sVc[threadIdx.x] = 0.0f;
 
     const float c3 = (float)(kPi * qp.beta3);
@@ -149,13 +164,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
     const int m0 = lane * K;
-
-    // owned step tables (registers), loaded when the profile is staged
-    float oA2d[K], oA2[K], oK2[K], oz[K], oc[K], odz[K], oeh[K], oel[K];
-    float e0h = 0.0f, e0l = 0.0f;
-    float R[K], Rp[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) { R[k] = 0.0f; Rp[k] = 0.0f; }
+    float4 *myPs = sPs + warp * 64;
+    float2 *myF = sF + warp * K * 32;
+    double2 *myB = sB + warp * K * 32;
     int cur_prof = -1;
 
     for (;;) {
@@ -179,17 +190,22 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 sR[m].y = v.y;
             }
             __syncthreads();
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const int m = m0 + k;
+            // lane-contiguous copy of every lane's owned step tables
+            for (int t = threadIdx.x; t < K * 32; t += blockDim.x) {
+                const int k = t >> 5, l = t & 31, m = l * K + k;
                 const bool ok = m < M;
                 const float4 a = ok ? sT[m] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float4 e = ok ? sE[m] : make_float4(0.f, 0.f, 0.f, 0.f);
-                oA2d[k] = a.x; oK2[k] = a.y; oz[k] = a.z; oc[k] = a.w;
-                oeh[k] = e.x; oel[k] = e.y; oA2[k] = e.z;
-                odz[k] = ok ? sR[m].w : 0.0f;
+                const float dz = ok ? sR[m].w : 0.0f;
+                const float vals[kOwnFields] = {a.x, e.z, a.y, a.z, a.w, dz, e.x, e.y};
+#pragma unroll
+                for (int f = 0; f < kOwnFields; ++f) sO[(f * K + k) * 32 + l] = vals[f];
             }
-            if (m0 > 0 && m0 < M) { e0h = sE[m0 - 1].x; e0l = sE[m0 - 1].y; }
+            if (threadIdx.x < 32) {
+                const int l = threadIdx.x, mm = l * K;
+                sE0[0][l] = (mm > 0 && mm < M) ? sE[mm - 1].x : 0.0f;
+                sE0[1][l] = (mm > 0 && mm < M) ? sE[mm - 1].y : 0.0f;
+            }
             cur_prof = item.prof;
         }
         double acc = 0.0;
@@ -198,6 +214,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
+            cheb_setup(qp, pc, item.prof, sT, M, kc, ct);
+            __syncthreads();
+            const bool cheb = ct.ok != 0;
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2, mult = kc.mult;
             const float three_fi2 = 3.0f * fi * fi;
             float sum = 0.0f, comp = 0.0f;
@@ -234,7 +253,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                             float S2;
                             if (aphi <= phi_small) {
                                 path = kPathSmall;
-                                zsum_small_m(phi, Fc, at, sT, M, q0, q1, q2);
+                                if (cheb) cheb_moments(ct, ci, u, q0, q1, q2);
+                                else zsum_small_m(phi, Fc, at, sT, M, q0, q1, q2);
                                 S2 = fmaf(-phi * phi, fmaf(q0, q2, -q1 * q1), q0 * q0);
                             } else if (aphi <= phi_direct) {
                                 path = kPathDirect;
@@ -259,18 +279,34 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         }
                     }
                 }
+                myPs[2 * lane] = make_float4(cpt, phi, Fc, at);
+                myPs[2 * lane + 1] = make_float4(q0, q1, q2, __int_as_float(path));
                 __syncwarp();
                 // ---- pass 2: the warp's 32 points, each lane on its own steps
+                float oA2d[K], oA2[K], oK2[K], oz[K], oc[K], odz[K], oeh[K], oel[K];
+                float R[K], Rp[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    oA2d[k] = sO[(0 * K + k) * 32 + lane];
+                    oA2[k] = sO[(1 * K + k) * 32 + lane];
+                    oK2[k] = sO[(2 * K + k) * 32 + lane];
+                    oz[k] = sO[(3 * K + k) * 32 + lane];
+                    oc[k] = sO[(4 * K + k) * 32 + lane];
+                    odz[k] = sO[(5 * K + k) * 32 + lane];
+                    oeh[k] = sO[(6 * K + k) * 32 + lane];
+                    oel[k] = sO[(7 * K + k) * 32 + lane];
+                    R[k] = 0.0f;
+                    Rp[k] = 0.0f;
+                }
+                const float e0h = sE0[0][lane], e0l = sE0[1][lane];
                 for (int p = 0; p < 32; ++p) {
-                    const float cp = __shfl_sync(kFull, cpt, p);
+                    const float4 st0 = myPs[2 * p];
+                    const float cp = st0.x;
                     if (cp == 0.0f) continue;
-                    const float ph = __shfl_sync(kFull, phi, p);
-                    const float fc = __shfl_sync(kFull, Fc, p);
-                    const float a_t = __shfl_sync(kFull, at, p);
-                    const float p0 = __shfl_sync(kFull, q0, p);
-                    const float p1 = __shfl_sync(kFull, q1, p);
-                    const float p2 = __shfl_sync(kFull, q2, p);
-                    const int pth = __shfl_sync(kFull, path, p);
+                    const float4 st1 = myPs[2 * p + 1];
+                    const float ph = st0.y, fc = st0.z, a_t = st0.w;
+                    const float p0 = st1.x, p1 = st1.y, p2 = st1.z;
+                    const int pth = __float_as_int(st1.w);
                     const float cF = cp * fc;
                     if (pth == kPathSmall) {
                         // d|S|^2/d ln p_m = w_m (2 M0 - phi^2 (M2 + M0 c_m - 2 M1 z_m))
@@ -326,26 +362,33 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         }
                     }
                 }
-                // FP32 lane buckets are moved to the warp's FP64 buckets every 8 batches
+                // lane buckets -> FP32 shared accumulators; folded to FP64 every 8 batches
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    float2 &b = myF[k * 32 + lane];
+                    b.x += R[k];
+                    b.y += Rp[k];
+                }
                 if (++batches == 8) {
                     batches = 0;
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        double2 &b = sB[(warp * K + k) * 32 + lane];
-                        b.x += (double)R[k];
-                        b.y += (double)Rp[k];
-                        R[k] = 0.0f;
-                        Rp[k] = 0.0f;
+                        float2 &b = myF[k * 32 + lane];
+                        double2 &d = myB[k * 32 + lane];
+                        d.x += (double)b.x;
+                        d.y += (double)b.y;
+                        b = make_float2(0.0f, 0.0f);
                     }
                 }
+                __syncwarp();          // the next batch overwrites the staged states
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                double2 &b = sB[(warp * K + k) * 32 + lane];
-                b.x += (double)R[k];
-                b.y += (double)Rp[k];
-                R[k] = 0.0f;
-                Rp[k] = 0.0f;
+                float2 &b = myF[k * 32 + lane];
+                double2 &d = myB[k * 32 + lane];
+                d.x += (double)b.x;
+                d.y += (double)b.y;
+                b = make_float2(0.0f, 0.0f);
             }
             // piece totals: the forward sum and the PSD buckets V_ij
             const double ptot = block_sum_d((double)sum - (double)comp, scratch);
@@ -518,9 +561,9 @@ __global__ void __launch_bounds__(256) k_chain(ChainParams cp)
 // ---------------------------------------------------------------------------
 size_t adjoint_smem_bytes(int n_steps, int G, int block)
 {
-    const int K = (n_steps + 31) / 32;
-    return (size_t)n_steps * 3 * sizeof(float4) + (size_t)G * sizeof(RowF) +
-           (size_t)(block / 32) * K * 32 * sizeof(double2);
+    const int K = (n_steps + 31) / 32, nw = block / 32;
+    return (size_t)n_steps * 3 * sizeof(float4) + (size_t)G * sizeof(RowF) + (size_t)nw * 64 * sizeof(float4) +
+           (size_t)nw * K * 32 * (sizeof(double2) + sizeof(float2)) + (size_t)kOwnFields * K * 32 * sizeof(float);
 }
 
 template <int K>

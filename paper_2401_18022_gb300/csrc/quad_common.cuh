@@ -138,4 +138,81 @@ __device__ __forceinline__ void phasor_rev_ff(float phi, float hi, float lo, flo
 }
 
 
+// ---------------------------------------------------------------------------
+// Chebyshev contraction of the small-phase moments (App. A, Eq. slow_vary to
+// second order in phi).  Inside candidate channel c, F_c - f_ref = F0 + h x
+// with x in [-1, 1], and the per-step weight factorises:
+//   w_m = 2^{A2d_m + K2_m F_c - at z_m} = 2^{A2d_m - at z_m + K2_m F0} e^{a_m x},
+//   a_m = K2_m h ln 2,  e^{a x} = I0(a) + 2 sum_{n>=1} In(a) Tn(x)
+// so M_k(x) = sum_n C_kn Tn(x), n <= 3, with C_kn summed over the steps once
+// per piece and candidate.  Truncation ~ (a/2)^4/12 < 4e-8 for |a| <= 0.05,
+// which holds when kappa(L) h <= 0.05; otherwise the per-step sum is used.
+// ---------------------------------------------------------------------------
+constexpr float kChebMaxA = 0.05f;
+
+struct ChebTab {
+    float c[kMaxCand][12];      // [candidate][k * 4 + n], k: g = 1, z, z^2 + dz^2/12
+    float mid[kMaxCand];        // channel centre relative to the CUT
+    float invh[kMaxCand];       // 1 / (B_c / 2)
+    int ok;
+};
+
+// Called by every thread of the block after piece_consts; the caller syncs.
+__device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece &pc, int prof,
+                                           const float4 *sT, int M, const PieceConst<float> &k, ChebTab &ct)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int coff = qp.plan_ch_off[pc.plan];
+    const double kapL = qp.kap_L ? qp.kap_L[prof] : 1e30;
+    double hmax = 0.0;
+    for (int c = 0; c < k.nc; ++c) hmax = fmax(hmax, 0.5 * qp.ch_B[coff + pc.c_lo + c]);
+    const bool ok = kapL * hmax <= (double)kChebMaxA;
+    if (threadIdx.x == 0) ct.ok = ok ? 1 : 0;
+    if (!ok) return;
+    for (int c = warp; c < k.nc; c += nw) {
+        const double F0 = qp.ch_frel[coff + pc.c_lo + c];
+        const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
+        const double at = (double)(k.at_ab + k.hat[c]);
+        for (int kk = 0; kk < 3; ++kk) {          // one moment at a time keeps registers low
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (int m = lane; m < M; m += 32) {
+                const float4 a = sT[m];
+                const double g = kk == 0 ? 1.0 : (kk == 1 ? (double)a.z : (double)a.w);
+                const double base = g * exp2((double)a.x - at * (double)a.z + (double)a.y * F0);
+                const double t = 0.5 * (double)a.y * h * 0.69314718055994530942, t2 = t * t;
+                s0 += base * (1.0 + t2 * (1.0 + t2 * (0.25 + t2 / 36.0)));                   // I0
+                s1 += base * (2.0 * t * (1.0 + t2 * (0.5 + t2 / 12.0)));                     // 2 I1
+                s2 += base * (2.0 * t2 * (0.5 + t2 * (1.0 / 6.0 + t2 / 48.0)));              // 2 I2
+                s3 += base * (2.0 * t2 * t * (1.0 / 6.0 + t2 * (1.0 / 24.0 + t2 / 240.0)));  // 2 I3
+            }
+            s0 = warp_sum_d(s0);
+            s1 = warp_sum_d(s1);
+            s2 = warp_sum_d(s2);
+            s3 = warp_sum_d(s3);
+            if (lane == 0) {
+                ct.c[c][kk * 4 + 0] = (float)s0;
+                ct.c[c][kk * 4 + 1] = (float)s1;
+                ct.c[c][kk * 4 + 2] = (float)s2;
+                ct.c[c][kk * 4 + 3] = (float)s3;
+            }
+        }
+        if (lane == 0) {
+            ct.mid[c] = 0.5f * (k.lo[c] + k.hi[c]);
+            ct.invh[c] = (float)(1.0 / h);
+        }
+    }
+}
+
+// Small-phase |S|^2 of a point in candidate ci from the contracted moments.
+__device__ __forceinline__ void cheb_moments(const ChebTab &ct, int ci, float u, float &M0, float &M1, float &M2)
+{
+    const float x = (u - ct.mid[ci]) * ct.invh[ci];
+    const float T2 = fmaf(2.0f * x, x, -1.0f);
+    const float T3 = fmaf(2.0f * x, T2, -x);
+    const float *c = ct.c[ci];
+    M0 = fmaf(c[3], T3, fmaf(c[2], T2, fmaf(c[1], x, c[0])));
+    M1 = fmaf(c[7], T3, fmaf(c[6], T2, fmaf(c[5], x, c[4])));
+    M2 = fmaf(c[11], T3, fmaf(c[10], T2, fmaf(c[9], x, c[8])));
+}
+
 }  // namespace isrs

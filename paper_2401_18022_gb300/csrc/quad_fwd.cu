@@ -95,7 +95,10 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams pp)
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         pp.lnrho_L[poff + c] = -pp.ch_alpha[coff + c] * pp.L + lnPtot - s_lnN_L - s_kap_L * fr[c];
     }
-    if (threadIdx.x == 0) pp.ptot[p] = Ptot;
+    if (threadIdx.x == 0) {
+        pp.ptot[p] = Ptot;
+        if (pp.kap_L) pp.kap_L[p] = s_kap_L;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -187,7 +190,7 @@ __device__ __forceinline__ float zsum_tele_f(float phi, float Fc, float at, cons
 // ---------------------------------------------------------------------------
 // k_quad_f32: persistent FP32 quadrature.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
+__global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
 {
     extern __shared__ float4 smem_f4[];
     const int M = qp.n_steps, G = qp.G;
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
     float4 *sR = sE + M;                               // [M] {A2 + log2 dz, K2, z, dz}
     RowF *rows = reinterpret_cast<RowF *>(sR + M);     // [G]
     __shared__ PieceConst<float> kc;
+    __shared__ ChebTab ct;
     __shared__ double scratch[32];
     __shared__ int s_item;
 
@@ -244,8 +248,11 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
+            cheb_setup(qp, pc, item.prof, sT, M, kc, ct);
+            __syncthreads();
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2;
             const float three_fi2 = 3.0f * fi * fi;
+            const bool cheb = ct.ok != 0;
             float sum = 0.0f, comp = 0.0f;
             const int npts = G * G;
             for (int q = threadIdx.x; q < npts; q += blockDim.x) {
@@ -274,7 +281,13 @@ __global__ void __launch_bounds__(256) k_quad_f32(QuadParams qp)
                 const float aphi = fabsf(phi);
                 float S2;
                 if (aphi <= phi_small) {
-                    S2 = zsum_small_f(phi, Fc, at, sT, M);
+                    if (cheb) {
+                        float M0, M1, M2;
+                        cheb_moments(ct, ci, u, M0, M1, M2);
+                        S2 = fmaf(-phi * phi, fmaf(M0, M2, -M1 * M1), M0 * M0);
+                    } else {
+                        S2 = zsum_small_f(phi, Fc, at, sT, M);
+                    }
                     ++n_small;
                 } else if (aphi <= phi_direct) {
                     S2 = zsum_direct_f(phi, Fc, at, sR, M);

@@ -46,3 +46,39 @@ def test_sinc_polynomial_on_direct_range():
     poly = sum(ck * x ** (2 * k) for k, ck in enumerate(c))
     ref = np.sinc(x / np.pi)
     assert np.max(np.abs(poly - ref)) < 4e-8
+
+
+def _bessel_i(n, a):
+    """Modified Bessel I_n(a) by its power series (|a| small)."""
+    from math import factorial
+    return sum((a / 2) ** (2 * k + n) / (factorial(k) * factorial(k + n)) for k in range(8))
+
+
+def test_chebyshev_contraction_of_small_phase_moments(orc):
+    """For F_c = F0 + h x in one channel, the moments M_k = sum_m w_m(F_c) g_k(m)
+    with w_m = 2^(A_m + K_m F_c) equal sum_n C_kn T_n(x), n <= 3, where
+    C_kn = sum_m 2^(A_m + K_m F0) g_k(m) b_n(K_m h ln 2), b_0 = I_0, b_n = 2 I_n
+    (the Chebyshev expansion of e^{a x}); truncation about (a/2)^4/12, below
+    4e-8 for |a| <= 0.05 (the kernel's bound)."""
+    import math
+    ze = orc.zgrid(80.0, 0.0571, 113)
+    zm, dz = 0.5 * (ze[1:] + ze[:-1]), np.diff(ze)
+    rng = np.random.default_rng(4)
+    kappa = np.linspace(0.0, 0.36, len(zm))              # ISRS exponent per THz along z
+    K = -kappa / math.log(2.0)                            # log2 slope per THz
+    A = np.log2(dz) - 0.05 * zm / math.log(2.0)
+    g = [np.ones_like(zm), zm, zm ** 2 + dz ** 2 / 12]
+    for h in (0.048, 0.19):                               # a_max = 0.017 and 0.068
+        F0 = rng.uniform(-30, 30)
+        a = K * h * math.log(2.0)
+        b = np.array([[_bessel_i(n, am) * (1 if n == 0 else 2) for n in range(4)] for am in a])
+        base = 2.0 ** (A + K * F0)
+        C = np.array([[np.sum(base * gk * b[:, n]) for n in range(4)] for gk in g])
+        for x in np.linspace(-1, 1, 21):
+            T = [1.0, x, 2 * x * x - 1, x * (4 * x * x - 3)]
+            w = 2.0 ** (A + K * (F0 + h * x))
+            for k in range(3):
+                exact = np.sum(w * g[k])
+                approx = sum(C[k, n] * T[n] for n in range(4))
+                amax = float(np.max(np.abs(a)))
+                assert abs(approx / exact - 1) < max(1e-12, (amax / 2) ** 4 / 6)
