@@ -74,6 +74,10 @@ typedef struct {
     double beta2, beta3, beta4;
     double Cr;
     double alpha_R_per_km;
+    int n_spans;                /* identical spans (0 or 1: one span); each amplifier
+                                 * restores the launch profile (Sec. IV), so span k adds
+                                 * the phase offset (k-1) L of Eq. new_gn_model and the
+                                 * ASE of n amplifiers adds up; at most 100 */
 } isrs_fibre;
 
 /* Channel plan (host pointers, n_ch entries each).  nf_dB and guard may be

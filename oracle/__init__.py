@@ -57,6 +57,8 @@ def _load():
         lib.orc_lnrho.argtypes = [ctypes.c_int, _D, _D, _D, _D] + [ctypes.c_double] * 5
         lib.orc_lnrho.restype = ctypes.c_double
         lib.orc_zsum.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, _D]
+        lib.orc_zsum_spans.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, _D]
         lib.orc_pieces_flat.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_int, _D]
         lib.orc_pieces_flat.restype = ctypes.c_int
         lib.orc_sigma.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _I, ctypes.c_double, _I,
@@ -128,6 +130,14 @@ def zsum(z_mid, dz, p, phi_: float) -> complex:
     return complex(out[0], out[1])
 
 
+def zsum_spans(z_mid, dz, p, phi_: float, L: float, n_spans: int) -> complex:
+    """Eq. new_gn_model: the z-sum over n identical spans with offsets (k-1) L."""
+    z_mid, dz, p = _f64(z_mid), _f64(dz), _f64(p)
+    out = np.zeros(2)
+    _load().orc_zsum_spans(len(z_mid), _dp(z_mid), _dp(dz), _dp(p), phi_, L, int(n_spans), _dp(out))
+    return complex(out[0], out[1])
+
+
 def pieces(f, B, cut: int, cell_set: int) -> np.ndarray:
     """Pieces of one CUT: rows (a, b, s1, s2, xlo, xhi, ylo, yhi)."""
     f, B = _f64(f), _f64(B)
@@ -142,9 +152,18 @@ def pieces(f, B, cut: int, cell_set: int) -> np.ndarray:
 # Workload-level evaluation
 # --------------------------------------------------------------------------
 def fibre_params(wl) -> np.ndarray:
-    """[L, f_ref, beta2, beta3, beta4, Cr, alpha_R] of a workload-like object."""
+    """[L, f_ref, beta2, beta3, beta4, Cr, alpha_R, n_spans] of a workload-like object."""
     b = beta_from_dispersion(C_NM_PER_PS / wl.f_ref_THz, wl.D_ref, wl.S_ref, wl.Sdot_ref)
-    return np.array([wl.L_km, wl.f_ref_THz, b[0], b[1], b[2], wl.Cr, wl.alpha_R_per_km])
+    return np.array([wl.L_km, wl.f_ref_THz, b[0], b[1], b[2], wl.Cr, wl.alpha_R_per_km,
+                     float(getattr(wl, "n_spans", 1))])
+
+
+def _fib8(fib, wl) -> np.ndarray:
+    """Accepts the 7-entry single-span form and appends the workload's span count."""
+    fib = _f64(fib)
+    if fib.shape[0] == 7:
+        fib = np.concatenate([fib, [float(getattr(wl, "n_spans", 1))]])
+    return np.ascontiguousarray(fib)
 
 
 C_NM_PER_PS = 299792.458
@@ -163,7 +182,7 @@ def sigma(wl, P=None, cuts: Optional[Sequence[int]] = None, threads: Optional[in
     f, B = _f64(wl.f_THz), _f64(wl.B_THz)
     P = _f64(wl.P_W if P is None else P)
     alpha = _f64(wl.alpha_per_km)
-    fib = _f64(fibre_params(wl) if fibre is None else fibre)
+    fib = _fib8(fibre_params(wl) if fibre is None else fibre, wl)
     quad = np.array([wl.G, wl.n_edges, wl.cell_set], dtype=np.int32)
     cuts = np.arange(len(f), dtype=np.int32) if cuts is None else np.asarray(cuts, dtype=np.int32)
     cuts = np.ascontiguousarray(cuts)
@@ -190,7 +209,7 @@ def time_sample(wl, cuts, stride: int, threads: Optional[int] = None) -> dict:
     import time
     f, B = _f64(wl.f_THz), _f64(wl.B_THz)
     P, alpha = _f64(wl.P_W), _f64(wl.alpha_per_km)
-    fib = _f64(fibre_params(wl))
+    fib = _fib8(fibre_params(wl), wl)
     quad = np.array([wl.G, wl.n_edges, wl.cell_set], dtype=np.int32)
     cuts = np.ascontiguousarray(np.asarray(cuts, dtype=np.int32))
     threads = threads or os.cpu_count() or 1
@@ -226,7 +245,7 @@ def snr_throughput(wl, eta_all: np.ndarray, P=None, fibre=None):
     """Per-channel SNR (Sec. IV, Eq. loss), ASE power, and throughput T [Tb/s]."""
     f, B, alpha = _f64(wl.f_THz), _f64(wl.B_THz), _f64(wl.alpha_per_km)
     P = _f64(wl.P_W if P is None else P)
-    fib = _f64(fibre_params(wl) if fibre is None else fibre)
+    fib = _fib8(fibre_params(wl) if fibre is None else fibre, wl)
     nf = _f64(wl.nf_dB)
     e = _f64(eta_all)
     g = getattr(wl, "guard", None)

@@ -200,6 +200,23 @@ void orc_zsum(int n_steps, const double *z_mid, const double *dz, const double *
     S[1] = im;
 }
 
+/* Eq. new_gn_model: the link's z-sum over n identical spans, span k adding */
+/* the phase offset L-tilde_k = (k - 1) L:                                 */
+/*   S = sum_k sum_m p_m dz_m sinc(phi dz_m / 2) e^{j phi ((k-1) L + z_m)}  */
+void orc_zsum_spans(int n_steps, const double *z_mid, const double *dz, const double *p, double phi,
+                    double L, int n_spans, double *S /* [2] */)
+{
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < n_spans; ++k)
+        for (int m = 0; m < n_steps; ++m) {
+            double a = p[m] * dz[m] * orc_sinc(0.5 * phi * dz[m]);
+            re += a * cos(phi * (k * L + z_mid[m]));
+            im += a * sin(phi * (k * L + z_mid[m]));
+        }
+    S[0] = re;
+    S[1] = im;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Pieces.  The plane of offsets (f1, f2) of CUT i is split into channel-  */
 /* pair cells (a,b): F_a = f_i + f1 in channel a, F_b = f_i + f2 in        */
@@ -270,6 +287,7 @@ int orc_pieces_flat(int n, const double *f, const double *B, int i, int cell_set
 typedef struct {
     orc_plan pl;
     double L, f_ref, b2, b3, b4, Cr, alpha_R, eps;
+    int n_spans;                        /* identical spans, launch profile restored per span */
     int G, n_steps, cell_set;
     double lnPtot;
     double *z_mid, *dz, *kappa, *lnN;   /* per step */
@@ -317,6 +335,7 @@ static double orc_piece_sum(const orc_problem *pr, int i, const orc_piece *q)
     if (u1_lo < pr->eps * u1_hi) u1_lo = pr->eps * u1_hi;
     double ds = (log(u1_hi) - log(u1_lo)) / G;
     double total = 0.0, comp = 0.0;
+    double *pv = (double *)malloc(sizeof(double) * (size_t)pr->n_steps);   /* p_m of a point */
     for (int r = 0; r < G; ++r) {
         double u1 = exp(log(u1_lo) + (r + 0.5) * ds);
         double ymin = q->ylo, ymax = q->yhi;
@@ -342,7 +361,6 @@ static double orc_piece_sum(const orc_problem *pr, int i, const orc_piece *q)
                 double W = (pl->P[ca] / pl->B[ca]) * (pl->P[cb] / pl->B[cb]) * (pl->P[cc] / pl->B[cc]);
                 if (W == 0.0) continue;
                 double phi = orc_phi(f1, f2, fi_off, pr->b2, pr->b3, pr->b4);
-                double Sre = 0.0, Sim = 0.0;
                 for (int m = 0; m < pr->n_steps; ++m) {
                     double z = pr->z_mid[m];
                     /* Eq. pk: p = sqrt(rho(F_a) rho(F_b) rho(F_c) / rho(f)) */
@@ -350,14 +368,12 @@ static double orc_piece_sum(const orc_problem *pr, int i, const orc_piece *q)
                     double lrb = orc_lnrho_c(pl, cb, z, Fb, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
                     double lrc = orc_lnrho_c(pl, cc, z, Fc, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
                     double lri = orc_lnrho_c(pl, i, z, fi, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
-                    double p = exp(0.5 * (lra + lrb + lrc - lri));
-                    /* Eq. slow_vary: p dz sinc(phi dz / 2) e^{j phi z_m} */
-                    double amp = p * pr->dz[m] * orc_sinc(0.5 * phi * pr->dz[m]);
-                    double sn, cs;
-                    sincos(phi * z, &sn, &cs);
-                    Sre += amp * cs;
-                    Sim += amp * sn;
+                    pv[m] = exp(0.5 * (lra + lrb + lrc - lri));
                 }
+                /* Eqs. slow_vary / new_gn_model: the z-sum, over every span */
+                double S[2];
+                orc_zsum_spans(pr->n_steps, pr->z_mid, pr->dz, pv, phi, pr->L, pr->n_spans, S);
+                double Sre = S[0], Sim = S[1];
                 val = W * (Sre * Sre + Sim * Sim);
             }
             /* Neumaier-compensated accumulation in FP64 */
@@ -367,6 +383,7 @@ static double orc_piece_sum(const orc_problem *pr, int i, const orc_piece *q)
             total = t;
         }
     }
+    free(pv);
     return total + comp;
 }
 
@@ -404,7 +421,7 @@ static void *orc_worker(void *arg)
  * integral of Eq. gain_fin at f = f_i without the 16/27 gamma^2 factor
  * [W^3 km^2 / THz].
  *
- * fibre[7] = {L_km, f_ref_THz, beta2, beta3, beta4, Cr, alpha_R}
+ * fibre[8] = {L_km, f_ref_THz, beta2, beta3, beta4, Cr, alpha_R, n_spans}
  * quad[3]  = {G, n_edges, cell_set}
  * piece_out (optional): per-piece sums, in the order of orc_pieces, for each
  * requested CUT one after another.
@@ -423,6 +440,7 @@ int orc_sigma_sampled(int n, const double *f, const double *B, const double *P, 
     pr.pl.n = n; pr.pl.f = f; pr.pl.B = B; pr.pl.P = P; pr.pl.alpha = alpha;
     pr.L = fibre[0]; pr.f_ref = fibre[1]; pr.b2 = fibre[2]; pr.b3 = fibre[3]; pr.b4 = fibre[4];
     pr.Cr = fibre[5]; pr.alpha_R = fibre[6];
+    pr.n_spans = fibre[7] >= 1.0 ? (int)fibre[7] : 1;
     pr.G = quad[0]; pr.cell_set = quad[2]; pr.eps = eps; pr.unit_integrand = unit_integrand;
     orc_problem_tables(&pr, quad[1]);
 
@@ -499,6 +517,7 @@ double orc_snr_throughput(int n, const double *f, const double *B, const double 
 {
     orc_plan pl = {n, f, B, P, alpha};
     double f_ref = fibre[1], Cr = fibre[5], alpha_R = fibre[6], L = fibre[0];
+    double n_spans = fibre[7] >= 1.0 ? fibre[7] : 1.0;
     double kappa = orc_kappa(&pl, L, Cr, alpha_R);
     double lnN = orc_lnN(&pl, kappa, f_ref), lnPtot = log(orc_ptot(&pl));
     double T = 0.0;
@@ -506,7 +525,8 @@ double orc_snr_throughput(int n, const double *f, const double *B, const double 
         double lr = orc_lnrho_c(&pl, i, L, f[i], lnPtot, lnN, kappa, f_ref);
         double gain = exp(-lr);
         double nf = pow(10.0, nf_dB[i] / 10.0);
-        double pa = nf * ORC_H_PLANCK * (f[i] * 1e12) * (gain - 1.0) * (B[i] * 1e12);
+        /* one amplifier per span, each restoring the launch power */
+        double pa = n_spans * nf * ORC_H_PLANCK * (f[i] * 1e12) * (gain - 1.0) * (B[i] * 1e12);
         if (pase) pase[i] = pa;
         if (P[i] <= 0.0 || (guard && guard[i])) { snr[i] = 0.0; continue; }
         double s = P[i] / (eta[i] * P[i] * P[i] * P[i] + pa);

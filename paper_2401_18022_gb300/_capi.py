@@ -19,7 +19,7 @@ PREC_FP32, PREC_FP64 = 0, 1
 class Fibre(ctypes.Structure):
     _fields_ = [("L_km", ctypes.c_double), ("f_ref_THz", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("beta3", ctypes.c_double), ("beta4", ctypes.c_double), ("Cr", ctypes.c_double),
-                ("alpha_R_per_km", ctypes.c_double)]
+                ("alpha_R_per_km", ctypes.c_double), ("n_spans", ctypes.c_int)]
 
 
 class Channels(ctypes.Structure):

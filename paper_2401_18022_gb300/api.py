@@ -84,7 +84,8 @@ class Engine:
 
     def fibre(self, wl) -> _capi.Fibre:
         b = self.beta(wl)
-        return _capi.Fibre(wl.L_km, wl.f_ref_THz, b[0], b[1], b[2], wl.Cr, wl.alpha_R_per_km)
+        return _capi.Fibre(wl.L_km, wl.f_ref_THz, b[0], b[1], b[2], wl.Cr, wl.alpha_R_per_km,
+                           int(getattr(wl, "n_spans", 1)))
 
     def channels(self, wl):
         keep = {k: np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for k, v in

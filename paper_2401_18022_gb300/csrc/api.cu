@@ -169,6 +169,7 @@ isrs_status check_fibre(isrs_handle h, const isrs_fibre *fb)
         return fail(h, ISRS_ERR_INVALID_ARG, "non-finite fibre parameter");
     if (!(fb->alpha_R_per_km >= 0.0) || !finite(fb->alpha_R_per_km))
         return fail(h, ISRS_ERR_INVALID_ARG, "alpha_R must be >= 0");
+    if (fb->n_spans < 0 || fb->n_spans > 100) return fail(h, ISRS_ERR_INVALID_ARG, "n_spans must be in [0, 100]");
     return ISRS_OK;
 }
 
@@ -633,6 +634,13 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     qp.dz_max = g->dz_max;
     qp.kap_L = (const double *)h->kapL.p;
     qp.L = (float)fb->L_km;
+    qp.n_spans = fb->n_spans > 1 ? fb->n_spans : 1;
+    {
+        const double lr = fb->L_km / (2.0 * 3.14159265358979323846);
+        qp.Lrev_hi = (float)lr;
+        qp.Lrev_lo = (float)(lr - (double)qp.Lrev_hi);
+        qp.Ld = fb->L_km;
+    }
     qp.partial = (double *)h->partial.p;
     qp.counter = (int *)h->counter.p;
     CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
@@ -700,6 +708,7 @@ isrs_status run_finish(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, 
     fp.lnrho_L = (const double *)h->lnrho_L.p;
     fp.f_ref = fb->f_ref_THz;
     fp.snr_trx_lin_inv = q->snr_trx_dB > 0.0 ? std::pow(10.0, -q->snr_trx_dB / 10.0) : 0.0;
+    fp.n_spans = fb->n_spans > 1 ? fb->n_spans : 1;
     fp.sigma = (double *)h->o_sigma.p;
     fp.pnli = (double *)h->o_pnli.p;
     fp.eta = (double *)h->o_eta.p;
@@ -768,8 +777,9 @@ std::vector<void *> workspace_ptrs(isrs_handle h)
 isrs_status run_batched_graph(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
 {
     isrs_status s;
-    Hasher hs;
-    hs.val(*fb);
+    Hasher hs;            // fields one by one: the struct has padding
+    hs.val(fb->L_km); hs.val(fb->f_ref_THz); hs.val(fb->beta2); hs.val(fb->beta3); hs.val(fb->beta4);
+    hs.val(fb->Cr); hs.val(fb->alpha_R_per_km); hs.val(fb->n_spans);
     hs.val(q->precision);
     hs.val(h->tile_threads);
     const uint64_t key = hs.v;
@@ -1125,6 +1135,7 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
     cp.alpha_R = fibre->alpha_R_per_km;
     cp.f_ref = fibre->f_ref_THz;
     cp.snr_trx_lin_inv = quad->snr_trx_dB > 0.0 ? std::pow(10.0, -quad->snr_trx_dB / 10.0) : 0.0;
+    cp.n_spans = fibre->n_spans > 1 ? fibre->n_spans : 1;
     cp.ybar = (double *)h->ybar.p;
     cp.aase = (double *)h->ybar.p + n;
     cp.Rb = (double2 *)h->gK.p;
@@ -1212,6 +1223,7 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     if ((s = check_quad(nullptr, quad)) != ISRS_OK) return s;
     if (!P_W || !eta || !is_device_ptr(P_W) || !is_device_ptr(eta) || (pnli && !is_device_ptr(pnli)))
         return ISRS_ERR_INVALID_ARG;
+    if (fibre->n_spans > 1) return ISRS_ERR_UNSUPPORTED;         // single span only
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ISRS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

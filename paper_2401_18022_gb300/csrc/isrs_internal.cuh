@@ -71,6 +71,9 @@ struct QuadParams {
     const double *kap_L;        // per profile: kappa(L) [1/THz]
     float dz_max;
     float L;                    // span length [km]
+    int n_spans;                // identical spans (array factor when > 1)
+    float Lrev_hi, Lrev_lo;     // L / 2pi as a float-float pair
+    double Ld;                  // L in double (FP64 path)
     // outputs / scheduling
     double *partial;            // one per item
     int *counter;               // persistent work counter (zeroed before launch)

@@ -35,6 +35,7 @@ struct FinishParams {
     const double *lnrho_L;
     double f_ref;
     double snr_trx_lin_inv;     // 10^(-SNR_TRX/10) or 0
+    double n_spans;             // ASE adds over the span amplifiers
     // outputs (indexed by slot; any may be null)
     double *sigma, *pnli, *eta, *snr, *pase;
     double *T;                  // per profile
@@ -60,7 +61,7 @@ struct ChainParams {
     const double *V;
     const int *item_slot, *slot_cut;
     int n_items, n_slots, n_ch, n_steps;
-    double L, Cr, alpha_R, f_ref, snr_trx_lin_inv;
+    double L, Cr, alpha_R, f_ref, snr_trx_lin_inv, n_spans;
     double *ybar;               // [n_slots] dT/dSigma_i
     double *aase;               // [n_slots] dT/dASE_i * dASE_i/d ln G_i
     double2 *Rb;                // [n_steps] sum_i ybar_i {R_im, R'_im}

@@ -265,7 +265,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                                 zsum_tele_c(phi, Fc, at, sT, sE, M, q0, q1);
                                 S2 = (q0 * q0 + q1 * q1) / (phi * phi);
                             }
-                            const float val = rw.w * W * S2;
+                            const float af = array_factor_f(phi, qp);
+                            const float val = rw.w * W * S2 * af;
                             const float y = val - comp;
                             const float t = sum + y;
                             comp = (t - sum) - y;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                             else if (ci == 2) v2 += val;
                             else if (ci == 3) v3 += val;
                             else atomicAdd(&sVc[ci], val);
-                            cpt = mult * rw.w * W;
+                            cpt = mult * rw.w * W * af;
                         }
                     }
                 }
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(256) k_ybar(ChainParams cp)
         const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
         const double dsdN = -snr * snr / P;
         const double nf = cp.ch_nf ? pow(10.0, cp.ch_nf[i] / 10.0) : 1.0;
-        const double hfb = nf * kHPlanck * ((cp.ch_frel[i] + cp.f_ref) * 1e12) * (B * 1e12);
+        const double hfb = cp.n_spans * nf * kHPlanck * ((cp.ch_frel[i] + cp.f_ref) * 1e12) * (B * 1e12);
         cp.ybar[s] = dTds * dsdN * (16.0 / 27.0) * g * g * B;
         cp.aase[s] = dTds * dsdN * (cp.pase[s] + hfb);    // dT/dASE * dASE/d ln G
     }

@@ -138,6 +138,41 @@ __device__ __forceinline__ void phasor_rev_ff(float phi, float hi, float lo, flo
 }
 
 
+// Phased-array factor of n identical spans (Eq. new_gn_model with
+// L-tilde_k = (k-1) L): |sum_{k<n} e^{j k phi L}|^2, by rotation from the
+// float-float phase phi L / 2pi.
+__device__ __forceinline__ float array_factor_f(float phi, const QuadParams &qp)
+{
+    if (qp.n_spans <= 1) return 1.0f;
+    float sn, cs;
+    phasor_rev_ff(phi, qp.Lrev_hi, qp.Lrev_lo, sn, cs);
+    float sr = 0.0f, si = 0.0f, zr = 1.0f, zi = 0.0f;
+    for (int k = 0; k < qp.n_spans; ++k) {
+        sr += zr;
+        si += zi;
+        const float t = fmaf(zr, cs, -zi * sn);
+        zi = fmaf(zr, sn, zi * cs);
+        zr = t;
+    }
+    return fmaf(sr, sr, si * si);
+}
+
+__device__ __forceinline__ double array_factor_d(double phi, const QuadParams &qp)
+{
+    if (qp.n_spans <= 1) return 1.0;
+    double sn, cs;
+    sincos(phi * qp.Ld, &sn, &cs);
+    double sr = 0.0, si = 0.0, zr = 1.0, zi = 0.0;
+    for (int k = 0; k < qp.n_spans; ++k) {
+        sr += zr;
+        si += zi;
+        const double t = zr * cs - zi * sn;
+        zi = zr * sn + zi * cs;
+        zr = t;
+    }
+    return sr * sr + si * si;
+}
+
 // ---------------------------------------------------------------------------
 // Chebyshev contraction of the small-phase moments (App. A, Eq. slow_vary to
 // second order in phi).  Inside candidate channel c, F_c - f_ref = F0 + h x

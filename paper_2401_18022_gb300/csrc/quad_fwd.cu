@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
                     ++n_tele;
                 }
                 // compensated accumulation over this thread's points
-                const float y = rw.w * W * S2 - comp;
+                const float y = rw.w * W * S2 * array_factor_f(phi, qp) - comp;
                 const float t = sum + y;
                 comp = (t - sum) - y;
                 sum = t;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(256) k_quad_f64(QuadParams qp)
                     Sr += amp * cs;
                     Si += amp * sn;
                 }
-                sum += rw.w * W * (Sr * Sr + Si * Si);
+                sum += rw.w * W * (Sr * Sr + Si * Si) * array_factor_d(phi, qp);
             }
             acc += kc.mult * sum;
             __syncthreads();
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) k_finish(FinishParams fp)
             const double nf = fp.ch_nf ? pow(10.0, fp.ch_nf[coff + i] / 10.0) : 1.0;
             const double f_abs = fp.ch_frel[coff + i] + fp.f_ref;
             const double gain = exp(-fp.lnrho_L[poff + i]);
-            const double pase = nf * 6.62607015e-34 * (f_abs * 1e12) * (gain - 1.0) * (B * 1e12);
+            const double pase = fp.n_spans * nf * 6.62607015e-34 * (f_abs * 1e12) * (gain - 1.0) * (B * 1e12);
             const bool off = !(P > 0.0) || (fp.guard && fp.guard[coff + i]);
             double snr = 0.0;
             if (!off) {

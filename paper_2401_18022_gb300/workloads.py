@@ -117,6 +117,7 @@ class Workload:
     cell_set: int = CELLS_SCI_XCI
     snr_trx_dB: float = 0.0         # <= 0: no transceiver noise
     guard: Optional[np.ndarray] = None
+    n_spans: int = 1                # identical spans, launch profile restored per span
 
     @property
     def n_ch(self) -> int:

@@ -156,3 +156,16 @@ def test_batched_matches_oracle(eng, orc):
         ref, _ = orc.eta(wl, orc.sigma(wl, P=bw.P_W[p]), P=bw.P_W[p])
         np.testing.assert_allclose(eta_b[off:off + wl.n_ch], ref, rtol=RTOL_F64)
         off += wl.n_ch
+
+
+@pytest.mark.parametrize("n_spans", [3, 10])
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_multispan(eng, orc, n_spans, prec, rtol):
+    """Eq. new_gn_model's sum over identical spans (phase offsets (k-1) L)."""
+    wl = W.tiny(G=32, n_edges=41).with_(n_spans=n_spans)
+    ref = _oracle_sigma(orc, wl)
+    got = eng.eta(wl, precision=prec)
+    np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)
+    r = orc.evaluate(wl)
+    s = eng.snr(wl, precision=prec)
+    np.testing.assert_allclose(s["snr"], r["snr"], rtol=max(rtol, 1e-9))

@@ -97,3 +97,10 @@ def test_grad_rejects_bad_arguments(eng):
         eng.grad(wl, P=P)
     with pytest.raises(IsrsError):
         eng.grad(wl.with_(n_edges=200))
+
+
+def test_adjoint_multispan(eng):
+    wl = W.tiny(G=32, n_edges=41).with_(n_spans=4)
+    r = eng.grad(wl)
+    fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], wl.P_W, range(5))
+    _check(r["dT_dP"], fd)

@@ -339,3 +339,32 @@ def test_snr_ase_textbook(orc):
     assert np.allclose(pase, ref, rtol=1e-12)
     assert np.allclose(snr, wl.P_W / ref, rtol=1e-12)
     assert T == pytest.approx(float(np.sum(2 * wl.B_THz * np.log2(1 + wl.P_W / ref))), rel=1e-12)
+
+
+def test_multispan_sum_is_phased_array_times_one_span(orc):
+    """Identical spans: |sum_k S e^{j phi (k-1) L}|^2 = |S|^2 sin^2(n phi L/2)/sin^2(phi L/2)
+    (the phased-array term the multi-span sum reduces to)."""
+    L = 80.0
+    ze = orc.zgrid(L, 0.05, 41)
+    zm, dz = 0.5 * (ze[1:] + ze[:-1]), np.diff(ze)
+    p = np.exp(-0.05 * zm)
+    for n in (1, 2, 5, 13):
+        for ph in (1e-4, 0.013, 0.9, 37.0):
+            one = abs(orc.zsum(zm, dz, p, ph)) ** 2
+            x = ph * L / 2
+            af = (math.sin(n * x) / math.sin(x)) ** 2 if abs(math.sin(x)) > 1e-12 else n * n
+            got = abs(orc.zsum_spans(zm, dz, p, ph, L, n)) ** 2
+            assert got == pytest.approx(one * af, rel=1e-9, abs=1e-12 * one * n * n)
+
+
+def test_multispan_quadrature_and_ase(orc):
+    """n spans: Sigma grows between n and n^2 times (coherent array factor), the
+    ASE adds over the n amplifiers."""
+    wl = W.tiny(G=16, n_edges=17)
+    s1 = orc.sigma(wl)
+    for n in (2, 4):
+        sn = orc.sigma(wl.with_(n_spans=n))
+        assert np.all(sn > n * s1 * 0.999) and np.all(sn < n * n * s1)
+        snr1, pase1, _ = orc.snr_throughput(wl, np.zeros(5))
+        snrn, pasen, _ = orc.snr_throughput(wl.with_(n_spans=n), np.zeros(5))
+        np.testing.assert_allclose(pasen, n * pase1, rtol=1e-14)
