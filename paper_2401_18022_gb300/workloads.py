@@ -195,6 +195,56 @@ def uwb(G: int = 256, n_edges: int = 113, p_dbm: float = 1.0,
     return _wdm_models("uwb-589ch", f, P, 80.0, f_ref, 0.028, G, n_edges, cell_set)
 
 
+# Loaded channels per band (Table "Per band characteristics"), the guard-band
+# gap between adjacent bands (Table "Simulation parameters") and the slot
+# pitch of the 589-slot grid.
+TABLE_BAND_COUNTS = {"O": 171, "E": 143, "S": 88, "C": 38, "L": 65, "U": 52}
+GUARD_GAP_NM = 5.0
+SLOT_THZ = 0.1
+
+
+def guard_gap_slots(edge_nm: float, gap_nm: float = GUARD_GAP_NM, slot_thz: float = SLOT_THZ) -> int:
+    """Whole slots inside a gap of `gap_nm` at wavelength `edge_nm`:
+    floor(c * gap / lambda^2 / slot)."""
+    return int(np.floor(C_NM_PER_PS * gap_nm / edge_nm ** 2 / slot_thz + 1e-9))
+
+
+def guard_plan(n_slots: int = 589, counts=None, gap_nm: float = GUARD_GAP_NM):
+    """Loaded slots, their band, and the guard set A of the 589-slot grid.
+
+    Walking the grid from its low-frequency end (U band), each band takes the
+    table's number of consecutive slots and every boundary between two bands
+    leaves guard_gap_slots(boundary) slots empty.  Returns
+    (loaded slot indices, band index per loaded slot (0 = O ... 5 = U),
+    guard slot indices).
+    """
+    counts = TABLE_BAND_COUNTS if counts is None else counts
+    loaded, band, guards = [], [], []
+    pos = 0
+    for b in range(5, -1, -1):                       # U, L, C, S, E, O: increasing frequency
+        n = int(counts[BAND_NAMES[b]])
+        loaded.extend(range(pos, pos + n))
+        band.extend([b] * n)
+        pos += n
+        if b > 0:
+            g = guard_gap_slots(BAND_EDGES_NM[b], gap_nm)
+            guards.extend(range(pos, pos + g))
+            pos += g
+    if pos != n_slots:
+        raise ValueError(f"band counts and guard gaps cover {pos} slots, not {n_slots}")
+    return np.asarray(loaded), np.asarray(band), np.asarray(guards)
+
+
+def uwb_guarded(G: int = 64, n_edges: int = 113, p_dbm: float = 0.0,
+                cell_set: int = CELLS_SCI_XCI) -> Workload:
+    """The 589-slot grid with the guard set A left empty: 557 loaded channels.
+    An empty slot carries no power, so it adds nothing to the Raman
+    normaliser, the integrand or the throughput: the plan simply omits it."""
+    base = uwb(G=G, n_edges=n_edges, p_dbm=p_dbm, cell_set=cell_set)
+    loaded, _, _ = guard_plan(base.n_ch)
+    return subset_plan(base, loaded, "uwb-557ch-guarded")
+
+
 def subset_plan(base: Workload, idx: np.ndarray, name: str) -> Workload:
     idx = np.sort(np.asarray(idx))
     return base.with_(name=name, f_THz=base.f_THz[idx], B_THz=base.B_THz[idx],
