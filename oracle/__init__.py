@@ -61,16 +61,22 @@ def _load():
                                        ctypes.c_int, _D]
         lib.orc_pieces_flat.argtypes = [ctypes.c_int, _D, _D, ctypes.c_int, ctypes.c_int, _D]
         lib.orc_pieces_flat.restype = ctypes.c_int
-        lib.orc_sigma.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _I, ctypes.c_double, _I,
+        lib.orc_sigma.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _I, ctypes.c_double, _I,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
         lib.orc_sigma.restype = ctypes.c_int
-        lib.orc_sigma_sampled.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _I, ctypes.c_double, _I,
-                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.orc_sigma_sampled.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _I, ctypes.c_double,
+                                          _I, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          _D, _D]
         lib.orc_sigma_sampled.restype = ctypes.c_int
         lib.orc_eta_from_sigma.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D]
-        lib.orc_snr_throughput.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _D,
+        lib.orc_snr_throughput.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, ctypes.c_int, _D, _D,
                                            ctypes.c_double, ctypes.POINTER(ctypes.c_ubyte), _D, _D]
         lib.orc_snr_throughput.restype = ctypes.c_double
+        lib.orc_raman_solve.argtypes = [ctypes.c_int, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, _D, _I, _D]
+        lib.orc_raman_solve.restype = ctypes.c_int
+        lib.orc_raman_profile.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, ctypes.c_int, _D, _D, _D]
+        lib.orc_raman_profile.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -151,19 +157,65 @@ def pieces(f, B, cut: int, cell_set: int) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Workload-level evaluation
 # --------------------------------------------------------------------------
+def _raman_tail(wl) -> list:
+    return [float(getattr(wl, "profile", 0)), float(getattr(wl, "raman_max_THz", 15.0)),
+            float(getattr(wl, "raman_photon", 1)), float(getattr(wl, "ode_h_km", 0.25))]
+
+
 def fibre_params(wl) -> np.ndarray:
-    """[L, f_ref, beta2, beta3, beta4, Cr, alpha_R, n_spans] of a workload-like object."""
+    """[L, f_ref, beta2, beta3, beta4, Cr, alpha_R, n_spans, profile, df_max, photon, h_max]
+    of a workload-like object."""
     b = beta_from_dispersion(C_NM_PER_PS / wl.f_ref_THz, wl.D_ref, wl.S_ref, wl.Sdot_ref)
     return np.array([wl.L_km, wl.f_ref_THz, b[0], b[1], b[2], wl.Cr, wl.alpha_R_per_km,
-                     float(getattr(wl, "n_spans", 1))])
+                     float(getattr(wl, "n_spans", 1))] + _raman_tail(wl))
 
 
-def _fib8(fib, wl) -> np.ndarray:
-    """Accepts the 7-entry single-span form and appends the workload's span count."""
+def _fib12(fib, wl) -> np.ndarray:
+    """Accepts the 7- or 8-entry forms (single span, closed-form profile) and
+    completes them from the workload."""
     fib = _f64(fib)
     if fib.shape[0] == 7:
         fib = np.concatenate([fib, [float(getattr(wl, "n_spans", 1))]])
+    if fib.shape[0] == 8:
+        fib = np.concatenate([fib, _raman_tail(wl)])
     return np.ascontiguousarray(fib)
+
+
+def _scale(wl):
+    sc = getattr(wl, "raman_scale", None)
+    return None if sc is None else _f64(sc)
+
+
+def raman_solve(f, P, alpha, Cr, df_max, photon, z_nodes, n_sub, scale=None) -> np.ndarray:
+    """RK4 solution of the Raman ODE (profile model R2) at the given nodes:
+    rows = nodes, columns = channels, values y = ln P (0 at z = 0 for empty slots)."""
+    f, P, alpha, z = _f64(f), _f64(P), _f64(alpha), _f64(z_nodes)
+    ns = np.ascontiguousarray(np.asarray(n_sub, dtype=np.int32))
+    sc = None if scale is None else _f64(scale)
+    out = np.zeros((len(z), len(f)))
+    rc = _load().orc_raman_solve(len(f), _dp(f), _dp(P), _dp(alpha), None if sc is None else _dp(sc),
+                                 float(Cr), float(df_max), int(photon), len(z) - 1, _dp(z),
+                                 ns.ctypes.data_as(_I), _dp(out))
+    if rc != 0:
+        raise ValueError("bad Raman ODE arguments")
+    return out
+
+
+def raman_profile(wl, P=None):
+    """Profile model R2 on the workload's z-grid: (a [n, M], b [n, M], a_L [n])
+    with ln rho(z_m, F) = a[c, m] + b[c, m] (F - f_c) inside channel c."""
+    f, alpha = _f64(wl.f_THz), _f64(wl.alpha_per_km)
+    P = _f64(wl.P_W if P is None else P)
+    fib = fibre_params(wl)
+    fib[8] = 1.0
+    n, M = len(f), wl.n_edges - 1
+    a, b, aL = np.zeros((n, M)), np.zeros((n, M)), np.zeros(n)
+    sc = _scale(wl)
+    rc = _load().orc_raman_profile(n, _dp(f), _dp(P), _dp(alpha), None if sc is None else _dp(sc),
+                                   _dp(fib), int(wl.n_edges), _dp(a), _dp(b), _dp(aL))
+    if rc != 0:
+        raise ValueError("bad Raman profile arguments")
+    return a, b, aL
 
 
 C_NM_PER_PS = 299792.458
@@ -182,7 +234,7 @@ def sigma(wl, P=None, cuts: Optional[Sequence[int]] = None, threads: Optional[in
     f, B = _f64(wl.f_THz), _f64(wl.B_THz)
     P = _f64(wl.P_W if P is None else P)
     alpha = _f64(wl.alpha_per_km)
-    fib = _fib8(fibre_params(wl) if fibre is None else fibre, wl)
+    fib = _fib12(fibre_params(wl) if fibre is None else fibre, wl)
     quad = np.array([wl.G, wl.n_edges, wl.cell_set], dtype=np.int32)
     cuts = np.arange(len(f), dtype=np.int32) if cuts is None else np.asarray(cuts, dtype=np.int32)
     cuts = np.ascontiguousarray(cuts)
@@ -191,7 +243,9 @@ def sigma(wl, P=None, cuts: Optional[Sequence[int]] = None, threads: Optional[in
     n_pieces = sum(_load().orc_pieces_flat(len(f), _dp(f), _dp(B), int(c), int(wl.cell_set),
                                            None) for c in cuts)
     pout = np.zeros(max(n_pieces, 1))
-    rc = _load().orc_sigma(len(f), _dp(f), _dp(B), _dp(P), _dp(alpha), _dp(fib),
+    sc = _scale(wl)
+    rc = _load().orc_sigma(len(f), _dp(f), _dp(B), _dp(P), _dp(alpha), None if sc is None else _dp(sc),
+                           _dp(fib),
                            quad.ctypes.data_as(_I), float(wl.eps_v1),
                            cuts.ctypes.data_as(_I), len(cuts), int(threads),
                            1 if unit_integrand else 0, _dp(out), _dp(pout))
@@ -209,7 +263,7 @@ def time_sample(wl, cuts, stride: int, threads: Optional[int] = None) -> dict:
     import time
     f, B = _f64(wl.f_THz), _f64(wl.B_THz)
     P, alpha = _f64(wl.P_W), _f64(wl.alpha_per_km)
-    fib = _fib8(fibre_params(wl), wl)
+    fib = _fib12(fibre_params(wl), wl)
     quad = np.array([wl.G, wl.n_edges, wl.cell_set], dtype=np.int32)
     cuts = np.ascontiguousarray(np.asarray(cuts, dtype=np.int32))
     threads = threads or os.cpu_count() or 1
@@ -218,7 +272,9 @@ def time_sample(wl, cuts, stride: int, threads: Optional[int] = None) -> dict:
     pout = np.zeros(max(n_pieces, 1))
     out = np.zeros(len(cuts))
     t0 = time.perf_counter()
-    rc = _load().orc_sigma_sampled(len(f), _dp(f), _dp(B), _dp(P), _dp(alpha), _dp(fib),
+    sc = _scale(wl)
+    rc = _load().orc_sigma_sampled(len(f), _dp(f), _dp(B), _dp(P), _dp(alpha),
+                                   None if sc is None else _dp(sc), _dp(fib),
                                    quad.ctypes.data_as(_I), float(wl.eps_v1), cuts.ctypes.data_as(_I),
                                    len(cuts), int(threads), 0, int(stride), _dp(out), _dp(pout))
     dt = time.perf_counter() - t0
@@ -245,7 +301,7 @@ def snr_throughput(wl, eta_all: np.ndarray, P=None, fibre=None):
     """Per-channel SNR (Sec. IV, Eq. loss), ASE power, and throughput T [Tb/s]."""
     f, B, alpha = _f64(wl.f_THz), _f64(wl.B_THz), _f64(wl.alpha_per_km)
     P = _f64(wl.P_W if P is None else P)
-    fib = _fib8(fibre_params(wl) if fibre is None else fibre, wl)
+    fib = _fib12(fibre_params(wl) if fibre is None else fibre, wl)
     nf = _f64(wl.nf_dB)
     e = _f64(eta_all)
     g = getattr(wl, "guard", None)
@@ -254,7 +310,9 @@ def snr_throughput(wl, eta_all: np.ndarray, P=None, fibre=None):
         g = np.ascontiguousarray(np.asarray(g, dtype=np.uint8))
         gp = g.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
     snr, pase = np.zeros(len(f)), np.zeros(len(f))
-    T = _load().orc_snr_throughput(len(f), _dp(f), _dp(B), _dp(P), _dp(alpha), _dp(fib), _dp(e),
+    sc = _scale(wl)
+    T = _load().orc_snr_throughput(len(f), _dp(f), _dp(B), _dp(P), _dp(alpha),
+                                   None if sc is None else _dp(sc), _dp(fib), int(wl.n_edges), _dp(e),
                                    _dp(nf), float(wl.snr_trx_dB), gp, _dp(snr), _dp(pase))
     return snr, pase, float(T)
 

@@ -17,9 +17,12 @@
  *    uniform in upsilon2 between the row's limits; upsilon1 is cut off below
  *    at eps * upsilon1_max.
  *  - z-grid: N_M edges with equal power drop per step, z-tilde_m = z_m.
- *  - Power profile: the closed-form ISRS profile for a linear Raman slope
+ *  - Power profile R1: the closed-form ISRS profile for a linear Raman slope
  *    (the model the paper builds on, App. A), normalised by the integral of
  *    the transmitted PSD, with per-channel attenuation.
+ *  - Power profile R2: RK4 solution of the Raman ODEs for line channels,
+ *    triangular gain cut off at df_max, photon ratio, Aeff scale; inside a
+ *    channel ln rho is linear with the central-difference slope.
  *  - P_NLI,i = G(f_i) B_i and eta_i = P_NLI,i / P_i^3.
  *
  * Units: THz, ps, km, W.  phi in rad/km.
@@ -177,6 +180,138 @@ double orc_lnrho(int n, const double *f, const double *B, const double *P, const
 }
 
 /* ---------------------------------------------------------------------- */
+/* Profile model R2 (Sec. III and App. A: the profile is the solution of   */
+/* the Raman power-evolution ODEs, with the Raman gain scaled by the       */
+/* effective area at the channel frequency).  Channel k is a line of power */
+/* P_k at f_k (THz, absolute); with y_i = ln P_i                           */
+/*   dy_i/dz = -alpha_i + s_i C_r sum_{k != i} h(f_k, f_i) P_k,            */
+/*   h = f_k - f_i                 if 0 < f_k - f_i <= df_max (k pumps i), */
+/*   h = (f_k - f_i) f_i / f_k     if 0 < f_i - f_k <= df_max (i pumps k;  */
+/*                                  the photon ratio, replaced by 1 when   */
+/*                                  photon == 0),                          */
+/*   h = 0 beyond df_max (df_max <= 0: no cut-off),                        */
+/* i.e. a triangular gain C_r |df| cut off at df_max, and s_i =            */
+/* Aeff(f_ref)/Aeff(f_i).  A slot with P_k = 0 pumps nothing; its y_k      */
+/* starts at 0 and follows the gain a zero-power probe would see.          */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int n;
+    const double *f, *P0, *alpha, *scale;
+    double Cr, df_max;
+    int photon;
+} orc_raman;
+
+static void orc_raman_rhs(const orc_raman *r, const double *y, double *dy)
+{
+    for (int i = 0; i < r->n; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < r->n; ++k) {
+            if (k == i || !(r->P0[k] > 0.0)) continue;
+            double d = r->f[k] - r->f[i];
+            if (r->df_max > 0.0 && fabs(d) > r->df_max) continue;
+            double h = (d > 0.0 || !r->photon) ? d : d * r->f[i] / r->f[k];
+            s += h * exp(y[k]);
+        }
+        double si = r->scale ? r->scale[i] : 1.0;
+        dy[i] = -r->alpha[i] + si * r->Cr * s;
+    }
+}
+
+/* one classical RK4 step of length h, in place */
+static void orc_rk4_step(const orc_raman *r, double h, double *y, double *w /* 5 n */)
+{
+    int n = r->n;
+    double *k1 = w, *k2 = w + n, *k3 = w + 2 * n, *k4 = w + 3 * n, *t = w + 4 * n;
+    orc_raman_rhs(r, y, k1);
+    for (int i = 0; i < n; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+    orc_raman_rhs(r, t, k2);
+    for (int i = 0; i < n; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+    orc_raman_rhs(r, t, k3);
+    for (int i = 0; i < n; ++i) t[i] = y[i] + h * k3[i];
+    orc_raman_rhs(r, t, k4);
+    for (int i = 0; i < n; ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/*
+ * Integrates the ODE through nodes z_nodes[0..n_seg], segment s split into
+ * n_sub[s] equal RK4 steps.  y_out[(s * n) + i] = y_i at node s (node 0: ln P
+ * of loaded channels, 0 for empty ones).
+ */
+int orc_raman_solve(int n, const double *f, const double *P, const double *alpha, const double *scale,
+                    double Cr, double df_max, int photon, int n_seg, const double *z_nodes,
+                    const int *n_sub, double *y_out)
+{
+    if (n < 1 || n_seg < 0) return -1;
+    orc_raman r = {n, f, P, alpha, scale, Cr, df_max, photon};
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)(5 * n));
+    for (int i = 0; i < n; ++i) y[i] = P[i] > 0.0 ? log(P[i]) : 0.0;
+    memcpy(y_out, y, sizeof(double) * (size_t)n);
+    for (int s = 0; s < n_seg; ++s) {
+        int ns = n_sub[s] > 0 ? n_sub[s] : 1;
+        double h = (z_nodes[s + 1] - z_nodes[s]) / ns;
+        for (int k = 0; k < ns; ++k) orc_rk4_step(&r, h, y, w);
+        memcpy(y_out + (size_t)(s + 1) * n, y, sizeof(double) * (size_t)n);
+    }
+    free(y);
+    free(w);
+    return 0;
+}
+
+/* RK4 steps in each half of a z-step of length dz: ceil((dz/2) / h_max). */
+static int orc_half_steps(double dz, double h_max)
+{
+    int ns = (int)ceil(0.5 * dz / h_max - 1e-9);
+    return ns < 1 ? 1 : ns;
+}
+
+/*
+ * The R2 tables on the z-grid of n_edges equal-power-drop edges: the ODE is
+ * integrated edge -> midpoint -> edge through every step, each half in
+ * orc_half_steps equal RK4 steps.  Per channel c and step m:
+ *   a[c M + m] = ln rho_c(z_m) = y_c(z_m) - y_c(0),
+ *   b[c M + m] = d ln rho / dF inside channel c: the central difference, over
+ *                the neighbouring channels, of the Raman part a + alpha z_m
+ *                (one-sided at the ends of the plan, 0 for one channel),
+ * and aL[c] = ln rho_c(L).  Inside channel c, ln rho(z_m, F) = a + b (F - f_c).
+ * fibre[12]: {L, f_ref, b2, b3, b4, Cr, alpha_R, n_spans, profile,
+ *             df_max, photon, h_max}.
+ */
+int orc_raman_profile(int n, const double *f, const double *P, const double *alpha, const double *scale,
+                      const double *fibre, int n_edges, double *a, double *b, double *aL)
+{
+    if (n < 1 || n_edges < 2 || !(fibre[11] > 0.0)) return -1;
+    int M = n_edges - 1;
+    double *ze = (double *)malloc(sizeof(double) * (size_t)n_edges);
+    orc_zgrid(fibre[0], fibre[6], n_edges, ze);
+    double *zn = (double *)malloc(sizeof(double) * (size_t)(2 * M + 1));
+    int *ns = (int *)malloc(sizeof(int) * (size_t)(2 * M));
+    for (int m = 0; m < M; ++m) {
+        zn[2 * m] = ze[m];
+        zn[2 * m + 1] = 0.5 * (ze[m] + ze[m + 1]);
+        ns[2 * m] = ns[2 * m + 1] = orc_half_steps(ze[m + 1] - ze[m], fibre[11]);
+    }
+    zn[2 * M] = ze[M];
+    double *yo = (double *)malloc(sizeof(double) * (size_t)(2 * M + 1) * (size_t)n);
+    orc_raman_solve(n, f, P, alpha, scale, fibre[5], fibre[9], fibre[10] != 0.0, 2 * M, zn, ns, yo);
+    for (int c = 0; c < n; ++c) {
+        for (int m = 0; m < M; ++m) a[c * M + m] = yo[(size_t)(2 * m + 1) * n + c] - yo[c];
+        aL[c] = yo[(size_t)(2 * M) * n + c] - yo[c];
+    }
+    for (int m = 0; m < M; ++m) {
+        double zm = zn[2 * m + 1];
+        for (int c = 0; c < n; ++c) {
+            int lo = c > 0 ? c - 1 : 0, hi = c < n - 1 ? c + 1 : n - 1;
+            if (lo == hi) { b[c * M + m] = 0.0; continue; }
+            double rlo = a[lo * M + m] + alpha[lo] * zm, rhi = a[hi * M + m] + alpha[hi] * zm;
+            b[c * M + m] = (rhi - rlo) / (f[hi] - f[lo]);
+        }
+    }
+    free(ze); free(zn); free(ns); free(yo);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* App. A, Eq. slow_vary: the z-sum                                        */
 /*   S = sum_m p_m dz_m sinc(phi dz_m / 2) e^{j phi z_m}                   */
 /* for given per-step powers p_m (single span, L-tilde = 0).               */
@@ -293,6 +428,10 @@ typedef struct {
     double *z_mid, *dz, *kappa, *lnN;   /* per step */
     /* ones-mode: Psi's PSD product and link factor replaced by 1 (area). */
     int unit_integrand;
+    /* profile model: 0 closed form (linear slope), 1 Raman ODE tables */
+    int profile;
+    const double *fibre, *scale;
+    double *ra, *rb, *raL;              /* R2: [n x n_steps], [n x n_steps], [n] */
 } orc_problem;
 
 static void orc_problem_tables(orc_problem *pr, int n_edges)
@@ -312,11 +451,30 @@ static void orc_problem_tables(orc_problem *pr, int n_edges)
         pr->lnN[m] = orc_lnN(&pr->pl, pr->kappa[m], pr->f_ref);
     }
     free(ze);
+    if (pr->profile == 1) {
+        size_t nm = (size_t)pr->pl.n * (size_t)pr->n_steps;
+        pr->ra = (double *)malloc(sizeof(double) * nm);
+        pr->rb = (double *)malloc(sizeof(double) * nm);
+        pr->raL = (double *)malloc(sizeof(double) * (size_t)pr->pl.n);
+        orc_raman_profile(pr->pl.n, pr->pl.f, pr->pl.P, pr->pl.alpha, pr->scale, pr->fibre, n_edges,
+                          pr->ra, pr->rb, pr->raL);
+    }
 }
 
 static void orc_problem_free(orc_problem *pr)
 {
     free(pr->z_mid); free(pr->dz); free(pr->kappa); free(pr->lnN);
+    free(pr->ra); free(pr->rb); free(pr->raL);
+}
+
+/* ln rho(z_m, F) for F inside channel c, under the problem's profile model */
+static double orc_lnrho_m(const orc_problem *pr, int c, int m, double F)
+{
+    if (pr->profile == 1) {
+        size_t k = (size_t)c * (size_t)pr->n_steps + (size_t)m;
+        return pr->ra[k] + pr->rb[k] * (F - pr->pl.f[c]);
+    }
+    return orc_lnrho_c(&pr->pl, c, pr->z_mid[m], F, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -362,12 +520,11 @@ static double orc_piece_sum(const orc_problem *pr, int i, const orc_piece *q)
                 if (W == 0.0) continue;
                 double phi = orc_phi(f1, f2, fi_off, pr->b2, pr->b3, pr->b4);
                 for (int m = 0; m < pr->n_steps; ++m) {
-                    double z = pr->z_mid[m];
                     /* Eq. pk: p = sqrt(rho(F_a) rho(F_b) rho(F_c) / rho(f)) */
-                    double lra = orc_lnrho_c(pl, ca, z, Fa, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
-                    double lrb = orc_lnrho_c(pl, cb, z, Fb, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
-                    double lrc = orc_lnrho_c(pl, cc, z, Fc, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
-                    double lri = orc_lnrho_c(pl, i, z, fi, pr->lnPtot, pr->lnN[m], pr->kappa[m], pr->f_ref);
+                    double lra = orc_lnrho_m(pr, ca, m, Fa);
+                    double lrb = orc_lnrho_m(pr, cb, m, Fb);
+                    double lrc = orc_lnrho_m(pr, cc, m, Fc);
+                    double lri = orc_lnrho_m(pr, i, m, fi);
                     pv[m] = exp(0.5 * (lra + lrb + lrc - lri));
                 }
                 /* Eqs. slow_vary / new_gn_model: the z-sum, over every span */
@@ -421,7 +578,10 @@ static void *orc_worker(void *arg)
  * integral of Eq. gain_fin at f = f_i without the 16/27 gamma^2 factor
  * [W^3 km^2 / THz].
  *
- * fibre[8] = {L_km, f_ref_THz, beta2, beta3, beta4, Cr, alpha_R, n_spans}
+ * fibre[12] = {L_km, f_ref_THz, beta2, beta3, beta4, Cr, alpha_R, n_spans,
+ *              profile (0 closed form, 1 Raman ODE), df_max_THz, photon, h_max_km};
+ * scale: per-channel Raman gain scale s_i of the ODE (NULL: 1).
+ * the last four entries and scale are read only when profile == 1.
  * quad[3]  = {G, n_edges, cell_set}
  * piece_out (optional): per-piece sums, in the order of orc_pieces, for each
  * requested CUT one after another.
@@ -430,9 +590,9 @@ static void *orc_worker(void *arg)
  * left at zero): a bounded sample used to time the oracle, not a result.
  */
 int orc_sigma_sampled(int n, const double *f, const double *B, const double *P, const double *alpha,
-                      const double *fibre, const int *quad, double eps, const int *cuts, int n_cuts,
-                      int n_threads, int unit_integrand, int item_stride, double *sigma_out,
-                      double *piece_out)
+                      const double *scale, const double *fibre, const int *quad, double eps,
+                      const int *cuts, int n_cuts, int n_threads, int unit_integrand, int item_stride,
+                      double *sigma_out, double *piece_out)
 {
     if (n < 1 || n_cuts < 0 || quad[0] < 1 || quad[1] < 2) return -1;
     orc_problem pr;
@@ -442,6 +602,9 @@ int orc_sigma_sampled(int n, const double *f, const double *B, const double *P, 
     pr.Cr = fibre[5]; pr.alpha_R = fibre[6];
     pr.n_spans = fibre[7] >= 1.0 ? (int)fibre[7] : 1;
     pr.G = quad[0]; pr.cell_set = quad[2]; pr.eps = eps; pr.unit_integrand = unit_integrand;
+    pr.profile = fibre[8] == 1.0 ? 1 : 0;
+    pr.fibre = fibre; pr.scale = scale;
+    if (pr.profile == 1 && !(fibre[11] > 0.0)) return -1;
     orc_problem_tables(&pr, quad[1]);
 
     long total = 0;
@@ -511,18 +674,29 @@ void orc_eta_from_sigma(int n_cuts, const double *sigma, const double *gamma, co
 /*   T = 2 sum_{i not guard} B_i log2(1 + SNR_i)    [Tb/s with B in THz]. */
 /* ---------------------------------------------------------------------- */
 double orc_snr_throughput(int n, const double *f, const double *B, const double *P,
-                          const double *alpha, const double *fibre, const double *eta,
-                          const double *nf_dB, double snr_trx_dB, const unsigned char *guard,
-                          double *snr, double *pase)
+                          const double *alpha, const double *scale, const double *fibre, int n_edges,
+                          const double *eta, const double *nf_dB, double snr_trx_dB,
+                          const unsigned char *guard, double *snr, double *pase)
 {
     orc_plan pl = {n, f, B, P, alpha};
     double f_ref = fibre[1], Cr = fibre[5], alpha_R = fibre[6], L = fibre[0];
     double n_spans = fibre[7] >= 1.0 ? fibre[7] : 1.0;
     double kappa = orc_kappa(&pl, L, Cr, alpha_R);
     double lnN = orc_lnN(&pl, kappa, f_ref), lnPtot = log(orc_ptot(&pl));
+    double *aL = NULL;
+    if (fibre[8] == 1.0) {          /* R2: ln rho(L, f_i) from the ODE on the same z-grid */
+        size_t nm = (size_t)n * (size_t)(n_edges > 1 ? n_edges - 1 : 1);
+        double *ta = (double *)malloc(sizeof(double) * nm), *tb = (double *)malloc(sizeof(double) * nm);
+        aL = (double *)malloc(sizeof(double) * (size_t)n);
+        if (orc_raman_profile(n, f, P, alpha, scale, fibre, n_edges, ta, tb, aL) != 0) {
+            free(ta); free(tb); free(aL);
+            return NAN;
+        }
+        free(ta); free(tb);
+    }
     double T = 0.0;
     for (int i = 0; i < n; ++i) {
-        double lr = orc_lnrho_c(&pl, i, L, f[i], lnPtot, lnN, kappa, f_ref);
+        double lr = aL ? aL[i] : orc_lnrho_c(&pl, i, L, f[i], lnPtot, lnN, kappa, f_ref);
         double gain = exp(-lr);
         double nf = pow(10.0, nf_dB[i] / 10.0);
         /* one amplifier per span, each restoring the launch power */
@@ -534,13 +708,14 @@ double orc_snr_throughput(int n, const double *f, const double *B, const double 
         snr[i] = s;
         T += 2.0 * B[i] * log2(1.0 + s);
     }
+    free(aL);
     return T;
 }
 
 int orc_sigma(int n, const double *f, const double *B, const double *P, const double *alpha,
-              const double *fibre, const int *quad, double eps, const int *cuts, int n_cuts,
-              int n_threads, int unit_integrand, double *sigma_out, double *piece_out)
+              const double *scale, const double *fibre, const int *quad, double eps, const int *cuts,
+              int n_cuts, int n_threads, int unit_integrand, double *sigma_out, double *piece_out)
 {
-    return orc_sigma_sampled(n, f, B, P, alpha, fibre, quad, eps, cuts, n_cuts, n_threads,
+    return orc_sigma_sampled(n, f, B, P, alpha, scale, fibre, quad, eps, cuts, n_cuts, n_threads,
                              unit_integrand, 1, sigma_out, piece_out);
 }

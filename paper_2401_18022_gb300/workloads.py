@@ -118,6 +118,11 @@ class Workload:
     snr_trx_dB: float = 0.0         # <= 0: no transceiver noise
     guard: Optional[np.ndarray] = None
     n_spans: int = 1                # identical spans, launch profile restored per span
+    profile: int = 0                # power profile: 0 closed form (linear slope), 1 Raman ODE
+    raman_max_THz: float = 15.0     # Raman ODE: triangular gain cut-off
+    raman_photon: int = 1           # Raman ODE: photon-number ratio in the pump depletion
+    ode_h_km: float = 0.25          # Raman ODE: largest RK4 step
+    raman_scale: Optional[np.ndarray] = None   # Raman ODE: Aeff(f_ref) / Aeff(f_i); None -> 1
 
     @property
     def n_ch(self) -> int:
@@ -247,10 +252,24 @@ def uwb_guarded(G: int = 64, n_edges: int = 113, p_dbm: float = 0.0,
 
 def subset_plan(base: Workload, idx: np.ndarray, name: str) -> Workload:
     idx = np.sort(np.asarray(idx))
+    sc = None if base.raman_scale is None else np.asarray(base.raman_scale)[idx]
     return base.with_(name=name, f_THz=base.f_THz[idx], B_THz=base.B_THz[idx],
                       P_W=base.P_W[idx], alpha_per_km=base.alpha_per_km[idx],
                       lambda_nm=base.lambda_nm[idx], aeff_um2=base.aeff_um2[idx],
-                      nf_dB=base.nf_dB[idx])
+                      nf_dB=base.nf_dB[idx], raman_scale=sc)
+
+
+def raman(wl: Workload, raman_max_THz: float = 15.0, photon: int = 1, ode_h_km: float = 0.25,
+          aeff_scaling: bool = True) -> Workload:
+    """The same scenario with the Raman-ODE power profile: triangular gain
+    C_r |df| up to raman_max_THz, scaled per channel by Aeff(f_ref)/Aeff(f_i)
+    (Aeff at f_ref interpolated linearly in frequency over the plan)."""
+    sc = None
+    if aeff_scaling:
+        a_ref = float(np.interp(wl.f_ref_THz, wl.f_THz, wl.aeff_um2))
+        sc = a_ref / np.asarray(wl.aeff_um2, dtype=np.float64)
+    return wl.with_(profile=1, raman_max_THz=float(raman_max_THz), raman_photon=int(photon),
+                    ode_h_km=float(ode_h_km), raman_scale=sc)
 
 
 @dataclass
