@@ -63,11 +63,29 @@ typedef struct isrs_handle_s *isrs_handle;
 #define ISRS_PREC_FP32 0       /* FP32 bulk, float-float phase, compensated sums */
 #define ISRS_PREC_FP64 1       /* plain FP64 throughout (reference GPU path) */
 
+/* Power-profile models (the rho(z, f) of Eq. pk). */
+#define ISRS_PROFILE_CLOSED_FORM 0   /* linear Raman slope, closed form */
+#define ISRS_PROFILE_RAMAN_ODE   1   /* Raman power-evolution ODEs (RK4) */
+
 /* Fibre of one span (Sec. II; App. A).  beta_k are the Taylor coefficients of
- * the propagation constant at f_ref (Eqs. d, d_slope, d_curve).  The power
- * profile is the closed-form ISRS solution for a linear Raman gain slope
- * C_r, with L_eff(z) = (1 - exp(-alpha_R z)) / alpha_R; alpha_R also sets the
- * equal-power-drop z-grid. */
+ * the propagation constant at f_ref (Eqs. d, d_slope, d_curve).  alpha_R sets
+ * the equal-power-drop z-grid.  Power profile:
+ *  - ISRS_PROFILE_CLOSED_FORM: the ISRS solution for a linear Raman gain
+ *    slope C_r over the whole band, L_eff(z) = (1 - exp(-alpha_R z))/alpha_R,
+ *    normalised by the integral of the transmitted PSD;
+ *  - ISRS_PROFILE_RAMAN_ODE: the Raman power-evolution ODEs of Sec. III /
+ *    App. A for the channel powers (each channel a line at f_c):
+ *      dy_i/dz = -alpha_i + s_i C_r sum_k h(f_k, f_i) P_k,  y = ln P,
+ *      h = f_k - f_i for 0 < f_k - f_i <= raman_max_THz (k pumps i),
+ *      h = (f_k - f_i) f_i / f_k for 0 < f_i - f_k <= raman_max_THz (i pumps
+ *          k; the ratio f_i/f_k is 1 when raman_photon is 0),
+ *      h = 0 beyond raman_max_THz (<= 0: no cut-off),
+ *    s_i = isrs_channels.raman_scale[i] (the effective-area ratio
+ *    Aeff(f_ref)/Aeff(f_i); 1 when NULL), solved by classical RK4 (step
+ *    bound isrs_quad.ode_h_km) through the midpoint of every z-step; inside
+ *    channel c, ln rho(z_m, F) = ln rho_c(z_m) + b_c(z_m) (F - f_c) with b_c
+ *    the central difference of ln rho + alpha z over the neighbouring
+ *    channels.  At most 2048 channels per plan. */
 typedef struct {
     double L_km;
     double f_ref_THz;
@@ -78,6 +96,9 @@ typedef struct {
                                  * restores the launch profile (Sec. IV), so span k adds
                                  * the phase offset (k-1) L of Eq. new_gn_model and the
                                  * ASE of n amplifiers adds up; at most 100 */
+    int profile;                /* ISRS_PROFILE_* (0 for a zero-initialised struct) */
+    double raman_max_THz;       /* Raman ODE: gain cut-off [THz]; <= 0: none */
+    int raman_photon;           /* Raman ODE: 1 = photon ratio in the pump depletion */
 } isrs_fibre;
 
 /* Channel plan (host pointers, n_ch entries each).  nf_dB and guard may be
@@ -91,6 +112,7 @@ typedef struct {
     const double *gamma_per_W_km;
     const double *nf_dB;
     const unsigned char *guard;
+    const double *raman_scale;  /* Raman ODE gain scale s_i > 0 (NULL: 1); unused otherwise */
 } isrs_channels;
 
 /* Quadrature settings.  G x G grid points per piece (a cell clipped to one
@@ -104,6 +126,7 @@ typedef struct {
     int cell_set;
     int precision;
     double snr_trx_dB;          /* <= 0: no transceiver noise (Sec. IV) */
+    double ode_h_km;            /* Raman ODE: largest RK4 step [km]; <= 0 selects 0.25 */
 } isrs_quad;
 
 /* ------------------------------------------------------------------------ */
@@ -151,9 +174,11 @@ double isrs_gamma_from_aeff(double lambda_nm, double n2_m2_per_W, double aeff_um
  *   sigma[n_out]    the frequency integral without 16/27 gamma^2
  *                   [W^3 km^2/THz]                                (nullable)
  * n_out = n_cuts (or n_ch).  Errors: INVALID_ARG (plan not sorted/disjoint,
- * B <= 0, P < 0 or NaN, G < 1, n_edges < 2, L <= 0, bad cell_set/precision,
- * bad cut index), UNSUPPORTED (a piece whose F_c range covers more than 16
- * channels), ALLOC, CUDA, NUMERIC. */
+ * B <= 0, P < 0 or NaN, G < 1, n_edges < 2, L <= 0, bad cell_set/precision/
+ * profile, raman_scale <= 0, bad cut index), UNSUPPORTED (a piece whose F_c
+ * range covers more than 16 channels; the Raman ODE with more than 2048
+ * channels or with per-piece tables beyond shared memory), ALLOC, CUDA,
+ * NUMERIC. */
 isrs_status isrs_gn_eta(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch,
                         const double *P_W, const isrs_quad *quad, const int *cuts, int n_cuts,
                         double *eta, double *pnli, double *sigma, void *stream);
@@ -252,7 +277,7 @@ isrs_status isrs_last_path_counts(isrs_handle h, int64_t *counts);
  * the plan tables, then runs asynchronously.
  * Errors: INVALID_ARG (as isrs_gn_eta, or a host pointer), UNSUPPORTED
  * (the tables need more than the 4 MiB scratch: e.g. more than ~5e4 pieces,
- * or the FP32 phase range), CUDA. */
+ * or the FP32 phase range; more than one span; the Raman-ODE profile), CUDA. */
 isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
                                 const isrs_quad *quad, double *eta, double *pnli, void *stream);
 

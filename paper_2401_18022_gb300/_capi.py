@@ -19,18 +19,20 @@ PREC_FP32, PREC_FP64 = 0, 1
 class Fibre(ctypes.Structure):
     _fields_ = [("L_km", ctypes.c_double), ("f_ref_THz", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("beta3", ctypes.c_double), ("beta4", ctypes.c_double), ("Cr", ctypes.c_double),
-                ("alpha_R_per_km", ctypes.c_double), ("n_spans", ctypes.c_int)]
+                ("alpha_R_per_km", ctypes.c_double), ("n_spans", ctypes.c_int), ("profile", ctypes.c_int),
+                ("raman_max_THz", ctypes.c_double), ("raman_photon", ctypes.c_int)]
 
 
 class Channels(ctypes.Structure):
     _fields_ = [("n_ch", ctypes.c_int), ("f_THz", c_double_p), ("B_THz", c_double_p),
                 ("alpha_per_km", c_double_p), ("gamma_per_W_km", c_double_p), ("nf_dB", c_double_p),
-                ("guard", ctypes.POINTER(ctypes.c_ubyte))]
+                ("guard", ctypes.POINTER(ctypes.c_ubyte)), ("raman_scale", c_double_p)]
 
 
 class Quad(ctypes.Structure):
     _fields_ = [("G", ctypes.c_int), ("n_edges", ctypes.c_int), ("eps_v1", ctypes.c_double),
-                ("cell_set", ctypes.c_int), ("precision", ctypes.c_int), ("snr_trx_dB", ctypes.c_double)]
+                ("cell_set", ctypes.c_int), ("precision", ctypes.c_int), ("snr_trx_dB", ctypes.c_double),
+                ("ode_h_km", ctypes.c_double)]
 
 
 class IsrsError(RuntimeError):

@@ -85,7 +85,8 @@ class Engine:
     def fibre(self, wl) -> _capi.Fibre:
         b = self.beta(wl)
         return _capi.Fibre(wl.L_km, wl.f_ref_THz, b[0], b[1], b[2], wl.Cr, wl.alpha_R_per_km,
-                           int(getattr(wl, "n_spans", 1)))
+                           int(getattr(wl, "n_spans", 1)), int(getattr(wl, "profile", 0)),
+                           float(getattr(wl, "raman_max_THz", 15.0)), int(getattr(wl, "raman_photon", 1)))
 
     def channels(self, wl):
         keep = {k: np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for k, v in
@@ -96,14 +97,18 @@ class Engine:
         if getattr(wl, "guard", None) is not None:
             keep["guard"] = np.ascontiguousarray(np.asarray(wl.guard, dtype=np.uint8))
             guard = keep["guard"].ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        scale = None
+        if getattr(wl, "raman_scale", None) is not None:
+            keep["scale"] = np.ascontiguousarray(np.asarray(wl.raman_scale, dtype=np.float64))
+            scale = dp(keep["scale"])
         ch = _capi.Channels(wl.n_ch, dp(keep["f"]), dp(keep["B"]), dp(keep["a"]), dp(keep["g"]),
-                            dp(keep["nf"]), guard)
+                            dp(keep["nf"]), guard, scale)
         return ch, keep
 
     @staticmethod
     def quad(wl, precision: int = PREC_FP32) -> _capi.Quad:
         return _capi.Quad(int(wl.G), int(wl.n_edges), float(wl.eps_v1), int(wl.cell_set), int(precision),
-                          float(wl.snr_trx_dB))
+                          float(wl.snr_trx_dB), float(getattr(wl, "ode_h_km", 0.25)))
 
     def set_tile(self, points_per_item: int = 0, threads_per_block: int = 0):
         check(self.lib.isrs_set_tile(self.h, points_per_item, threads_per_block), self.h)

@@ -46,6 +46,10 @@ struct Geom {
     DevBuf pieces, items, slot_items, slot_cut, prof_slot_off, plan_ch_off_d, plan_n_d, prof_ch_off_d,
         prof_plan_d, ch_frel, ch_B, ch_alpha, ch_gamma, ch_nf, guard, zs_a, zs_b, zs_d, item_slot;
     bool has_nf = false, has_guard = false;
+    // Raman-ODE profile: partner windows and gain scale per plan channel, RK4
+    // steps per half z-step, largest candidate count of a piece
+    int profile = 0, nc_max = 1, n_rk = 0, max_plan_n = 0;
+    DevBuf win_lo, win_hi, ch_scale, half_steps;
     // replayable graph of the batched launch (prep -> quadrature -> finish)
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey = 0;                 // fibre, precision and tile the graph was captured with
@@ -60,7 +64,7 @@ struct isrs_handle_s {
     std::string err;
     DevBuf paths, kapL;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
-        o_pase, o_T, gA, gK, gPd, ybar, dTdP;
+        o_pase, o_T, gA, gK, gPd, ybar, dTdP, ab, ode_y;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
@@ -170,6 +174,11 @@ isrs_status check_fibre(isrs_handle h, const isrs_fibre *fb)
     if (!(fb->alpha_R_per_km >= 0.0) || !finite(fb->alpha_R_per_km))
         return fail(h, ISRS_ERR_INVALID_ARG, "alpha_R must be >= 0");
     if (fb->n_spans < 0 || fb->n_spans > 100) return fail(h, ISRS_ERR_INVALID_ARG, "n_spans must be in [0, 100]");
+    if (fb->profile != ISRS_PROFILE_CLOSED_FORM && fb->profile != ISRS_PROFILE_RAMAN_ODE)
+        return fail(h, ISRS_ERR_INVALID_ARG, "bad profile %d", fb->profile);
+    if (fb->profile == ISRS_PROFILE_RAMAN_ODE &&
+        (!finite(fb->raman_max_THz) || (fb->raman_photon != 0 && fb->raman_photon != 1)))
+        return fail(h, ISRS_ERR_INVALID_ARG, "bad Raman cut-off or photon flag");
     return ISRS_OK;
 }
 
@@ -185,6 +194,8 @@ isrs_status check_plan(isrs_handle h, const isrs_channels *c)
         if (!(c->alpha_per_km[k] >= 0.0) || !finite(c->alpha_per_km[k]) || !finite(c->gamma_per_W_km[k]))
             return fail(h, ISRS_ERR_INVALID_ARG, "channel %d: bad alpha or gamma", k);
         if (c->nf_dB && !finite(c->nf_dB[k])) return fail(h, ISRS_ERR_INVALID_ARG, "channel %d: bad NF", k);
+        if (c->raman_scale && !(c->raman_scale[k] > 0.0 && finite(c->raman_scale[k])))
+            return fail(h, ISRS_ERR_INVALID_ARG, "channel %d: raman_scale must be > 0", k);
         if (k > 0) {
             if (!(c->f_THz[k] > c->f_THz[k - 1]))
                 return fail(h, ISRS_ERR_INVALID_ARG, "channels not sorted at %d", k);
@@ -207,6 +218,7 @@ isrs_status check_quad(isrs_handle h, const isrs_quad *q)
     if (q->precision != ISRS_PREC_FP32 && q->precision != ISRS_PREC_FP64)
         return fail(h, ISRS_ERR_INVALID_ARG, "bad precision");
     if (!finite(q->snr_trx_dB)) return fail(h, ISRS_ERR_INVALID_ARG, "bad snr_trx_dB");
+    if (!finite(q->ode_h_km)) return fail(h, ISRS_ERR_INVALID_ARG, "bad ode_h_km");
     return ISRS_OK;
 }
 
@@ -391,6 +403,16 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     hs.val(q->G); hs.val(q->n_edges); hs.val(q->eps_v1); hs.val(q->cell_set);
     hs.val(fb->L_km); hs.val(fb->f_ref_THz); hs.val(fb->alpha_R_per_km);
     hs.val(h->tile_points);
+    hs.val(fb->profile);
+    const double ode_h = q->ode_h_km > 0.0 ? q->ode_h_km : 0.25;
+    if (fb->profile == ISRS_PROFILE_RAMAN_ODE) {
+        hs.val(fb->raman_max_THz);
+        hs.val(ode_h);
+        for (int k = 0; k < n_plans; ++k) {
+            hs.val((int)(plans[k].raman_scale != nullptr));
+            if (plans[k].raman_scale) hs.bytes(plans[k].raman_scale, sizeof(double) * plans[k].n_ch);
+        }
+    }
     const uint64_t key = hs.v;
     for (size_t k = 0; k < h->cache.size(); ++k) {
         if (h->cache[k]->key == key) {
@@ -506,6 +528,48 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     std::vector<double2> zd;
     zgrid_tables(fb->L_km, fb->alpha_R_per_km, q->n_edges, za, zb, zd, g->dz_max);
 
+    // Raman-ODE profile: the partners of channel i are the k != i with
+    // |f_k - f_i| <= raman_max_THz, one index window of the sorted plan; the
+    // RK4 steps in each half of z-step m are ceil((dz_m / 2) / h).
+    g->profile = fb->profile;
+    std::vector<int> wlo, whi, hsteps;
+    std::vector<double> scl;
+    if (fb->profile == ISRS_PROFILE_RAMAN_ODE) {
+        const double dfm = fb->raman_max_THz;
+        for (int k = 0; k < n_plans; ++k) {
+            const isrs_channels &c = plans[k];
+            if (c.n_ch > kMaxRamanCh)
+                return fail(h, ISRS_ERR_UNSUPPORTED, "Raman-ODE profile supports at most %d channels", kMaxRamanCh);
+            g->max_plan_n = std::max(g->max_plan_n, c.n_ch);
+            int lo = 0, hi = 0;
+            for (int i = 0; i < c.n_ch; ++i) {
+                if (dfm > 0.0) {
+                    while (std::fabs(c.f_THz[lo] - c.f_THz[i]) > dfm) ++lo;
+                    if (hi < i) hi = i;
+                    while (hi + 1 < c.n_ch && std::fabs(c.f_THz[hi + 1] - c.f_THz[i]) <= dfm) ++hi;
+                } else {
+                    lo = 0;
+                    hi = c.n_ch - 1;
+                }
+                wlo.push_back(lo);
+                whi.push_back(hi);
+                scl.push_back(c.raman_scale ? c.raman_scale[i] : 1.0);
+            }
+        }
+        g->n_rk = 0;
+        for (int m = 0; m < g->n_steps; ++m) {
+            const int ns = std::max(1, (int)std::ceil(0.5 * zd[m].y / ode_h - 1e-9));
+            hsteps.push_back(ns);
+            g->n_rk += 2 * ns;
+        }
+        int ncm = 1;
+        for (const DevPiece &pc : pieces) ncm = std::max(ncm, std::min(pc.c_hi - pc.c_lo + 1, kMaxCand));
+        g->nc_max = ncm;
+        if (quad_tab_smem_bytes(0, g->n_steps, q->G, ncm) > 200 * 1024)
+            return fail(h, ISRS_ERR_UNSUPPORTED, "Raman-ODE tables of %d candidates x %d steps exceed shared memory",
+                        ncm, g->n_steps);
+    }
+
     isrs_status s;
 #define UP(buf, vec) if ((s = upload(h, g->buf, vec, st)) != ISRS_OK) return s
     UP(pieces, pieces);
@@ -527,6 +591,12 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     UP(zs_b, zb);
     UP(zs_d, zd);
     UP(item_slot, item_slot);
+    if (g->profile == ISRS_PROFILE_RAMAN_ODE) {
+        UP(win_lo, wlo);
+        UP(win_hi, whi);
+        UP(ch_scale, scl);
+        UP(half_steps, hsteps);
+    }
 #undef UP
     CK(cudaStreamSynchronize(st));   // host vectors die at return
 
@@ -537,7 +607,8 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
         DevBuf *bufs[] = {&old->pieces, &old->items, &old->slot_items, &old->slot_cut, &old->prof_slot_off,
                           &old->plan_ch_off_d, &old->plan_n_d, &old->prof_ch_off_d, &old->prof_plan_d,
                           &old->ch_frel, &old->ch_B, &old->ch_alpha, &old->ch_gamma, &old->ch_nf,
-                          &old->guard, &old->zs_a, &old->zs_b, &old->zs_d, &old->item_slot};
+                          &old->guard, &old->zs_a, &old->zs_b, &old->zs_d, &old->item_slot,
+                          &old->win_lo, &old->win_hi, &old->ch_scale, &old->half_steps};
         for (DevBuf *b : bufs) release(*b);
         h->cache.pop_back();
     }
@@ -552,7 +623,8 @@ void free_geom(Geom *g)
     DevBuf *bufs[] = {&g->pieces, &g->items, &g->slot_items, &g->slot_cut, &g->prof_slot_off,
                       &g->plan_ch_off_d, &g->plan_n_d, &g->prof_ch_off_d, &g->prof_plan_d,
                       &g->ch_frel, &g->ch_B, &g->ch_alpha, &g->ch_gamma, &g->ch_nf,
-                      &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->item_slot};
+                      &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->item_slot,
+                      &g->win_lo, &g->win_hi, &g->ch_scale, &g->half_steps};
     for (DevBuf *b : bufs) release(*b);
 }
 
@@ -606,6 +678,35 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     pp.ptot = (double *)h->ptot.p;
     pp.kap_L = (double *)h->kapL.p;
     CK(launch_prep(pp, g->n_prof, st));
+    if (g->profile == ISRS_PROFILE_RAMAN_ODE) {
+        // the Raman ODE overwrites ln rho(L) and fills the {a, b} tables
+        if ((s = ensure(h, h->ab, sizeof(double2) * (size_t)g->total_prof_ch * M)) != ISRS_OK) return s;
+        if (adjoint &&
+            (s = ensure(h, h->ode_y, sizeof(double) * (size_t)(g->n_rk + 1) * g->plan_n[0])) != ISRS_OK)
+            return s;
+        RamanParams rp;
+        std::memset(&rp, 0, sizeof(rp));
+        rp.P = (const double *)h->P.p;
+        rp.ch_frel = (const double *)g->ch_frel.p;
+        rp.ch_alpha = (const double *)g->ch_alpha.p;
+        rp.ch_scale = (const double *)g->ch_scale.p;
+        rp.win_lo = (const int *)g->win_lo.p;
+        rp.win_hi = (const int *)g->win_hi.p;
+        rp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
+        rp.plan_n = (const int *)g->plan_n_d.p;
+        rp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
+        rp.prof_plan = (const int *)g->prof_plan_d.p;
+        rp.zs_d = (const double2 *)g->zs_d.p;
+        rp.half_steps = (const int *)g->half_steps.p;
+        rp.n_steps = M;
+        rp.f_ref = fb->f_ref_THz;
+        rp.Cr = fb->Cr;
+        rp.photon = fb->raman_photon;
+        rp.ab = (double2 *)h->ab.p;
+        rp.lnrho_L = (double *)h->lnrho_L.p;
+        rp.y_nodes = adjoint ? (double *)h->ode_y.p : nullptr;
+        CK(launch_raman(rp, g->n_prof, g->max_plan_n, st));
+    }
 
     QuadParams qp;
     std::memset(&qp, 0, sizeof(qp));
@@ -643,6 +744,8 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     }
     qp.partial = (double *)h->partial.p;
     qp.counter = (int *)h->counter.p;
+    qp.ab = g->profile == ISRS_PROFILE_RAMAN_ODE ? (const double2 *)h->ab.p : nullptr;
+    qp.nc_max = g->nc_max;
     CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
     if ((s = ensure(h, h->paths, sizeof(unsigned long long) * 4)) != ISRS_OK) return s;
     CK(cudaMemsetAsync(h->paths.p, 0, sizeof(unsigned long long) * 4, st));
@@ -666,16 +769,21 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
         if (g->n_items > 0) CK(launch_adjoint(ap, grid, block, st));
         if ((s = mark(h, 1, 1, st)) != ISRS_OK) return s;
     } else {
-        const int per_sm = quad_blocks_per_sm(precision, M, g->G, block);
+        const bool tab = g->profile == ISRS_PROFILE_RAMAN_ODE;
+        if (tab && quad_tab_smem_bytes(precision, M, g->G, g->nc_max) > 200 * 1024)
+            return fail(h, ISRS_ERR_UNSUPPORTED, "profile tables exceed shared memory at this precision");
+        const int per_sm = tab ? quad_tab_blocks_per_sm(precision, M, g->G, g->nc_max, block)
+                               : quad_blocks_per_sm(precision, M, g->G, block);
         int grid = h->num_sms * per_sm;
         if (g->n_items < grid) grid = std::max(1, g->n_items);
         if ((s = mark(h, 0, 0, st)) != ISRS_OK) return s;
-        if (g->n_items > 0) CK(launch_quad(qp, precision, grid, block, st));
+        if (g->n_items > 0) CK(tab ? launch_quad_tab(qp, precision, grid, block, st)
+                                   : launch_quad(qp, precision, grid, block, st));
         if ((s = mark(h, 0, 1, st)) != ISRS_OK) return s;
     }
     h->last_points = g->n_points;
     h->last_psteps = g->n_points * (int64_t)M;
-    h->last_launches = 2;   // prep + quadrature
+    h->last_launches = g->profile == ISRS_PROFILE_RAMAN_ODE ? 3 : 2;   // prep (+ Raman ODE) + quadrature
     return ISRS_OK;
 }
 
@@ -771,7 +879,8 @@ isrs_status set_device(isrs_handle h)
 std::vector<void *> workspace_ptrs(isrs_handle h)
 {
     return {h->P.p, h->pd_d.p, h->pd_f.p, h->lnrho_L.p, h->step_d.p, h->step_f.p, h->ptot.p, h->partial.p,
-            h->counter.p, h->paths.p, h->kapL.p, h->o_sigma.p, h->o_pnli.p, h->o_eta.p, h->o_snr.p, h->o_pase.p, h->o_T.p};
+            h->counter.p, h->paths.p, h->kapL.p, h->o_sigma.p, h->o_pnli.p, h->o_eta.p, h->o_snr.p, h->o_pase.p, h->o_T.p,
+            h->ab.p};
 }
 
 isrs_status run_batched_graph(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
@@ -780,6 +889,7 @@ isrs_status run_batched_graph(isrs_handle h, const isrs_fibre *fb, const isrs_qu
     Hasher hs;            // fields one by one: the struct has padding
     hs.val(fb->L_km); hs.val(fb->f_ref_THz); hs.val(fb->beta2); hs.val(fb->beta3); hs.val(fb->beta4);
     hs.val(fb->Cr); hs.val(fb->alpha_R_per_km); hs.val(fb->n_spans);
+    hs.val(fb->profile); hs.val(fb->raman_max_THz); hs.val(fb->raman_photon);
     hs.val(q->precision);
     hs.val(h->tile_threads);
     const uint64_t key = hs.v;
@@ -873,7 +983,7 @@ isrs_status isrs_destroy(isrs_handle h)
     for (auto &g : h->cache) free_geom(g.get());
     DevBuf *bufs[] = {&h->P, &h->pd_d, &h->pd_f, &h->step_d, &h->step_f, &h->lnrho_L, &h->ptot, &h->partial,
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
-                      &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP};
+                      &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP, &h->ab, &h->ode_y};
     for (DevBuf *b : bufs) release(*b);
     release(h->paths);
     release(h->kapL);
@@ -1081,6 +1191,8 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
     if (quad->precision != ISRS_PREC_FP32)
         return fail(h, ISRS_ERR_INVALID_ARG, "the gradient is the adjoint of the FP32 path");
     if (quad->n_edges - 1 > 128) return fail(h, ISRS_ERR_UNSUPPORTED, "gradient supports at most 128 z-steps");
+    if (fibre->profile != ISRS_PROFILE_CLOSED_FORM)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "gradient of the Raman-ODE profile not available");
     if (ch->guard)
         for (int k = 0; k < ch->n_ch; ++k)
             if (ch->guard[k]) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs every channel lit (guard %d)", k);
@@ -1224,6 +1336,7 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     if (!P_W || !eta || !is_device_ptr(P_W) || !is_device_ptr(eta) || (pnli && !is_device_ptr(pnli)))
         return ISRS_ERR_INVALID_ARG;
     if (fibre->n_spans > 1) return ISRS_ERR_UNSUPPORTED;         // single span only
+    if (fibre->profile != ISRS_PROFILE_CLOSED_FORM) return ISRS_ERR_UNSUPPORTED;   // closed-form profile only
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ISRS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

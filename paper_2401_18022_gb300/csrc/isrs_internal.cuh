@@ -17,6 +17,7 @@ namespace isrs {
 constexpr int kMaxCand = 16;        // max channels a piece's F_c range may touch
 constexpr int kMaxSteps = 2048;     // max z-steps (n_edges - 1)
 constexpr int kMaxG = 4096;         // max grid points per dimension
+constexpr int kMaxRamanCh = 2048;   // max channels of a plan with the Raman-ODE profile
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kLog2e = 1.44269504088896340736;
 
@@ -79,6 +80,11 @@ struct QuadParams {
     int *counter;               // persistent work counter (zeroed before launch)
     int *err_flag;
     unsigned long long *path_count;   // [3] grid points per z-sum form (small, direct, telescoped)
+    // tabulated profile (Raman ODE): per profile, channel and step {a, b} with
+    // ln rho(z_m, F) = a + b (F - f_c) inside channel c; index
+    // (prof_ch_off[prof] + c) * n_steps + m.  Null for the closed-form profile.
+    const double2 *ab;
+    int nc_max;                 // largest F_c candidate count of any piece
 };
 
 }  // namespace isrs

@@ -68,10 +68,33 @@ struct ChainParams {
     double *dT_dP;              // [n_ch]
 };
 
+// Raman-ODE profile (one block per profile): RK4 on y = ln P through the
+// edge -> midpoint -> edge nodes of every z-step, then the tables {a, b}.
+struct RamanParams {
+    const double *P;            // per profile channel powers (prof_ch_off)
+    const double *ch_frel, *ch_alpha, *ch_scale;   // plan-concatenated
+    const int *win_lo, *win_hi; // per plan channel: first / last partner (plan-local)
+    const int *plan_ch_off, *plan_n, *prof_ch_off, *prof_plan;
+    const double2 *zs_d;        // {z_m, dz_m}
+    const int *half_steps;      // per z-step: RK4 steps in each half
+    int n_steps;
+    double f_ref, Cr;
+    int photon;
+    double2 *ab;                // out: (prof_ch_off[p] + c) * n_steps + m -> {a, b}
+    double *lnrho_L;            // out: prof_ch_off[p] + c
+    double *y_nodes;            // out (nullable, profile 0 only): state before every RK4 step and at L
+};
+
+size_t raman_smem_bytes(int n_ch);
+cudaError_t launch_raman(const RamanParams &rp, int n_prof, int max_n, cudaStream_t st);
 size_t quad_smem_bytes(int precision, int n_steps, int G);
 int quad_blocks_per_sm(int precision, int n_steps, int G, int block);
 cudaError_t launch_prep(const PrepParams &pp, int n_prof, cudaStream_t st);
 cudaError_t launch_quad(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
+// the same quadratures with the tabulated profile (qp.ab set)
+size_t quad_tab_smem_bytes(int precision, int n_steps, int G, int nc_max);
+int quad_tab_blocks_per_sm(int precision, int n_steps, int G, int nc_max, int block);
+cudaError_t launch_quad_tab(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
 cudaError_t launch_finish(const FinishParams &fp, int n_prof, cudaStream_t st);
 size_t adjoint_smem_bytes(int n_steps, int G, int block);
 int adjoint_blocks_per_sm(int n_steps, int G, int block);

@@ -138,6 +138,11 @@ __device__ __forceinline__ void phasor_rev_ff(float phi, float hi, float lo, flo
 }
 
 
+__device__ __forceinline__ double sinc_d(double x)
+{
+    return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x;
+}
+
 // Phased-array factor of n identical spans (Eq. new_gn_model with
 // L-tilde_k = (k-1) L): |sum_{k<n} e^{j k phi L}|^2, by rotation from the
 // float-float phase phi L / 2pi.

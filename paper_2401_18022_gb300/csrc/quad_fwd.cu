@@ -327,11 +327,6 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
 // ---------------------------------------------------------------------------
 // k_quad_f64: the same quadrature in plain FP64 (direct form, libm functions).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double sinc_d(double x)
-{
-    return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x;
-}
-
 __global__ void __launch_bounds__(256) k_quad_f64(QuadParams qp)
 {
     extern __shared__ double2 smem_d2[];

@@ -58,3 +58,32 @@ def test_host_beta_helper_matches_oracle(lib, orc):
     g = lib.isrs_gamma_from_aeff(1550.0, 2.6e-20, 80.0)
     assert g == pytest.approx(orc.gamma(1550.0, 2.6e-20, 80.0), rel=1e-14)
     assert np.isnan(lib.isrs_gamma_from_aeff(0.0, 2.6e-20, 80.0))
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of isrs_fibre / isrs_channels / isrs_quad have the
+    C header's field offsets and sizes (compiled with the host C compiler)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2401_18022_gb300 import _capi
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    structs = {"isrs_fibre": _capi.Fibre, "isrs_channels": _capi.Channels, "isrs_quad": _capi.Quad}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "isrs_gn.h"', 'int main(void) {']
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-I", inc, "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)

@@ -1,0 +1,119 @@
+"""GPU parity of the Raman-ODE power profile (Sec. III, App. A: the profile
+of Eq. pk from the Raman power-evolution ODEs) against the FP64 oracle,
+through the C ABI.
+
+The GPU integrates the same ODE with the same RK4 node schedule, but sums
+the Raman terms by windowed prefix sums instead of the oracle's n x n loop,
+so the tables agree to rounding (~1e-13).  Tolerances on Sigma are those of
+the closed-form profile: 1e-9 (FP64 path) and 2e-4 (FP32 path).
+"""
+import numpy as np
+import pytest
+
+from paper_2401_18022_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL_F64 = 1e-9
+RTOL_F32 = 2e-4
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2401_18022_gb300 import api
+    return api.Engine(0)
+
+
+def _tiny_r2(G=48, n_edges=41, **kw):
+    """5 channels with a strong Raman slope and a cut-off inside the plan,
+    so that some pairs interact and others do not."""
+    wl = W.tiny(G=G, n_edges=n_edges).with_(Cr=0.4, P_W=W.dbm_to_w(np.array([2.0, -1.0, 4.0, 0.5, 3.0])))
+    return W.raman(wl, raman_max_THz=0.25, **kw)
+
+
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+@pytest.mark.parametrize("photon", [0, 1])
+def test_tiny_all_cuts(eng, orc, prec, rtol, photon):
+    wl = _tiny_r2(photon=photon)
+    ref = orc.sigma(wl)
+    got = eng.eta(wl, precision=prec)
+    np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)
+    # the profile matters: the closed-form result differs
+    r1 = orc.sigma(wl.with_(profile=0))
+    assert np.max(np.abs(ref / r1 - 1)) > 1e-3
+
+
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_oband_zero_dispersion_subset(eng, orc, prec, rtol):
+    wl = W.raman(W.oband(G=20, n_edges=33))
+    cuts = [0, 13, 20, 40]
+    np.testing.assert_allclose(eng.eta(wl, cuts=cuts, precision=prec)["sigma"], orc.sigma(wl, cuts=cuts),
+                               rtol=rtol)
+
+
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_uwb_sampled_cuts(eng, orc, prec, rtol):
+    """589 channels, 15 THz cut-off, Aeff scaling, photon ratio, G = 12."""
+    wl = W.raman(W.uwb(G=12, n_edges=57), ode_h_km=0.5)
+    cuts = [0, 150, 294, 451, 588]
+    np.testing.assert_allclose(eng.eta(wl, cuts=cuts, precision=prec)["sigma"], orc.sigma(wl, cuts=cuts),
+                               rtol=rtol)
+
+
+def test_snr_and_throughput(eng, orc):
+    wl = _tiny_r2().with_(snr_trx_dB=20.0)
+    r = orc.evaluate(wl)
+    s64 = eng.snr(wl, precision=1)
+    np.testing.assert_allclose(s64["snr"], r["snr"], rtol=1e-9)
+    assert s64["T"] == pytest.approx(r["T"], rel=1e-11)
+    s32 = eng.snr(wl, precision=0)
+    assert np.max(np.abs(10 * np.log10(s32["snr"] / r["snr"]))) < 1e-3
+
+
+def test_empty_slot_probe(eng, orc):
+    wl = _tiny_r2()
+    P = wl.P_W.copy()
+    P[1] = 0.0
+    np.testing.assert_allclose(eng.eta(wl, P=P, precision=1)["sigma"], orc.sigma(wl, P=P), rtol=RTOL_F64)
+    r = orc.evaluate(wl, P=P)
+    s = eng.snr(wl, P=P, precision=1)
+    assert s["T"] == pytest.approx(r["T"], rel=1e-11)
+
+
+def test_without_raman_equals_closed_form(eng):
+    """C_r = 0: both profiles are pure attenuation."""
+    wl = W.tiny(G=32, n_edges=41).with_(Cr=0.0)
+    a = eng.eta(wl, precision=1)["sigma"]
+    b = eng.eta(W.raman(wl), precision=1)["sigma"]
+    np.testing.assert_allclose(b, a, rtol=1e-12)
+
+
+def test_batched_equals_single_and_oracle(eng, orc):
+    base = W.raman(W.uwb(G=6, n_edges=17), ode_h_km=1.0)
+    bw = W.batched(n_prof=4, G=6, n_edges=17, sizes=(40, 23))
+    bw.plans = [W.raman(W.subset_plan(base, np.searchsorted(base.f_THz, p.f_THz), p.name), ode_h_km=1.0)
+                for p in bw.plans]
+    eta_b = eng.eta_batched(bw)
+    off = 0
+    for p in range(4):
+        wl = bw.plans[bw.plan_of_profile[p]]
+        n = wl.n_ch
+        np.testing.assert_array_equal(eta_b[off:off + n], eng.eta(wl, P=bw.P_W[p])["eta"])
+        if p < 2:
+            ref, _ = orc.eta(wl, orc.sigma(wl, P=bw.P_W[p]), P=bw.P_W[p])
+            np.testing.assert_allclose(eta_b[off:off + n], ref, rtol=RTOL_F32)
+        off += n
+
+
+def test_rejects_bad_raman_arguments(eng):
+    from paper_2401_18022_gb300._capi import IsrsError
+    wl = _tiny_r2(G=8)
+    with pytest.raises(IsrsError):
+        eng.eta(wl.with_(raman_scale=np.array([1.0, 1.0, 0.0, 1.0, 1.0])))
+    with pytest.raises(IsrsError):
+        eng.eta(wl.with_(raman_photon=2))
+    with pytest.raises(IsrsError):
+        eng.eta(wl.with_(profile=2))
