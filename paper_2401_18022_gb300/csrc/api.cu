@@ -64,7 +64,7 @@ struct isrs_handle_s {
     std::string err;
     DevBuf paths, kapL;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
-        o_pase, o_T, gA, gK, gPd, ybar, dTdP, ab, ode_y;
+        o_pase, o_T, gA, gK, gPd, ybar, dTdP, ab, ode_y, gAB, gV, gAt;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
@@ -634,12 +634,83 @@ struct Launch {
     int block = 256;
 };
 
-// Runs prep + quadrature on the powers already in h->P (device, concatenated).
-// Runs prep + quadrature on the powers already in h->P.  With adjoint set, the
-// fused forward + adjoint kernel also fills the step buckets and the PSD
-// buckets (single profile, FP32).
+RamanParams raman_params(isrs_handle h, const isrs_fibre *fb, Geom *g, bool keep_nodes)
+{
+    RamanParams rp;
+    std::memset(&rp, 0, sizeof(rp));
+    rp.P = (const double *)h->P.p;
+    rp.ch_frel = (const double *)g->ch_frel.p;
+    rp.ch_alpha = (const double *)g->ch_alpha.p;
+    rp.ch_scale = (const double *)g->ch_scale.p;
+    rp.win_lo = (const int *)g->win_lo.p;
+    rp.win_hi = (const int *)g->win_hi.p;
+    rp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
+    rp.plan_n = (const int *)g->plan_n_d.p;
+    rp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
+    rp.prof_plan = (const int *)g->prof_plan_d.p;
+    rp.zs_d = (const double2 *)g->zs_d.p;
+    rp.half_steps = (const int *)g->half_steps.p;
+    rp.n_steps = g->n_steps;
+    rp.f_ref = fb->f_ref_THz;
+    rp.Cr = fb->Cr;
+    rp.photon = fb->raman_photon;
+    rp.ab = (double2 *)h->ab.p;
+    rp.lnrho_L = (double *)h->lnrho_L.p;
+    rp.y_nodes = keep_nodes ? (double *)h->ode_y.p : nullptr;
+    return rp;
+}
+
+// Launch constants of the quadrature kernels over the handle's workspace.
+QuadParams quad_params(isrs_handle h, const isrs_fibre *fb, Geom *g)
+{
+    QuadParams qp;
+    std::memset(&qp, 0, sizeof(qp));
+    qp.pieces = (const DevPiece *)g->pieces.p;
+    qp.items = (const DevItem *)g->items.p;
+    qp.n_items = g->n_items;
+    qp.G = g->G;
+    qp.eps_v1 = g->eps_v1;
+    qp.n_steps = g->n_steps;
+    qp.beta2 = fb->beta2;
+    qp.beta3 = fb->beta3;
+    qp.beta4 = fb->beta4;
+    qp.ch_frel = (const double *)g->ch_frel.p;
+    qp.ch_B = (const double *)g->ch_B.p;
+    qp.ch_alpha = (const double *)g->ch_alpha.p;
+    qp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
+    qp.pd_f = (const float *)h->pd_f.p;
+    qp.pd_d = (const double *)h->pd_d.p;
+    qp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
+    qp.prof_plan = (const int *)g->prof_plan_d.p;
+    qp.step_f = (const float2 *)h->step_f.p;
+    qp.step_d = (const double2 *)h->step_d.p;
+    qp.zs_a = (const float4 *)g->zs_a.p;
+    qp.zs_b = (const float4 *)g->zs_b.p;
+    qp.zs_d = (const double2 *)g->zs_d.p;
+    qp.dz_max = g->dz_max;
+    qp.kap_L = (const double *)h->kapL.p;
+    qp.L = (float)fb->L_km;
+    qp.n_spans = fb->n_spans > 1 ? fb->n_spans : 1;
+    {
+        const double lr = fb->L_km / (2.0 * 3.14159265358979323846);
+        qp.Lrev_hi = (float)lr;
+        qp.Lrev_lo = (float)(lr - (double)qp.Lrev_hi);
+        qp.Ld = fb->L_km;
+    }
+    qp.partial = (double *)h->partial.p;
+    qp.counter = (int *)h->counter.p;
+    qp.ab = g->profile == ISRS_PROFILE_RAMAN_ODE ? (const double2 *)h->ab.p : nullptr;
+    qp.nc_max = g->nc_max;
+    qp.path_count = (unsigned long long *)h->paths.p;
+    return qp;
+}
+
+// Runs prep (+ Raman ODE) + quadrature on the powers already in h->P (device,
+// concatenated).  With adjoint set, the fused forward + adjoint kernel of the
+// closed-form profile also fills the step buckets and the PSD buckets (single
+// profile, FP32).  keep_nodes keeps the Raman ODE's RK4 states (profile 0).
 isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precision, cudaStream_t st,
-                        bool adjoint = false)
+                        bool adjoint = false, bool keep_nodes = false)
 {
     isrs_status s;
     const int M = g->n_steps;
@@ -681,75 +752,16 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     if (g->profile == ISRS_PROFILE_RAMAN_ODE) {
         // the Raman ODE overwrites ln rho(L) and fills the {a, b} tables
         if ((s = ensure(h, h->ab, sizeof(double2) * (size_t)g->total_prof_ch * M)) != ISRS_OK) return s;
-        if (adjoint &&
+        if (keep_nodes &&
             (s = ensure(h, h->ode_y, sizeof(double) * (size_t)(g->n_rk + 1) * g->plan_n[0])) != ISRS_OK)
             return s;
-        RamanParams rp;
-        std::memset(&rp, 0, sizeof(rp));
-        rp.P = (const double *)h->P.p;
-        rp.ch_frel = (const double *)g->ch_frel.p;
-        rp.ch_alpha = (const double *)g->ch_alpha.p;
-        rp.ch_scale = (const double *)g->ch_scale.p;
-        rp.win_lo = (const int *)g->win_lo.p;
-        rp.win_hi = (const int *)g->win_hi.p;
-        rp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
-        rp.plan_n = (const int *)g->plan_n_d.p;
-        rp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
-        rp.prof_plan = (const int *)g->prof_plan_d.p;
-        rp.zs_d = (const double2 *)g->zs_d.p;
-        rp.half_steps = (const int *)g->half_steps.p;
-        rp.n_steps = M;
-        rp.f_ref = fb->f_ref_THz;
-        rp.Cr = fb->Cr;
-        rp.photon = fb->raman_photon;
-        rp.ab = (double2 *)h->ab.p;
-        rp.lnrho_L = (double *)h->lnrho_L.p;
-        rp.y_nodes = adjoint ? (double *)h->ode_y.p : nullptr;
-        CK(launch_raman(rp, g->n_prof, g->max_plan_n, st));
+        CK(launch_raman(raman_params(h, fb, g, keep_nodes), g->n_prof, g->max_plan_n, st));
     }
 
-    QuadParams qp;
-    std::memset(&qp, 0, sizeof(qp));
-    qp.pieces = (const DevPiece *)g->pieces.p;
-    qp.items = (const DevItem *)g->items.p;
-    qp.n_items = g->n_items;
-    qp.G = g->G;
-    qp.eps_v1 = g->eps_v1;
-    qp.n_steps = M;
-    qp.beta2 = fb->beta2;
-    qp.beta3 = fb->beta3;
-    qp.beta4 = fb->beta4;
-    qp.ch_frel = (const double *)g->ch_frel.p;
-    qp.ch_B = (const double *)g->ch_B.p;
-    qp.ch_alpha = (const double *)g->ch_alpha.p;
-    qp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
-    qp.pd_f = (const float *)h->pd_f.p;
-    qp.pd_d = (const double *)h->pd_d.p;
-    qp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
-    qp.prof_plan = (const int *)g->prof_plan_d.p;
-    qp.step_f = (const float2 *)h->step_f.p;
-    qp.step_d = (const double2 *)h->step_d.p;
-    qp.zs_a = (const float4 *)g->zs_a.p;
-    qp.zs_b = (const float4 *)g->zs_b.p;
-    qp.zs_d = (const double2 *)g->zs_d.p;
-    qp.dz_max = g->dz_max;
-    qp.kap_L = (const double *)h->kapL.p;
-    qp.L = (float)fb->L_km;
-    qp.n_spans = fb->n_spans > 1 ? fb->n_spans : 1;
-    {
-        const double lr = fb->L_km / (2.0 * 3.14159265358979323846);
-        qp.Lrev_hi = (float)lr;
-        qp.Lrev_lo = (float)(lr - (double)qp.Lrev_hi);
-        qp.Ld = fb->L_km;
-    }
-    qp.partial = (double *)h->partial.p;
-    qp.counter = (int *)h->counter.p;
-    qp.ab = g->profile == ISRS_PROFILE_RAMAN_ODE ? (const double2 *)h->ab.p : nullptr;
-    qp.nc_max = g->nc_max;
-    CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
     if ((s = ensure(h, h->paths, sizeof(unsigned long long) * 4)) != ISRS_OK) return s;
+    QuadParams qp = quad_params(h, fb, g);
+    CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
     CK(cudaMemsetAsync(h->paths.p, 0, sizeof(unsigned long long) * 4, st));
-    qp.path_count = (unsigned long long *)h->paths.p;
     const int block = h->tile_threads > 0 ? h->tile_threads : 256;
     if (adjoint) {
         const int n_ch = g->plan_n[0];
@@ -933,6 +945,107 @@ isrs_status run_batched_graph(isrs_handle h, const isrs_fibre *fb, const isrs_qu
     return ISRS_OK;
 }
 
+ChainParams chain_params(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, int n)
+{
+    ChainParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.P = (const double *)h->P.p;
+    cp.ch_frel = (const double *)g->ch_frel.p;
+    cp.ch_B = (const double *)g->ch_B.p;
+    cp.ch_gamma = (const double *)g->ch_gamma.p;
+    cp.ch_nf = g->has_nf ? (const double *)g->ch_nf.p : nullptr;
+    cp.zs_d = (const double2 *)g->zs_d.p;
+    cp.step_d = (const double2 *)h->step_d.p;
+    cp.snr = (const double *)h->o_snr.p;
+    cp.pnli = (const double *)h->o_pnli.p;
+    cp.pase = (const double *)h->o_pase.p;
+    cp.lnrho_L = (const double *)h->lnrho_L.p;
+    cp.item_slot = (const int *)g->item_slot.p;
+    cp.slot_cut = (const int *)g->slot_cut.p;
+    cp.n_items = g->n_items;
+    cp.n_slots = g->n_slots;
+    cp.n_ch = n;
+    cp.n_steps = g->n_steps;
+    cp.L = fb->L_km;
+    cp.Cr = fb->Cr;
+    cp.alpha_R = fb->alpha_R_per_km;
+    cp.f_ref = fb->f_ref_THz;
+    cp.snr_trx_lin_inv = q->snr_trx_dB > 0.0 ? std::pow(10.0, -q->snr_trx_dB / 10.0) : 0.0;
+    cp.n_spans = fb->n_spans > 1 ? fb->n_spans : 1;
+    cp.ybar = (double *)h->ybar.p;
+    cp.aase = (double *)h->ybar.p + n;
+    cp.dT_dP = (double *)h->dTdP.p;
+    return cp;
+}
+
+// Gradient with the Raman-ODE profile: forward (keeping the RK4 states),
+// dT/dSigma per CUT, the adjoint quadrature into dT/d{a, b} and the PSD
+// terms, then the discrete adjoint of the profile tables and the ODE.
+isrs_status run_grad_tab(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
+{
+    isrs_status s;
+    const int n = g->plan_n[0], M = g->n_steps;
+    if ((s = run_forward(h, fb, g, ISRS_PREC_FP32, st, false, true)) != ISRS_OK) return s;
+    if ((s = run_finish(h, fb, q, g, true, st)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->ybar, sizeof(double) * 2 * n)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->dTdP, sizeof(double) * n)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->gAB, sizeof(double2) * (size_t)n * M)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->gAt, sizeof(double) * (size_t)n * M)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->gV, sizeof(double) * n)) != ISRS_OK) return s;
+    const ChainParams cp = chain_params(h, fb, q, g, n);
+    CK(launch_ybar(cp, st));
+    CK(cudaMemsetAsync(h->gAB.p, 0, sizeof(double2) * (size_t)n * M, st));
+    CK(cudaMemsetAsync(h->gV.p, 0, sizeof(double) * n, st));
+    CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
+    AdjTabParams ap;
+    ap.q = quad_params(h, fb, g);
+    ap.ybar = cp.ybar;
+    ap.item_slot = (const int *)g->item_slot.p;
+    ap.gAB = (double2 *)h->gAB.p;
+    ap.gV = (double *)h->gV.p;
+    const int block = h->tile_threads > 0 ? h->tile_threads : 256;
+    int grid = h->num_sms * adjoint_tab_blocks_per_sm(M, g->G, g->nc_max, block);
+    if (g->n_items < grid) grid = std::max(1, g->n_items);
+    if ((s = mark(h, 1, 0, st)) != ISRS_OK) return s;
+    if (g->n_items > 0) CK(launch_adjoint_tab(ap, grid, block, st));
+    if ((s = mark(h, 1, 1, st)) != ISRS_OK) return s;
+    RamanAdjParams rap;
+    std::memset(&rap, 0, sizeof(rap));
+    rap.r = raman_params(h, fb, g, true);
+    rap.n = n;
+    rap.n_rk = g->n_rk;
+    rap.y_nodes = (const double *)h->ode_y.p;
+    rap.gAB = (const double2 *)h->gAB.p;
+    rap.gAt = (double *)h->gAt.p;
+    rap.aase = cp.aase;
+    rap.gV = (const double *)h->gV.p;
+    rap.snr = (const double *)h->o_snr.p;
+    rap.pnli = (const double *)h->o_pnli.p;
+    rap.pase = (const double *)h->o_pase.p;
+    rap.ch_B = (const double *)g->ch_B.p;
+    rap.dT_dP = (double *)h->dTdP.p;
+    CK(launch_raman_adj(rap, st));
+    h->last_launches += 4;   // ybar, adjoint quadrature, slope fold, ODE adjoint
+    return ISRS_OK;
+}
+
+isrs_status grad_outputs(isrs_handle h, int n, double *dT_dP, double *snr, double *eta, double *T_host,
+                         cudaStream_t st)
+{
+    isrs_status s;
+    bool host_out = false;
+    if ((s = copy_out(h, dT_dP, h->dTdP, n, st, host_out)) != ISRS_OK) return s;
+    if ((s = copy_out(h, snr, h->o_snr, n, st, host_out)) != ISRS_OK) return s;
+    if ((s = copy_out(h, eta, h->o_eta, n, st, host_out)) != ISRS_OK) return s;
+    if (T_host) {
+        CK(cudaMemcpyAsync(T_host, h->o_T.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (host_out) CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return ISRS_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -983,7 +1096,8 @@ isrs_status isrs_destroy(isrs_handle h)
     for (auto &g : h->cache) free_geom(g.get());
     DevBuf *bufs[] = {&h->P, &h->pd_d, &h->pd_f, &h->step_d, &h->step_f, &h->lnrho_L, &h->ptot, &h->partial,
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
-                      &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP, &h->ab, &h->ode_y};
+                      &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP, &h->ab, &h->ode_y, &h->gAB, &h->gV,
+                      &h->gAt};
     for (DevBuf *b : bufs) release(*b);
     release(h->paths);
     release(h->kapL);
@@ -1191,8 +1305,8 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
     if (quad->precision != ISRS_PREC_FP32)
         return fail(h, ISRS_ERR_INVALID_ARG, "the gradient is the adjoint of the FP32 path");
     if (quad->n_edges - 1 > 128) return fail(h, ISRS_ERR_UNSUPPORTED, "gradient supports at most 128 z-steps");
-    if (fibre->profile != ISRS_PROFILE_CLOSED_FORM)
-        return fail(h, ISRS_ERR_UNSUPPORTED, "gradient of the Raman-ODE profile not available");
+    if (fibre->profile == ISRS_PROFILE_RAMAN_ODE && ch->n_ch > kMaxRamanGradCh)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "Raman-ODE gradient supports at most %d channels", kMaxRamanGradCh);
     if (ch->guard)
         for (int k = 0; k < ch->n_ch; ++k)
             if (ch->guard[k]) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs every channel lit (guard %d)", k);
@@ -1215,56 +1329,23 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
     std::vector<int> pp{0};
     if ((s = get_geom(h, fibre, 1, ch, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
     if ((s = load_powers(h, P_W, ch->n_ch, st)) != ISRS_OK) return s;
+    const int n = ch->n_ch, M = g->n_steps;
+    if (fibre->profile == ISRS_PROFILE_RAMAN_ODE) {
+        if ((s = run_grad_tab(h, fibre, quad, g, st)) != ISRS_OK) return s;
+        return grad_outputs(h, n, dT_dP, snr, eta, T_host, st);
+    }
     if ((s = run_forward(h, fibre, g, ISRS_PREC_FP32, st, true)) != ISRS_OK) return s;
     if ((s = run_finish(h, fibre, quad, g, true, st)) != ISRS_OK) return s;
-    const int n = ch->n_ch, M = g->n_steps;
     if ((s = ensure(h, h->ybar, sizeof(double) * 2 * n)) != ISRS_OK) return s;
     if ((s = ensure(h, h->gK, sizeof(double2) * M)) != ISRS_OK) return s;
     if ((s = ensure(h, h->dTdP, sizeof(double) * n)) != ISRS_OK) return s;
-    ChainParams cp;
-    std::memset(&cp, 0, sizeof(cp));
-    cp.P = (const double *)h->P.p;
-    cp.ch_frel = (const double *)g->ch_frel.p;
-    cp.ch_B = (const double *)g->ch_B.p;
-    cp.ch_gamma = (const double *)g->ch_gamma.p;
-    cp.ch_nf = g->has_nf ? (const double *)g->ch_nf.p : nullptr;
-    cp.zs_d = (const double2 *)g->zs_d.p;
-    cp.step_d = (const double2 *)h->step_d.p;
-    cp.snr = (const double *)h->o_snr.p;
-    cp.pnli = (const double *)h->o_pnli.p;
-    cp.pase = (const double *)h->o_pase.p;
-    cp.lnrho_L = (const double *)h->lnrho_L.p;
+    ChainParams cp = chain_params(h, fibre, quad, g, n);
     cp.item_R = (const double2 *)h->gA.p;
     cp.V = (const double *)h->gPd.p;
-    cp.item_slot = (const int *)g->item_slot.p;
-    cp.slot_cut = (const int *)g->slot_cut.p;
-    cp.n_items = g->n_items;
-    cp.n_slots = g->n_slots;
-    cp.n_ch = n;
-    cp.n_steps = M;
-    cp.L = fibre->L_km;
-    cp.Cr = fibre->Cr;
-    cp.alpha_R = fibre->alpha_R_per_km;
-    cp.f_ref = fibre->f_ref_THz;
-    cp.snr_trx_lin_inv = quad->snr_trx_dB > 0.0 ? std::pow(10.0, -quad->snr_trx_dB / 10.0) : 0.0;
-    cp.n_spans = fibre->n_spans > 1 ? fibre->n_spans : 1;
-    cp.ybar = (double *)h->ybar.p;
-    cp.aase = (double *)h->ybar.p + n;
     cp.Rb = (double2 *)h->gK.p;
-    cp.dT_dP = (double *)h->dTdP.p;
     CK(launch_chain(cp, st));
     h->last_launches += 3;
-    bool host_out = false;
-    if ((s = copy_out(h, dT_dP, h->dTdP, n, st, host_out)) != ISRS_OK) return s;
-    if ((s = copy_out(h, snr, h->o_snr, n, st, host_out)) != ISRS_OK) return s;
-    if ((s = copy_out(h, eta, h->o_eta, n, st, host_out)) != ISRS_OK) return s;
-    if (T_host) {
-        CK(cudaMemcpyAsync(T_host, h->o_T.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-        host_out = true;
-    }
-    if (host_out) CK(cudaStreamSynchronize(st));
-    CK(cudaGetLastError());
-    return ISRS_OK;
+    return grad_outputs(h, n, dT_dP, snr, eta, T_host, st);
 }
 
 }  // extern "C"

@@ -18,6 +18,7 @@ constexpr int kMaxCand = 16;        // max channels a piece's F_c range may touc
 constexpr int kMaxSteps = 2048;     // max z-steps (n_edges - 1)
 constexpr int kMaxG = 4096;         // max grid points per dimension
 constexpr int kMaxRamanCh = 2048;   // max channels of a plan with the Raman-ODE profile
+constexpr int kMaxRamanGradCh = 1536;   // ... and of its gradient (shared memory of the ODE adjoint)
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kLog2e = 1.44269504088896340736;
 

@@ -85,7 +85,42 @@ struct RamanParams {
     double *y_nodes;            // out (nullable, profile 0 only): state before every RK4 step and at L
 };
 
+// Discrete adjoint of the Raman ODE and of the profile tables (single
+// profile): from dT/d{a, b} (per channel and step) and dT/d ln rho(L) to
+// dT/dP through the RK4 steps (states of k_raman_ode's y_nodes), then the
+// total gradient with the PSD and SNR-numerator terms.
+struct RamanAdjParams {
+    RamanParams r;              // the forward's tables (profile 0)
+    int n;                      // channels
+    int n_rk;                   // RK4 steps
+    const double *y_nodes;      // [(n_rk + 1) x n]
+    const double2 *gAB;         // [n x n_steps] dT/da, dT/db
+    double *gAt;                // [n x n_steps] scratch: dT/da with the slope stencil folded in
+    const double *aase;         // [n] dT/d ln G_i (G = 1/rho(L))
+    const double *gV;           // [n] dT/d ln P_j through the PSD products
+    const double *snr, *pnli, *pase, *ch_B;
+    double *dT_dP;              // [n]
+};
+
+// Adjoint of the FP32 quadrature with the tabulated profile (single profile):
+// dT/d{a, b} per channel and step, and dT/d ln P through the PSD products,
+// given dT/dSigma of every output slot.
+struct AdjTabParams {
+    QuadParams q;
+    const double *ybar;         // [n_slots] dT/dSigma_i
+    const int *item_slot;
+    double2 *gAB;               // [n_ch x n_steps], zeroed before launch
+    double *gV;                 // [n_ch], zeroed before launch
+};
+
+size_t adjoint_tab_smem_bytes(int n_steps, int G, int nc_max, int block);
+int adjoint_tab_blocks_per_sm(int n_steps, int G, int nc_max, int block);
+cudaError_t launch_adjoint_tab(const AdjTabParams &ap, int grid, int block, cudaStream_t st);
+cudaError_t launch_ybar(const ChainParams &cp, cudaStream_t st);
+
 size_t raman_smem_bytes(int n_ch);
+size_t raman_adj_smem_bytes(int n_ch);
+cudaError_t launch_raman_adj(const RamanAdjParams &ap, cudaStream_t st);
 cudaError_t launch_raman(const RamanParams &rp, int n_prof, int max_n, cudaStream_t st);
 size_t quad_smem_bytes(int precision, int n_steps, int G);
 int quad_blocks_per_sm(int precision, int n_steps, int G, int block);

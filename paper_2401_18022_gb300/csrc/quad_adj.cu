@@ -607,6 +607,12 @@ cudaError_t launch_adjoint(const AdjParams &ap, int grid, int block, cudaStream_
     return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st);
 }
 
+cudaError_t launch_ybar(const ChainParams &cp, cudaStream_t st)
+{
+    k_ybar<<<1, 256, 0, st>>>(cp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_chain(const ChainParams &cp, cudaStream_t st)
 {
     if (cp.n_steps > kMaxAdjSteps) return cudaErrorInvalidValue;

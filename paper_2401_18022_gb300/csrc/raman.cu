@@ -272,6 +272,183 @@ cudaError_t launch_raman(const RamanParams &rp, int n_prof, int max_n, cudaStrea
 }
 
 // ---------------------------------------------------------------------------
+// Discrete adjoint of the profile (single profile, plan 0).
+//
+// T depends on the tables through a_c(m) = y_c(z_m) - y_c(0), b_c(m) (central
+// differences of a + alpha z) and ln rho_c(L) = y_c(L) - y_c(0).  k_fold_slope
+// moves dT/db onto dT/da (the stencil), k_raman_adj runs the RK4 steps
+// backwards: with lambda = dT/dy after a step y' = y + h/6 (k1 + 2k2 + 2k3 + k4),
+//   mu4 = J(Y4)^T (h/6 lambda),            mu3 = J(Y3)^T (h/3 lambda + h mu4),
+//   mu2 = J(Y2)^T (h/3 lambda + h/2 mu3),  mu1 = J(Y1)^T (h/6 lambda + h/2 mu2),
+//   dT/dy = lambda + mu1 + mu2 + mu3 + mu4,
+// with the stage states Y recomputed from the stored step states, the table
+// sensitivities injected at the nodes z_m and L, and
+//   (J^T v)_k = C_r e^{Y_k} sum_i s_i v_i h(f_k, f_i)
+// again by prefix sums over the partner window of k:
+//   i below k:  sum u_i (fr_k - fr_i)              = fr_k S(u) - S(fr u)
+//   i above k:  sum u_i (fr_k - fr_i) f_i / f_k    = (fr_k S(f u) - S(fr f u)) / f_k
+// (u = s v; the ratio f_i/f_k is 1 without the photon term).  Finally
+//   dT/dP_j = (dT/dy_j(0) + dT/d ln P_j|_PSD) / P_j + dT/dSNR_j dSNR_j/dP_j|_N.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fold_slope(RamanAdjParams ap)
+{
+    const int n = ap.n, M = ap.r.n_steps;
+    const double *fr = ap.r.ch_frel;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * M; t += gridDim.x * blockDim.x) {
+        const int c = t / M, m = t - c * M;
+        double g = ap.gAB[t].x;
+        for (int q = max(0, c - 1); q <= min(n - 1, c + 1); ++q) {
+            const int lo = q > 0 ? q - 1 : 0, hi = q < n - 1 ? q + 1 : n - 1;
+            if (lo == hi) continue;
+            const double gb = ap.gAB[(size_t)q * M + m].y / (fr[hi] - fr[lo]);
+            if (hi == c) g += gb;
+            if (lo == c) g -= gb;
+        }
+        ap.gAt[t] = g;
+    }
+}
+
+namespace {
+
+// out = J(Y)^T v (shared arrays; every thread calls)
+__device__ void raman_jt(const RamanParams &rp, int n, const double *Y, const double *v, double *out,
+                         const OdeShared &s, double *wsum)
+{
+    const double *fr = rp.ch_frel;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double u = rp.ch_scale[i] * v[i];
+        const double f = fr[i] + rp.f_ref;
+        s.ev0[i] = u;
+        s.ev1[i] = fr[i] * u;
+        s.ev2[i] = f * u;
+        s.ev3[i] = fr[i] * f * u;
+    }
+    __syncthreads();
+    scan4(s.ev0, s.ev1, s.ev2, s.ev3, s.x0, s.x1, s.x2, s.x3, n, wsum);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double r = 0.0;
+        if (rp.P[k] > 0.0) {
+            const int lo = rp.win_lo[k], hi = rp.win_hi[k];
+            const double frk = fr[k];
+            double g = 0.0;
+            if (lo < k) g += frk * (s.x0[k] - s.x0[lo]) - (s.x1[k] - s.x1[lo]);
+            if (hi > k) {
+                if (rp.photon)
+                    g += (frk * (s.x2[hi + 1] - s.x2[k + 1]) - (s.x3[hi + 1] - s.x3[k + 1])) / (frk + rp.f_ref);
+                else
+                    g += frk * (s.x0[hi + 1] - s.x0[k + 1]) - (s.x1[hi + 1] - s.x1[k + 1]);
+            }
+            r = rp.Cr * exp(Y[k]) * g;
+        }
+        out[k] = r;
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kOdeThreads) k_raman_adj(RamanAdjParams ap)
+{
+    extern __shared__ double smem_d[];
+    __shared__ double wsum[128];
+    const RamanParams &rp = ap.r;
+    const int n = ap.n, M = rp.n_steps;
+    double *lam = smem_d, *acc = lam + n, *w = acc + n, *mu = w + n, *Y2 = mu + n, *Y3 = Y2 + n, *Y4 = Y3 + n;
+    OdeShared s;
+    s.y = s.yt = s.kacc = nullptr;
+    s.ev0 = Y4 + n;
+    s.ev1 = s.ev0 + n;
+    s.ev2 = s.ev1 + n;
+    s.ev3 = s.ev2 + n;
+    s.x0 = s.ev3 + n;
+    s.x1 = s.x0 + n + 1;
+    s.x2 = s.x1 + n + 1;
+    s.x3 = s.x2 + n + 1;
+
+    for (int c = threadIdx.x; c < n; c += blockDim.x) lam[c] = -ap.aase[c];      // dT/d ln rho(L)
+    __syncthreads();
+    int node = ap.n_rk;
+    for (int m = M - 1; m >= 0; --m) {
+        const int ns = rp.half_steps[m];
+        const double h = 0.5 * rp.zs_d[m].y / ns;
+        for (int half = 1; half >= 0; --half) {
+            for (int t = 0; t < ns; ++t) {
+                --node;
+                const double *Y1 = ap.y_nodes + (size_t)node * n;
+                // stage states of this step
+                raman_rhs(rp, 0, 0, n, Y1, mu, s, wsum);
+                for (int c = threadIdx.x; c < n; c += blockDim.x) Y2[c] = Y1[c] + 0.5 * h * mu[c];
+                __syncthreads();
+                raman_rhs(rp, 0, 0, n, Y2, mu, s, wsum);
+                for (int c = threadIdx.x; c < n; c += blockDim.x) Y3[c] = Y1[c] + 0.5 * h * mu[c];
+                __syncthreads();
+                raman_rhs(rp, 0, 0, n, Y3, mu, s, wsum);
+                for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                    Y4[c] = Y1[c] + h * mu[c];
+                    acc[c] = lam[c];
+                    w[c] = h / 6.0 * lam[c];
+                }
+                __syncthreads();
+                raman_jt(rp, n, Y4, w, mu, s, wsum);                         // mu4
+                for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                    acc[c] += mu[c];
+                    w[c] = h / 3.0 * lam[c] + h * mu[c];
+                }
+                __syncthreads();
+                raman_jt(rp, n, Y3, w, mu, s, wsum);                         // mu3
+                for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                    acc[c] += mu[c];
+                    w[c] = h / 3.0 * lam[c] + 0.5 * h * mu[c];
+                }
+                __syncthreads();
+                raman_jt(rp, n, Y2, w, mu, s, wsum);                         // mu2
+                for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                    acc[c] += mu[c];
+                    w[c] = h / 6.0 * lam[c] + 0.5 * h * mu[c];
+                }
+                __syncthreads();
+                raman_jt(rp, n, Y1, w, mu, s, wsum);                         // mu1
+                for (int c = threadIdx.x; c < n; c += blockDim.x) lam[c] = acc[c] + mu[c];
+                __syncthreads();
+            }
+            if (half == 1)
+                for (int c = threadIdx.x; c < n; c += blockDim.x) lam[c] += ap.gAt[(size_t)c * M + m];
+            __syncthreads();
+        }
+    }
+    // a = y - y(0): every table entry also depends on y(0) directly
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double direct = ap.aase[j];                                    // - dT/d ln rho(L)
+        for (int m = 0; m < M; ++m) direct -= ap.gAt[(size_t)j * M + m];
+        const double P = rp.P[j];
+        double g = (lam[j] + direct + ap.gV[j]) / P;
+        const double snr = ap.snr[j], B = ap.ch_B[j];
+        const double N = ap.pnli[j] + ap.pase[j];
+        const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
+        g += dTds * snr * snr * N / (P * P);
+        ap.dT_dP[j] = g;
+    }
+}
+
+size_t raman_adj_smem_bytes(int n_ch)
+{
+    return sizeof(double) * (size_t)(15 * n_ch + 4);
+}
+
+cudaError_t launch_raman_adj(const RamanAdjParams &ap, cudaStream_t st)
+{
+    const int nm = ap.n * ap.r.n_steps;
+    k_fold_slope<<<(nm + 255) / 256, 256, 0, st>>>(ap);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = raman_adj_smem_bytes(ap.n);
+    e = cudaFuncSetAttribute(k_raman_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_raman_adj<<<1, kOdeThreads, smem, st>>>(ap);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Quadratures with the tabulated profile.
 // ---------------------------------------------------------------------------
 namespace {

@@ -117,3 +117,63 @@ def test_rejects_bad_raman_arguments(eng):
         eng.eta(wl.with_(raman_photon=2))
     with pytest.raises(IsrsError):
         eng.eta(wl.with_(profile=2))
+
+
+# ---------------------------------------------------------------------------
+# Gradient: discrete adjoint of the FP32 quadrature, the profile tables and
+# the RK4 steps, against central differences (1e-4 dB) of the FP64 GPU path
+# and of the oracle, 1e-3 relative per channel (floored at 1e-3 of the
+# largest component).
+# ---------------------------------------------------------------------------
+STEP_DB = 1e-4
+
+
+def _fd(T_of_P, P, chans):
+    g = np.zeros(len(chans))
+    for k, j in enumerate(chans):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[j] = P[j] * 10 ** (STEP_DB / 10)
+        Pm[j] = P[j] * 10 ** (-STEP_DB / 10)
+        g[k] = (T_of_P(Pp) - T_of_P(Pm)) / (2 * STEP_DB) / (P[j] * np.log(10) / 10)
+    return g
+
+
+def _check(adj, fd, rtol=1e-3):
+    floor = rtol * np.max(np.abs(fd))
+    err = np.abs(adj - fd) / np.maximum(np.abs(fd), floor)
+    assert err.max() < rtol, (err.max(), adj, fd)
+
+
+@pytest.mark.parametrize("trx", [0.0, 20.0])
+@pytest.mark.parametrize("photon", [0, 1])
+def test_adjoint_vs_fd_of_fp64_path(eng, trx, photon):
+    wl = _tiny_r2(G=48, n_edges=57, photon=photon).with_(snr_trx_dB=trx)
+    r = eng.grad(wl)
+    fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], wl.P_W, range(5))
+    _check(r["dT_dP"], fd)
+    s = eng.snr(wl, precision=0)
+    np.testing.assert_allclose(r["snr"], s["snr"], rtol=1e-6)
+    assert r["T"] == pytest.approx(s["T"], rel=1e-9)
+
+
+def test_adjoint_vs_fd_of_oracle(eng, orc):
+    wl = _tiny_r2(G=16, n_edges=17)
+    r = eng.grad(wl)
+    fd = _fd(lambda Q: orc.evaluate(wl, P=Q)["T"], wl.P_W, range(5))
+    _check(r["dT_dP"], fd)
+
+
+def test_adjoint_uwb_sampled_channels(eng):
+    """589 channels, 15 THz cut-off, Aeff scaling: FD on 8 seeded channels."""
+    wl = W.raman(W.uwb(G=8, n_edges=33), ode_h_km=0.5)
+    chans = W.gradient_fd_channels(k=8)
+    r = eng.grad(wl)
+    fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], wl.P_W, chans)
+    _check(r["dT_dP"][chans], fd)
+
+
+def test_adjoint_multispan(eng):
+    wl = _tiny_r2(G=32, n_edges=41).with_(n_spans=3)
+    r = eng.grad(wl)
+    fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], wl.P_W, range(5))
+    _check(r["dT_dP"], fd)
