@@ -205,14 +205,19 @@ def band_report(engine, wl, P, band: np.ndarray, snr_trx_dB: float = 0.0, precis
 
 
 def run_stages(engine, case: int = 1, stages: Sequence[int] = (32, 64), n_edges: int = 113,
-               gtol: float = 0.01, maxiter: int = 500, log: Optional[Callable] = None) -> dict:
+               gtol: float = 0.01, maxiter: int = 500, log: Optional[Callable] = None,
+               profile: str = "closed") -> dict:
     """Case 1 (segments) or Case 2 (uniform) on the guarded 557-channel plan:
     one L-BFGS-B run per quadrature size G in `stages`, each started from the
-    previous result (the first from 0 dBm)."""
+    previous result (the first from 0 dBm).  profile "raman" uses the
+    Raman-ODE power profile (15 THz gain cut-off, photon ratio, Aeff
+    scaling), "closed" the linear-slope closed form."""
     x = None
-    out = {"case": case, "stages": []}
+    out = {"case": case, "profile": profile, "stages": []}
     for G in stages:
         wl = W.uwb_guarded(G=G, n_edges=n_edges)
+        if profile == "raman":
+            wl = W.raman(wl)
         band = band_of(wl)
         param = segments(wl.f_THz, band) if case == 1 else uniform(wl.n_ch)
         obj = Objective(engine, wl, param)
@@ -237,12 +242,13 @@ def main(argv=None):
     ap.add_argument("--stages", default="32,64", help="quadrature sizes G, comma separated")
     ap.add_argument("--gtol", type=float, default=0.01)
     ap.add_argument("--maxiter", type=int, default=500)
+    ap.add_argument("--profile", default="raman", choices=("raman", "closed"))
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     eng = api.Engine(0)
     stages = [int(s) for s in a.stages.split(",")]
     res = run_stages(eng, a.case, stages, gtol=a.gtol, maxiter=a.maxiter,
-                     log=lambda h: print(json.dumps(h), flush=True))
+                     log=lambda h: print(json.dumps(h), flush=True), profile=a.profile)
     print(json.dumps({k: v for k, v in res.items()}), flush=True)
     if a.out:
         json.dump(res, open(a.out, "w"), indent=1)
