@@ -258,6 +258,8 @@ def run_gpu(args):
             "clocks": clocks, "roofline": roof, "wall_s": wall}
     if rank == 0 and use_grad:
         line["snr_eval"] = _snr_eval(eng, wl, P, dev, n_grid)
+    if rank == 0 and args.extras:
+        line["extras"] = _extras(eng, wl, P, dev)
     if rank == 0 and not args.quick:
         line["e2e"] = _e2e(eng, wl, args, world, n_grid)
         line["fp64_path"] = _fp64_path(eng, wl, P, args)
@@ -287,6 +289,55 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
     t = float(np.median(ms))
     return {"ms": t, "grid_pts_per_s": n_grid / (t / 1e3), "kernel": "k_quad_f32",
             "kernel_ms": eng.last_kernel_ms(0)}
+
+
+def _timed(fn, dev, reps: int = 2):
+    """Median of `reps` calls timed with CUDA events on the current stream
+    (after one untimed call)."""
+    import torch
+    st = torch.cuda.current_stream(dev)
+    fn()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms))
+
+
+def _extras(eng, wl, P, dev):
+    """Side measurements of the widened rows on the same 589-ch workload:
+    the Raman-ODE power profile (SNR and gradient) and the MCI cells on their
+    own grid (SNR, and the MCI share of eta per band)."""
+    from paper_2401_18022_gb300 import workloads as W
+    out = {}
+    wr = W.raman(wl)
+    out["raman_snr_ms"] = _timed(lambda: eng.snr(wr, P=P), dev)
+    out["raman_snr_quad_kernel_ms"] = eng.last_kernel_ms(0)
+    out["raman_grad_ms"] = _timed(lambda: eng.grad(wr, P=P), dev)
+    out["raman_grad_adjoint_kernel_ms"] = eng.last_kernel_ms(1)
+    r2 = eng.snr(wr, P=P)
+    out["raman_T_Tbps"] = r2["T"]
+    g_mci = 8
+    wm = wl.with_(cell_set=W.CELLS_ALL, G_mci=g_mci)
+    out["mci_G"] = g_mci
+    out["mci_snr_ms"] = _timed(lambda: eng.snr(wm, P=P), dev)
+    out["mci_quad_kernels_ms"] = eng.last_kernel_ms(0)
+    e_all = eng.eta(wm, P=P)["eta"]
+    e_sx = eng.eta(wl, P=P)["eta"]
+    e_all = e_all.cpu().numpy() if hasattr(e_all, "cpu") else np.asarray(e_all)
+    e_sx = e_sx.cpu().numpy() if hasattr(e_sx, "cpu") else np.asarray(e_sx)
+    share = 1.0 - e_sx / e_all
+    lam = W.nm_from_thz(wl.f_THz)
+    band = np.clip(np.searchsorted(W.BAND_EDGES_NM, lam, side="right") - 1, 0, 5)
+    out["mci_share_of_eta_by_band"] = {W.BAND_NAMES[b]: [float(share[band == b].min()), float(share[band == b].max())]
+                                       for b in range(6)}
+    n = wl.n_ch
+    out["mci_cells_per_cut"] = (n - 1) * n // 2
+    return out
 
 
 def _unfolded_points(wl):
@@ -412,6 +463,8 @@ def main():
     ap.add_argument("--mode", default="grad", choices=["snr", "grad"],
                     help="grad: SNR + dT/dP (all hot-path steps); snr: forward only")
     ap.add_argument("--quick", action="store_true", help="skip e2e, FP64 and CPU legs")
+    ap.add_argument("--extras", action="store_true",
+                    help="also time the Raman-ODE profile and the MCI cells on the same workload")
     ap.add_argument("--workload", default="uwb", choices=["uwb", "batched"],
                     help="uwb: the 589-ch system (default); batched: 512 profiles over 3 plans")
     ap.add_argument("--profile-case", default=None, choices=["quad", "quad64", "adjoint"],

@@ -127,6 +127,11 @@ typedef struct {
     int precision;
     double snr_trx_dB;          /* <= 0: no transceiver noise (Sec. IV) */
     double ode_h_km;            /* Raman ODE: largest RK4 step [km]; <= 0 selects 0.25 */
+    int G_mci;                  /* with ISRS_CELLS_ALL and > 0: the multi-channel-interference
+                                 * cells (neither F_a nor F_b in the CUT's channel) get their own
+                                 * G_mci x G_mci grid (<= 32) and are enumerated on the device
+                                 * (no piece list); closed-form profile, forward only.  0: every
+                                 * cell uses G. */
 } isrs_quad;
 
 /* ------------------------------------------------------------------------ */

@@ -235,7 +235,7 @@ def sigma(wl, P=None, cuts: Optional[Sequence[int]] = None, threads: Optional[in
     P = _f64(wl.P_W if P is None else P)
     alpha = _f64(wl.alpha_per_km)
     fib = _fib12(fibre_params(wl) if fibre is None else fibre, wl)
-    quad = np.array([wl.G, wl.n_edges, wl.cell_set], dtype=np.int32)
+    quad = np.array([wl.G, wl.n_edges, wl.cell_set, int(getattr(wl, "G_mci", 0))], dtype=np.int32)
     cuts = np.arange(len(f), dtype=np.int32) if cuts is None else np.asarray(cuts, dtype=np.int32)
     cuts = np.ascontiguousarray(cuts)
     threads = threads or os.cpu_count() or 1
@@ -264,7 +264,7 @@ def time_sample(wl, cuts, stride: int, threads: Optional[int] = None) -> dict:
     f, B = _f64(wl.f_THz), _f64(wl.B_THz)
     P, alpha = _f64(wl.P_W), _f64(wl.alpha_per_km)
     fib = _fib12(fibre_params(wl), wl)
-    quad = np.array([wl.G, wl.n_edges, wl.cell_set], dtype=np.int32)
+    quad = np.array([wl.G, wl.n_edges, wl.cell_set, int(getattr(wl, "G_mci", 0))], dtype=np.int32)
     cuts = np.ascontiguousarray(np.asarray(cuts, dtype=np.int32))
     threads = threads or os.cpu_count() or 1
     n_pieces = sum(_load().orc_pieces_flat(len(f), _dp(f), _dp(B), int(c), int(wl.cell_set), None)

@@ -424,6 +424,7 @@ typedef struct {
     double L, f_ref, b2, b3, b4, Cr, alpha_R, eps;
     int n_spans;                        /* identical spans, launch profile restored per span */
     int G, n_steps, cell_set;
+    int G_mci;                          /* grid of cells with a != i and b != i (0: G) */
     double lnPtot;
     double *z_mid, *dz, *kappa, *lnN;   /* per step */
     /* ones-mode: Psi's PSD product and link factor replaced by 1 (area). */
@@ -485,7 +486,9 @@ static double orc_lnrho_m(const orc_problem *pr, int c, int m, double F)
 static double orc_piece_sum(const orc_problem *pr, int i, const orc_piece *q)
 {
     const orc_plan *pl = &pr->pl;
-    const int G = pr->G;
+    /* multi-channel-interference cells (neither F_a nor F_b in the CUT's
+       channel) may use their own grid size */
+    const int G = (pr->G_mci > 0 && q->a != i && q->b != i) ? pr->G_mci : pr->G;
     double fi = pl->f[i];
     double fi_off = fi - pr->f_ref;
     double u1_hi = q->xhi * q->yhi;
@@ -582,7 +585,8 @@ static void *orc_worker(void *arg)
  *              profile (0 closed form, 1 Raman ODE), df_max_THz, photon, h_max_km};
  * scale: per-channel Raman gain scale s_i of the ODE (NULL: 1).
  * the last four entries and scale are read only when profile == 1.
- * quad[3]  = {G, n_edges, cell_set}
+ * quad[4]  = {G, n_edges, cell_set, G_mci}: G x G points per piece, except
+ *            G_mci x G_mci in cells with a != i and b != i when G_mci > 0
  * piece_out (optional): per-piece sums, in the order of orc_pieces, for each
  * requested CUT one after another.
  * unit_integrand != 0 replaces the integrand by 1 (returns covered area).
@@ -602,6 +606,7 @@ int orc_sigma_sampled(int n, const double *f, const double *B, const double *P, 
     pr.Cr = fibre[5]; pr.alpha_R = fibre[6];
     pr.n_spans = fibre[7] >= 1.0 ? (int)fibre[7] : 1;
     pr.G = quad[0]; pr.cell_set = quad[2]; pr.eps = eps; pr.unit_integrand = unit_integrand;
+    pr.G_mci = quad[3] > 0 ? quad[3] : 0;
     pr.profile = fibre[8] == 1.0 ? 1 : 0;
     pr.fibre = fibre; pr.scale = scale;
     if (pr.profile == 1 && !(fibre[11] > 0.0)) return -1;

@@ -32,7 +32,7 @@ class Channels(ctypes.Structure):
 class Quad(ctypes.Structure):
     _fields_ = [("G", ctypes.c_int), ("n_edges", ctypes.c_int), ("eps_v1", ctypes.c_double),
                 ("cell_set", ctypes.c_int), ("precision", ctypes.c_int), ("snr_trx_dB", ctypes.c_double),
-                ("ode_h_km", ctypes.c_double)]
+                ("ode_h_km", ctypes.c_double), ("G_mci", ctypes.c_int)]
 
 
 class IsrsError(RuntimeError):

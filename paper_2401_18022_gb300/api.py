@@ -108,7 +108,8 @@ class Engine:
     @staticmethod
     def quad(wl, precision: int = PREC_FP32) -> _capi.Quad:
         return _capi.Quad(int(wl.G), int(wl.n_edges), float(wl.eps_v1), int(wl.cell_set), int(precision),
-                          float(wl.snr_trx_dB), float(getattr(wl, "ode_h_km", 0.25)))
+                          float(wl.snr_trx_dB), float(getattr(wl, "ode_h_km", 0.25)),
+                          int(getattr(wl, "G_mci", 0)))
 
     def set_tile(self, points_per_item: int = 0, threads_per_block: int = 0):
         check(self.lib.isrs_set_tile(self.h, points_per_item, threads_per_block), self.h)

@@ -50,6 +50,11 @@ struct Geom {
     // steps per half z-step, largest candidate count of a piece
     int profile = 0, nc_max = 1, n_rk = 0, max_plan_n = 0;
     DevBuf win_lo, win_hi, ch_scale, half_steps;
+    // multi-channel-interference cells on their own grid: work items over
+    // triangular cell ranges and, per output slot, their item range
+    int G_mci = 0, n_mci_items = 0;
+    double mci_phase_rev_max = 0.0;
+    DevBuf mci_items, slot_items2;
     // replayable graph of the batched launch (prep -> quadrature -> finish)
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey = 0;                 // fibre, precision and tile the graph was captured with
@@ -64,7 +69,7 @@ struct isrs_handle_s {
     std::string err;
     DevBuf paths, kapL;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
-        o_pase, o_T, gA, gK, gPd, ybar, dTdP, ab, ode_y, gAB, gV, gAt;
+        o_pase, o_T, gA, gK, gPd, ybar, dTdP, ab, ode_y, gAB, gV, gAt, partial_mci;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
@@ -219,6 +224,9 @@ isrs_status check_quad(isrs_handle h, const isrs_quad *q)
         return fail(h, ISRS_ERR_INVALID_ARG, "bad precision");
     if (!finite(q->snr_trx_dB)) return fail(h, ISRS_ERR_INVALID_ARG, "bad snr_trx_dB");
     if (!finite(q->ode_h_km)) return fail(h, ISRS_ERR_INVALID_ARG, "bad ode_h_km");
+    if (q->G_mci < 0 || q->G_mci > 32) return fail(h, ISRS_ERR_INVALID_ARG, "G_mci must be in [0, 32]");
+    if (q->G_mci > 0 && q->cell_set != ISRS_CELLS_ALL)
+        return fail(h, ISRS_ERR_INVALID_ARG, "G_mci needs cell_set ISRS_CELLS_ALL");
     return ISRS_OK;
 }
 
@@ -403,6 +411,7 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     hs.val(q->G); hs.val(q->n_edges); hs.val(q->eps_v1); hs.val(q->cell_set);
     hs.val(fb->L_km); hs.val(fb->f_ref_THz); hs.val(fb->alpha_R_per_km);
     hs.val(h->tile_points);
+    hs.val(q->G_mci);
     hs.val(fb->profile);
     const double ode_h = q->ode_h_km > 0.0 ? q->ode_h_km : 0.25;
     if (fb->profile == ISRS_PROFILE_RAMAN_ODE) {
@@ -456,7 +465,13 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     }
     g->total_plan_ch = (int)frel.size();
 
-    // pieces per plan and CUT
+    // pieces per plan and CUT (with a separate MCI grid only the SCI and XCI
+    // cells become pieces)
+    const bool mci = q->cell_set == ISRS_CELLS_ALL && q->G_mci > 0;
+    if (mci && fb->profile != ISRS_PROFILE_CLOSED_FORM)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "separate MCI grid needs the closed-form profile");
+    const int piece_cells = mci ? ISRS_CELLS_SCI_XCI : q->cell_set;
+    g->G_mci = mci ? q->G_mci : 0;
     std::vector<DevPiece> pieces;
     std::vector<std::vector<std::pair<int, int>>> cut_range(n_plans);   // per plan, per listed CUT
     for (int k = 0; k < n_plans; ++k) {
@@ -465,7 +480,7 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
         for (int s = 0; s < ncut; ++s) {
             const int i = cl.empty() ? s : cl[s];
             const int p0 = (int)pieces.size();
-            isrs_status st2 = cut_pieces(h, &plans[k], k, i, q->cell_set, pieces);
+            isrs_status st2 = cut_pieces(h, &plans[k], k, i, piece_cells, pieces);
             if (st2 != ISRS_OK) return st2;
             cut_range[k].push_back({p0, (int)pieces.size()});
         }
@@ -486,14 +501,33 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
             tmax = std::max(tmax, 4.0 * pi * pi * v1 * br * fb->L_km / (2.0 * pi));
         }
         g->phase_rev_max = tmax;
+        // MCI cells: bound over the whole band of every plan
+        double tm = 0.0;
+        if (mci)
+            for (int k = 0; k < n_plans; ++k) {
+                const isrs_channels &c = plans[k];
+                const double flo = c.f_THz[0] - 0.5 * c.B_THz[0];
+                const double fhi = c.f_THz[c.n_ch - 1] + 0.5 * c.B_THz[c.n_ch - 1];
+                for (int i = 0; i < c.n_ch; ++i) {
+                    const double xm = std::max(fhi - c.f_THz[i], c.f_THz[i] - flo);
+                    const double fi = std::fabs(c.f_THz[i] - fb->f_ref_THz);
+                    const double v1 = xm * xm, s12 = 2.0 * xm;
+                    const double br = std::fabs(fb->beta2) + pi * std::fabs(fb->beta3) * (s12 + 2.0 * fi) +
+                                      2.0 * pi * pi / 3.0 * std::fabs(fb->beta4) *
+                                          (s12 * s12 + 1.5 * v1 + 3.0 * fi * s12 + 3.0 * fi * fi);
+                    tm = std::max(tm, 4.0 * pi * pi * v1 * br * fb->L_km / (2.0 * pi));
+                }
+            }
+        g->mci_phase_rev_max = tm;
     }
 
     // work items, output slots
     const int tile_pts = h->tile_points > 0 ? h->tile_points : (1 << 20);
     const int chunk = (int)std::max<int64_t>(1, tile_pts / G2);
-    std::vector<DevItem> items;
-    std::vector<int2> slot_items;
+    std::vector<DevItem> items, mitems;
+    std::vector<int2> slot_items, slot_items2;
     std::vector<int> slot_cut, prof_slot_off, item_slot;
+    const int mchunk = mci ? (int)std::max<int64_t>(1, tile_pts / ((int64_t)q->G_mci * q->G_mci)) : 1;
     g->n_points = 0;
     g->n_points_unfolded = 0;
     for (int p = 0; p < g->n_prof; ++p) {
@@ -518,11 +552,23 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
             }
             slot_items.push_back(make_int2(it0, (int)items.size()));
             slot_cut.push_back(i);
+            if (mci) {
+                // cells (a, b), a <= b, a, b != i: triangular index over n - 1 channels
+                const int n2 = plans[k].n_ch - 1;
+                const int ncell = n2 * (n2 + 1) / 2;
+                const int m0 = (int)mitems.size();
+                for (int t = 0; t < ncell; t += mchunk)
+                    mitems.push_back(DevItem{p, t, std::min(t + mchunk, ncell), i});
+                slot_items2.push_back(make_int2(m0, (int)mitems.size()));
+                g->n_points += (int64_t)ncell * q->G_mci * q->G_mci;
+                g->n_points_unfolded += (int64_t)n2 * n2 * q->G_mci * q->G_mci;
+            }
         }
     }
     prof_slot_off.push_back((int)slot_items.size());
     g->n_items = (int)items.size();
     g->n_slots = (int)slot_items.size();
+    g->n_mci_items = (int)mitems.size();
 
     std::vector<float4> za, zb;
     std::vector<double2> zd;
@@ -591,6 +637,10 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     UP(zs_b, zb);
     UP(zs_d, zd);
     UP(item_slot, item_slot);
+    if (mci) {
+        UP(mci_items, mitems);
+        UP(slot_items2, slot_items2);
+    }
     if (g->profile == ISRS_PROFILE_RAMAN_ODE) {
         UP(win_lo, wlo);
         UP(win_hi, whi);
@@ -608,7 +658,8 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
                           &old->plan_ch_off_d, &old->plan_n_d, &old->prof_ch_off_d, &old->prof_plan_d,
                           &old->ch_frel, &old->ch_B, &old->ch_alpha, &old->ch_gamma, &old->ch_nf,
                           &old->guard, &old->zs_a, &old->zs_b, &old->zs_d, &old->item_slot,
-                          &old->win_lo, &old->win_hi, &old->ch_scale, &old->half_steps};
+                          &old->win_lo, &old->win_hi, &old->ch_scale, &old->half_steps, &old->mci_items,
+                          &old->slot_items2};
         for (DevBuf *b : bufs) release(*b);
         h->cache.pop_back();
     }
@@ -624,7 +675,7 @@ void free_geom(Geom *g)
                       &g->plan_ch_off_d, &g->plan_n_d, &g->prof_ch_off_d, &g->prof_plan_d,
                       &g->ch_frel, &g->ch_B, &g->ch_alpha, &g->ch_gamma, &g->ch_nf,
                       &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->item_slot,
-                      &g->win_lo, &g->win_hi, &g->ch_scale, &g->half_steps};
+                      &g->win_lo, &g->win_hi, &g->ch_scale, &g->half_steps, &g->mci_items, &g->slot_items2};
     for (DevBuf *b : bufs) release(*b);
 }
 
@@ -702,6 +753,9 @@ QuadParams quad_params(isrs_handle h, const isrs_fibre *fb, Geom *g)
     qp.ab = g->profile == ISRS_PROFILE_RAMAN_ODE ? (const double2 *)h->ab.p : nullptr;
     qp.nc_max = g->nc_max;
     qp.path_count = (unsigned long long *)h->paths.p;
+    qp.plan_n = (const int *)g->plan_n_d.p;
+    qp.mci_n_max = 0;
+    for (int k = 0; k < g->n_plans; ++k) qp.mci_n_max = std::max(qp.mci_n_max, g->plan_n[k]);
     return qp;
 }
 
@@ -717,6 +771,13 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     if (precision == ISRS_PREC_FP32 && g->phase_rev_max > 2097152.0)
         return fail(h, ISRS_ERR_UNSUPPORTED, "phase range %.3g revolutions exceeds the FP32 reduction range",
                     g->phase_rev_max);
+    if (precision == ISRS_PREC_FP32 && g->mci_phase_rev_max > 536870912.0)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "MCI phase range %.3g revolutions exceeds the FP32 reduction range",
+                    g->mci_phase_rev_max);
+    if (adjoint && g->n_mci_items > 0)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "the adjoint does not cover the separate MCI grid");
+    if (g->n_mci_items > 0 && (s = ensure(h, h->partial_mci, sizeof(double) * g->n_mci_items)) != ISRS_OK)
+        return s;
     if ((s = ensure(h, h->pd_d, sizeof(double) * g->total_prof_ch)) != ISRS_OK) return s;
     if ((s = ensure(h, h->pd_f, sizeof(float) * g->total_prof_ch)) != ISRS_OK) return s;
     if ((s = ensure(h, h->lnrho_L, sizeof(double) * g->total_prof_ch)) != ISRS_OK) return s;
@@ -791,11 +852,23 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
         if ((s = mark(h, 0, 0, st)) != ISRS_OK) return s;
         if (g->n_items > 0) CK(tab ? launch_quad_tab(qp, precision, grid, block, st)
                                    : launch_quad(qp, precision, grid, block, st));
+        if (g->n_mci_items > 0) {
+            QuadParams qm = qp;
+            qm.items = (const DevItem *)g->mci_items.p;
+            qm.n_items = g->n_mci_items;
+            qm.G = g->G_mci;
+            qm.partial = (double *)h->partial_mci.p;
+            qm.counter = (int *)h->counter.p + 1;
+            int mgrid = h->num_sms * quad_mci_blocks_per_sm(precision, M, qm.mci_n_max, block);
+            if (g->n_mci_items < mgrid) mgrid = g->n_mci_items;
+            CK(launch_quad_mci(qm, precision, mgrid, block, st));
+        }
         if ((s = mark(h, 0, 1, st)) != ISRS_OK) return s;
     }
     h->last_points = g->n_points;
     h->last_psteps = g->n_points * (int64_t)M;
-    h->last_launches = g->profile == ISRS_PROFILE_RAMAN_ODE ? 3 : 2;   // prep (+ Raman ODE) + quadrature
+    h->last_launches = (g->profile == ISRS_PROFILE_RAMAN_ODE ? 3 : 2) +   // prep (+ Raman ODE) + quadrature
+                       (g->n_mci_items > 0 ? 1 : 0);                       // + MCI cells
     return ISRS_OK;
 }
 
@@ -814,6 +887,10 @@ isrs_status run_finish(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, 
     std::memset(&fp, 0, sizeof(fp));
     fp.partial = (const double *)h->partial.p;
     fp.slot_items = (const int2 *)g->slot_items.p;
+    if (g->n_mci_items > 0) {
+        fp.partial2 = (const double *)h->partial_mci.p;
+        fp.slot_items2 = (const int2 *)g->slot_items2.p;
+    }
     fp.slot_cut = (const int *)g->slot_cut.p;
     fp.prof_slot_off = (const int *)g->prof_slot_off.p;
     fp.prof_plan = (const int *)g->prof_plan_d.p;
@@ -892,7 +969,7 @@ std::vector<void *> workspace_ptrs(isrs_handle h)
 {
     return {h->P.p, h->pd_d.p, h->pd_f.p, h->lnrho_L.p, h->step_d.p, h->step_f.p, h->ptot.p, h->partial.p,
             h->counter.p, h->paths.p, h->kapL.p, h->o_sigma.p, h->o_pnli.p, h->o_eta.p, h->o_snr.p, h->o_pase.p, h->o_T.p,
-            h->ab.p};
+            h->ab.p, h->partial_mci.p};
 }
 
 isrs_status run_batched_graph(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
@@ -1097,7 +1174,7 @@ isrs_status isrs_destroy(isrs_handle h)
     DevBuf *bufs[] = {&h->P, &h->pd_d, &h->pd_f, &h->step_d, &h->step_f, &h->lnrho_L, &h->ptot, &h->partial,
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
                       &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP, &h->ab, &h->ode_y, &h->gAB, &h->gV,
-                      &h->gAt};
+                      &h->gAt, &h->partial_mci};
     for (DevBuf *b : bufs) release(*b);
     release(h->paths);
     release(h->kapL);
@@ -1305,6 +1382,8 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
     if (quad->precision != ISRS_PREC_FP32)
         return fail(h, ISRS_ERR_INVALID_ARG, "the gradient is the adjoint of the FP32 path");
     if (quad->n_edges - 1 > 128) return fail(h, ISRS_ERR_UNSUPPORTED, "gradient supports at most 128 z-steps");
+    if (quad->G_mci > 0)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "the gradient does not cover the separate MCI grid");
     if (fibre->profile == ISRS_PROFILE_RAMAN_ODE && ch->n_ch > kMaxRamanGradCh)
         return fail(h, ISRS_ERR_UNSUPPORTED, "Raman-ODE gradient supports at most %d channels", kMaxRamanGradCh);
     if (ch->guard)
@@ -1418,6 +1497,7 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
         return ISRS_ERR_INVALID_ARG;
     if (fibre->n_spans > 1) return ISRS_ERR_UNSUPPORTED;         // single span only
     if (fibre->profile != ISRS_PROFILE_CLOSED_FORM) return ISRS_ERR_UNSUPPORTED;   // closed-form profile only
+    if (quad->G_mci > 0) return ISRS_ERR_UNSUPPORTED;                             // one grid for every cell
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ISRS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

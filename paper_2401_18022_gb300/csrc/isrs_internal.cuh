@@ -86,6 +86,10 @@ struct QuadParams {
     // (prof_ch_off[prof] + c) * n_steps + m.  Null for the closed-form profile.
     const double2 *ab;
     int nc_max;                 // largest F_c candidate count of any piece
+    // multi-channel-interference cells (k_quad_mci_*): items are cell ranges
+    // of one CUT (DevItem.piece0/piece1 = triangular cell indices), G = G_mci
+    const int *plan_n;          // channels per plan
+    int mci_n_max;              // largest plan
 };
 
 }  // namespace isrs

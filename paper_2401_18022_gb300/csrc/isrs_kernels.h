@@ -26,6 +26,8 @@ struct PrepParams {
 struct FinishParams {
     const double *partial;
     const int2 *slot_items;     // per output slot: item range
+    const double *partial2;     // MCI cell items (nullable)
+    const int2 *slot_items2;    // per output slot: MCI item range (nullable)
     const int *slot_cut;        // per output slot: plan-local CUT index
     const int *prof_slot_off;   // [n_prof + 1]
     const int *prof_plan, *plan_ch_off, *prof_ch_off;
@@ -131,6 +133,10 @@ size_t quad_tab_smem_bytes(int precision, int n_steps, int G, int nc_max);
 int quad_tab_blocks_per_sm(int precision, int n_steps, int G, int nc_max, int block);
 cudaError_t launch_quad_tab(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
 cudaError_t launch_finish(const FinishParams &fp, int n_prof, cudaStream_t st);
+// MCI cells with their own grid (closed-form profile)
+size_t quad_mci_smem_bytes(int precision, int n_steps, int n_max);
+int quad_mci_blocks_per_sm(int precision, int n_steps, int n_max, int block);
+cudaError_t launch_quad_mci(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
 size_t adjoint_smem_bytes(int n_steps, int G, int block);
 int adjoint_blocks_per_sm(int n_steps, int G, int block);
 cudaError_t launch_adjoint(const AdjParams &ap, int grid, int block, cudaStream_t st);

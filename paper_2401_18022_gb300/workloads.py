@@ -115,6 +115,7 @@ class Workload:
     n_edges: int = 113              # z-grid edges (n_edges - 1 steps)
     eps_v1: float = 1e-10           # lower cut-off of upsilon1 (relative)
     cell_set: int = CELLS_SCI_XCI
+    G_mci: int = 0                  # with CELLS_ALL: grid of the MCI cells (a, b != CUT); 0 = G
     snr_trx_dB: float = 0.0         # <= 0: no transceiver noise
     guard: Optional[np.ndarray] = None
     n_spans: int = 1                # identical spans, launch profile restored per span
