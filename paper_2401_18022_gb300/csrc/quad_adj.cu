@@ -14,10 +14,13 @@
 //
 // k_quad_adj evaluates the forward sum and these buckets in one pass over the
 // grid.  Pass 1 (one grid point per lane) forms S as the forward kernel does.
-// Pass 2 turns the warp around: every lane owns a block of K consecutive
-// steps (their tables live in registers) and the warp walks its 32 points,
-// broadcasting each point's state by shuffles, so bucket sums over points
-// need neither atomics nor shared-memory traffic per step.
+// Pass 2 turns the warp around on half-warps: each of the 16 lanes of a half
+// owns a block of K = ceil(M/16) consecutive steps (so 16 K covers the M
+// steps with little waste; 112 = 16 x 7), the two halves take two of the
+// warp's 32 staged points per iteration, and every lane accumulates its own
+// steps' buckets in registers: bucket sums over points need neither atomics
+// nor per-step shared-memory traffic, and the per-point set-up is shared by
+// K steps.
 #include <cuda_runtime.h>
 
 #include "isrs_internal.cuh"
@@ -106,15 +109,16 @@ __device__ __forceinline__ void zsum_tele_c(float phi, float Fc, float at, const
 // ---------------------------------------------------------------------------
 // k_quad_adj<K>: fused forward + adjoint, persistent over work tiles of one
 // profile.  Pass 1: lane = grid point.  Pass 2: lane l owns steps
-// [K l, K l + K); the warp walks its 32 points, whose state pass 1 staged in
-// shared memory (two broadcast 128-bit loads per point).  The owned step
-// tables and the lane buckets live in registers only during pass 2 (a
-// lane-contiguous shared copy of the tables; FP32 shared bucket accumulators
-// folded into FP64 every 8 batches), so pass 1 runs at forward-like register
-// pressure.
+// [K (l mod 16), K (l mod 16) + K); half-warp h walks the points 2j + h of
+// the 32 that pass 1 staged in shared memory (two 128-bit loads per point).
+// The owned step tables are read from a lane-contiguous shared copy
+// (conflict-free, both halves broadcast), which keeps the kernel at 80
+// registers and 3 resident blocks per SM; lane buckets accumulate in
+// registers, go to FP32 shared accumulators per batch and are folded into
+// FP64 every 8 batches; the two halves' buckets meet in the tile reduction.
 // ---------------------------------------------------------------------------
 #ifndef ISRS_ADJ_MIN_BLOCKS
-#define ISRS_ADJ_MIN_BLOCKS 2   // resident blocks per SM the register budget is sized for
+#define ISRS_ADJ_MIN_BLOCKS 3   // resident blocks per SM the register budget is sized for
 #endif
 
 constexpr int kOwnFields = 8;   // A2d, A2, K2, z, c, dz, edge hi, edge lo
@@ -133,11 +137,11 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     float4 *sPs = reinterpret_cast<float4 *>(rows + G);       // [nw][32][2] staged point states
     double2 *sB = reinterpret_cast<double2 *>(sPs + nw * 64); // [nw][K][32] FP64 step buckets
     float2 *sF = reinterpret_cast<float2 *>(sB + nw * K * 32);    // [nw][K][32] FP32 step buckets
-    float *sO = reinterpret_cast<float *>(sF + nw * K * 32);      // [kOwnFields][K][32] owned tables
+    float *sO = reinterpret_cast<float *>(sF + nw * K * 32);      // [kOwnFields][K][16] owned tables
     __shared__ PieceConst<float> kc;
     __shared__ ChebTab ct;
     __shared__ float sVc[kMaxCand];
-    __shared__ float sE0[2][32];                              // first edge of each lane's block
+    __shared__ float sE0[2][16];                              // first edge of each lane's block
     __shared__ double scratch[32];
     __shared__ int s_item;
 
@@ -163,7 +167,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     const float phi_small = 0.02f / qp.L;
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
-    const int m0 = lane * K;
+    // pass 2 runs on half-warps: lane l owns steps [K (l mod 16), K (l mod 16) + K)
+    const int l16 = lane & 15, half = lane >> 4;
+    const int m0 = l16 * K;
     float4 *myPs = sPs + warp * 64;
     float2 *myF = sF + warp * K * 32;
     double2 *myB = sB + warp * K * 32;
@@ -191,17 +197,17 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             }
             __syncthreads();
             // lane-contiguous copy of every lane's owned step tables
-            for (int t = threadIdx.x; t < K * 32; t += blockDim.x) {
-                const int k = t >> 5, l = t & 31, m = l * K + k;
+            for (int t = threadIdx.x; t < K * 16; t += blockDim.x) {
+                const int k = t >> 4, l = t & 15, m = l * K + k;
                 const bool ok = m < M;
                 const float4 a = ok ? sT[m] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float4 e = ok ? sE[m] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const float dz = ok ? sR[m].w : 0.0f;
                 const float vals[kOwnFields] = {a.x, e.z, a.y, a.z, a.w, dz, e.x, e.y};
 #pragma unroll
-                for (int f = 0; f < kOwnFields; ++f) sO[(f * K + k) * 32 + l] = vals[f];
+                for (int f = 0; f < kOwnFields; ++f) sO[(f * K + k) * 16 + l] = vals[f];
             }
-            if (threadIdx.x < 32) {
+            if (threadIdx.x < 16) {
                 const int l = threadIdx.x, mm = l * K;
                 sE0[0][l] = (mm > 0 && mm < M) ? sE[mm - 1].x : 0.0f;
                 sE0[1][l] = (mm > 0 && mm < M) ? sE[mm - 1].y : 0.0f;
@@ -284,23 +290,15 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 myPs[2 * lane + 1] = make_float4(q0, q1, q2, __int_as_float(path));
                 __syncwarp();
                 // ---- pass 2: the warp's 32 points, each lane on its own steps
-                float oA2d[K], oA2[K], oK2[K], oz[K], oc[K], odz[K], oeh[K], oel[K];
                 float R[K], Rp[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    oA2d[k] = sO[(0 * K + k) * 32 + lane];
-                    oA2[k] = sO[(1 * K + k) * 32 + lane];
-                    oK2[k] = sO[(2 * K + k) * 32 + lane];
-                    oz[k] = sO[(3 * K + k) * 32 + lane];
-                    oc[k] = sO[(4 * K + k) * 32 + lane];
-                    odz[k] = sO[(5 * K + k) * 32 + lane];
-                    oeh[k] = sO[(6 * K + k) * 32 + lane];
-                    oel[k] = sO[(7 * K + k) * 32 + lane];
                     R[k] = 0.0f;
                     Rp[k] = 0.0f;
                 }
-                const float e0h = sE0[0][lane], e0l = sE0[1][lane];
-                for (int p = 0; p < 32; ++p) {
+                const float e0h = sE0[0][l16], e0l = sE0[1][l16];
+                for (int pp = 0; pp < 16; ++pp) {
+                    const int p = 2 * pp + half;           // the two half-warps take two points
                     const float4 st0 = myPs[2 * p];
                     const float cp = st0.x;
                     if (cp == 0.0f) continue;
@@ -316,10 +314,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
                             if (m0 + k < M) {
-                                float lp = fmaf(oK2[k], fc, oA2d[k]);
-                                lp = fmaf(-a_t, oz[k], lp);
+                                float lp = fmaf(sO[(2 * K + k) * 16 + l16], fc, sO[(0 * K + k) * 16 + l16]);
+                                lp = fmaf(-a_t, sO[(3 * K + k) * 16 + l16], lp);
                                 const float w = ex2_approx(lp);
-                                const float rr = w * fmaf(al2, oz[k], fmaf(al1, oc[k], al0));
+                                const float rr = w * fmaf(al2, sO[(3 * K + k) * 16 + l16], fmaf(al1, sO[(4 * K + k) * 16 + l16], al0));
                                 R[k] = fmaf(cp, rr, R[k]);
                                 Rp[k] = fmaf(cF, rr, Rp[k]);
                             }
@@ -332,10 +330,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         for (int k = 0; k < K; ++k) {
                             if (m0 + k < M) {
                                 float sn, cs;
-                                sincos_rev(phr * oz[k], sn, cs);
-                                float lp = fmaf(oK2[k], fc, oA2d[k]);
-                                lp = fmaf(-a_t, oz[k], lp);
-                                const float amp = ex2_approx(lp) * sinc_poly(hph * odz[k]);
+                                sincos_rev(phr * sO[(3 * K + k) * 16 + l16], sn, cs);
+                                float lp = fmaf(sO[(2 * K + k) * 16 + l16], fc, sO[(0 * K + k) * 16 + l16]);
+                                lp = fmaf(-a_t, sO[(3 * K + k) * 16 + l16], lp);
+                                const float amp = ex2_approx(lp) * sinc_poly(hph * sO[(5 * K + k) * 16 + l16]);
                                 const float rr = 2.0f * amp * fmaf(p0, cs, p1 * sn);
                                 R[k] = fmaf(cp, rr, R[k]);
                                 Rp[k] = fmaf(cF, rr, Rp[k]);
@@ -350,9 +348,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         for (int k = 0; k < K; ++k) {
                             if (m0 + k < M) {
                                 float sn, cs;
-                                phasor_rev_ff(ph, oeh[k], oel[k], sn, cs);
-                                float lp = fmaf(oK2[k], fc, oA2[k]);
-                                lp = fmaf(-a_t, oz[k], lp);
+                                phasor_rev_ff(ph, sO[(6 * K + k) * 16 + l16], sO[(7 * K + k) * 16 + l16], sn, cs);
+                                float lp = fmaf(sO[(2 * K + k) * 16 + l16], fc, sO[(1 * K + k) * 16 + l16]);
+                                lp = fmaf(-a_t, sO[(3 * K + k) * 16 + l16], lp);
                                 const float pm = ex2_approx(lp);
                                 const float rr = g * pm * fmaf(p0, cs - Er, p1 * (sn - Ei));
                                 R[k] = fmaf(cp, rr, R[k]);
@@ -417,10 +415,12 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             const int ln = m / K, kk = m - ln * K;
             double rx = 0.0, ry = 0.0;
             for (int w = 0; w < nw; ++w) {
-                double2 &b = sB[(w * K + kk) * 32 + ln];
-                rx += b.x;
-                ry += b.y;
-                b = make_double2(0.0, 0.0);
+                for (int h = 0; h < 2; ++h) {
+                    double2 &b = sB[(w * K + kk) * 32 + ln + 16 * h];
+                    rx += b.x;
+                    ry += b.y;
+                    b = make_double2(0.0, 0.0);
+                }
             }
             ap.item_R[(size_t)it * M + m] = make_double2(rx, ry);
         }
@@ -562,9 +562,9 @@ __global__ void __launch_bounds__(256) k_chain(ChainParams cp)
 // ---------------------------------------------------------------------------
 size_t adjoint_smem_bytes(int n_steps, int G, int block)
 {
-    const int K = (n_steps + 31) / 32, nw = block / 32;
+    const int K = (n_steps + 15) / 16, nw = block / 32;
     return (size_t)n_steps * 3 * sizeof(float4) + (size_t)G * sizeof(RowF) + (size_t)nw * 64 * sizeof(float4) +
-           (size_t)nw * K * 32 * (sizeof(double2) + sizeof(float2)) + (size_t)kOwnFields * K * 32 * sizeof(float);
+           (size_t)nw * K * 32 * (sizeof(double2) + sizeof(float2)) + (size_t)kOwnFields * K * 16 * sizeof(float);
 }
 
 template <int K>
@@ -575,12 +575,16 @@ static void *adj_fn()
 
 static void *adj_kernel_for(int n_steps)
 {
-    const int K = (n_steps + 31) / 32;
+    const int K = (n_steps + 15) / 16;
     switch (K) {
     case 1: return adj_fn<1>();
     case 2: return adj_fn<2>();
     case 3: return adj_fn<3>();
     case 4: return adj_fn<4>();
+    case 5: return adj_fn<5>();
+    case 6: return adj_fn<6>();
+    case 7: return adj_fn<7>();
+    case 8: return adj_fn<8>();
     }
     return nullptr;
 }
