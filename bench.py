@@ -223,8 +223,8 @@ def run_gpu(args):
     # the z-sum form the point took: direct 3 (sin, cos, exp), telescoped 3
     # (sin, cos of the edge phasor, exp), small-phase 0 (its moments are
     # contracted once per piece and channel: ~nc x 112 exps per 65,536 points).
-    # The fused adjoint repeats the direct/telescoped work in pass 2 and
-    # evaluates the small-phase step terms there (1 exp per step).
+    # The fused adjoint repeats the direct/telescoped work in pass 2; its
+    # small-phase points use contracted moment sums there too (no per-step work).
     quad_ms = float(np.mean(quad_ms))
     if use_grad:
         _fwd_point_steps(eng, wl, P)
@@ -232,7 +232,7 @@ def run_gpu(args):
     n_steps = wl.n_edges - 1
     sfu_ops = n_steps * 3 * (paths["direct"] + paths["telescoped"])
     if use_grad:
-        sfu_ops = 2 * sfu_ops + n_steps * paths["small"]
+        sfu_ops = 2 * sfu_ops
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sfu_peak = N_SMS * SFU_PER_CLK_PER_SM * sm_max * 1e6 / 1e12       # Tops/s

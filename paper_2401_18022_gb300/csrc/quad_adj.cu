@@ -20,7 +20,11 @@
 // warp's 32 staged points per iteration, and every lane accumulates its own
 // steps' buckets in registers: bucket sums over points need neither atomics
 // nor per-step shared-memory traffic, and the per-point set-up is shared by
-// K steps.
+// K steps.  Small-phase points whose moments come from the Chebyshev
+// contraction skip pass 2: their bucket terms w_m (al0 + al1 c_m + al2 z_m)
+// are expanded in the same Chebyshev series in the point's in-channel
+// coordinate, so per F_c candidate only 15 point sums are kept (warp
+// shuffles per batch) and turned into per-step terms once per piece.
 #include <cuda_runtime.h>
 
 #include "isrs_internal.cuh"
@@ -122,6 +126,15 @@ __device__ __forceinline__ void zsum_tele_c(float phi, float Fc, float at, const
 #endif
 
 constexpr int kOwnFields = 8;   // A2d, A2, K2, z, c, dz, edge hi, edge lo
+constexpr int kCtr = 4;         // F_c candidates whose small-phase points are contracted
+constexpr int kCtrN = 15;       // per candidate: 3 weights x T_0..T_4
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
 
 template <int K>
 __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams ap)
@@ -144,8 +157,15 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     __shared__ float sE0[2][16];                              // first edge of each lane's block
     __shared__ double scratch[32];
     __shared__ int s_item;
+    // small-phase points of contracted candidates: per-warp moment sums, their
+    // block totals, and the per-step bucket terms they give for the tile
+    __shared__ double sY[8][kCtr][kCtrN];
+    __shared__ double sYt[kCtr][kCtrN];
+    __shared__ double2 sC[128];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < 8 * kCtr * kCtrN; t += blockDim.x) (&sY[0][0][0])[t] = 0.0;
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) sC[t] = make_double2(0.0, 0.0);
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         const float4 za = qp.zs_a[m];
         const float4 zb = qp.zs_b[m];
@@ -234,6 +254,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 const int q = qb + lane;
                 float phi = 0.0f, Fc = 0.0f, at = 0.0f, cpt = 0.0f, q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
                 int path = 0;
+                bool ctr = false;            // contracted small-phase point
+                int ci_c = -1;
+                float cx = 0.0f;
                 if (q < npts) {
                     const int r = (int)(((float)q + 0.5f) * invG);
                     const int j = q - r * G;
@@ -259,8 +282,16 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                             float S2;
                             if (aphi <= phi_small) {
                                 path = kPathSmall;
-                                if (cheb) cheb_moments(ct, ci, u, q0, q1, q2);
-                                else zsum_small_m(phi, Fc, at, sT, M, q0, q1, q2);
+                                if (cheb) {
+                                    cheb_moments(ct, ci, u, q0, q1, q2);
+                                    if (ci < kCtr) {
+                                        ctr = true;
+                                        ci_c = ci;
+                                        cx = (u - ct.mid[ci]) * ct.invh[ci];
+                                    }
+                                } else {
+                                    zsum_small_m(phi, Fc, at, sT, M, q0, q1, q2);
+                                }
                                 S2 = fmaf(-phi * phi, fmaf(q0, q2, -q1 * q1), q0 * q0);
                             } else if (aphi <= phi_direct) {
                                 path = kPathDirect;
@@ -285,6 +316,36 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                             cpt = mult * rw.w * W * af;
                         }
                     }
+                }
+                // Contracted small-phase points: d|S|^2/d ln p_m = w_m (al0 + al1 c_m
+                // + al2 z_m) with w_m = base_m e^{a_m x} = base_m sum_n b_n(a_m) T_n(x),
+                // so their bucket terms need only the sums of cp al_j T_n(x) per
+                // candidate (n <= 4 for the F_c-weighted bucket, x T_n = (T_{n+1} +
+                // T_{|n-1|})/2).  They are summed over the warp here and turned into
+                // per-step terms once per piece; pass 2 skips these points.
+                unsigned cmask = __ballot_sync(kFull, ctr);
+                if (cmask) {
+                    const float T2 = fmaf(2.0f * cx, cx, -1.0f);
+                    const float T3 = fmaf(2.0f * cx, T2, -cx);
+                    const float T4 = fmaf(2.0f * cx, T3, -T2);
+                    const float Tn[5] = {1.0f, cx, T2, T3, T4};
+                    const float ph2 = phi * phi;
+                    const float al[3] = {2.0f * q0 - ph2 * q2, -ph2 * q0, 2.0f * ph2 * q1};
+                    while (cmask) {
+                        const int cl = __shfl_sync(kFull, ci_c, __ffs(cmask) - 1);
+                        const bool mine = ctr && ci_c == cl;
+                        const float cw = mine ? cpt : 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                            for (int n = 0; n < 5; ++n) {
+                                const float v = warp_sum_f(cw * al[j] * Tn[n]);
+                                if (lane == 0) sY[warp][cl][j * 5 + n] += (double)v;
+                            }
+                        }
+                        cmask &= ~__ballot_sync(kFull, mine);
+                    }
+                    if (ctr) cpt = 0.0f;
                 }
                 myPs[2 * lane] = make_float4(cpt, phi, Fc, at);
                 myPs[2 * lane + 1] = make_float4(q0, q1, q2, __int_as_float(path));
@@ -391,6 +452,45 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             }
             // piece totals: the forward sum and the PSD buckets V_ij
             const double ptot = block_sum_d((double)sum - (double)comp, scratch);
+            if (cheb) {
+                // contracted small-phase terms of this piece -> per-step tile buckets
+                const int ncc = min(kc.nc, kCtr);
+                for (int t = threadIdx.x; t < ncc * kCtrN; t += blockDim.x) {
+                    const int c = t / kCtrN, e = t - c * kCtrN;
+                    double y = 0.0;
+                    for (int w = 0; w < nw; ++w) {
+                        y += sY[w][c][e];
+                        sY[w][c][e] = 0.0;
+                    }
+                    sYt[c][e] = y;
+                }
+                __syncthreads();
+                const int coff = qp.plan_ch_off[pc.plan];
+                for (int m = threadIdx.x; m < M; m += blockDim.x) {
+                    const float4 a = sT[m];           // {A2 + log2 dz, K2, z, z^2 + dz^2/12}
+                    double rx = 0.0, ry = 0.0;
+                    for (int c = 0; c < ncc; ++c) {
+                        const double *Y = sYt[c];
+                        const double F0 = qp.ch_frel[coff + pc.c_lo + c];
+                        const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
+                        const double atc = (double)(kc.at_ab + kc.hat[c]);
+                        const double base = exp2((double)a.x - atc * (double)a.z + (double)a.y * F0);
+                        const double t = 0.5 * (double)a.y * h * 0.69314718055994530942, t2 = t * t;
+                        const double b0 = 1.0 + t2 * (1.0 + t2 * (0.25 + t2 / 36.0));                 // I0
+                        const double b1 = 2.0 * t * (1.0 + t2 * (0.5 + t2 / 12.0));                    // 2 I1
+                        const double b2 = 2.0 * t2 * (0.5 + t2 * (1.0 / 6.0 + t2 / 48.0));             // 2 I2
+                        const double b3 = 2.0 * t2 * t * (1.0 / 6.0 + t2 * (1.0 / 24.0 + t2 / 240.0)); // 2 I3
+                        double Q[5];
+                        for (int n = 0; n < 5; ++n) Q[n] = Y[n] + (double)a.w * Y[5 + n] + (double)a.z * Y[10 + n];
+                        const double rs = b0 * Q[0] + b1 * Q[1] + b2 * Q[2] + b3 * Q[3];
+                        const double xs = b0 * Q[1] + 0.5 * (b1 * (Q[2] + Q[0]) + b2 * (Q[3] + Q[1]) + b3 * (Q[4] + Q[2]));
+                        rx += base * rs;
+                        ry += base * (F0 * rs + h * xs);
+                    }
+                    sC[m].x += rx;
+                    sC[m].y += ry;
+                }
+            }
             const double t0 = block_sum_d((double)v0, scratch);
             const double t1 = block_sum_d((double)v1, scratch);
             const double t2 = block_sum_d((double)v2, scratch);
@@ -422,7 +522,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                     b = make_double2(0.0, 0.0);
                 }
             }
-            ap.item_R[(size_t)it * M + m] = make_double2(rx, ry);
+            ap.item_R[(size_t)it * M + m] = make_double2(rx + sC[m].x, ry + sC[m].y);
+            sC[m] = make_double2(0.0, 0.0);
         }
     }
 }
