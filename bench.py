@@ -238,8 +238,11 @@ def run_gpu(args):
     sfu_peak = N_SMS * SFU_PER_CLK_PER_SM * sm_max * 1e6 / 1e12       # Tops/s
     achieved = sfu_ops / (quad_ms / 1e3) / 1e12
     tot_pts = max(1, sum(paths.values()))
+    traffic = (ADJ_DRAM_CAPTURE["bytes"] * n_eval / ADJ_DRAM_CAPTURE["points"]) if use_grad else None
     roof = {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Tops/s (SFU: sin, cos, ex2)",
-            "frac": achieved / sfu_peak, "traffic": None,
+            "frac": achieved / sfu_peak, "traffic": traffic,
+            "traffic_note": ("DRAM bytes per launch, scaled by evaluated points from an ncu capture of the "
+                             "148-ch G=256 case (profiles/k_quad_adj_uwb148_every4th_G256.md)") if use_grad else None,
             "kernel": "k_quad_adj" if use_grad else "k_quad_f32", "kernel_ms": quad_ms,
             "sfu_ops_per_launch": sfu_ops,
             "path_fraction": {k: v / tot_pts for k, v in paths.items()},
@@ -289,6 +292,14 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
     t = float(np.median(ms))
     return {"ms": t, "grid_pts_per_s": n_grid / (t / 1e3), "kernel": "k_quad_f32",
             "kernel_ms": eng.last_kernel_ms(0)}
+
+
+# DRAM bytes of one k_quad_adj launch from an ncu capture of the 148-ch
+# profiling case (--profile-case adjoint256; dram__bytes.sum.per_second x
+# gpu__time_duration), and the points that launch evaluated.  The kernel reads
+# the piece list and writes one bucket row per tile, both proportional to the
+# evaluated points at fixed G, so a full launch's traffic is scaled by points.
+ADJ_DRAM_CAPTURE = {"bytes": 4.278e6, "points": 2880700416}
 
 
 def _timed(fn, dev, reps: int = 2):
