@@ -223,16 +223,14 @@ def run_gpu(args):
     # the z-sum form the point took: direct 3 (sin, cos, exp), telescoped 3
     # (sin, cos of the edge phasor, exp), small-phase 0 (its moments are
     # contracted once per piece and channel: ~nc x 112 exps per 65,536 points).
-    # The fused adjoint repeats the direct/telescoped work in pass 2; its
-    # small-phase points use contracted moment sums there too (no per-step work).
+    # The fused adjoint evaluates each step term once and keeps it in registers
+    # for the bucket terms, so its algorithmic SFU work equals the forward's.
     quad_ms = float(np.mean(quad_ms))
     if use_grad:
         _fwd_point_steps(eng, wl, P)
     paths = eng.last_path_counts()
     n_steps = wl.n_edges - 1
     sfu_ops = n_steps * 3 * (paths["direct"] + paths["telescoped"])
-    if use_grad:
-        sfu_ops = 2 * sfu_ops
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sfu_peak = N_SMS * SFU_PER_CLK_PER_SM * sm_max * 1e6 / 1e12       # Tops/s
@@ -299,7 +297,7 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
 # gpu__time_duration), and the points that launch evaluated.  The kernel reads
 # the piece list and writes one bucket row per tile, both proportional to the
 # evaluated points at fixed G, so a full launch's traffic is scaled by points.
-ADJ_DRAM_CAPTURE = {"bytes": 4.278e6, "points": 2880700416}
+ADJ_DRAM_CAPTURE = {"bytes": 4.281e6, "points": 2880700416}
 
 
 def _timed(fn, dev, reps: int = 2):

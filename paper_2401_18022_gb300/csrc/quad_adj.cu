@@ -13,18 +13,18 @@
 //   V_ij  = sum_points w W |S|^2 (number of j among the point's a, b, c).
 //
 // k_quad_adj evaluates the forward sum and these buckets in one pass over the
-// grid.  Pass 1 (one grid point per lane) forms S as the forward kernel does.
-// Pass 2 turns the warp around on half-warps: each of the 16 lanes of a half
-// owns a block of K = ceil(M/16) consecutive steps (so 16 K covers the M
-// steps with little waste; 112 = 16 x 7), the two halves take two of the
-// warp's 32 staged points per iteration, and every lane accumulates its own
-// steps' buckets in registers: bucket sums over points need neither atomics
-// nor per-step shared-memory traffic, and the per-point set-up is shared by
-// K steps.  Small-phase points whose moments come from the Chebyshev
-// contraction skip pass 2: their bucket terms w_m (al0 + al1 c_m + al2 z_m)
-// are expanded in the same Chebyshev series in the point's in-channel
-// coordinate, so per F_c candidate only 15 point sums are kept (warp
-// shuffles per batch) and turned into per-step terms once per piece.
+// grid, and every step term of Eq. slow_vary is evaluated once.  A warp first
+// takes 32 grid points, one per lane, for their geometry, phase and z-sum
+// form.  Small-phase points whose moments come from the Chebyshev contraction
+// are finished there: their bucket terms w_m (al0 + al1 c_m + al2 z_m) are
+// expanded in the same Chebyshev series in the point's in-channel coordinate,
+// so per F_c candidate only 15 point sums are kept and turned into per-step
+// terms once per piece.  The other points join one list per z-sum form and
+// are walked two at a time on half-warps: each of the 16 lanes of a half owns
+// K = ceil(M/16) consecutive steps (112 = 16 x 7), computes their terms t_m
+// into registers, the half sums them with shuffles into S, and the same
+// registers give d|S|^2/d ln p_m = 2 Re(conj(S) t_m) for the lane's own step
+// buckets, which stay in registers between FP64 folds.
 #include <cuda_runtime.h>
 
 #include "isrs_internal.cuh"
@@ -36,105 +36,203 @@ namespace isrs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kPathSmall = 0, kPathDirect = 1, kPathTele = 2;
-
-// Pass-1 z-sums that keep the quantities the derivative needs.
-//   small:  M0, M1, M2 with |S|^2 = M0^2 - phi^2 (M0 M2 - M1^2)
-//   direct: S
-//   tele:   U = sum_m p_m (E_{m+1} - E_m) with |S|^2 = |U|^2 / phi^2
-__device__ __forceinline__ void zsum_small_m(float phi, float Fc, float at, const float4 *sT, int M,
-                                             float &M0, float &M1, float &M2)
-{
-    M0 = 0.0f; M1 = 0.0f; M2 = 0.0f;
-#pragma unroll 4
-    for (int m = 0; m < M; ++m) {
-        const float4 a = sT[m];
-        float lp = fmaf(a.y, Fc, a.x);
-        lp = fmaf(-at, a.z, lp);
-        const float w = ex2_approx(lp);
-        M0 += w;
-        M1 = fmaf(w, a.z, M1);
-        M2 = fmaf(w, a.w, M2);
-    }
-}
+constexpr int kClsSmall = 0, kClsDirect = 1, kClsTele = 2;
+constexpr int kListCap = 34;    // a form's list: one carried point + 32 new (+1 pad)
+constexpr int kCtr = 4;         // F_c candidates whose small-phase points are contracted
+constexpr int kCtrN = 15;       // per candidate: 3 weights x T_0..T_4
+constexpr int kFoldBatches = 8; // batches between FP64 folds of the FP32 accumulators
+constexpr float kPadLog2 = -1000.0f;   // log2 weight of the padding steps (ex2 -> 0)
 
 __device__ __forceinline__ float sinc_poly(float x)
 {
     const float x2 = x * x;
-    float sc = fmaf(x2, -2.5052108e-8f, 2.7557319e-6f);
-    sc = fmaf(x2, sc, -1.9841270e-4f);
-    sc = fmaf(x2, sc, 8.3333333e-3f);
-    sc = fmaf(x2, sc, -1.6666667e-1f);
+    float sc = fmaf(x2, -2.5052108e-8f, 2.7557319e-6f);   // -1/11!, 1/9!
+    sc = fmaf(x2, sc, -1.9841270e-4f);                     // -1/7!
+    sc = fmaf(x2, sc, 8.3333333e-3f);                      // 1/5!
+    sc = fmaf(x2, sc, -1.6666667e-1f);                     // -1/3!
     return fmaf(x2, sc, 1.0f);
 }
 
-__device__ __forceinline__ void zsum_direct_c(float phi, float Fc, float at, const float4 *sR, int M,
-                                              float &Sr, float &Si)
+// sum over the 16 lanes of each half-warp (both halves in step)
+__device__ __forceinline__ float half_sum(float v)
 {
-    Sr = 0.0f; Si = 0.0f;
-    const float hphi = 0.5f * phi;
-    const float phir = phi * 0.15915494309189535f;
-#pragma unroll 4
-    for (int m = 0; m < M; ++m) {
-        const float4 a = sR[m];
-        float sn, cs;
-        sincos_rev(phir * a.z, sn, cs);
-        float lp = fmaf(a.y, Fc, a.x);
-        lp = fmaf(-at, a.z, lp);
-        const float amp = ex2_approx(lp) * sinc_poly(hphi * a.w);
-        Sr = fmaf(amp, cs, Sr);
-        Si = fmaf(amp, sn, Si);
-    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o, 16);
+    return v;
 }
 
-__device__ __forceinline__ void zsum_tele_c(float phi, float Fc, float at, const float4 *sT,
-                                            const float4 *sE, int M, float &Ur, float &Ui)
+// ---------------------------------------------------------------------------
+// Half-warp walks of one grid point (state: weight w W af, phi, F_c - f_ref,
+// at).  Lane l16 owns steps [K l16, K l16 + K) with tables
+//   o0[k] = {A2 + log2 dz, K2, z, dz},  o1[k] = {edge/2pi hi, lo, A2, c}
+// (padding steps carry log2 weight -1000, so their terms vanish).  Each walk
+// adds the lane's bucket terms and returns the point's w W af |S|^2.
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ float walk_direct(const float4 *o0s, float wq, float ph, float fc, float at, float mult,
+                                             float (&R)[K], float (&Rp)[K])
 {
-    float Er = 1.0f, Ei = 0.0f;
-    Ur = 0.0f; Ui = 0.0f;
-#pragma unroll 4
-    for (int m = 0; m < M; ++m) {
-        const float4 e = sE[m];
-        const float zm = sT[m].z;
+    // S = sum_m p_m dz_m sinc(phi dz_m/2) e^{j phi z_m}; d|S|^2/d ln p_m = 2 Re(conj(S) t_m)
+    const float hph = 0.5f * ph;
+    const float phr = ph * 0.15915494309189535f;
+    float tr[K], ti[K];
+    float sr = 0.0f, si = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 o = o0s[k * 16];
         float sn, cs;
-        phasor_rev_ff(phi, e.x, e.y, sn, cs);
-        float lp = fmaf(e.w, Fc, e.z);
-        lp = fmaf(-at, zm, lp);
-        const float p = ex2_approx(lp);
-        Ur = fmaf(p, cs - Er, Ur);
-        Ui = fmaf(p, sn - Ei, Ui);
+        sincos_rev(phr * o.z, sn, cs);
+        float lp = fmaf(o.y, fc, o.x);
+        lp = fmaf(-at, o.z, lp);
+        const float amp = ex2_approx(lp) * sinc_poly(hph * o.w);
+        tr[k] = amp * cs;
+        ti[k] = amp * sn;
+        sr += tr[k];
+        si += ti[k];
+    }
+    sr = half_sum(sr);
+    si = half_sum(si);
+    const float c2 = 2.0f * mult * wq, c2F = c2 * fc;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float rr = fmaf(sr, tr[k], si * ti[k]);
+        R[k] = fmaf(c2, rr, R[k]);
+        Rp[k] = fmaf(c2F, rr, Rp[k]);
+    }
+    return wq * fmaf(sr, sr, si * si);
+}
+
+template <int K>
+__device__ __forceinline__ float walk_tele(const float4 *o0s, const float4 *o1s, int l16, float wq, float ph,
+                                           float fc, float at, float mult, float (&R)[K], float (&Rp)[K])
+{
+    // U = sum_m p_m (E_{m+1} - E_m), E_e = e^{j phi z_e}, |S|^2 = |U|^2/phi^2;
+    // d|S|^2/d ln p_m = 2 Re(conj(U) p_m (E_{m+1} - E_m)) / phi^2
+    float tr[K], ti[K];
+    float Er = 1.0f, Ei = 0.0f, p0 = 0.0f, e1r = 1.0f, e1i = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 a = o0s[k * 16];
+        const float4 b = o1s[k * 16];
+        float sn, cs;
+        phasor_rev_ff(ph, b.x, b.y, sn, cs);
+        float lp = fmaf(a.y, fc, b.z);
+        lp = fmaf(-at, a.z, lp);
+        const float pm = ex2_approx(lp);
+        if (k == 0) {
+            p0 = pm;
+            e1r = cs;
+            e1i = sn;
+            tr[0] = 0.0f;
+            ti[0] = 0.0f;
+        } else {
+            tr[k] = pm * (cs - Er);
+            ti[k] = pm * (sn - Ei);
+        }
         Er = cs;
         Ei = sn;
     }
+    // the lower edge of this lane's first step is the previous lane's last edge
+    float elr = __shfl_up_sync(kFull, Er, 1, 16);
+    float eli = __shfl_up_sync(kFull, Ei, 1, 16);
+    elr = l16 == 0 ? 1.0f : elr;
+    eli = l16 == 0 ? 0.0f : eli;
+    tr[0] = p0 * (e1r - elr);
+    ti[0] = p0 * (e1i - eli);
+    float ur = 0.0f, ui = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        ur += tr[k];
+        ui += ti[k];
+    }
+    ur = half_sum(ur);
+    ui = half_sum(ui);
+    const float iph2 = 1.0f / (ph * ph);
+    const float c2 = 2.0f * mult * wq * iph2, c2F = c2 * fc;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float rr = fmaf(ur, tr[k], ui * ti[k]);
+        R[k] = fmaf(c2, rr, R[k]);
+        Rp[k] = fmaf(c2F, rr, Rp[k]);
+    }
+    return wq * fmaf(ur, ur, ui * ui) * iph2;
+}
+
+template <int K>
+__device__ __forceinline__ float walk_small(const float4 *o0s, const float4 *o1s, float wq, float ph, float fc,
+                                            float at, float mult, float (&R)[K], float (&Rp)[K])
+{
+    // |S|^2 = M0^2 - phi^2 (M0 M2 - M1^2);
+    // d|S|^2/d ln p_m = w_m (2 M0 - phi^2 (M2 + M0 c_m - 2 M1 z_m))
+    float wk[K];
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 a = o0s[k * 16];
+        const float cm = o1s[k * 16].w;
+        float lp = fmaf(a.y, fc, a.x);
+        lp = fmaf(-at, a.z, lp);
+        wk[k] = ex2_approx(lp);
+        s0 += wk[k];
+        s1 = fmaf(wk[k], a.z, s1);
+        s2 = fmaf(wk[k], cm, s2);
+    }
+    s0 = half_sum(s0);
+    s1 = half_sum(s1);
+    s2 = half_sum(s2);
+    const float ph2 = ph * ph;
+    const float al0 = 2.0f * s0 - ph2 * s2, al1 = -ph2 * s0, al2 = 2.0f * ph2 * s1;
+    const float cp = mult * wq, cF = cp * fc;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float zm = o0s[k * 16].z;
+        const float cm = o1s[k * 16].w;
+        const float rr = wk[k] * fmaf(al2, zm, fmaf(al1, cm, al0));
+        R[k] = fmaf(cp, rr, R[k]);
+        Rp[k] = fmaf(cF, rr, Rp[k]);
+    }
+    return wq * fmaf(-ph2, fmaf(s0, s2, -s1 * s1), s0 * s0);
+}
+
+// Forward-sum bookkeeping of one walked point: lane 0 of each half adds the
+// point's value to its compensated sum and to its F_c candidate's PSD bucket.
+struct FwdAcc {
+    float sum, comp, v0, v1, v2, v3;
+};
+
+__device__ __forceinline__ void fwd_add(FwdAcc &a, float val, int ci, bool owner, float *sVc)
+{
+    const float vv = owner ? val : 0.0f;
+    const float y = vv - a.comp;
+    const float t = a.sum + y;
+    a.comp = (t - a.sum) - y;
+    a.sum = t;
+    a.v0 += ci == 0 ? vv : 0.0f;
+    a.v1 += ci == 1 ? vv : 0.0f;
+    a.v2 += ci == 2 ? vv : 0.0f;
+    a.v3 += ci == 3 ? vv : 0.0f;
+    if (owner && ci >= 4) atomicAdd(&sVc[ci], val);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // k_quad_adj<K>: fused forward + adjoint, persistent over work tiles of one
-// profile.  Pass 1: lane = grid point.  Pass 2: lane l owns steps
-// [K (l mod 16), K (l mod 16) + K); half-warp h walks the points 2j + h of
-// the 32 that pass 1 staged in shared memory (two 128-bit loads per point).
-// The owned step tables are read from a lane-contiguous shared copy
-// (conflict-free, both halves broadcast), which keeps the kernel at 80
-// registers and 3 resident blocks per SM; lane buckets accumulate in
-// registers, go to FP32 shared accumulators per batch and are folded into
-// FP64 every 8 batches; the two halves' buckets meet in the tile reduction.
+// profile.  Per batch of 32 grid points a warp
+//  1. classifies its points (one per lane); contracted small-phase points are
+//     finished here, the others are appended to the warp's list of their
+//     z-sum form (non-contracted small phase, direct, telescoped);
+//  2. walks every list two points at a time, one per half-warp, so both
+//     halves always run the same form; an odd point waits for the next batch
+//     (or, at the end of the piece, is walked beside a zero-weight copy).
+// The owned step tables are lane-contiguous float4 copies in shared memory
+// (conflict-free, both halves broadcast).  Lane buckets accumulate in
+// registers and are folded into per-warp FP64 shared buckets every 8 batches.
+// Every reduction has a fixed order, so results are reproducible.
 // ---------------------------------------------------------------------------
 #ifndef ISRS_ADJ_MIN_BLOCKS
 #define ISRS_ADJ_MIN_BLOCKS 3   // resident blocks per SM the register budget is sized for
 #endif
-
-constexpr int kOwnFields = 8;   // A2d, A2, K2, z, c, dz, edge hi, edge lo
-constexpr int kCtr = 4;         // F_c candidates whose small-phase points are contracted
-constexpr int kCtrN = 15;       // per candidate: 3 weights x T_0..T_4
-
-__device__ __forceinline__ float warp_sum_f(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
 
 template <int K>
 __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams ap)
@@ -143,40 +241,32 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     extern __shared__ float4 smem_f4[];
     const int M = qp.n_steps, G = qp.G;
     const int nw = blockDim.x >> 5;
-    float4 *sT = smem_f4;                                     // {A2 + log2 dz, K2, z, z^2 + dz^2/12}
-    float4 *sE = sT + M;                                      // {edge/2pi hi, lo, A2, K2}
-    float4 *sR = sE + M;                                      // {A2 + log2 dz, K2, z, dz}
-    RowF *rows = reinterpret_cast<RowF *>(sR + M);            // [G]
-    float4 *sPs = reinterpret_cast<float4 *>(rows + G);       // [nw][32][2] staged point states
-    double2 *sB = reinterpret_cast<double2 *>(sPs + nw * 64); // [nw][K][32] FP64 step buckets
-    float2 *sF = reinterpret_cast<float2 *>(sB + nw * K * 32);    // [nw][K][32] FP32 step buckets
-    float *sO = reinterpret_cast<float *>(sF + nw * K * 32);      // [kOwnFields][K][16] owned tables
+    float4 *sT = smem_f4;                                     // [M] {A2 + log2 dz, K2, z, z^2 + dz^2/12}
+    float4 *sO0 = sT + M;                                     // [K][16] owned {A2 + log2 dz, K2, z, dz}
+    float4 *sO1 = sO0 + K * 16;                               // [K][16] owned {edge/2pi hi, lo, A2, c}
+    float4 *sL = sO1 + K * 16;                                // [nw][3][kListCap] {w W af, phi, F_c, ci}
+    double2 *sB = reinterpret_cast<double2 *>(sL + nw * 3 * kListCap);   // [nw][K][16] FP64 step buckets
+    RowF *rows = reinterpret_cast<RowF *>(sB + nw * K * 16);             // [G]
     __shared__ PieceConst<float> kc;
     __shared__ ChebTab ct;
     __shared__ float sVc[kMaxCand];
-    __shared__ float sE0[2][16];                              // first edge of each lane's block
     __shared__ double scratch[32];
     __shared__ int s_item;
-    // small-phase points of contracted candidates: per-warp moment sums, their
-    // block totals, and the per-step bucket terms they give for the tile
-    __shared__ double sY[8][kCtr][kCtrN];
+    // small-phase points of contracted candidates: per-warp moment sums (FP32
+    // between folds, FP64 after), their block totals, and the per-step bucket
+    // terms they give for the tile
+    __shared__ float sYf[8][kCtr][16];
+    __shared__ double sY[8][kCtr][16];
     __shared__ double sYt[kCtr][kCtrN];
     __shared__ double2 sC[128];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < 8 * kCtr * kCtrN; t += blockDim.x) (&sY[0][0][0])[t] = 0.0;
+    for (int t = threadIdx.x; t < 8 * kCtr * 16; t += blockDim.x) {
+        (&sY[0][0][0])[t] = 0.0;
+        (&sYf[0][0][0])[t] = 0.0f;
+    }
     for (int t = threadIdx.x; t < 128; t += blockDim.x) sC[t] = make_double2(0.0, 0.0);
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const float4 za = qp.zs_a[m];
-        const float4 zb = qp.zs_b[m];
-        sT[m] = make_float4(0.0f, 0.0f, za.x, za.y);
-        sE[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
-        sR[m] = make_float4(0.0f, 0.0f, za.x, za.w);
-    }
-    for (int t = threadIdx.x; t < nw * K * 32; t += blockDim.x) {
-        sB[t] = make_double2(0.0, 0.0);
-        sF[t] = make_float2(0.0f, 0.0f);
-    }
+    for (int t = threadIdx.x; t < nw * K * 16; t += blockDim.x) sB[t] = make_double2(0.0, 0.0);
     if (threadIdx.x < kMaxCand) sVc[threadIdx.x] = 0.0f;
 
     const float c3 = (float)(kPi * qp.beta3);
@@ -187,12 +277,15 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     const float phi_small = 0.02f / qp.L;
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
-    // pass 2 runs on half-warps: lane l owns steps [K (l mod 16), K (l mod 16) + K)
+    // the walks run on half-warps: lane l owns steps [K (l mod 16), K (l mod 16) + K)
     const int l16 = lane & 15, half = lane >> 4;
-    const int m0 = l16 * K;
-    float4 *myPs = sPs + warp * 64;
-    float2 *myF = sF + warp * K * 32;
-    double2 *myB = sB + warp * K * 32;
+    const float4 *o0s = sO0 + l16;
+    const float4 *o1s = sO1 + l16;
+    float4 *Ls = sL + warp * 3 * kListCap;
+    float4 *Ld = Ls + kListCap;
+    float4 *Lt = Ld + kListCap;
+    double2 *myB = sB + warp * K * 16;
+    const unsigned lt_mask = (1u << lane) - 1u;
     int cur_prof = -1;
 
     for (;;) {
@@ -207,30 +300,25 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             const float2 *st = qp.step_f + (size_t)item.prof * M;
             for (int m = threadIdx.x; m < M; m += blockDim.x) {
                 const float2 v = st[m];
-                const float a2d = v.x + qp.zs_a[m].z;
-                sT[m].x = a2d;
-                sT[m].y = v.y;
-                sE[m].z = v.x;
-                sE[m].w = v.y;
-                sR[m].x = a2d;
-                sR[m].y = v.y;
+                const float4 za = qp.zs_a[m];
+                sT[m] = make_float4(v.x + za.z, v.y, za.x, za.y);
             }
-            __syncthreads();
-            // lane-contiguous copy of every lane's owned step tables
+            // lane-contiguous copies of every lane's owned step tables; the
+            // padding steps past M have zero weight and repeat the last edge
+            const float4 zl = qp.zs_b[M - 1];
             for (int t = threadIdx.x; t < K * 16; t += blockDim.x) {
                 const int k = t >> 4, l = t & 15, m = l * K + k;
-                const bool ok = m < M;
-                const float4 a = ok ? sT[m] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 e = ok ? sE[m] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float dz = ok ? sR[m].w : 0.0f;
-                const float vals[kOwnFields] = {a.x, e.z, a.y, a.z, a.w, dz, e.x, e.y};
-#pragma unroll
-                for (int f = 0; f < kOwnFields; ++f) sO[(f * K + k) * 16 + l] = vals[f];
-            }
-            if (threadIdx.x < 16) {
-                const int l = threadIdx.x, mm = l * K;
-                sE0[0][l] = (mm > 0 && mm < M) ? sE[mm - 1].x : 0.0f;
-                sE0[1][l] = (mm > 0 && mm < M) ? sE[mm - 1].y : 0.0f;
+                float4 o0 = make_float4(kPadLog2, 0.f, 0.f, 0.f);
+                float4 o1 = make_float4(zl.x, zl.y, kPadLog2, 0.f);
+                if (m < M) {
+                    const float2 v = st[m];
+                    const float4 za = qp.zs_a[m];
+                    const float4 zb = qp.zs_b[m];
+                    o0 = make_float4(v.x + za.z, v.y, za.x, za.w);
+                    o1 = make_float4(zb.x, zb.y, v.x, za.y);
+                }
+                sO0[k * 16 + l] = o0;
+                sO1[k * 16 + l] = o1;
             }
             cur_prof = item.prof;
         }
@@ -245,18 +333,23 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             const bool cheb = ct.ok != 0;
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2, mult = kc.mult;
             const float three_fi2 = 3.0f * fi * fi;
-            float sum = 0.0f, comp = 0.0f;
-            float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f, v3 = 0.0f;
+            FwdAcc fa = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            float R[K], Rp[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                R[k] = 0.0f;
+                Rp[k] = 0.0f;
+            }
+            int ns = 0, nd = 0, nt = 0;      // list lengths (warp-uniform)
             const int npts = G * G;
             int batches = 0;
             for (int qb = warp * 32; qb < npts; qb += blockDim.x) {
-                // ---- pass 1: this lane's grid point
+                // ---- 1. this lane's grid point
                 const int q = qb + lane;
-                float phi = 0.0f, Fc = 0.0f, at = 0.0f, cpt = 0.0f, q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
-                int path = 0;
+                float phi = 0.0f, Fc = 0.0f, wwa = 0.0f, cpt = 0.0f;
+                int cls = -1, ci = -1;
                 bool ctr = false;            // contracted small-phase point
-                int ci_c = -1;
-                float cx = 0.0f;
+                float cx = 0.0f, q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
                 if (q < npts) {
                     const int r = (int)(((float)q + 0.5f) * invG);
                     const int j = q - r * G;
@@ -267,53 +360,30 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         const float f1 = s1g * (rw.xc * e);
                         const float f2 = s2g * (rw.yc * __frcp_rn(e));
                         const float u = f1 + f2;
-                        int ci = -1;
                         for (int c = 0; c < kc.nc; ++c) {
                             if (u >= kc.lo[c] && u < kc.hi[c]) { ci = c; break; }
                         }
                         if (ci >= 0) {
                             const float W = kc.wab * kc.pd[ci];
-                            at = kc.at_ab + kc.hat[ci];
                             Fc = fi + u;
                             const float br = b2 + c3 * (u + 2.0f * fi) +
                                              c4 * (f1 * f1 + 1.5f * f1 * f2 + 3.0f * fi * u + f2 * f2 + three_fi2);
                             phi = m4pi2 * f1 * f2 * br;
                             const float aphi = fabsf(phi);
-                            float S2;
+                            wwa = rw.w * W * array_factor_f(phi, qp);
                             if (aphi <= phi_small) {
-                                path = kPathSmall;
-                                if (cheb) {
+                                cls = kClsSmall;
+                                if (cheb && ci < kCtr) {
                                     cheb_moments(ct, ci, u, q0, q1, q2);
-                                    if (ci < kCtr) {
-                                        ctr = true;
-                                        ci_c = ci;
-                                        cx = (u - ct.mid[ci]) * ct.invh[ci];
-                                    }
-                                } else {
-                                    zsum_small_m(phi, Fc, at, sT, M, q0, q1, q2);
+                                    ctr = true;
+                                    cx = (u - ct.mid[ci]) * ct.invh[ci];
+                                    const float S2 = fmaf(-phi * phi, fmaf(q0, q2, -q1 * q1), q0 * q0);
+                                    fwd_add(fa, wwa * S2, ci, true, sVc);
+                                    cpt = mult * wwa;
                                 }
-                                S2 = fmaf(-phi * phi, fmaf(q0, q2, -q1 * q1), q0 * q0);
-                            } else if (aphi <= phi_direct) {
-                                path = kPathDirect;
-                                zsum_direct_c(phi, Fc, at, sR, M, q0, q1);
-                                S2 = q0 * q0 + q1 * q1;
                             } else {
-                                path = kPathTele;
-                                zsum_tele_c(phi, Fc, at, sT, sE, M, q0, q1);
-                                S2 = (q0 * q0 + q1 * q1) / (phi * phi);
+                                cls = aphi <= phi_direct ? kClsDirect : kClsTele;
                             }
-                            const float af = array_factor_f(phi, qp);
-                            const float val = rw.w * W * S2 * af;
-                            const float y = val - comp;
-                            const float t = sum + y;
-                            comp = (t - sum) - y;
-                            sum = t;
-                            if (ci == 0) v0 += val;
-                            else if (ci == 1) v1 += val;
-                            else if (ci == 2) v2 += val;
-                            else if (ci == 3) v3 += val;
-                            else atomicAdd(&sVc[ci], val);
-                            cpt = mult * rw.w * W * af;
                         }
                     }
                 }
@@ -321,137 +391,151 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 // + al2 z_m) with w_m = base_m e^{a_m x} = base_m sum_n b_n(a_m) T_n(x),
                 // so their bucket terms need only the sums of cp al_j T_n(x) per
                 // candidate (n <= 4 for the F_c-weighted bucket, x T_n = (T_{n+1} +
-                // T_{|n-1|})/2).  They are summed over the warp here and turned into
-                // per-step terms once per piece; pass 2 skips these points.
+                // T_{|n-1|})/2).  The 15 sums of a candidate are reduced over the
+                // warp in one butterfly (each level halves the values a lane
+                // carries), after which lane pair (2v, 2v+1) holds sum v.
                 unsigned cmask = __ballot_sync(kFull, ctr);
                 if (cmask) {
                     const float T2 = fmaf(2.0f * cx, cx, -1.0f);
                     const float T3 = fmaf(2.0f * cx, T2, -cx);
                     const float T4 = fmaf(2.0f * cx, T3, -T2);
-                    const float Tn[5] = {1.0f, cx, T2, T3, T4};
                     const float ph2 = phi * phi;
-                    const float al[3] = {2.0f * q0 - ph2 * q2, -ph2 * q0, 2.0f * ph2 * q1};
+                    const float al0 = 2.0f * q0 - ph2 * q2, al1 = -ph2 * q0, al2 = 2.0f * ph2 * q1;
                     while (cmask) {
-                        const int cl = __shfl_sync(kFull, ci_c, __ffs(cmask) - 1);
-                        const bool mine = ctr && ci_c == cl;
+                        const int cl = __shfl_sync(kFull, ci, __ffs(cmask) - 1);
+                        const bool mine = ctr && ci == cl;
                         const float cw = mine ? cpt : 0.0f;
+                        const float w0 = cw * al0, w1 = cw * al1, w2 = cw * al2;
+                        float a[16] = {w0, w0 * cx, w0 * T2, w0 * T3, w0 * T4,
+                                       w1, w1 * cx, w1 * T2, w1 * T3, w1 * T4,
+                                       w2, w2 * cx, w2 * T2, w2 * T3, w2 * T4, 0.0f};
+                        const bool up4 = lane & 16, up3 = lane & 8, up2 = lane & 4, up1 = lane & 2;
+                        float b8[8];
 #pragma unroll
-                        for (int j = 0; j < 3; ++j) {
+                        for (int i = 0; i < 8; ++i)
+                            b8[i] = (up4 ? a[i + 8] : a[i]) + __shfl_xor_sync(kFull, up4 ? a[i] : a[i + 8], 16);
+                        float b4[4];
 #pragma unroll
-                            for (int n = 0; n < 5; ++n) {
-                                const float v = warp_sum_f(cw * al[j] * Tn[n]);
-                                if (lane == 0) sY[warp][cl][j * 5 + n] += (double)v;
-                            }
-                        }
+                        for (int i = 0; i < 4; ++i)
+                            b4[i] = (up3 ? b8[i + 4] : b8[i]) + __shfl_xor_sync(kFull, up3 ? b8[i] : b8[i + 4], 8);
+                        float b2v[2];
+#pragma unroll
+                        for (int i = 0; i < 2; ++i)
+                            b2v[i] = (up2 ? b4[i + 2] : b4[i]) + __shfl_xor_sync(kFull, up2 ? b4[i] : b4[i + 2], 4);
+                        float s = (up1 ? b2v[1] : b2v[0]) + __shfl_xor_sync(kFull, up1 ? b2v[0] : b2v[1], 2);
+                        s += __shfl_xor_sync(kFull, s, 1);
+                        if ((lane & 1) == 0) sYf[warp][cl][lane >> 1] += s;
                         cmask &= ~__ballot_sync(kFull, mine);
                     }
-                    if (ctr) cpt = 0.0f;
                 }
-                myPs[2 * lane] = make_float4(cpt, phi, Fc, at);
-                myPs[2 * lane + 1] = make_float4(q0, q1, q2, __int_as_float(path));
+                // append the other points to their form's list
+                const bool stage = cls >= 0 && !ctr;
+                const unsigned bs = __ballot_sync(kFull, stage && cls == kClsSmall);
+                const unsigned bd = __ballot_sync(kFull, stage && cls == kClsDirect);
+                const unsigned bt = __ballot_sync(kFull, stage && cls == kClsTele);
+                if (stage) {
+                    const float4 v = make_float4(wwa, phi, Fc, __int_as_float(ci));
+                    if (cls == kClsSmall) Ls[ns + __popc(bs & lt_mask)] = v;
+                    else if (cls == kClsDirect) Ld[nd + __popc(bd & lt_mask)] = v;
+                    else Lt[nt + __popc(bt & lt_mask)] = v;
+                }
+                ns += __popc(bs);
+                nd += __popc(bd);
+                nt += __popc(bt);
                 __syncwarp();
-                // ---- pass 2: the warp's 32 points, each lane on its own steps
-                float R[K], Rp[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    R[k] = 0.0f;
-                    Rp[k] = 0.0f;
+                // ---- 2. walk the lists in pairs, one point per half-warp
+                for (int p = half; p + 1 - half < nd; p += 2) {
+                    const float4 st = Ld[p];
+                    const int pci = __float_as_int(st.w);
+                    const float at = kc.at_ab + kc.hat[pci];
+                    const float val = walk_direct<K>(o0s, st.x, st.y, st.z, at, mult, R, Rp);
+                    fwd_add(fa, val, pci, l16 == 0, sVc);
                 }
-                const float e0h = sE0[0][l16], e0l = sE0[1][l16];
-                for (int pp = 0; pp < 16; ++pp) {
-                    const int p = 2 * pp + half;           // the two half-warps take two points
-                    const float4 st0 = myPs[2 * p];
-                    const float cp = st0.x;
-                    if (cp == 0.0f) continue;
-                    const float4 st1 = myPs[2 * p + 1];
-                    const float ph = st0.y, fc = st0.z, a_t = st0.w;
-                    const float p0 = st1.x, p1 = st1.y, p2 = st1.z;
-                    const int pth = __float_as_int(st1.w);
-                    const float cF = cp * fc;
-                    if (pth == kPathSmall) {
-                        // d|S|^2/d ln p_m = w_m (2 M0 - phi^2 (M2 + M0 c_m - 2 M1 z_m))
-                        const float ph2 = ph * ph;
-                        const float al0 = 2.0f * p0 - ph2 * p2, al1 = -ph2 * p0, al2 = 2.0f * ph2 * p1;
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            if (m0 + k < M) {
-                                float lp = fmaf(sO[(2 * K + k) * 16 + l16], fc, sO[(0 * K + k) * 16 + l16]);
-                                lp = fmaf(-a_t, sO[(3 * K + k) * 16 + l16], lp);
-                                const float w = ex2_approx(lp);
-                                const float rr = w * fmaf(al2, sO[(3 * K + k) * 16 + l16], fmaf(al1, sO[(4 * K + k) * 16 + l16], al0));
-                                R[k] = fmaf(cp, rr, R[k]);
-                                Rp[k] = fmaf(cF, rr, Rp[k]);
-                            }
-                        }
-                    } else if (pth == kPathDirect) {
-                        // d|S|^2/d ln p_m = 2 Re(conj(S) p_m dz_m sinc e^{j phi z_m})
-                        const float hph = 0.5f * ph;
-                        const float phr = ph * 0.15915494309189535f;
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            if (m0 + k < M) {
-                                float sn, cs;
-                                sincos_rev(phr * sO[(3 * K + k) * 16 + l16], sn, cs);
-                                float lp = fmaf(sO[(2 * K + k) * 16 + l16], fc, sO[(0 * K + k) * 16 + l16]);
-                                lp = fmaf(-a_t, sO[(3 * K + k) * 16 + l16], lp);
-                                const float amp = ex2_approx(lp) * sinc_poly(hph * sO[(5 * K + k) * 16 + l16]);
-                                const float rr = 2.0f * amp * fmaf(p0, cs, p1 * sn);
-                                R[k] = fmaf(cp, rr, R[k]);
-                                Rp[k] = fmaf(cF, rr, Rp[k]);
-                            }
-                        }
-                    } else {
-                        // d|S|^2/d ln p_m = 2 Re(conj(U) p_m (E_{m+1} - E_m)) / phi^2
-                        float Er, Ei;
-                        phasor_rev_ff(ph, e0h, e0l, Ei, Er);
-                        const float g = 2.0f / (ph * ph);
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            if (m0 + k < M) {
-                                float sn, cs;
-                                phasor_rev_ff(ph, sO[(6 * K + k) * 16 + l16], sO[(7 * K + k) * 16 + l16], sn, cs);
-                                float lp = fmaf(sO[(2 * K + k) * 16 + l16], fc, sO[(1 * K + k) * 16 + l16]);
-                                lp = fmaf(-a_t, sO[(3 * K + k) * 16 + l16], lp);
-                                const float pm = ex2_approx(lp);
-                                const float rr = g * pm * fmaf(p0, cs - Er, p1 * (sn - Ei));
-                                R[k] = fmaf(cp, rr, R[k]);
-                                Rp[k] = fmaf(cF, rr, Rp[k]);
-                                Er = cs;
-                                Ei = sn;
-                            }
-                        }
-                    }
+                for (int p = half; p + 1 - half < nt; p += 2) {
+                    const float4 st = Lt[p];
+                    const int pci = __float_as_int(st.w);
+                    const float at = kc.at_ab + kc.hat[pci];
+                    const float val = walk_tele<K>(o0s, o1s, l16, st.x, st.y, st.z, at, mult, R, Rp);
+                    fwd_add(fa, val, pci, l16 == 0, sVc);
                 }
-                // lane buckets -> FP32 shared accumulators; folded to FP64 every 8 batches
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    float2 &b = myF[k * 32 + lane];
-                    b.x += R[k];
-                    b.y += Rp[k];
+                for (int p = half; p + 1 - half < ns; p += 2) {
+                    const float4 st = Ls[p];
+                    const int pci = __float_as_int(st.w);
+                    const float at = kc.at_ab + kc.hat[pci];
+                    const float val = walk_small<K>(o0s, o1s, st.x, st.y, st.z, at, mult, R, Rp);
+                    fwd_add(fa, val, pci, l16 == 0, sVc);
                 }
-                if (++batches == 8) {
+                // an odd point waits at the head of its list for the next batch
+                __syncwarp();
+                if (lane == 0) {
+                    if (nd & 1) Ld[0] = Ld[nd - 1];
+                    if (nt & 1) Lt[0] = Lt[nt - 1];
+                    if (ns & 1) Ls[0] = Ls[ns - 1];
+                }
+                nd &= 1;
+                nt &= 1;
+                ns &= 1;
+                if (++batches == kFoldBatches) {
                     batches = 0;
+                    // step buckets: the two halves' registers meet, then FP64
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        float2 &b = myF[k * 32 + lane];
-                        double2 &d = myB[k * 32 + lane];
-                        d.x += (double)b.x;
-                        d.y += (double)b.y;
-                        b = make_float2(0.0f, 0.0f);
+                        const float rx = R[k] + __shfl_xor_sync(kFull, R[k], 16);
+                        const float ry = Rp[k] + __shfl_xor_sync(kFull, Rp[k], 16);
+                        if (half == 0) {
+                            double2 &d = myB[k * 16 + l16];
+                            d.x += (double)rx;
+                            d.y += (double)ry;
+                        }
+                        R[k] = 0.0f;
+                        Rp[k] = 0.0f;
+                    }
+                    for (int t = lane; t < kCtr * 16; t += 32) {
+                        (&sY[warp][0][0])[t] += (double)(&sYf[warp][0][0])[t];
+                        (&sYf[warp][0][0])[t] = 0.0f;
                     }
                 }
-                __syncwarp();          // the next batch overwrites the staged states
+                __syncwarp();          // the next batch appends to the lists
+            }
+            // the last odd point of each form, beside a zero-weight copy of itself
+            if (nd) {
+                float4 st = Ld[0];
+                const int pci = __float_as_int(st.w);
+                if (half) st.x = 0.0f;
+                const float val = walk_direct<K>(o0s, st.x, st.y, st.z, kc.at_ab + kc.hat[pci], mult, R, Rp);
+                fwd_add(fa, val, pci, l16 == 0, sVc);
+            }
+            if (nt) {
+                float4 st = Lt[0];
+                const int pci = __float_as_int(st.w);
+                if (half) st.x = 0.0f;
+                const float val = walk_tele<K>(o0s, o1s, l16, st.x, st.y, st.z, kc.at_ab + kc.hat[pci], mult, R, Rp);
+                fwd_add(fa, val, pci, l16 == 0, sVc);
+            }
+            if (ns) {
+                float4 st = Ls[0];
+                const int pci = __float_as_int(st.w);
+                if (half) st.x = 0.0f;
+                const float val = walk_small<K>(o0s, o1s, st.x, st.y, st.z, kc.at_ab + kc.hat[pci], mult, R, Rp);
+                fwd_add(fa, val, pci, l16 == 0, sVc);
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                float2 &b = myF[k * 32 + lane];
-                double2 &d = myB[k * 32 + lane];
-                d.x += (double)b.x;
-                d.y += (double)b.y;
-                b = make_float2(0.0f, 0.0f);
+                const float rx = R[k] + __shfl_xor_sync(kFull, R[k], 16);
+                const float ry = Rp[k] + __shfl_xor_sync(kFull, Rp[k], 16);
+                if (half == 0) {
+                    double2 &d = myB[k * 16 + l16];
+                    d.x += (double)rx;
+                    d.y += (double)ry;
+                }
+            }
+            __syncwarp();
+            for (int t = lane; t < kCtr * 16; t += 32) {
+                (&sY[warp][0][0])[t] += (double)(&sYf[warp][0][0])[t];
+                (&sYf[warp][0][0])[t] = 0.0f;
             }
             // piece totals: the forward sum and the PSD buckets V_ij
-            const double ptot = block_sum_d((double)sum - (double)comp, scratch);
+            const double ptot = block_sum_d((double)fa.sum - (double)fa.comp, scratch);
             if (cheb) {
                 // contracted small-phase terms of this piece -> per-step tile buckets
                 const int ncc = min(kc.nc, kCtr);
@@ -491,10 +575,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                     sC[m].y += ry;
                 }
             }
-            const double t0 = block_sum_d((double)v0, scratch);
-            const double t1 = block_sum_d((double)v1, scratch);
-            const double t2 = block_sum_d((double)v2, scratch);
-            const double t3 = block_sum_d((double)v3, scratch);
+            const double t0 = block_sum_d((double)fa.v0, scratch);
+            const double t1 = block_sum_d((double)fa.v1, scratch);
+            const double t2 = block_sum_d((double)fa.v2, scratch);
+            const double t3 = block_sum_d((double)fa.v3, scratch);
             acc += (double)mult * ptot;
             if (threadIdx.x == 0) {
                 double *Vrow = ap.V + (size_t)slot * ap.n_ch;
@@ -515,12 +599,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             const int ln = m / K, kk = m - ln * K;
             double rx = 0.0, ry = 0.0;
             for (int w = 0; w < nw; ++w) {
-                for (int h = 0; h < 2; ++h) {
-                    double2 &b = sB[(w * K + kk) * 32 + ln + 16 * h];
-                    rx += b.x;
-                    ry += b.y;
-                    b = make_double2(0.0, 0.0);
-                }
+                double2 &b = sB[(w * K + kk) * 16 + ln];
+                rx += b.x;
+                ry += b.y;
+                b = make_double2(0.0, 0.0);
             }
             ap.item_R[(size_t)it * M + m] = make_double2(rx + sC[m].x, ry + sC[m].y);
             sC[m] = make_double2(0.0, 0.0);
@@ -664,8 +746,8 @@ __global__ void __launch_bounds__(256) k_chain(ChainParams cp)
 size_t adjoint_smem_bytes(int n_steps, int G, int block)
 {
     const int K = (n_steps + 15) / 16, nw = block / 32;
-    return (size_t)n_steps * 3 * sizeof(float4) + (size_t)G * sizeof(RowF) + (size_t)nw * 64 * sizeof(float4) +
-           (size_t)nw * K * 32 * (sizeof(double2) + sizeof(float2)) + (size_t)kOwnFields * K * 16 * sizeof(float);
+    return (size_t)(n_steps + 2 * K * 16 + nw * 3 * kListCap) * sizeof(float4) +
+           (size_t)nw * K * 16 * sizeof(double2) + (size_t)G * sizeof(RowF);
 }
 
 template <int K>
