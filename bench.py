@@ -224,11 +224,10 @@ def run_gpu(args):
     # (sin, cos of the edge phasor, exp), small-phase 0 (its moments are
     # contracted once per piece and channel: ~nc x 112 exps per 65,536 points).
     # The fused adjoint evaluates each step term once and keeps it in registers
-    # for the bucket terms, so its algorithmic SFU work equals the forward's.
+    # for the bucket terms, so its algorithmic SFU work is that of its own
+    # point forms (it counts them like the forward kernel).
     quad_ms = float(np.mean(quad_ms))
-    if use_grad:
-        _fwd_point_steps(eng, wl, P)
-    paths = eng.last_path_counts()
+    paths = eng.last_path_counts()          # z-sum forms of the last timed launch (both kernels count)
     n_steps = wl.n_edges - 1
     sfu_ops = n_steps * 3 * (paths["direct"] + paths["telescoped"])
     peaks = _peaks()
@@ -297,7 +296,7 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
 # gpu__time_duration), and the points that launch evaluated.  The kernel reads
 # the piece list and writes one bucket row per tile, both proportional to the
 # evaluated points at fixed G, so a full launch's traffic is scaled by points.
-ADJ_DRAM_CAPTURE = {"bytes": 4.281e6, "points": 2880700416}
+ADJ_DRAM_CAPTURE = {"bytes": 4.306e6, "points": 2880700416}
 
 
 def _timed(fn, dev, reps: int = 2):
@@ -357,11 +356,6 @@ def _unfolded_points(wl):
     if per_cut is None:
         raise ValueError("bench counts SCI+XCI grids only")
     return n * per_cut * wl.G * wl.G
-
-
-def _fwd_point_steps(eng, wl, P):
-    eng.eta(wl, P=P)
-    return eng.last_launch_info()["point_steps"]
 
 
 def _e2e(eng, wl, args, world, n_grid):

@@ -253,9 +253,10 @@ isrs_status isrs_last_kernel_ms(isrs_handle h, int which, float *ms);
  * possible).  Errors: INVALID_ARG (NULL). */
 isrs_status isrs_last_graph_replay(isrs_handle h, int *replayed);
 
-/* Grid points of the last FP32 quadrature launch by the form its z-sum took
- * (App. A, Eq. slow_vary): counts[0] second-order small-phase expansion,
- * counts[1] direct form, counts[2] telescoped form.  Synchronises the
+/* Grid points of the last FP32 quadrature launch (forward, or the fused
+ * forward + adjoint of isrs_gn_grad) by the form its z-sum took (App. A,
+ * Eq. slow_vary): counts[0] small-phase moment expansion (contracted or per
+ * step), counts[1] direct form, counts[2] telescoped form.  Synchronises the
  * device.  Errors: INVALID_ARG (NULL, or no launch yet), CUDA. */
 isrs_status isrs_last_path_counts(isrs_handle h, int64_t *counts);
 

@@ -44,7 +44,7 @@ struct Geom {
     std::vector<int> prof_ch_off, plan_ch_off, plan_n, prof_plan;
     int total_prof_ch = 0, total_plan_ch = 0;
     DevBuf pieces, items, slot_items, slot_cut, prof_slot_off, plan_ch_off_d, plan_n_d, prof_ch_off_d,
-        prof_plan_d, ch_frel, ch_B, ch_alpha, ch_gamma, ch_nf, guard, zs_a, zs_b, zs_d, item_slot;
+        prof_plan_d, ch_frel, ch_B, ch_alpha, ch_gamma, ch_nf, guard, zs_a, zs_b, zs_d, zs_g, item_slot;
     bool has_nf = false, has_guard = false;
     // Raman-ODE profile: partner windows and gain scale per plan channel, RK4
     // steps per half z-step, largest candidate count of a piece
@@ -354,7 +354,7 @@ isrs_status cut_pieces(isrs_handle h, const isrs_channels *c, int plan, int i, i
 // positions in revolutions (z / 2 pi) as float-float pairs.
 // ----------------------------------------------------------------------------
 void zgrid_tables(double L, double a, int n_edges, std::vector<float4> &za, std::vector<float4> &zb,
-                  std::vector<double2> &zd, float &dz_max)
+                  std::vector<double2> &zd, float &dz_max, std::vector<float4> *zg = nullptr)
 {
     std::vector<double> ze(n_edges);
     const double drop = a > 0.0 ? -std::expm1(-a * L) : 0.0;
@@ -379,6 +379,24 @@ void zgrid_tables(double L, double a, int n_edges, std::vector<float4> &za, std:
         zb[m] = make_float4(reh, (float)(re - (double)reh), (float)rm, 0.f);
     }
     dz_max = (float)dmax;
+    if (zg) {
+        // centred step moments g_n(m) = mean of (zeta - L/2)^n over [ze_m, ze_{m+1}]
+        // = (b^{n+1} - a^{n+1}) / ((n + 1)(b - a)), n = 0..10, and g_11 = 0
+        zg->assign(3 * (size_t)M, make_float4(0.f, 0.f, 0.f, 0.f));
+        for (int m = 0; m < M; ++m) {
+            const double lo = ze[m] - 0.5 * L, hi = ze[m + 1] - 0.5 * L;
+            float g[12] = {0.f};
+            double pa = lo, pb = hi;
+            for (int n = 0; n <= 10; ++n) {
+                g[n] = (float)((pb - pa) / ((n + 1) * (hi - lo)));
+                pa *= lo;
+                pb *= hi;
+            }
+            (*zg)[3 * m] = make_float4(g[0], g[1], g[2], g[3]);
+            (*zg)[3 * m + 1] = make_float4(g[4], g[5], g[6], g[7]);
+            (*zg)[3 * m + 2] = make_float4(g[8], g[9], g[10], g[11]);
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -570,9 +588,9 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     g->n_slots = (int)slot_items.size();
     g->n_mci_items = (int)mitems.size();
 
-    std::vector<float4> za, zb;
+    std::vector<float4> za, zb, zg;
     std::vector<double2> zd;
-    zgrid_tables(fb->L_km, fb->alpha_R_per_km, q->n_edges, za, zb, zd, g->dz_max);
+    zgrid_tables(fb->L_km, fb->alpha_R_per_km, q->n_edges, za, zb, zd, g->dz_max, &zg);
 
     // Raman-ODE profile: the partners of channel i are the k != i with
     // |f_k - f_i| <= raman_max_THz, one index window of the sorted plan; the
@@ -636,6 +654,7 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     UP(zs_a, za);
     UP(zs_b, zb);
     UP(zs_d, zd);
+    UP(zs_g, zg);
     UP(item_slot, item_slot);
     if (mci) {
         UP(mci_items, mitems);
@@ -657,7 +676,7 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
         DevBuf *bufs[] = {&old->pieces, &old->items, &old->slot_items, &old->slot_cut, &old->prof_slot_off,
                           &old->plan_ch_off_d, &old->plan_n_d, &old->prof_ch_off_d, &old->prof_plan_d,
                           &old->ch_frel, &old->ch_B, &old->ch_alpha, &old->ch_gamma, &old->ch_nf,
-                          &old->guard, &old->zs_a, &old->zs_b, &old->zs_d, &old->item_slot,
+                          &old->guard, &old->zs_a, &old->zs_b, &old->zs_d, &old->zs_g, &old->item_slot,
                           &old->win_lo, &old->win_hi, &old->ch_scale, &old->half_steps, &old->mci_items,
                           &old->slot_items2};
         for (DevBuf *b : bufs) release(*b);
@@ -674,7 +693,7 @@ void free_geom(Geom *g)
     DevBuf *bufs[] = {&g->pieces, &g->items, &g->slot_items, &g->slot_cut, &g->prof_slot_off,
                       &g->plan_ch_off_d, &g->plan_n_d, &g->prof_ch_off_d, &g->prof_plan_d,
                       &g->ch_frel, &g->ch_B, &g->ch_alpha, &g->ch_gamma, &g->ch_nf,
-                      &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->item_slot,
+                      &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->zs_g, &g->item_slot,
                       &g->win_lo, &g->win_hi, &g->ch_scale, &g->half_steps, &g->mci_items, &g->slot_items2};
     for (DevBuf *b : bufs) release(*b);
 }
@@ -738,6 +757,7 @@ QuadParams quad_params(isrs_handle h, const isrs_fibre *fb, Geom *g)
     qp.zs_a = (const float4 *)g->zs_a.p;
     qp.zs_b = (const float4 *)g->zs_b.p;
     qp.zs_d = (const double2 *)g->zs_d.p;
+    qp.zs_g = (const float4 *)g->zs_g.p;
     qp.dz_max = g->dz_max;
     qp.kap_L = (const double *)h->kapL.p;
     qp.L = (float)fb->L_km;

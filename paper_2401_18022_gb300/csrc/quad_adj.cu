@@ -39,7 +39,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClsSmall = 0, kClsDirect = 1, kClsTele = 2;
 constexpr int kListCap = 34;    // a form's list: one carried point + 32 new (+1 pad)
 constexpr int kCtr = 4;         // F_c candidates whose small-phase points are contracted
-constexpr int kCtrN = 15;       // per candidate: 3 weights x T_0..T_4
+constexpr int kCtrN = kChebMom * 5;   // per candidate: moments nu_0..nu_10 x T_0..T_4
+constexpr int kCtrS = 64;       // slots per candidate (two 32-value butterflies)
 constexpr int kFoldBatches = 8; // batches between FP64 folds of the FP32 accumulators
 constexpr float kPadLog2 = -1000.0f;   // log2 weight of the padding steps (ex2 -> 0)
 
@@ -214,6 +215,32 @@ __device__ __forceinline__ void fwd_add(FwdAcc &a, float val, int ci, bool owner
     if (owner && ci >= 4) atomicAdd(&sVc[ci], val);
 }
 
+// Warp sum of 32 values per lane in one butterfly: each level halves the
+// values a lane carries, and lane L ends with the sum of value L.  val(i)
+// gives this lane's value i.
+template <typename F>
+__device__ __forceinline__ float butterfly32(const F &val, int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+    float x16[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        x16[i] = (b4 ? val(i + 16) : val(i)) + __shfl_xor_sync(kFull, b4 ? val(i) : val(i + 16), 16);
+    float x8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        x8[i] = (b3 ? x16[i + 8] : x16[i]) + __shfl_xor_sync(kFull, b3 ? x16[i] : x16[i + 8], 8);
+    float x4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        x4[i] = (b2 ? x8[i + 4] : x8[i]) + __shfl_xor_sync(kFull, b2 ? x8[i] : x8[i + 4], 4);
+    float x2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        x2[i] = (b1 ? x4[i + 2] : x4[i]) + __shfl_xor_sync(kFull, b1 ? x4[i] : x4[i + 2], 2);
+    return (b0 ? x2[1] : x2[0]) + __shfl_xor_sync(kFull, b0 ? x2[0] : x2[1], 1);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -255,16 +282,14 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     // small-phase points of contracted candidates: per-warp moment sums (FP32
     // between folds, FP64 after), their block totals, and the per-step bucket
     // terms they give for the tile
-    __shared__ float sYf[8][kCtr][16];
-    __shared__ double sY[8][kCtr][16];
+    __shared__ float sYf[8][kCtr][kCtrS];
+    __shared__ double sY[8][kCtr][kCtrN];
     __shared__ double sYt[kCtr][kCtrN];
     __shared__ double2 sC[128];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < 8 * kCtr * 16; t += blockDim.x) {
-        (&sY[0][0][0])[t] = 0.0;
-        (&sYf[0][0][0])[t] = 0.0f;
-    }
+    for (int t = threadIdx.x; t < 8 * kCtr * kCtrN; t += blockDim.x) (&sY[0][0][0])[t] = 0.0;
+    for (int t = threadIdx.x; t < 8 * kCtr * kCtrS; t += blockDim.x) (&sYf[0][0][0])[t] = 0.0f;
     for (int t = threadIdx.x; t < 128; t += blockDim.x) sC[t] = make_double2(0.0, 0.0);
     for (int t = threadIdx.x; t < nw * K * 16; t += blockDim.x) sB[t] = make_double2(0.0, 0.0);
     if (threadIdx.x < kMaxCand) sVc[threadIdx.x] = 0.0f;
@@ -275,6 +300,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     const float m4pi2 = (float)(-4.0 * kPi * kPi);
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
+    const float phi_cheb = kChebPhiL / qp.L;
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
     // the walks run on half-warps: lane l owns steps [K (l mod 16), K (l mod 16) + K)
@@ -286,6 +312,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     float4 *Lt = Ld + kListCap;
     double2 *myB = sB + warp * K * 16;
     const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned n_small = 0, n_direct = 0, n_tele = 0;    // points per z-sum form (lane 0 counts)
     int cur_prof = -1;
 
     for (;;) {
@@ -349,7 +376,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 float phi = 0.0f, Fc = 0.0f, wwa = 0.0f, cpt = 0.0f;
                 int cls = -1, ci = -1;
                 bool ctr = false;            // contracted small-phase point
-                float cx = 0.0f, q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
+                float cx = 0.0f, cA = 0.0f, cB = 0.0f;
                 if (q < npts) {
                     const int r = (int)(((float)q + 0.5f) * invG);
                     const int j = q - r * G;
@@ -371,60 +398,49 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                             phi = m4pi2 * f1 * f2 * br;
                             const float aphi = fabsf(phi);
                             wwa = rw.w * W * array_factor_f(phi, qp);
-                            if (aphi <= phi_small) {
+                            if (cheb && ci < kCtr && aphi <= phi_cheb) {
+                                float nu[kChebMom];
+                                cheb_moments<kChebMom>(ct, ci, u, nu, cx);
+                                cheb_AB<kChebMom>(nu, phi, cA, cB);
+                                ctr = true;
                                 cls = kClsSmall;
-                                if (cheb && ci < kCtr) {
-                                    cheb_moments(ct, ci, u, q0, q1, q2);
-                                    ctr = true;
-                                    cx = (u - ct.mid[ci]) * ct.invh[ci];
-                                    const float S2 = fmaf(-phi * phi, fmaf(q0, q2, -q1 * q1), q0 * q0);
-                                    fwd_add(fa, wwa * S2, ci, true, sVc);
-                                    cpt = mult * wwa;
-                                }
+                                fwd_add(fa, wwa * fmaf(cA, cA, cB * cB), ci, true, sVc);
+                                cpt = mult * wwa;
+                            } else if (aphi <= phi_small) {
+                                cls = kClsSmall;
                             } else {
                                 cls = aphi <= phi_direct ? kClsDirect : kClsTele;
                             }
                         }
                     }
                 }
-                // Contracted small-phase points: d|S|^2/d ln p_m = w_m (al0 + al1 c_m
-                // + al2 z_m) with w_m = base_m e^{a_m x} = base_m sum_n b_n(a_m) T_n(x),
-                // so their bucket terms need only the sums of cp al_j T_n(x) per
-                // candidate (n <= 4 for the F_c-weighted bucket, x T_n = (T_{n+1} +
-                // T_{|n-1|})/2).  The 15 sums of a candidate are reduced over the
-                // warp in one butterfly (each level halves the values a lane
-                // carries), after which lane pair (2v, 2v+1) holds sum v.
+                // Contracted small-phase points: |S|^2 = A^2 + B^2 with A (B) the sum of
+                // phi^n nu'_n over even (odd) n, so d|S|^2/d ln p_m = sum_n 2 (A|B)
+                // phi^n f_n w_m g_n(m) with w_m = base_m sum_k b_k(a_m) T_k(x).  Their
+                // bucket terms need only, per candidate, the sums of cp 2 (A|B) phi^n
+                // T_k(x) (k <= 4 for the F_c-weighted bucket, x T_k = (T_{k+1} +
+                // T_{|k-1|})/2): 55 values, reduced over the warp in two butterflies
+                // and turned into per-step terms once per piece.
                 unsigned cmask = __ballot_sync(kFull, ctr);
+                const unsigned cmask0 = cmask;
                 if (cmask) {
                     const float T2 = fmaf(2.0f * cx, cx, -1.0f);
                     const float T3 = fmaf(2.0f * cx, T2, -cx);
                     const float T4 = fmaf(2.0f * cx, T3, -T2);
-                    const float ph2 = phi * phi;
-                    const float al0 = 2.0f * q0 - ph2 * q2, al1 = -ph2 * q0, al2 = 2.0f * ph2 * q1;
+                    const float Tk[5] = {1.0f, cx, T2, T3, T4};
                     while (cmask) {
                         const int cl = __shfl_sync(kFull, ci, __ffs(cmask) - 1);
                         const bool mine = ctr && ci == cl;
-                        const float cw = mine ? cpt : 0.0f;
-                        const float w0 = cw * al0, w1 = cw * al1, w2 = cw * al2;
-                        float a[16] = {w0, w0 * cx, w0 * T2, w0 * T3, w0 * T4,
-                                       w1, w1 * cx, w1 * T2, w1 * T3, w1 * T4,
-                                       w2, w2 * cx, w2 * T2, w2 * T3, w2 * T4, 0.0f};
-                        const bool up4 = lane & 16, up3 = lane & 8, up2 = lane & 4, up1 = lane & 2;
-                        float b8[8];
+                        float al[kChebMom];
+                        al[0] = mine ? 2.0f * cpt * cA : 0.0f;
+                        al[1] = mine ? 2.0f * cpt * cB * phi : 0.0f;
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            b8[i] = (up4 ? a[i + 8] : a[i]) + __shfl_xor_sync(kFull, up4 ? a[i] : a[i + 8], 16);
-                        float b4[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            b4[i] = (up3 ? b8[i + 4] : b8[i]) + __shfl_xor_sync(kFull, up3 ? b8[i] : b8[i + 4], 8);
-                        float b2v[2];
-#pragma unroll
-                        for (int i = 0; i < 2; ++i)
-                            b2v[i] = (up2 ? b4[i + 2] : b4[i]) + __shfl_xor_sync(kFull, up2 ? b4[i] : b4[i + 2], 4);
-                        float s = (up1 ? b2v[1] : b2v[0]) + __shfl_xor_sync(kFull, up1 ? b2v[0] : b2v[1], 2);
-                        s += __shfl_xor_sync(kFull, s, 1);
-                        if ((lane & 1) == 0) sYf[warp][cl][lane >> 1] += s;
+                        for (int n = 2; n < kChebMom; ++n) al[n] = al[n - 2] * (phi * phi);
+                        const auto val = [&](int v) { return v < kCtrN ? al[v / 5] * Tk[v % 5] : 0.0f; };
+                        const float y0 = butterfly32([&](int v) { return val(v); }, lane);
+                        const float y1 = butterfly32([&](int v) { return val(v + 32); }, lane);
+                        sYf[warp][cl][lane] += y0;
+                        sYf[warp][cl][lane + 32] += y1;
                         cmask &= ~__ballot_sync(kFull, mine);
                     }
                 }
@@ -438,6 +454,11 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                     if (cls == kClsSmall) Ls[ns + __popc(bs & lt_mask)] = v;
                     else if (cls == kClsDirect) Ld[nd + __popc(bd & lt_mask)] = v;
                     else Lt[nt + __popc(bt & lt_mask)] = v;
+                }
+                if (lane == 0) {
+                    n_small += __popc(bs) + __popc(cmask0);
+                    n_direct += __popc(bd);
+                    n_tele += __popc(bt);
                 }
                 ns += __popc(bs);
                 nd += __popc(bd);
@@ -490,9 +511,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         R[k] = 0.0f;
                         Rp[k] = 0.0f;
                     }
-                    for (int t = lane; t < kCtr * 16; t += 32) {
-                        (&sY[warp][0][0])[t] += (double)(&sYf[warp][0][0])[t];
-                        (&sYf[warp][0][0])[t] = 0.0f;
+                    for (int t = lane; t < kCtr * kCtrS; t += 32) {
+                        const int c = t / kCtrS, v = t - c * kCtrS;
+                        if (v < kCtrN) sY[warp][c][v] += (double)sYf[warp][c][v];
+                        sYf[warp][c][v] = 0.0f;
                     }
                 }
                 __syncwarp();          // the next batch appends to the lists
@@ -530,9 +552,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 }
             }
             __syncwarp();
-            for (int t = lane; t < kCtr * 16; t += 32) {
-                (&sY[warp][0][0])[t] += (double)(&sYf[warp][0][0])[t];
-                (&sYf[warp][0][0])[t] = 0.0f;
+            for (int t = lane; t < kCtr * kCtrS; t += 32) {
+                const int c = t / kCtrS, v = t - c * kCtrS;
+                if (v < kCtrN) sY[warp][c][v] += (double)sYf[warp][c][v];
+                sYf[warp][c][v] = 0.0f;
             }
             // piece totals: the forward sum and the PSD buckets V_ij
             const double ptot = block_sum_d((double)fa.sum - (double)fa.comp, scratch);
@@ -552,6 +575,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 const int coff = qp.plan_ch_off[pc.plan];
                 for (int m = threadIdx.x; m < M; m += blockDim.x) {
                     const float4 a = sT[m];           // {A2 + log2 dz, K2, z, z^2 + dz^2/12}
+                    const float4 g0 = qp.zs_g[3 * m], g1 = qp.zs_g[3 * m + 1], g2 = qp.zs_g[3 * m + 2];
+                    const float gm[kChebMom] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y, g2.z};
                     double rx = 0.0, ry = 0.0;
                     for (int c = 0; c < ncc; ++c) {
                         const double *Y = sYt[c];
@@ -559,17 +584,23 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
                         const double atc = (double)(kc.at_ab + kc.hat[c]);
                         const double base = exp2((double)a.x - atc * (double)a.z + (double)a.y * F0);
-                        const double t = 0.5 * (double)a.y * h * 0.69314718055994530942, t2 = t * t;
-                        const double b0 = 1.0 + t2 * (1.0 + t2 * (0.25 + t2 / 36.0));                 // I0
-                        const double b1 = 2.0 * t * (1.0 + t2 * (0.5 + t2 / 12.0));                    // 2 I1
-                        const double b2 = 2.0 * t2 * (0.5 + t2 * (1.0 / 6.0 + t2 / 48.0));             // 2 I2
-                        const double b3 = 2.0 * t2 * t * (1.0 / 6.0 + t2 * (1.0 / 24.0 + t2 / 240.0)); // 2 I3
-                        double Q[5];
-                        for (int n = 0; n < 5; ++n) Q[n] = Y[n] + (double)a.w * Y[5 + n] + (double)a.z * Y[10 + n];
-                        const double rs = b0 * Q[0] + b1 * Q[1] + b2 * Q[2] + b3 * Q[3];
-                        const double xs = b0 * Q[1] + 0.5 * (b1 * (Q[2] + Q[0]) + b2 * (Q[3] + Q[1]) + b3 * (Q[4] + Q[2]));
-                        rx += base * rs;
-                        ry += base * (F0 * rs + h * xs);
+                        const float t = (float)(0.5 * (double)a.y * h * 0.69314718055994530942), t2 = t * t;
+                        const float b0 = 1.0f + t2 * (1.0f + t2 * (0.25f + t2 / 36.0f));                 // I0
+                        const float b1 = 2.0f * t * (1.0f + t2 * (0.5f + t2 / 12.0f));                    // 2 I1
+                        const float b2 = 2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 / 48.0f));            // 2 I2
+                        const float b3 = 2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 / 240.0f)); // 2 I3
+                        float rs = 0.0f, xs = 0.0f;
+#pragma unroll
+                        for (int n = 0; n < kChebMom; ++n) {
+                            const double *Yn = Y + 5 * n;
+                            const float y0 = (float)Yn[0], y1 = (float)Yn[1], y2 = (float)Yn[2], y3 = (float)Yn[3],
+                                        y4 = (float)Yn[4];
+                            const float gf = (float)cheb_fold(n) * gm[n];
+                            rs = fmaf(gf, b0 * y0 + b1 * y1 + b2 * y2 + b3 * y3, rs);
+                            xs = fmaf(gf, b0 * y1 + 0.5f * (b1 * (y2 + y0) + b2 * (y3 + y1) + b3 * (y4 + y2)), xs);
+                        }
+                        rx += base * (double)rs;
+                        ry += base * (F0 * (double)rs + h * (double)xs);
                     }
                     sC[m].x += rx;
                     sC[m].y += ry;
@@ -607,6 +638,11 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             ap.item_R[(size_t)it * M + m] = make_double2(rx + sC[m].x, ry + sC[m].y);
             sC[m] = make_double2(0.0, 0.0);
         }
+    }
+    if (qp.path_count && lane == 0) {
+        atomicAdd(&qp.path_count[0], (unsigned long long)n_small);
+        atomicAdd(&qp.path_count[1], (unsigned long long)n_direct);
+        atomicAdd(&qp.path_count[2], (unsigned long long)n_tele);
     }
 }
 

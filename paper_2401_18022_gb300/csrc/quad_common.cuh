@@ -179,25 +179,97 @@ __device__ __forceinline__ double array_factor_d(double phi, const QuadParams &q
 }
 
 // ---------------------------------------------------------------------------
-// Chebyshev contraction of the small-phase moments (App. A, Eq. slow_vary to
-// second order in phi).  Inside candidate channel c, F_c - f_ref = F0 + h x
-// with x in [-1, 1], and the per-step weight factorises:
-//   w_m = 2^{A2d_m + K2_m F_c - at z_m} = 2^{A2d_m - at z_m + K2_m F0} e^{a_m x},
-//   a_m = K2_m h ln 2,  e^{a x} = I0(a) + 2 sum_{n>=1} In(a) Tn(x)
-// so M_k(x) = sum_n C_kn Tn(x), n <= 3, with C_kn summed over the steps once
-// per piece and candidate.  Truncation ~ (a/2)^4/12 < 4e-8 for |a| <= 0.05,
-// which holds when kappa(L) h <= 0.05; otherwise the per-step sum is used.
+// Contracted small-phase z-sum (App. A, Eq. slow_vary).  With w_m = p_m dz_m,
+// dz_m sinc(phi dz_m/2) e^{j phi z_m} is the mean of e^{j phi zeta} over step
+// m, so about the span centre z0 = L/2
+//   S e^{-j phi z0} = sum_n (j phi)^n / n! nu_n,   nu_n = sum_m w_m g_n(m),
+//   g_n(m) = mean of (zeta - z0)^n over step m,
+// exactly; |S|^2 = A^2 + B^2 with A (B) the even (odd) part, and truncating
+// at n = N leaves a relative error below 2 (phi L/2)^{N+1}/(N+1)!.
+// The moments depend on the point only through F_c (and the candidate
+// channel's attenuation): inside channel c, F_c - f_ref = F0 + h x with
+// x in [-1, 1], and
+//   w_m = 2^{A2d_m - at z_m + K2_m F0} e^{a_m x},   a_m = K2_m h ln 2,
+//   e^{a x} = I0(a) + 2 sum_{k>=1} Ik(a) Tk(x),
+// so nu_n(x) = sum_{k<=3} C_nk Tk(x), with C_nk summed over the steps once
+// per piece and candidate.  Truncation in x ~ (a/2)^4/12 < 4e-8 for
+// |a| <= 0.05, which holds when kappa(L) h <= 0.05; otherwise the per-step
+// sum is used.
 // ---------------------------------------------------------------------------
 constexpr float kChebMaxA = 0.05f;
+constexpr int kChebMom = 11;        // nu_0 .. nu_10
+constexpr float kChebPhiL = 2.0f;   // |phi| L limit of the 11-moment form: error < 5e-8
 
 struct ChebTab {
-    float c[kMaxCand][12];      // [candidate][k * 4 + n], k: g = 1, z, z^2 + dz^2/12
-    float mid[kMaxCand];        // channel centre relative to the CUT
-    float invh[kMaxCand];       // 1 / (B_c / 2)
+    float4 c[kMaxCand][kChebMom];   // [candidate][n] = C_n0..C_n3 times (-1)^{floor(n/2)} / n!
+    float mid[kMaxCand];            // channel centre relative to the CUT
+    float invh[kMaxCand];           // 1 / (B_c / 2)
     int ok;
 };
 
+// (-1)^{floor(n/2)} / n!
+__host__ __device__ constexpr double cheb_fold(int n)
+{
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f /= (double)i;
+    return ((n >> 1) & 1) ? -f : f;
+}
+
+// 2^x for an FP64 exponent: the integer part goes to the FP32 exponent field,
+// the fraction (|f| <= 1/2, exact in FP32 to 1e-16 absolute) to ex2.approx.
+__device__ __forceinline__ float exp2_split(double x)
+{
+    const double xr = rint(x);
+    if (xr < -126.0) return 0.0f;
+    const float sc = __int_as_float(((int)fmin(xr, 127.0) + 127) << 23);
+    return ex2_approx((float)(x - xr)) * sc;
+}
+
+// Moment sums of one candidate for n in [N0, N0 + NN): s[n][k] = sum_m W_k(m) g_n(m).
+template <int N0, int NN>
+__device__ __forceinline__ void cheb_sums(const QuadParams &qp, const float4 *sT, int M, double F0, float h,
+                                          double at, int lane, float4 *out)
+{
+    float s[NN][4];
+#pragma unroll
+    for (int n = 0; n < NN; ++n) s[n][0] = s[n][1] = s[n][2] = s[n][3] = 0.0f;
+    for (int m = lane; m < M; m += 32) {
+        const float4 a = sT[m];
+        const float base = exp2_split((double)a.x - at * (double)a.z + (double)a.y * F0);
+        const float t = 0.5f * a.y * h * 0.69314718f, t2 = t * t;
+        const float W0 = base * (1.0f + t2 * (1.0f + t2 * (0.25f + t2 * (1.0f / 36.0f))));                  // I0
+        const float W1 = base * (2.0f * t * (1.0f + t2 * (0.5f + t2 * (1.0f / 12.0f))));                     // 2 I1
+        const float W2 = base * (2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 * (1.0f / 48.0f))));             // 2 I2
+        const float W3 = base * (2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
+        const float *g = reinterpret_cast<const float *>(qp.zs_g + 3 * m) + N0;
+#pragma unroll
+        for (int n = 0; n < NN; ++n) {
+            const float gn = g[n];
+            s[n][0] = fmaf(W0, gn, s[n][0]);
+            s[n][1] = fmaf(W1, gn, s[n][1]);
+            s[n][2] = fmaf(W2, gn, s[n][2]);
+            s[n][3] = fmaf(W3, gn, s[n][3]);
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NN; ++n) {
+        const float f = (float)cheb_fold(N0 + n);
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float x = s[n][j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            v[j] = x * f;
+        }
+        if (lane == 0) out[n] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 // Called by every thread of the block after piece_consts; the caller syncs.
+// sT[m] = {A2d_m, K2_m, z_m, .}; qp.zs_g[3 m .. 3 m + 2] = g_0..g_11 of step m.
+// One warp per candidate; the step weights are exact to FP32 rounding (FP64
+// exponent), the sums run over the lane's steps and a warp tree.
 __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece &pc, int prof,
                                            const float4 *sT, int M, const PieceConst<float> &k, ChebTab &ct)
 {
@@ -206,36 +278,15 @@ __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece 
     const double kapL = qp.kap_L ? qp.kap_L[prof] : 1e30;
     double hmax = 0.0;
     for (int c = 0; c < k.nc; ++c) hmax = fmax(hmax, 0.5 * qp.ch_B[coff + pc.c_lo + c]);
-    const bool ok = kapL * hmax <= (double)kChebMaxA;
+    const bool ok = qp.zs_g != nullptr && kapL * hmax <= (double)kChebMaxA;
     if (threadIdx.x == 0) ct.ok = ok ? 1 : 0;
     if (!ok) return;
     for (int c = warp; c < k.nc; c += nw) {
         const double F0 = qp.ch_frel[coff + pc.c_lo + c];
         const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
         const double at = (double)(k.at_ab + k.hat[c]);
-        for (int kk = 0; kk < 3; ++kk) {          // one moment at a time keeps registers low
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            for (int m = lane; m < M; m += 32) {
-                const float4 a = sT[m];
-                const double g = kk == 0 ? 1.0 : (kk == 1 ? (double)a.z : (double)a.w);
-                const double base = g * exp2((double)a.x - at * (double)a.z + (double)a.y * F0);
-                const double t = 0.5 * (double)a.y * h * 0.69314718055994530942, t2 = t * t;
-                s0 += base * (1.0 + t2 * (1.0 + t2 * (0.25 + t2 / 36.0)));                   // I0
-                s1 += base * (2.0 * t * (1.0 + t2 * (0.5 + t2 / 12.0)));                     // 2 I1
-                s2 += base * (2.0 * t2 * (0.5 + t2 * (1.0 / 6.0 + t2 / 48.0)));              // 2 I2
-                s3 += base * (2.0 * t2 * t * (1.0 / 6.0 + t2 * (1.0 / 24.0 + t2 / 240.0)));  // 2 I3
-            }
-            s0 = warp_sum_d(s0);
-            s1 = warp_sum_d(s1);
-            s2 = warp_sum_d(s2);
-            s3 = warp_sum_d(s3);
-            if (lane == 0) {
-                ct.c[c][kk * 4 + 0] = (float)s0;
-                ct.c[c][kk * 4 + 1] = (float)s1;
-                ct.c[c][kk * 4 + 2] = (float)s2;
-                ct.c[c][kk * 4 + 3] = (float)s3;
-            }
-        }
+        cheb_sums<0, 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c]);
+        cheb_sums<6, kChebMom - 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c] + 6);
         if (lane == 0) {
             ct.mid[c] = 0.5f * (k.lo[c] + k.hi[c]);
             ct.invh[c] = (float)(1.0 / h);
@@ -243,16 +294,33 @@ __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece 
     }
 }
 
-// Small-phase |S|^2 of a point in candidate ci from the contracted moments.
-__device__ __forceinline__ void cheb_moments(const ChebTab &ct, int ci, float u, float &M0, float &M1, float &M2)
+// Folded moments nu'_n (n < NM) of a point in candidate ci at u = F_c - f_i.
+template <int NM>
+__device__ __forceinline__ void cheb_moments(const ChebTab &ct, int ci, float u, float (&nu)[NM], float &x)
 {
-    const float x = (u - ct.mid[ci]) * ct.invh[ci];
+    x = (u - ct.mid[ci]) * ct.invh[ci];
     const float T2 = fmaf(2.0f * x, x, -1.0f);
     const float T3 = fmaf(2.0f * x, T2, -x);
-    const float *c = ct.c[ci];
-    M0 = fmaf(c[3], T3, fmaf(c[2], T2, fmaf(c[1], x, c[0])));
-    M1 = fmaf(c[7], T3, fmaf(c[6], T2, fmaf(c[5], x, c[4])));
-    M2 = fmaf(c[11], T3, fmaf(c[10], T2, fmaf(c[9], x, c[8])));
+#pragma unroll
+    for (int n = 0; n < NM; ++n) {
+        const float4 c = ct.c[ci][n];
+        nu[n] = fmaf(c.w, T3, fmaf(c.z, T2, fmaf(c.y, x, c.x)));
+    }
+}
+
+// A = sum_{n even} phi^n nu'_n, B = sum_{n odd} phi^n nu'_n, |S|^2 = A^2 + B^2.
+template <int NM>
+__device__ __forceinline__ void cheb_AB(const float (&nu)[NM], float phi, float &A, float &B)
+{
+    const float p2 = phi * phi;
+    constexpr int ne = (NM + 1) / 2, no = NM / 2;
+    A = nu[2 * (ne - 1)];
+#pragma unroll
+    for (int i = ne - 2; i >= 0; --i) A = fmaf(A, p2, nu[2 * i]);
+    float b = nu[2 * (no - 1) + 1];
+#pragma unroll
+    for (int i = no - 2; i >= 0; --i) b = fmaf(b, p2, nu[2 * i + 1]);
+    B = phi * b;
 }
 
 }  // namespace isrs

@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
     const float m4pi2 = (float)(-4.0 * kPi * kPi);
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
+    const float phi_cheb = kChebPhiL / qp.L;
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
     unsigned n_small = 0, n_direct = 0, n_tele = 0;
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2;
             const float three_fi2 = 3.0f * fi * fi;
             const bool cheb = ct.ok != 0;
+            const float phi_lim = cheb ? phi_cheb : phi_small;   // upper |phi| of the small-phase forms
             float sum = 0.0f, comp = 0.0f;
             const int npts = G * G;
             for (int q = threadIdx.x; q < npts; q += blockDim.x) {
@@ -195,11 +197,12 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
                 const float phi = m4pi2 * f1 * f2 * br;
                 const float aphi = fabsf(phi);
                 float S2;
-                if (aphi <= phi_small) {
+                if (aphi <= phi_lim) {
                     if (cheb) {
-                        float M0, M1, M2;
-                        cheb_moments(ct, ci, u, M0, M1, M2);
-                        S2 = fmaf(-phi * phi, fmaf(M0, M2, -M1 * M1), M0 * M0);
+                        float nu[kChebMom], x, A, B;
+                        cheb_moments<kChebMom>(ct, ci, u, nu, x);
+                        cheb_AB<kChebMom>(nu, phi, A, B);
+                        S2 = fmaf(A, A, B * B);
                     } else {
                         S2 = zsum_small_f(phi, Fc, at, sT, M);
                     }

@@ -14,9 +14,12 @@ namespace isrs {
 // with log2 p_m = A2_m + K2_m Fc - at z_m (Eq. pk for the closed-form
 // profile).  The phase is carried in revolutions (z / 2pi).
 //
-// Three exact-to-FP32 evaluations of S = sum_m p_m dz_m sinc(phi dz_m/2)
+// Exact-to-FP32 evaluations of S = sum_m p_m dz_m sinc(phi dz_m/2)
 // e^{j phi z_m} (Eq. slow_vary), chosen per grid point by |phi|:
-//  * small (|phi| L <= 0.02): second-order expansion in phi,
+//  * contracted small phase (|phi| L <= 2, when the piece's Chebyshev
+//    contraction applies): the 11-moment series about the span centre
+//    (quad_common.cuh), no per-step work;
+//  * small (|phi| L <= 0.02, otherwise): second-order expansion in phi,
 //      |S|^2 = M0^2 - phi^2 (M0 M2 - M1^2) + O((phi L)^4),
 //    M0 = sum p dz, M1 = sum p dz z, M2 = sum p dz (z^2 + dz^2/12); the
 //    truncation is below 1e-9 relative (one exp per step, no phasor).
