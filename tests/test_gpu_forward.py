@@ -169,3 +169,24 @@ def test_multispan(eng, orc, n_spans, prec, rtol):
     r = orc.evaluate(wl)
     s = eng.snr(wl, precision=prec)
     np.testing.assert_allclose(s["snr"], r["snr"], rtol=max(rtol, 1e-9))
+
+
+def _kappa_L_half_B(wl, P):
+    """kappa(L) B/2 of the closed-form profile: the Chebyshev contraction of
+    the small-phase moments applies when it is at most 0.05."""
+    a = wl.alpha_R_per_km
+    leff = (1.0 - np.exp(-a * wl.L_km)) / a
+    return float(np.sum(P) * wl.Cr * leff * np.max(wl.B_THz) / 2)
+
+
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_strong_raman_tilt_per_step_small_phase(eng, orc, prec, rtol):
+    """With kappa(L) B/2 > 0.05 the FP32 kernel sums every small-phase point
+    step by step (second-order form, |phi| L <= 0.02) instead of the contracted
+    11-moment series; parity holds on that path too."""
+    wl = W.tiny(G=48, n_edges=57).with_(Cr=8.0)
+    P = np.full(wl.n_ch, W.dbm_to_w(4.0))
+    assert _kappa_L_half_B(wl, P) > 0.05
+    ref = _oracle_sigma(orc, wl, P=P)
+    got = eng.eta(wl, P=P, precision=prec)
+    np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)

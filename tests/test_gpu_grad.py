@@ -104,3 +104,13 @@ def test_adjoint_multispan(eng):
     r = eng.grad(wl)
     fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], wl.P_W, range(5))
     _check(r["dT_dP"], fd)
+
+
+def test_adjoint_strong_raman_tilt_per_step_small_phase(eng):
+    """kappa(L) B/2 > 0.05: no contracted small-phase points; the adjoint's
+    small-phase points are walked step by step on half-warps."""
+    wl = W.tiny(G=32, n_edges=41).with_(Cr=8.0)
+    P = np.full(wl.n_ch, W.dbm_to_w(4.0)) * W.dbm_to_w(W.random_profile_dbm(5, seed=9, lo=-1, hi=1)) / 1e-3
+    r = eng.grad(wl, P=P)
+    fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], P, range(5))
+    _check(r["dT_dP"], fd)
