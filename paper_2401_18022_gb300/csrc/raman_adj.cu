@@ -15,13 +15,15 @@
 //   dT/d ln P_x += ybar_i w W |S|^2 for x = a, b, c.
 //
 // k_quad_adj_tab walks every piece once per candidate channel, so a warp's
-// buckets stay in registers: pass 1 (one grid point per lane, points of other
-// candidates skipped) forms the z-sum as the forward kernel does; pass 2 turns
-// the warp around (every lane owns K consecutive steps, their tables held in
-// registers) and accumulates the buckets over the warp's 32 points.  FP32
-// lane sums are folded into FP64 shared buckets every 8 batches; at the end of
-// a candidate the block reduces them and scatters to the channel tables with
-// FP64 atomics.
+// buckets stay in registers, and evaluates every step term once: the warp
+// classifies 32 grid points (one per lane; points of other candidates are
+// skipped), appends them to one list per z-sum form, and walks the lists two
+// points at a time on half-warps: each of the 16 lanes of a half owns
+// K = ceil(M/16) consecutive steps, keeps their terms t_m in registers, the
+// half sums them into S with shuffles, and the same registers give
+// d|S|^2/d ln p_m = 2 Re(conj(S) t_m).  FP32 lane buckets are folded into
+// FP64 shared buckets every 8 batches; at the end of a candidate the block
+// reduces them and scatters to the channel tables with FP64 atomics.
 #include <cuda_runtime.h>
 
 #include "isrs_internal.cuh"
@@ -32,7 +34,10 @@ namespace isrs {
 
 namespace {
 
-constexpr int kPathSmall = 0, kPathDirect = 1, kPathTele = 2;
+constexpr unsigned kFullT = 0xffffffffu;
+constexpr int kClsSmallT = 0, kClsDirectT = 1, kClsTeleT = 2;
+constexpr int kListCapT = 34;       // a form's list: one carried point + 32 new (+1 pad)
+constexpr float kPadLog2T = -1000.0f;
 
 __device__ __forceinline__ float sinc_poly_t(float x)
 {
@@ -42,6 +47,13 @@ __device__ __forceinline__ float sinc_poly_t(float x)
     sc = fmaf(x2, sc, 8.3333333e-3f);                      // 1/5!
     sc = fmaf(x2, sc, -1.6666667e-1f);                     // -1/3!
     return fmaf(x2, sc, 1.0f);
+}
+
+__device__ __forceinline__ float half_sum_t(float v)
+{
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(kFullT, v, o, 16);
+    return v;
 }
 
 // Per-piece table (the forward's layout): {A + log2 dz, Sa, Sb, A} in log2 units.
@@ -63,35 +75,181 @@ __device__ void tab_setup_adj(const QuadParams &qp, const DevPiece &pc, int nc, 
     }
 }
 
-}  // namespace
+// Half-warp walks of one grid point of the candidate (weight cp = mult w W af
+// ybar, phase rate ph, in-channel offsets da, db).  Lane l16 owns steps
+// [K l16, K l16 + K) with tables oq = {A + log2 dz, Sa, Sb, A},
+// oz = {z, z^2 + dz^2/12, dz, .}, oe = {edge/2pi hi, lo, ., .}; padding steps
+// carry log2 weight -1000.  Each walk adds the lane's bucket terms
+// R += cp d|S|^2/d ln p_m, Ra += da (same), Rb += db (same) and returns |S|^2.
+template <int K>
+__device__ __forceinline__ float walk_direct_t(const float4 *oq, const float4 *oz, float cp, float ph, float da,
+                                               float db, float (&R)[K], float (&Ra)[K], float (&Rb)[K])
+{
+    const float hph = 0.5f * ph;
+    const float phr = ph * 0.15915494309189535f;
+    float tr[K], ti[K];
+    float sr = 0.0f, si = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 q = oq[k * 16];
+        const float4 z = oz[k * 16];
+        float sn, cs;
+        sincos_rev(phr * z.x, sn, cs);
+        float lp = fmaf(q.y, da, q.x);
+        lp = fmaf(q.z, db, lp);
+        const float amp = ex2_approx(lp) * sinc_poly_t(hph * z.z);
+        tr[k] = amp * cs;
+        ti[k] = amp * sn;
+        sr += tr[k];
+        si += ti[k];
+    }
+    sr = half_sum_t(sr);
+    si = half_sum_t(si);
+    const float c2 = 2.0f * cp, ca = c2 * da, cb = c2 * db;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float rr = fmaf(sr, tr[k], si * ti[k]);
+        R[k] = fmaf(c2, rr, R[k]);
+        Ra[k] = fmaf(ca, rr, Ra[k]);
+        Rb[k] = fmaf(cb, rr, Rb[k]);
+    }
+    return fmaf(sr, sr, si * si);
+}
 
 template <int K>
-__global__ void __launch_bounds__(256, 2) k_quad_adj_tab(AdjTabParams ap)
+__device__ __forceinline__ float walk_tele_t(const float4 *oq, const float4 *oe, int l16, float cp, float ph,
+                                             float da, float db, float (&R)[K], float (&Ra)[K], float (&Rb)[K])
+{
+    float tr[K], ti[K];
+    float Er = 1.0f, Ei = 0.0f, p0 = 0.0f, e1r = 1.0f, e1i = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 q = oq[k * 16];
+        const float4 e = oe[k * 16];
+        float sn, cs;
+        phasor_rev_ff(ph, e.x, e.y, sn, cs);
+        float lp = fmaf(q.y, da, q.w);
+        lp = fmaf(q.z, db, lp);
+        const float pm = ex2_approx(lp);
+        if (k == 0) {
+            p0 = pm;
+            e1r = cs;
+            e1i = sn;
+            tr[0] = 0.0f;
+            ti[0] = 0.0f;
+        } else {
+            tr[k] = pm * (cs - Er);
+            ti[k] = pm * (sn - Ei);
+        }
+        Er = cs;
+        Ei = sn;
+    }
+    // the lower edge of this lane's first step is the previous lane's last edge
+    float elr = __shfl_up_sync(kFullT, Er, 1, 16);
+    float eli = __shfl_up_sync(kFullT, Ei, 1, 16);
+    elr = l16 == 0 ? 1.0f : elr;
+    eli = l16 == 0 ? 0.0f : eli;
+    tr[0] = p0 * (e1r - elr);
+    ti[0] = p0 * (e1i - eli);
+    float ur = 0.0f, ui = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        ur += tr[k];
+        ui += ti[k];
+    }
+    ur = half_sum_t(ur);
+    ui = half_sum_t(ui);
+    const float iph2 = 1.0f / (ph * ph);
+    const float c2 = 2.0f * cp * iph2, ca = c2 * da, cb = c2 * db;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float rr = fmaf(ur, tr[k], ui * ti[k]);
+        R[k] = fmaf(c2, rr, R[k]);
+        Ra[k] = fmaf(ca, rr, Ra[k]);
+        Rb[k] = fmaf(cb, rr, Rb[k]);
+    }
+    return fmaf(ur, ur, ui * ui) * iph2;
+}
+
+template <int K>
+__device__ __forceinline__ float walk_small_t(const float4 *oq, const float4 *oz, float cp, float ph, float da,
+                                              float db, float (&R)[K], float (&Ra)[K], float (&Rb)[K])
+{
+    // |S|^2 = M0^2 - phi^2 (M0 M2 - M1^2); d|S|^2/d ln p_m = w_m (2 M0 - phi^2 (M2 + M0 c_m - 2 M1 z_m))
+    float wk[K];
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 q = oq[k * 16];
+        const float4 z = oz[k * 16];
+        float lp = fmaf(q.y, da, q.x);
+        lp = fmaf(q.z, db, lp);
+        wk[k] = ex2_approx(lp);
+        s0 += wk[k];
+        s1 = fmaf(wk[k], z.x, s1);
+        s2 = fmaf(wk[k], z.y, s2);
+    }
+    s0 = half_sum_t(s0);
+    s1 = half_sum_t(s1);
+    s2 = half_sum_t(s2);
+    const float ph2 = ph * ph;
+    const float al0 = 2.0f * s0 - ph2 * s2, al1 = -ph2 * s0, al2 = 2.0f * ph2 * s1;
+    const float ca = cp * da, cb = cp * db;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 z = oz[k * 16];
+        const float rr = wk[k] * fmaf(al2, z.x, fmaf(al1, z.y, al0));
+        R[k] = fmaf(cp, rr, R[k]);
+        Ra[k] = fmaf(ca, rr, Ra[k]);
+        Rb[k] = fmaf(cb, rr, Rb[k]);
+    }
+    return fmaf(-ph2, fmaf(s0, s2, -s1 * s1), s0 * s0);
+}
+
+}  // namespace
+
+#ifndef ISRS_ADJ_TAB_MIN_BLOCKS
+#define ISRS_ADJ_TAB_MIN_BLOCKS 2   // resident blocks per SM the register budget is sized for
+#endif
+
+template <int K>
+__global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(AdjTabParams ap)
 {
     const QuadParams &qp = ap.q;
     extern __shared__ float4 smem_f4[];
     const int M = qp.n_steps, G = qp.G;
     const int nw = blockDim.x >> 5;
-    float4 *sZ = smem_f4;                                           // [M] {z, z^2 + dz^2/12, dz, 0}
-    float4 *sE = sZ + M;                                            // [M] {edge/2pi hi, lo, 0, 0}
-    float4 *sQ = sE + M;                                            // [nc_max][M]
-    RowF *rows = reinterpret_cast<RowF *>(sQ + (size_t)qp.nc_max * M);   // [G]
-    float4 *sPs = reinterpret_cast<float4 *>(rows + G);             // [nw][32][2] staged point states
-    double *sB = reinterpret_cast<double *>(sPs + nw * 64);         // [nw][3][K][32] FP64 buckets
+    float4 *sQ = smem_f4;                                           // [nc_max][M]
+    float4 *sOQ = sQ + (size_t)qp.nc_max * M;                       // [K][16] owned {Ad, Sa, Sb, A} of the candidate
+    float4 *sOZ = sOQ + K * 16;                                     // [K][16] owned {z, c, dz, 0}
+    float4 *sOE = sOZ + K * 16;                                     // [K][16] owned {edge hi, lo, 0, 0}
+    float4 *sL = sOE + K * 16;                                      // [nw][3][kListCapT] {cp, phi, da, db}
+    double *sB = reinterpret_cast<double *>(sL + nw * 3 * kListCapT);   // [nw][3][K][16] FP64 buckets
+    RowF *rows = reinterpret_cast<RowF *>(sB + (size_t)nw * 3 * K * 16);   // [G]
     __shared__ PieceConst<float> kc;
     __shared__ float s_d0[2];
     __shared__ double scratch[32];
     __shared__ int s_item;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const float4 za = qp.zs_a[m];
-        const float4 zb = qp.zs_b[m];
-        sZ[m] = make_float4(za.x, za.y, za.w, 0.0f);
-        sE[m] = make_float4(zb.x, zb.y, 0.0f, 0.0f);
+    const int l16 = lane & 15, half = lane >> 4;
+    // the owned z and edge tables never change; padding steps repeat the last edge
+    {
+        const float4 zl = qp.zs_b[M - 1];
+        for (int t = threadIdx.x; t < K * 16; t += blockDim.x) {
+            const int k = t >> 4, l = t & 15, m = l * K + k;
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f), e = make_float4(zl.x, zl.y, 0.f, 0.f);
+            if (m < M) {
+                const float4 za = qp.zs_a[m];
+                const float4 zb = qp.zs_b[m];
+                z = make_float4(za.x, za.y, za.w, 0.f);
+                e = make_float4(zb.x, zb.y, 0.f, 0.f);
+            }
+            sOZ[k * 16 + l] = z;
+            sOE[k * 16 + l] = e;
+        }
     }
-    for (int t = threadIdx.x; t < nw * 3 * K * 32; t += blockDim.x) sB[t] = 0.0;
-    __syncthreads();
+    for (int t = threadIdx.x; t < nw * 3 * K * 16; t += blockDim.x) sB[t] = 0.0;
 
     const float c3 = (float)(kPi * qp.beta3);
     const float c4 = (float)(2.0 * kPi * kPi / 3.0 * qp.beta4);
@@ -100,25 +258,12 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj_tab(AdjTabParams ap)
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
     const float invG = 1.0f / (float)G;
-    const int m0 = lane * K;
-    float4 *myPs = sPs + warp * 64;
-    double *myB = sB + (size_t)warp * 3 * K * 32;
-
-    // this lane's steps: the z tables never change
-    float oz[K], oc[K], odz[K], oeh[K], oel[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const bool ok = m0 + k < M;
-        const float4 z = ok ? sZ[m0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 e = ok ? sE[m0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        oz[k] = z.x;
-        oc[k] = z.y;
-        odz[k] = z.z;
-        oeh[k] = e.x;
-        oel[k] = e.y;
-    }
-    const float e0h = (m0 > 0 && m0 < M) ? sE[m0 - 1].x : 0.0f;     // lower edge of the lane's block
-    const float e0l = (m0 > 0 && m0 < M) ? sE[m0 - 1].y : 0.0f;
+    const float4 *oq = sOQ + l16, *oz = sOZ + l16, *oe = sOE + l16;
+    float4 *Ls = sL + warp * 3 * kListCapT;
+    float4 *Ld = Ls + kListCapT;
+    float4 *Lt = Ld + kListCapT;
+    double *myB = sB + (size_t)warp * 3 * K * 16;
+    const unsigned lt_mask = (1u << lane) - 1u;
 
     for (;;) {
         __syncthreads();
@@ -147,26 +292,23 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj_tab(AdjTabParams ap)
             const int npts = G * G;
             const int nc = kc.nc;
             for (int cc = 0; cc < nc; ++cc) {
-                const float4 *Q = sQ + cc * M;
-                float oAd[K], oA[K], oSa[K], oSb[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const float4 q = (m0 + k < M) ? Q[m0 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    oAd[k] = q.x;
-                    oSa[k] = q.y;
-                    oSb[k] = q.z;
-                    oA[k] = q.w;
+                // lane-contiguous copy of the candidate's owned step tables
+                for (int t = threadIdx.x; t < K * 16; t += blockDim.x) {
+                    const int k = t >> 4, l = t & 15, m = l * K + k;
+                    sOQ[k * 16 + l] = m < M ? sQ[cc * M + m] : make_float4(kPadLog2T, 0.f, 0.f, kPadLog2T);
                 }
+                __syncthreads();
                 float R[K], Ra[K], Rb[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) R[k] = Ra[k] = Rb[k] = 0.0f;
                 float vsum = 0.0f;
+                int ns = 0, nd = 0, nt = 0;
                 int batches = 0;
                 for (int qb = warp * 32; qb < npts; qb += blockDim.x) {
-                    // ---- pass 1: this lane's grid point, if its F_c is in candidate cc
+                    // ---- 1. this lane's grid point, if its F_c is in candidate cc
                     const int q = qb + lane;
-                    float cp = 0.0f, phi = 0.0f, da = 0.0f, db = 0.0f, q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
-                    int path = 0;
+                    float cp = 0.0f, phi = 0.0f, da = 0.0f, db = 0.0f;
+                    int cls = -1;
                     if (q < npts) {
                         const int r = (int)(((float)q + 0.5f) * invG);
                         const int j = q - r * G;
@@ -190,145 +332,98 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj_tab(AdjTabParams ap)
                                                            three_fi2);
                                     phi = m4pi2 * f1 * f2 * br;
                                     const float aphi = fabsf(phi);
-                                    float S2;
-                                    if (aphi <= phi_small) {
-                                        path = kPathSmall;
-                                        for (int m = 0; m < M; ++m) {
-                                            const float4 t = Q[m];
-                                            const float4 z = sZ[m];
-                                            float lp = fmaf(t.y, da, t.x);
-                                            lp = fmaf(t.z, db, lp);
-                                            const float w = ex2_approx(lp);
-                                            q0 += w;
-                                            q1 = fmaf(w, z.x, q1);
-                                            q2 = fmaf(w, z.y, q2);
-                                        }
-                                        S2 = fmaf(-phi * phi, fmaf(q0, q2, -q1 * q1), q0 * q0);
-                                    } else if (aphi <= phi_direct) {
-                                        path = kPathDirect;
-                                        const float hphi = 0.5f * phi;
-                                        const float phir = phi * 0.15915494309189535f;
-                                        for (int m = 0; m < M; ++m) {
-                                            const float4 t = Q[m];
-                                            const float4 z = sZ[m];
-                                            float sn, cs;
-                                            sincos_rev(phir * z.x, sn, cs);
-                                            float lp = fmaf(t.y, da, t.x);
-                                            lp = fmaf(t.z, db, lp);
-                                            const float amp = ex2_approx(lp) * sinc_poly_t(hphi * z.z);
-                                            q0 = fmaf(amp, cs, q0);
-                                            q1 = fmaf(amp, sn, q1);
-                                        }
-                                        S2 = q0 * q0 + q1 * q1;
-                                    } else {
-                                        path = kPathTele;
-                                        float Er = 1.0f, Ei = 0.0f;
-                                        for (int m = 0; m < M; ++m) {
-                                            const float4 t = Q[m];
-                                            const float4 eg = sE[m];
-                                            float sn, cs;
-                                            phasor_rev_ff(phi, eg.x, eg.y, sn, cs);
-                                            float lp = fmaf(t.y, da, t.w);
-                                            lp = fmaf(t.z, db, lp);
-                                            const float p = ex2_approx(lp);
-                                            q0 = fmaf(p, cs - Er, q0);
-                                            q1 = fmaf(p, sn - Ei, q1);
-                                            Er = cs;
-                                            Ei = sn;
-                                        }
-                                        S2 = (q0 * q0 + q1 * q1) / (phi * phi);
-                                    }
+                                    cls = aphi <= phi_small ? kClsSmallT : (aphi <= phi_direct ? kClsDirectT : kClsTeleT);
                                     cp = mult * rw.w * W * array_factor_f(phi, qp) * ybar;
-                                    vsum = fmaf(cp, S2, vsum);
                                 }
                             }
                         }
                     }
-                    myPs[2 * lane] = make_float4(cp, phi, da, db);
-                    myPs[2 * lane + 1] = make_float4(q0, q1, q2, __int_as_float(path));
+                    // append to the form's list
+                    const unsigned bs = __ballot_sync(kFullT, cls == kClsSmallT);
+                    const unsigned bd = __ballot_sync(kFullT, cls == kClsDirectT);
+                    const unsigned bt = __ballot_sync(kFullT, cls == kClsTeleT);
+                    if (cls >= 0) {
+                        const float4 v = make_float4(cp, phi, da, db);
+                        if (cls == kClsSmallT) Ls[ns + __popc(bs & lt_mask)] = v;
+                        else if (cls == kClsDirectT) Ld[nd + __popc(bd & lt_mask)] = v;
+                        else Lt[nt + __popc(bt & lt_mask)] = v;
+                    }
+                    ns += __popc(bs);
+                    nd += __popc(bd);
+                    nt += __popc(bt);
                     __syncwarp();
-                    // ---- pass 2: the warp's 32 points, every lane on its own steps
-                    for (int p = 0; p < 32; ++p) {
-                        const float4 st0 = myPs[2 * p];
-                        const float cpp = st0.x;
-                        if (cpp == 0.0f) continue;
-                        const float4 st1 = myPs[2 * p + 1];
-                        const float ph = st0.y, pda = st0.z, pdb = st0.w;
-                        const float p0 = st1.x, p1 = st1.y, p2 = st1.z;
-                        const int pth = __float_as_int(st1.w);
-                        const float ca = cpp * pda, cb = cpp * pdb;
-                        if (pth == kPathSmall) {
-                            // d|S|^2/d ln p_m = w_m (2 M0 - phi^2 (M2 + M0 c_m - 2 M1 z_m))
-                            const float ph2 = ph * ph;
-                            const float al0 = 2.0f * p0 - ph2 * p2, al1 = -ph2 * p0, al2 = 2.0f * ph2 * p1;
-#pragma unroll
-                            for (int k = 0; k < K; ++k) {
-                                if (m0 + k < M) {
-                                    float lp = fmaf(oSa[k], pda, oAd[k]);
-                                    lp = fmaf(oSb[k], pdb, lp);
-                                    const float rr = ex2_approx(lp) * fmaf(al2, oz[k], fmaf(al1, oc[k], al0));
-                                    R[k] = fmaf(cpp, rr, R[k]);
-                                    Ra[k] = fmaf(ca, rr, Ra[k]);
-                                    Rb[k] = fmaf(cb, rr, Rb[k]);
-                                }
-                            }
-                        } else if (pth == kPathDirect) {
-                            // d|S|^2/d ln p_m = 2 Re(conj(S) p_m dz_m sinc e^{j phi z_m})
-                            const float hph = 0.5f * ph;
-                            const float phr = ph * 0.15915494309189535f;
-#pragma unroll
-                            for (int k = 0; k < K; ++k) {
-                                if (m0 + k < M) {
-                                    float sn, cs;
-                                    sincos_rev(phr * oz[k], sn, cs);
-                                    float lp = fmaf(oSa[k], pda, oAd[k]);
-                                    lp = fmaf(oSb[k], pdb, lp);
-                                    const float amp = ex2_approx(lp) * sinc_poly_t(hph * odz[k]);
-                                    const float rr = 2.0f * amp * fmaf(p0, cs, p1 * sn);
-                                    R[k] = fmaf(cpp, rr, R[k]);
-                                    Ra[k] = fmaf(ca, rr, Ra[k]);
-                                    Rb[k] = fmaf(cb, rr, Rb[k]);
-                                }
-                            }
-                        } else {
-                            // d|S|^2/d ln p_m = 2 Re(conj(U) p_m (E_{m+1} - E_m)) / phi^2
-                            float Er = 1.0f, Ei = 0.0f;
-                            if (m0 > 0) phasor_rev_ff(ph, e0h, e0l, Ei, Er);
-                            const float g = 2.0f / (ph * ph);
-#pragma unroll
-                            for (int k = 0; k < K; ++k) {
-                                if (m0 + k < M) {
-                                    float sn, cs;
-                                    phasor_rev_ff(ph, oeh[k], oel[k], sn, cs);
-                                    float lp = fmaf(oSa[k], pda, oA[k]);
-                                    lp = fmaf(oSb[k], pdb, lp);
-                                    const float rr = g * ex2_approx(lp) * fmaf(p0, cs - Er, p1 * (sn - Ei));
-                                    R[k] = fmaf(cpp, rr, R[k]);
-                                    Ra[k] = fmaf(ca, rr, Ra[k]);
-                                    Rb[k] = fmaf(cb, rr, Rb[k]);
-                                    Er = cs;
-                                    Ei = sn;
-                                }
-                            }
-                        }
+                    // ---- 2. walk the lists in pairs, one point per half-warp
+                    for (int p = half; p + 1 - half < nd; p += 2) {
+                        const float4 st = Ld[p];
+                        const float s2 = walk_direct_t<K>(oq, oz, st.x, st.y, st.z, st.w, R, Ra, Rb);
+                        vsum += l16 == 0 ? st.x * s2 : 0.0f;
                     }
+                    for (int p = half; p + 1 - half < nt; p += 2) {
+                        const float4 st = Lt[p];
+                        const float s2 = walk_tele_t<K>(oq, oe, l16, st.x, st.y, st.z, st.w, R, Ra, Rb);
+                        vsum += l16 == 0 ? st.x * s2 : 0.0f;
+                    }
+                    for (int p = half; p + 1 - half < ns; p += 2) {
+                        const float4 st = Ls[p];
+                        const float s2 = walk_small_t<K>(oq, oz, st.x, st.y, st.z, st.w, R, Ra, Rb);
+                        vsum += l16 == 0 ? st.x * s2 : 0.0f;
+                    }
+                    // an odd point waits at the head of its list for the next batch
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (nd & 1) Ld[0] = Ld[nd - 1];
+                        if (nt & 1) Lt[0] = Lt[nt - 1];
+                        if (ns & 1) Ls[0] = Ls[ns - 1];
+                    }
+                    nd &= 1;
+                    nt &= 1;
+                    ns &= 1;
                     if (++batches == 8) {
                         batches = 0;
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
-                            myB[(0 * K + k) * 32 + lane] += (double)R[k];
-                            myB[(1 * K + k) * 32 + lane] += (double)Ra[k];
-                            myB[(2 * K + k) * 32 + lane] += (double)Rb[k];
+                            const float r0 = R[k] + __shfl_xor_sync(kFullT, R[k], 16);
+                            const float r1 = Ra[k] + __shfl_xor_sync(kFullT, Ra[k], 16);
+                            const float r2 = Rb[k] + __shfl_xor_sync(kFullT, Rb[k], 16);
+                            if (half == 0) {
+                                myB[(0 * K + k) * 16 + l16] += (double)r0;
+                                myB[(1 * K + k) * 16 + l16] += (double)r1;
+                                myB[(2 * K + k) * 16 + l16] += (double)r2;
+                            }
                             R[k] = Ra[k] = Rb[k] = 0.0f;
                         }
                     }
-                    __syncwarp();          // the next batch overwrites the staged states
+                    __syncwarp();          // the next batch appends to the lists
+                }
+                // the last odd point of each form, beside a zero-weight copy of itself
+                if (nd) {
+                    float4 st = Ld[0];
+                    if (half) st.x = 0.0f;
+                    const float s2 = walk_direct_t<K>(oq, oz, st.x, st.y, st.z, st.w, R, Ra, Rb);
+                    vsum += l16 == 0 ? st.x * s2 : 0.0f;
+                }
+                if (nt) {
+                    float4 st = Lt[0];
+                    if (half) st.x = 0.0f;
+                    const float s2 = walk_tele_t<K>(oq, oe, l16, st.x, st.y, st.z, st.w, R, Ra, Rb);
+                    vsum += l16 == 0 ? st.x * s2 : 0.0f;
+                }
+                if (ns) {
+                    float4 st = Ls[0];
+                    if (half) st.x = 0.0f;
+                    const float s2 = walk_small_t<K>(oq, oz, st.x, st.y, st.z, st.w, R, Ra, Rb);
+                    vsum += l16 == 0 ? st.x * s2 : 0.0f;
                 }
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    myB[(0 * K + k) * 32 + lane] += (double)R[k];
-                    myB[(1 * K + k) * 32 + lane] += (double)Ra[k];
-                    myB[(2 * K + k) * 32 + lane] += (double)Rb[k];
+                    const float r0 = R[k] + __shfl_xor_sync(kFullT, R[k], 16);
+                    const float r1 = Ra[k] + __shfl_xor_sync(kFullT, Ra[k], 16);
+                    const float r2 = Rb[k] + __shfl_xor_sync(kFullT, Rb[k], 16);
+                    if (half == 0) {
+                        myB[(0 * K + k) * 16 + l16] += (double)r0;
+                        myB[(1 * K + k) * 16 + l16] += (double)r1;
+                        myB[(2 * K + k) * 16 + l16] += (double)r2;
+                    }
                 }
                 const double vtot = block_sum_d((double)vsum, scratch);   // syncs the block
                 const int c = pc.c_lo + cc;
@@ -338,13 +433,13 @@ __global__ void __launch_bounds__(256, 2) k_quad_adj_tab(AdjTabParams ap)
                     const int ln = m / K, kk = m - ln * K;
                     double r0 = 0.0, r1 = 0.0, r2 = 0.0;
                     for (int w = 0; w < nw; ++w) {
-                        double *b = sB + (size_t)w * 3 * K * 32;
-                        r0 += b[(0 * K + kk) * 32 + ln];
-                        r1 += b[(1 * K + kk) * 32 + ln];
-                        r2 += b[(2 * K + kk) * 32 + ln];
-                        b[(0 * K + kk) * 32 + ln] = 0.0;
-                        b[(1 * K + kk) * 32 + ln] = 0.0;
-                        b[(2 * K + kk) * 32 + ln] = 0.0;
+                        double *b = sB + (size_t)w * 3 * K * 16;
+                        r0 += b[(0 * K + kk) * 16 + ln];
+                        r1 += b[(1 * K + kk) * 16 + ln];
+                        r2 += b[(2 * K + kk) * 16 + ln];
+                        b[(0 * K + kk) * 16 + ln] = 0.0;
+                        b[(1 * K + kk) * 16 + ln] = 0.0;
+                        b[(2 * K + kk) * 16 + ln] = 0.0;
                     }
                     if (r0 == 0.0 && r1 == 0.0 && r2 == 0.0) continue;
                     double2 *g = ap.gAB;
@@ -378,11 +473,15 @@ void *adj_tab_fn()
 
 void *adj_tab_kernel_for(int n_steps)
 {
-    switch ((n_steps + 31) / 32) {
+    switch ((n_steps + 15) / 16) {
     case 1: return adj_tab_fn<1>();
     case 2: return adj_tab_fn<2>();
     case 3: return adj_tab_fn<3>();
     case 4: return adj_tab_fn<4>();
+    case 5: return adj_tab_fn<5>();
+    case 6: return adj_tab_fn<6>();
+    case 7: return adj_tab_fn<7>();
+    case 8: return adj_tab_fn<8>();
     }
     return nullptr;
 }
@@ -391,9 +490,9 @@ void *adj_tab_kernel_for(int n_steps)
 
 size_t adjoint_tab_smem_bytes(int n_steps, int G, int nc_max, int block)
 {
-    const int K = (n_steps + 31) / 32, nw = block / 32;
-    return (size_t)n_steps * (2 + nc_max) * sizeof(float4) + (size_t)G * sizeof(RowF) +
-           (size_t)nw * 64 * sizeof(float4) + (size_t)nw * 3 * K * 32 * sizeof(double);
+    const int K = (n_steps + 15) / 16, nw = block / 32;
+    return ((size_t)n_steps * nc_max + 3 * K * 16 + (size_t)nw * 3 * kListCapT) * sizeof(float4) +
+           (size_t)nw * 3 * K * 16 * sizeof(double) + (size_t)G * sizeof(RowF);
 }
 
 int adjoint_tab_blocks_per_sm(int n_steps, int G, int nc_max, int block)
