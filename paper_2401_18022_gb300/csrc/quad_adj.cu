@@ -41,6 +41,11 @@ constexpr int kListCap = 34;    // a form's list: one carried point + 32 new (+1
 constexpr int kCtr = 4;         // F_c candidates whose small-phase points are contracted
 constexpr int kCtrN = kChebMom * 5;   // per candidate: moments nu_0..nu_10 x T_0..T_4
 constexpr int kCtrS = 64;       // slots per candidate (two 32-value butterflies)
+// A batch whose contracted points all have |phi| L <= 0.2 keeps n <= 5 in its
+// bucket sums (30 values, one butterfly): the omitted orders are below
+// (0.1)^6/6! = 1.4e-9 of the derivative.
+constexpr int kShortN = 30;
+constexpr float kShortPhiL = 0.2f;
 constexpr int kFoldBatches = 8; // batches between FP64 folds of the FP32 accumulators
 constexpr float kPadLog2 = -1000.0f;   // log2 weight of the padding steps (ex2 -> 0)
 
@@ -424,6 +429,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 unsigned cmask = __ballot_sync(kFull, ctr);
                 const unsigned cmask0 = cmask;
                 if (cmask) {
+                    // positive floats order as their bit patterns
+                    const unsigned phl = __reduce_max_sync(kFull, __float_as_uint(ctr ? fabsf(phi) * qp.L : 0.0f));
+                    const bool short_form = __uint_as_float(phl) <= kShortPhiL;
                     const float T2 = fmaf(2.0f * cx, cx, -1.0f);
                     const float T3 = fmaf(2.0f * cx, T2, -cx);
                     const float T4 = fmaf(2.0f * cx, T3, -T2);
@@ -436,11 +444,17 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         al[1] = mine ? 2.0f * cpt * cB * phi : 0.0f;
 #pragma unroll
                         for (int n = 2; n < kChebMom; ++n) al[n] = al[n - 2] * (phi * phi);
-                        const auto val = [&](int v) { return v < kCtrN ? al[v / 5] * Tk[v % 5] : 0.0f; };
-                        const float y0 = butterfly32([&](int v) { return val(v); }, lane);
-                        const float y1 = butterfly32([&](int v) { return val(v + 32); }, lane);
-                        sYf[warp][cl][lane] += y0;
-                        sYf[warp][cl][lane + 32] += y1;
+                        if (short_form) {
+                            const float y0 = butterfly32(
+                                [&](int v) { return v < kShortN ? al[v / 5] * Tk[v % 5] : 0.0f; }, lane);
+                            if (lane < kShortN) sYf[warp][cl][lane] += y0;
+                        } else {
+                            const auto val = [&](int v) { return v < kCtrN ? al[v / 5] * Tk[v % 5] : 0.0f; };
+                            const float y0 = butterfly32([&](int v) { return val(v); }, lane);
+                            const float y1 = butterfly32([&](int v) { return val(v + 32); }, lane);
+                            sYf[warp][cl][lane] += y0;
+                            sYf[warp][cl][lane + 32] += y1;
+                        }
                         cmask &= ~__ballot_sync(kFull, mine);
                     }
                 }
