@@ -545,6 +545,106 @@ __device__ __forceinline__ float zsum_tele_t(float phi, float da, float db, cons
     return (Sr * Sr + Si * Si) / (phi * phi);
 }
 
+// ---------------------------------------------------------------------------
+// Contracted small-phase series for the tabulated profile (the 11-moment
+// series of the closed-form kernels, App. A Eq. slow_vary).  Inside the piece,
+// log2 w_m = Ad_m + Sa_m da + Sb_m db with da = h_a x, db = h_b y the offsets
+// of F_a and F_b inside their channels, so
+//   w_m = 2^{Ad_m} e^{alpha_m x} e^{beta_m y},  alpha = Sa h_a ln 2, beta = Sb h_b ln 2,
+// and with e^{a x} = I0(a) + 2 sum Ik(a) Tk(x) in each offset
+//   nu_n(x, y) = sum_{k,l <= 3} C_nkl Tk(x) Tl(y),
+//   C_nkl = sum_m 2^{Ad_m} b_k(alpha_m) b_l(beta_m) g_n(m)
+// (truncation ~ (a/2)^4/12 per offset for |alpha|, |beta| <= 0.05).  The
+// coefficients are stored times (-1)^{floor(n/2)}/n!, as row k = float4 over l.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 bessel_b4(float a)
+{
+    const float t = 0.5f * a, t2 = t * t;
+    return make_float4(1.0f + t2 * (1.0f + t2 * (0.25f + t2 * (1.0f / 36.0f))),              // I0
+                       2.0f * t * (1.0f + t2 * (0.5f + t2 * (1.0f / 12.0f))),                 // 2 I1
+                       2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 * (1.0f / 48.0f))),         // 2 I2
+                       2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
+}
+
+// Every thread calls after tab_setup_f (synced); returns whether the piece's
+// small-phase points use the contraction.  sW: [M][4] float4 scratch,
+// sG: [M][12] moments, sC: [nc][kChebMom][4] float4, s_flag: shared int.
+__device__ bool tab_cheb_setup(const QuadParams &qp, const DevPiece &pc, int nc, const float4 *sQ, float4 *sW,
+                               float *sG, float4 *sC, float *s_amax)
+{
+    const int M = qp.n_steps;
+    if (qp.zs_g == nullptr) return false;
+    const int coff = qp.plan_ch_off[pc.plan];
+    const float ha = (float)(0.5 * qp.ch_B[coff + pc.a]), hb = (float)(0.5 * qp.ch_B[coff + pc.b]);
+    const float ln2 = 0.69314718f;
+    if (threadIdx.x == 0) *s_amax = 0.0f;
+    __syncthreads();
+    float amax = 0.0f;
+    for (int t = threadIdx.x; t < nc * M; t += blockDim.x) {
+        const float4 q = sQ[t];
+        amax = fmaxf(amax, fmaxf(fabsf(q.y * ha), fabsf(q.z * hb)) * ln2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned *>(s_amax), __float_as_uint(amax));
+    for (int t = threadIdx.x; t < M * 12; t += blockDim.x) sG[t] = reinterpret_cast<const float *>(qp.zs_g)[t];
+    __syncthreads();
+    if (!(*s_amax <= kChebMaxA)) return false;
+    for (int c = 0; c < nc; ++c) {
+        const float4 *Q = sQ + c * M;
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            const float4 q = Q[m];
+            const float base = ex2_approx(q.x);
+            const float4 bk = bessel_b4(q.y * ha * ln2), bl = bessel_b4(q.z * hb * ln2);
+            const float bkv[4] = {bk.x, bk.y, bk.z, bk.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float wk = base * bkv[k];
+                sW[m * 4 + k] = make_float4(wk * bl.x, wk * bl.y, wk * bl.z, wk * bl.w);
+            }
+        }
+        __syncthreads();
+        // one coefficient (n, k, l) per thread: compensated sum over the steps
+        for (int t = threadIdx.x; t < kChebMom * 16; t += blockDim.x) {
+            const int n = t >> 4, k = (t >> 2) & 3, l = t & 3;
+            float sum = 0.0f, comp = 0.0f;
+            for (int m = 0; m < M; ++m) {
+                const float4 w = sW[m * 4 + k];
+                const float wl = l == 0 ? w.x : (l == 1 ? w.y : (l == 2 ? w.z : w.w));
+                const float y = wl * sG[m * 12 + n] - comp;
+                const float tt = sum + y;
+                comp = (tt - sum) - y;
+                sum = tt;
+            }
+            reinterpret_cast<float *>(sC + (c * kChebMom + n) * 4 + k)[l] = sum * (float)cheb_fold(n);
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// |S|^2 of a small-phase point of candidate ci from the contracted series.
+__device__ __forceinline__ float tab_cheb_s2(const float4 *sC, int ci, float x, float y, float phi)
+{
+    const float Tx2 = fmaf(2.0f * x, x, -1.0f), Tx3 = fmaf(2.0f * x, Tx2, -x);
+    const float Ty2 = fmaf(2.0f * y, y, -1.0f), Ty3 = fmaf(2.0f * y, Ty2, -y);
+    float nu[kChebMom];
+    const float4 *C = sC + ci * kChebMom * 4;
+#pragma unroll
+    for (int n = 0; n < kChebMom; ++n) {
+        float r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 c = C[n * 4 + k];
+            r[k] = fmaf(c.w, Ty3, fmaf(c.z, Ty2, fmaf(c.y, y, c.x)));
+        }
+        nu[n] = fmaf(r[3], Tx3, fmaf(r[2], Tx2, fmaf(r[1], x, r[0])));
+    }
+    float A, B;
+    cheb_AB<kChebMom>(nu, phi, A, B);
+    return fmaf(A, A, B * B);
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
@@ -554,9 +654,13 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
     float4 *sZ = smem_f4;                              // [M] {z, z^2 + dz^2/12, dz, 0}
     float4 *sE = sZ + M;                               // [M] {edge/2pi hi, lo, 0, 0}
     float4 *sQ = sE + M;                               // [nc_max][M] {A + log2 dz, Sa, Sb, A}
-    RowF *rows = reinterpret_cast<RowF *>(sQ + (size_t)qp.nc_max * M);   // [G]
+    float4 *sW = sQ + (size_t)qp.nc_max * M;           // [M][4] contraction weights of one candidate
+    float4 *sC = sW + (size_t)M * 4;                   // [nc_max][kChebMom][4] contracted coefficients
+    float *sG = reinterpret_cast<float *>(sC + (size_t)qp.nc_max * kChebMom * 4);   // [M][12] step moments
+    RowF *rows = reinterpret_cast<RowF *>(sG + (size_t)M * 12);   // [G]
     __shared__ PieceConst<float> kc;
     __shared__ float s_d0[2];
+    __shared__ float s_amax;
     __shared__ double scratch[32];
     __shared__ int s_item;
 
@@ -572,6 +676,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
     const float m4pi2 = (float)(-4.0 * kPi * kPi);
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
+    const float phi_cheb = kChebPhiL / qp.L;
     const float invG = 1.0f / (float)G;
     unsigned n_small = 0, n_direct = 0, n_tele = 0;
 
@@ -596,6 +701,14 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
             __syncthreads();
             tab_setup_f(qp, pc, item.prof, kc.nc, sQ);
             __syncthreads();
+            const bool cheb = tab_cheb_setup(qp, pc, kc.nc, sQ, sW, sG, sC, &s_amax);
+            const float phi_lim = cheb ? phi_cheb : phi_small;   // upper |phi| of the small-phase forms
+            float inv_ha = 0.0f, inv_hb = 0.0f;
+            {
+                const int coff = qp.plan_ch_off[pc.plan];
+                inv_ha = (float)(2.0 / qp.ch_B[coff + pc.a]);
+                inv_hb = (float)(2.0 / qp.ch_B[coff + pc.b]);
+            }
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2;
             const float da0 = s_d0[0], db0 = s_d0[1];
             const float three_fi2 = 3.0f * fi * fi;
@@ -625,8 +738,8 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
                 const float phi = m4pi2 * f1 * f2 * br;
                 const float aphi = fabsf(phi);
                 float S2;
-                if (aphi <= phi_small) {
-                    S2 = zsum_small_t(phi, da, db, Q, sZ, M);
+                if (aphi <= phi_lim) {
+                    S2 = cheb ? tab_cheb_s2(sC, ci, da * inv_ha, db * inv_hb, phi) : zsum_small_t(phi, da, db, Q, sZ, M);
                     ++n_small;
                 } else if (aphi <= phi_direct) {
                     S2 = zsum_direct_t(phi, da, db, Q, sZ, M);
@@ -760,7 +873,8 @@ __global__ void __launch_bounds__(256) k_quad_f64_tab(QuadParams qp)
 size_t quad_tab_smem_bytes(int precision, int n_steps, int G, int nc_max)
 {
     if (precision == 0)
-        return (size_t)n_steps * (2 + nc_max) * sizeof(float4) + (size_t)G * sizeof(RowF);
+        return (size_t)n_steps * (2 + nc_max + 4) * sizeof(float4) + (size_t)nc_max * kChebMom * 4 * sizeof(float4) +
+               (size_t)n_steps * 12 * sizeof(float) + (size_t)G * sizeof(RowF);
     return (size_t)n_steps * (1 + 2 * nc_max) * sizeof(double2) + (size_t)G * sizeof(RowD);
 }
 

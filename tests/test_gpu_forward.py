@@ -190,3 +190,15 @@ def test_strong_raman_tilt_per_step_small_phase(eng, orc, prec, rtol):
     ref = _oracle_sigma(orc, wl, P=P)
     got = eng.eta(wl, P=P, precision=prec)
     np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)
+
+
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_many_fc_candidates(eng, orc, prec, rtol):
+    """A 300 GHz channel between narrow channels: six F_c candidates per SCI
+    piece of the wide channel."""
+    from _plans import wide_cut_plan
+    wl = wide_cut_plan(G=40)
+    cuts = [4, 5, 6]
+    ref = _oracle_sigma(orc, wl, cuts=cuts)
+    got = eng.eta(wl, cuts=cuts, precision=prec)
+    np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)

@@ -115,3 +115,39 @@ def test_small_phi_centred_moment_series(orc):
             worst_bound = max(worst_bound, err - 2 * (abs(x) / 2) ** 11 / math.factorial(11))
     assert worst < 5e-8, worst
     assert worst_bound < 1e-12, worst_bound
+
+
+def test_chebyshev_contraction_two_offsets(orc):
+    """The tabulated (Raman-ODE) profile: log2 w_m = Ad_m + Sa_m da + Sb_m db
+    with da = h_a x, db = h_b y the offsets of F_a, F_b inside their channels.
+    Then w_m = base_m e^{alpha_m x} e^{beta_m y} (alpha = Sa h_a ln 2, beta =
+    Sb h_b ln 2), and the moments nu_n = sum_m w_m g_n(m) equal
+    sum_{k,l <= 3} C_nkl T_k(x) T_l(y) with C_nkl = sum_m base_m b_k(alpha_m)
+    b_l(beta_m) g_n(m); the truncation is that of each 1-D expansion."""
+    import math
+    L = 80.0
+    ze = orc.zgrid(L, 0.0571, 113)
+    zm, dz = 0.5 * (ze[1:] + ze[:-1]), np.diff(ze)
+    lo, hi = ze[:-1] - L / 2, ze[1:] - L / 2
+    g = np.array([(hi ** (n + 1) - lo ** (n + 1)) / ((n + 1) * (hi - lo)) for n in range(11)])
+    rng = np.random.default_rng(6)
+    Ad = np.log2(dz) - 0.05 * zm / math.log(2.0) + rng.normal(0, 0.1, len(zm))
+    Sa = -np.linspace(0.0, 0.5, len(zm)) / math.log(2.0)
+    Sb = -np.linspace(0.0, 0.4, len(zm)) / math.log(2.0) + 0.02
+    for ha, hb in ((0.048, 0.048), (0.048, 0.19)):
+        alpha, beta = Sa * ha * math.log(2.0), Sb * hb * math.log(2.0)
+        bk = np.array([[_bessel_i(k, a) * (1 if k == 0 else 2) for k in range(4)] for a in alpha])
+        bl = np.array([[_bessel_i(k, b) * (1 if k == 0 else 2) for k in range(4)] for b in beta])
+        base = 2.0 ** Ad
+        C = np.einsum("m,mk,ml,nm->nkl", base, bk, bl, g)
+        amax = float(max(np.max(np.abs(alpha)), np.max(np.abs(beta))))
+        tol = max(1e-12, 2 * (amax / 2) ** 4 / 6)
+        for x, y in rng.uniform(-1, 1, (25, 2)):
+            Tx = np.array([1.0, x, 2 * x * x - 1, x * (4 * x * x - 3)])
+            Ty = np.array([1.0, y, 2 * y * y - 1, y * (4 * y * y - 3)])
+            w = 2.0 ** (Ad + Sa * ha * x + Sb * hb * y)
+            for n in (0, 1, 2, 5, 10):
+                exact = np.sum(w * g[n])
+                approx = Tx @ C[n] @ Ty
+                scale = np.sum(np.abs(w * g[n]))
+                assert abs(approx - exact) <= tol * scale, (n, abs(approx - exact) / scale, tol)
