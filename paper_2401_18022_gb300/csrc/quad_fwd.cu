@@ -105,6 +105,13 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams pp)
 // ---------------------------------------------------------------------------
 // k_quad_f32: persistent FP32 quadrature.
 // ---------------------------------------------------------------------------
+constexpr int kFwdCand = 4;          // F_c candidates with their own step rows (attenuation folded in) ...
+constexpr int kFwdCandSteps = 256;   // ... when the z-grid has at most this many steps (shared memory)
+
+__host__ __device__ constexpr int fwd_cand_rows(int n_steps)
+{
+    return n_steps <= kFwdCandSteps ? kFwdCand : 0;
+}
 __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
 {
     extern __shared__ float4 smem_f4[];
@@ -112,7 +119,10 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
     float4 *sT = smem_f4;                              // [M] {A2 + log2 dz, K2, z, z^2 + dz^2/12}
     float4 *sE = sT + M;                               // [M] {edge/2pi hi, lo, A2, K2}
     float4 *sR = sE + M;                               // [M] {A2 + log2 dz, K2, z, dz}
-    RowF *rows = reinterpret_cast<RowF *>(sR + M);     // [G]
+    const int ncr = fwd_cand_rows(M);
+    float4 *sRc = sR + M;                              // [ncr][M] sR rows with - at_c z folded in
+    float4 *sEc = sRc + ncr * M;                       // [ncr][M] sE rows with - at_c z folded in
+    RowF *rows = reinterpret_cast<RowF *>(sEc + ncr * M);   // [G]
     __shared__ PieceConst<float> kc;
     __shared__ ChebTab ct;
     __shared__ double scratch[32];
@@ -165,6 +175,15 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
             cheb_setup(qp, pc, item.prof, sT, M, kc, ct);
+            // per-candidate step rows with the candidate's attenuation folded in
+            const int ncf = min(kc.nc, ncr);
+            for (int t = threadIdx.x; t < ncf * M; t += blockDim.x) {
+                const int c = t / M, m = t - c * M;
+                const float at = kc.at_ab + kc.hat[c];
+                const float4 r = sR[m], e = sE[m];
+                sRc[t] = make_float4(fmaf(-at, r.z, r.x), r.y, r.z, r.w);
+                sEc[t] = make_float4(e.x, e.y, fmaf(-at, r.z, e.z), e.w);
+            }
             __syncthreads();
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2;
             const float three_fi2 = 3.0f * fi * fi;
@@ -208,10 +227,10 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
                     }
                     ++n_small;
                 } else if (aphi <= phi_direct) {
-                    S2 = zsum_direct_f(phi, Fc, at, sR, M);
+                    S2 = ci < ncr ? zsum_direct_fc(phi, Fc, sRc + ci * M, M) : zsum_direct_f(phi, Fc, at, sR, M);
                     ++n_direct;
                 } else {
-                    S2 = zsum_tele_f(phi, Fc, at, sT, sE, M);
+                    S2 = ci < ncr ? zsum_tele_fc(phi, Fc, sEc + ci * M, M) : zsum_tele_f(phi, Fc, at, sT, sE, M);
                     ++n_tele;
                 }
                 // compensated accumulation over this thread's points
@@ -379,7 +398,8 @@ __global__ void __launch_bounds__(256) k_finish(FinishParams fp)
 // ---------------------------------------------------------------------------
 size_t quad_smem_bytes(int precision, int n_steps, int G)
 {
-    if (precision == 0) return (size_t)n_steps * 3 * sizeof(float4) + (size_t)G * sizeof(RowF);
+    if (precision == 0)
+        return (size_t)n_steps * (3 + 2 * fwd_cand_rows(n_steps)) * sizeof(float4) + (size_t)G * sizeof(RowF);
     return (size_t)n_steps * 2 * sizeof(double2) + (size_t)G * sizeof(RowD);
 }
 

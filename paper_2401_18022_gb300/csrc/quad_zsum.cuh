@@ -95,6 +95,52 @@ __device__ __forceinline__ float zsum_tele_f(float phi, float Fc, float at, cons
     return (Sr * Sr + Si * Si) / (phi * phi);
 }
 
+// The same two forms with the candidate's attenuation folded into the step
+// tables (rows of a per-candidate copy):
+//   sRc[m] = {A2_m + log2 dz_m - at z_m, K2_m, z_m, dz_m},
+//   sEc[m] = {z_{m+1}/2pi hi, lo, A2_m - at z_m, K2_m},
+// so log2 p_m = row + K2_m Fc in one FMA and the telescoped form needs no z.
+__device__ __forceinline__ float zsum_direct_fc(float phi, float Fc, const float4 *sRc, int M)
+{
+    float Sr = 0.0f, Si = 0.0f;
+    const float hphi = 0.5f * phi;
+    const float phir = phi * 0.15915494309189535f;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 a = sRc[m];
+        float sn, cs;
+        sincos_rev(phir * a.z, sn, cs);
+        const float x = hphi * a.w;
+        const float x2 = x * x;
+        float sc = fmaf(x2, -2.5052108e-8f, 2.7557319e-6f);   // -1/11!, 1/9!
+        sc = fmaf(x2, sc, -1.9841270e-4f);                     // -1/7!
+        sc = fmaf(x2, sc, 8.3333333e-3f);                      // 1/5!
+        sc = fmaf(x2, sc, -1.6666667e-1f);                     // -1/3!
+        sc = fmaf(x2, sc, 1.0f);
+        const float amp = ex2_approx(fmaf(a.y, Fc, a.x)) * sc;
+        Sr = fmaf(amp, cs, Sr);
+        Si = fmaf(amp, sn, Si);
+    }
+    return Sr * Sr + Si * Si;
+}
+
+__device__ __forceinline__ float zsum_tele_fc(float phi, float Fc, const float4 *sEc, int M)
+{
+    float Er = 1.0f, Ei = 0.0f, Sr = 0.0f, Si = 0.0f;
+#pragma unroll 4
+    for (int m = 0; m < M; ++m) {
+        const float4 e = sEc[m];
+        float sn, cs;
+        phasor_rev_ff(phi, e.x, e.y, sn, cs);
+        const float p = ex2_approx(fmaf(e.w, Fc, e.z));
+        Sr = fmaf(p, cs - Er, Sr);
+        Si = fmaf(p, sn - Ei, Si);
+        Er = cs;
+        Ei = sn;
+    }
+    return (Sr * Sr + Si * Si) / (phi * phi);
+}
+
 // As zsum_tele_f, with a phase reduction valid far beyond 2^22 revolutions:
 // the first magic-number rounding leaves an integer (or half-integer) on top
 // of the fraction once |phi z / 2pi| >= 2^22; a second one removes it.
