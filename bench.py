@@ -296,7 +296,7 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
 # gpu__time_duration), and the points that launch evaluated.  The kernel reads
 # the piece list and writes one bucket row per tile, both proportional to the
 # evaluated points at fixed G, so a full launch's traffic is scaled by points.
-ADJ_DRAM_CAPTURE = {"bytes": 4.306e6, "points": 2880700416}
+ADJ_DRAM_CAPTURE = {"bytes": 4.466e6, "points": 2880700416}
 
 
 def _timed(fn, dev, reps: int = 2):

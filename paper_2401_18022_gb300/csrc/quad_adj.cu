@@ -15,11 +15,13 @@
 // k_quad_adj evaluates the forward sum and these buckets in one pass over the
 // grid, and every step term of Eq. slow_vary is evaluated once.  A warp first
 // takes 32 grid points, one per lane, for their geometry, phase and z-sum
-// form.  Small-phase points whose moments come from the Chebyshev contraction
-// are finished there: their bucket terms w_m (al0 + al1 c_m + al2 z_m) are
-// expanded in the same Chebyshev series in the point's in-channel coordinate,
-// so per F_c candidate only 15 point sums are kept and turned into per-step
-// terms once per piece.  The other points join one list per z-sum form and
+// form.  Small-phase points (|phi| L <= 2) whose moments come from the
+// contracted 11-moment series are finished there: their bucket terms
+// sum_n 2 (A|B) phi^n f_n w_m g_n(m) are expanded in the same Chebyshev series
+// in the point's in-channel coordinate, so per F_c candidate only 55 point
+// sums are kept (one or two warp butterflies per batch) and turned into
+// per-step terms once per piece.  The other points join one list per z-sum
+// form and
 // are walked two at a time on half-warps: each of the 16 lanes of a half owns
 // K = ceil(M/16) consecutive steps (112 = 16 x 7), computes their terms t_m
 // into registers, the half sums them with shuffles into S, and the same
