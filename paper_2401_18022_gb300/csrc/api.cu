@@ -381,20 +381,19 @@ void zgrid_tables(double L, double a, int n_edges, std::vector<float4> &za, std:
     dz_max = (float)dmax;
     if (zg) {
         // centred step moments g_n(m) = mean of (zeta - L/2)^n over [ze_m, ze_{m+1}]
-        // = (b^{n+1} - a^{n+1}) / ((n + 1)(b - a)), n = 0..10, and g_11 = 0
-        zg->assign(3 * (size_t)M, make_float4(0.f, 0.f, 0.f, 0.f));
+        // = (b^{n+1} - a^{n+1}) / ((n + 1)(b - a)), n = 0..18, and g_19 = 0
+        zg->assign(5 * (size_t)M, make_float4(0.f, 0.f, 0.f, 0.f));
         for (int m = 0; m < M; ++m) {
             const double lo = ze[m] - 0.5 * L, hi = ze[m + 1] - 0.5 * L;
-            float g[12] = {0.f};
+            float g[20] = {0.f};
             double pa = lo, pb = hi;
-            for (int n = 0; n <= 10; ++n) {
+            for (int n = 0; n <= 18; ++n) {
                 g[n] = (float)((pb - pa) / ((n + 1) * (hi - lo)));
                 pa *= lo;
                 pb *= hi;
             }
-            (*zg)[3 * m] = make_float4(g[0], g[1], g[2], g[3]);
-            (*zg)[3 * m + 1] = make_float4(g[4], g[5], g[6], g[7]);
-            (*zg)[3 * m + 2] = make_float4(g[8], g[9], g[10], g[11]);
+            for (int q = 0; q < 5; ++q)
+                (*zg)[5 * m + q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
         }
     }
 }

@@ -70,7 +70,7 @@ struct QuadParams {
     const float4 *zs_a;         // {z_m, z_m^2 + dz_m^2/12, log2 dz_m, dz_m}
     const float4 *zs_b;         // {z_{m+1}/2pi hi, lo (float-float), z_m/2pi, 0}
     const double2 *zs_d;        // {z_m, dz_m}
-    const float4 *zs_g;         // [3 per step] g_0..g_11: mean of (zeta - L/2)^n over step m (g_11 = 0)
+    const float4 *zs_g;         // [5 per step] g_0..g_19: mean of (zeta - L/2)^n over step m (g_19 = 0)
     const double *kap_L;        // per profile: kappa(L) [1/THz]
     float dz_max;
     float L;                    // span length [km]

@@ -41,7 +41,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClsSmall = 0, kClsDirect = 1, kClsTele = 2;
 constexpr int kListCap = 34;    // a form's list: one carried point + 32 new (+1 pad)
 constexpr int kCtr = 4;         // F_c candidates whose small-phase points are contracted
-constexpr int kCtrN = kChebMom * 5;   // per candidate: moments nu_0..nu_10 x T_0..T_4
+constexpr int kCtrN = kChebMomA * 5;  // per candidate: moments nu_0..nu_10 x T_0..T_4
 constexpr int kCtrS = 64;       // slots per candidate (two 32-value butterflies)
 // A batch whose contracted points all have |phi| L <= 0.2 keeps n <= 5 in its
 // bucket sums (30 values, one butterfly): the omitted orders are below
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     const float m4pi2 = (float)(-4.0 * kPi * kPi);
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
-    const float phi_cheb = kChebPhiL / qp.L;
+    const float phi_cheb = kChebPhiLA / qp.L;
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
     // the walks run on half-warps: lane l owns steps [K (l mod 16), K (l mod 16) + K)
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
-            cheb_setup(qp, pc, item.prof, sT, M, kc, ct);
+            cheb_setup<kChebMomA>(qp, pc, item.prof, sT, M, kc, ct);
             __syncthreads();
             const bool cheb = ct.ok != 0;
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2, mult = kc.mult;
@@ -406,9 +406,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                             const float aphi = fabsf(phi);
                             wwa = rw.w * W * array_factor_f(phi, qp);
                             if (cheb && ci < kCtr && aphi <= phi_cheb) {
-                                float nu[kChebMom];
-                                cheb_moments<kChebMom>(ct, ci, u, nu, cx);
-                                cheb_AB<kChebMom>(nu, phi, cA, cB);
+                                float nu[kChebMomA];
+                                cheb_moments<kChebMomA>(ct, ci, u, nu, cx);
+                                cheb_AB<kChebMomA>(nu, phi, cA, cB);
                                 ctr = true;
                                 cls = kClsSmall;
                                 fwd_add(fa, wwa * fmaf(cA, cA, cB * cB), ci, true, sVc);
@@ -441,11 +441,11 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                     while (cmask) {
                         const int cl = __shfl_sync(kFull, ci, __ffs(cmask) - 1);
                         const bool mine = ctr && ci == cl;
-                        float al[kChebMom];
+                        float al[kChebMomA];
                         al[0] = mine ? 2.0f * cpt * cA : 0.0f;
                         al[1] = mine ? 2.0f * cpt * cB * phi : 0.0f;
 #pragma unroll
-                        for (int n = 2; n < kChebMom; ++n) al[n] = al[n - 2] * (phi * phi);
+                        for (int n = 2; n < kChebMomA; ++n) al[n] = al[n - 2] * (phi * phi);
                         if (short_form) {
                             const float y0 = butterfly32(
                                 [&](int v) { return v < kShortN ? al[v / 5] * Tk[v % 5] : 0.0f; }, lane);
@@ -591,8 +591,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 const int coff = qp.plan_ch_off[pc.plan];
                 for (int m = threadIdx.x; m < M; m += blockDim.x) {
                     const float4 a = sT[m];           // {A2 + log2 dz, K2, z, z^2 + dz^2/12}
-                    const float4 g0 = qp.zs_g[3 * m], g1 = qp.zs_g[3 * m + 1], g2 = qp.zs_g[3 * m + 2];
-                    const float gm[kChebMom] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y, g2.z};
+                    const float4 g0 = qp.zs_g[kZsG * m], g1 = qp.zs_g[kZsG * m + 1], g2 = qp.zs_g[kZsG * m + 2];
+                    const float gm[kChebMomA] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y, g2.z};
                     double rx = 0.0, ry = 0.0;
                     for (int c = 0; c < ncc; ++c) {
                         const double *Y = sYt[c];
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         const float b3 = 2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 / 240.0f)); // 2 I3
                         float rs = 0.0f, xs = 0.0f;
 #pragma unroll
-                        for (int n = 0; n < kChebMom; ++n) {
+                        for (int n = 0; n < kChebMomA; ++n) {
                             const double *Yn = Y + 5 * n;
                             const float y0 = (float)Yn[0], y1 = (float)Yn[1], y2 = (float)Yn[2], y3 = (float)Yn[3],
                                         y4 = (float)Yn[4];

@@ -185,7 +185,9 @@ __device__ __forceinline__ double array_factor_d(double phi, const QuadParams &q
 //   S e^{-j phi z0} = sum_n (j phi)^n / n! nu_n,   nu_n = sum_m w_m g_n(m),
 //   g_n(m) = mean of (zeta - z0)^n over step m,
 // exactly; |S|^2 = A^2 + B^2 with A (B) the even (odd) part, and truncating
-// at n = N leaves a relative error below 2 (phi L/2)^{N+1}/(N+1)!.
+// at n = N leaves a relative error below 2 (phi L/2)^{N+1}/(N+1)!: the forward
+// kernels keep n <= 18 for |phi| L <= 6 (< 2e-8), the adjoint n <= 10 for
+// |phi| L <= 2 (< 5e-8; its bucket sums grow with the order).
 // The moments depend on the point only through F_c (and the candidate
 // channel's attenuation): inside channel c, F_c - f_ref = F0 + h x with
 // x in [-1, 1], and
@@ -197,8 +199,11 @@ __device__ __forceinline__ double array_factor_d(double phi, const QuadParams &q
 // sum is used.
 // ---------------------------------------------------------------------------
 constexpr float kChebMaxA = 0.05f;
-constexpr int kChebMom = 11;        // nu_0 .. nu_10
-constexpr float kChebPhiL = 2.0f;   // |phi| L limit of the 11-moment form: error < 5e-8
+constexpr int kChebMom = 19;        // nu_0 .. nu_18 (forward kernels)
+constexpr float kChebPhiL = 6.0f;   // |phi| L limit of the 19-moment form: error < 2e-8
+constexpr int kChebMomA = 11;       // nu_0 .. nu_10 (adjoint)
+constexpr float kChebPhiLA = 2.0f;  // |phi| L limit of the 11-moment form: error < 5e-8
+constexpr int kZsG = 5;             // float4 per step of the centred step moments g_0..g_19 (g_19 = 0)
 
 struct ChebTab {
     float4 c[kMaxCand][kChebMom];   // [candidate][n] = C_n0..C_n3 times (-1)^{floor(n/2)} / n!
@@ -241,7 +246,7 @@ __device__ __forceinline__ void cheb_sums(const QuadParams &qp, const float4 *sT
         const float W1 = base * (2.0f * t * (1.0f + t2 * (0.5f + t2 * (1.0f / 12.0f))));                     // 2 I1
         const float W2 = base * (2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 * (1.0f / 48.0f))));             // 2 I2
         const float W3 = base * (2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
-        const float *g = reinterpret_cast<const float *>(qp.zs_g + 3 * m) + N0;
+        const float *g = reinterpret_cast<const float *>(qp.zs_g + kZsG * m) + N0;
 #pragma unroll
         for (int n = 0; n < NN; ++n) {
             const float gn = g[n];
@@ -267,9 +272,11 @@ __device__ __forceinline__ void cheb_sums(const QuadParams &qp, const float4 *sT
 }
 
 // Called by every thread of the block after piece_consts; the caller syncs.
-// sT[m] = {A2d_m, K2_m, z_m, .}; qp.zs_g[3 m .. 3 m + 2] = g_0..g_11 of step m.
-// One warp per candidate; the step weights are exact to FP32 rounding (FP64
-// exponent), the sums run over the lane's steps and a warp tree.
+// sT[m] = {A2d_m, K2_m, z_m, .}; qp.zs_g[kZsG m ...] = g_0..g_19 of step m.
+// One warp per candidate fills nu_0..nu_{NM-1}; the step weights are exact to
+// FP32 rounding (FP64 exponent), the sums run over the lane's steps and a
+// warp tree.
+template <int NM>
 __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece &pc, int prof,
                                            const float4 *sT, int M, const PieceConst<float> &k, ChebTab &ct)
 {
@@ -285,8 +292,14 @@ __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece 
         const double F0 = qp.ch_frel[coff + pc.c_lo + c];
         const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
         const double at = (double)(k.at_ab + k.hat[c]);
+        static_assert(NM > 6 && NM <= kChebMom, "moment count");
         cheb_sums<0, 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c]);
-        cheb_sums<6, kChebMom - 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c] + 6);
+        if constexpr (NM <= 12) {
+            cheb_sums<6, NM - 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c] + 6);
+        } else {
+            cheb_sums<6, 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c] + 6);
+            cheb_sums<12, NM - 12>(qp, sT, M, F0, (float)h, at, lane, ct.c[c] + 12);
+        }
         if (lane == 0) {
             ct.mid[c] = 0.5f * (k.lo[c] + k.hi[c]);
             ct.invh[c] = (float)(1.0 / h);

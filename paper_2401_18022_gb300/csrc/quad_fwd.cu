@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
-            cheb_setup(qp, pc, item.prof, sT, M, kc, ct);
+            cheb_setup<kChebMom>(qp, pc, item.prof, sT, M, kc, ct);
             // per-candidate step rows with the candidate's attenuation folded in
             const int ncf = min(kc.nc, ncr);
             for (int t = threadIdx.x; t < ncf * M; t += blockDim.x) {

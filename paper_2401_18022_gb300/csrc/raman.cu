@@ -546,9 +546,10 @@ __device__ __forceinline__ float zsum_tele_t(float phi, float da, float db, cons
 }
 
 // ---------------------------------------------------------------------------
-// Contracted small-phase series for the tabulated profile (the 11-moment
-// series of the closed-form kernels, App. A Eq. slow_vary).  Inside the piece,
-// log2 w_m = Ad_m + Sa_m da + Sb_m db with da = h_a x, db = h_b y the offsets
+// Contracted small-phase series for the tabulated profile (the moment series
+// of the closed-form kernels, App. A Eq. slow_vary, at 11 moments for
+// |phi| L <= 2: the 2-D expansion costs 16 coefficients per moment).  Inside
+// the piece, log2 w_m = Ad_m + Sa_m da + Sb_m db with da = h_a x, db = h_b y the offsets
 // of F_a and F_b inside their channels, so
 //   w_m = 2^{Ad_m} e^{alpha_m x} e^{beta_m y},  alpha = Sa h_a ln 2, beta = Sb h_b ln 2,
 // and with e^{a x} = I0(a) + 2 sum Ik(a) Tk(x) in each offset
@@ -557,6 +558,8 @@ __device__ __forceinline__ float zsum_tele_t(float phi, float da, float db, cons
 // (truncation ~ (a/2)^4/12 per offset for |alpha|, |beta| <= 0.05).  The
 // coefficients are stored times (-1)^{floor(n/2)}/n!, as row k = float4 over l.
 // ---------------------------------------------------------------------------
+constexpr int kTabMom = kChebMomA;
+
 __device__ __forceinline__ float4 bessel_b4(float a)
 {
     const float t = 0.5f * a, t2 = t * t;
@@ -568,7 +571,7 @@ __device__ __forceinline__ float4 bessel_b4(float a)
 
 // Every thread calls after tab_setup_f (synced); returns whether the piece's
 // small-phase points use the contraction.  sW: [M][4] float4 scratch,
-// sG: [M][12] moments, sC: [nc][kChebMom][4] float4, s_flag: shared int.
+// sG: [M][4 kZsG] moments, sC: [nc][kTabMom][4] float4, s_flag: shared int.
 __device__ bool tab_cheb_setup(const QuadParams &qp, const DevPiece &pc, int nc, const float4 *sQ, float4 *sW,
                                float *sG, float4 *sC, float *s_amax)
 {
@@ -587,7 +590,7 @@ __device__ bool tab_cheb_setup(const QuadParams &qp, const DevPiece &pc, int nc,
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned *>(s_amax), __float_as_uint(amax));
-    for (int t = threadIdx.x; t < M * 12; t += blockDim.x) sG[t] = reinterpret_cast<const float *>(qp.zs_g)[t];
+    for (int t = threadIdx.x; t < M * 4 * kZsG; t += blockDim.x) sG[t] = reinterpret_cast<const float *>(qp.zs_g)[t];
     __syncthreads();
     if (!(*s_amax <= kChebMaxA)) return false;
     for (int c = 0; c < nc; ++c) {
@@ -605,18 +608,18 @@ __device__ bool tab_cheb_setup(const QuadParams &qp, const DevPiece &pc, int nc,
         }
         __syncthreads();
         // one coefficient (n, k, l) per thread: compensated sum over the steps
-        for (int t = threadIdx.x; t < kChebMom * 16; t += blockDim.x) {
+        for (int t = threadIdx.x; t < kTabMom * 16; t += blockDim.x) {
             const int n = t >> 4, k = (t >> 2) & 3, l = t & 3;
             float sum = 0.0f, comp = 0.0f;
             for (int m = 0; m < M; ++m) {
                 const float4 w = sW[m * 4 + k];
                 const float wl = l == 0 ? w.x : (l == 1 ? w.y : (l == 2 ? w.z : w.w));
-                const float y = wl * sG[m * 12 + n] - comp;
+                const float y = wl * sG[m * 4 * kZsG + n] - comp;
                 const float tt = sum + y;
                 comp = (tt - sum) - y;
                 sum = tt;
             }
-            reinterpret_cast<float *>(sC + (c * kChebMom + n) * 4 + k)[l] = sum * (float)cheb_fold(n);
+            reinterpret_cast<float *>(sC + (c * kTabMom + n) * 4 + k)[l] = sum * (float)cheb_fold(n);
         }
         __syncthreads();
     }
@@ -628,10 +631,10 @@ __device__ __forceinline__ float tab_cheb_s2(const float4 *sC, int ci, float x, 
 {
     const float Tx2 = fmaf(2.0f * x, x, -1.0f), Tx3 = fmaf(2.0f * x, Tx2, -x);
     const float Ty2 = fmaf(2.0f * y, y, -1.0f), Ty3 = fmaf(2.0f * y, Ty2, -y);
-    float nu[kChebMom];
-    const float4 *C = sC + ci * kChebMom * 4;
+    float nu[kTabMom];
+    const float4 *C = sC + ci * kTabMom * 4;
 #pragma unroll
-    for (int n = 0; n < kChebMom; ++n) {
+    for (int n = 0; n < kTabMom; ++n) {
         float r[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -641,7 +644,7 @@ __device__ __forceinline__ float tab_cheb_s2(const float4 *sC, int ci, float x, 
         nu[n] = fmaf(r[3], Tx3, fmaf(r[2], Tx2, fmaf(r[1], x, r[0])));
     }
     float A, B;
-    cheb_AB<kChebMom>(nu, phi, A, B);
+    cheb_AB<kTabMom>(nu, phi, A, B);
     return fmaf(A, A, B * B);
 }
 
@@ -655,9 +658,9 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
     float4 *sE = sZ + M;                               // [M] {edge/2pi hi, lo, 0, 0}
     float4 *sQ = sE + M;                               // [nc_max][M] {A + log2 dz, Sa, Sb, A}
     float4 *sW = sQ + (size_t)qp.nc_max * M;           // [M][4] contraction weights of one candidate
-    float4 *sC = sW + (size_t)M * 4;                   // [nc_max][kChebMom][4] contracted coefficients
-    float *sG = reinterpret_cast<float *>(sC + (size_t)qp.nc_max * kChebMom * 4);   // [M][12] step moments
-    RowF *rows = reinterpret_cast<RowF *>(sG + (size_t)M * 12);   // [G]
+    float4 *sC = sW + (size_t)M * 4;                   // [nc_max][kTabMom][4] contracted coefficients
+    float *sG = reinterpret_cast<float *>(sC + (size_t)qp.nc_max * kTabMom * 4);   // [M][4 kZsG] step moments
+    RowF *rows = reinterpret_cast<RowF *>(sG + (size_t)M * 4 * kZsG);   // [G]
     __shared__ PieceConst<float> kc;
     __shared__ float s_d0[2];
     __shared__ float s_amax;
@@ -676,7 +679,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
     const float m4pi2 = (float)(-4.0 * kPi * kPi);
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
-    const float phi_cheb = kChebPhiL / qp.L;
+    const float phi_cheb = kChebPhiLA / qp.L;
     const float invG = 1.0f / (float)G;
     unsigned n_small = 0, n_direct = 0, n_tele = 0;
 
@@ -873,8 +876,8 @@ __global__ void __launch_bounds__(256) k_quad_f64_tab(QuadParams qp)
 size_t quad_tab_smem_bytes(int precision, int n_steps, int G, int nc_max)
 {
     if (precision == 0)
-        return (size_t)n_steps * (2 + nc_max + 4) * sizeof(float4) + (size_t)nc_max * kChebMom * 4 * sizeof(float4) +
-               (size_t)n_steps * 12 * sizeof(float) + (size_t)G * sizeof(RowF);
+        return (size_t)n_steps * (2 + nc_max + 4) * sizeof(float4) + (size_t)nc_max * kTabMom * 4 * sizeof(float4) +
+               (size_t)n_steps * 4 * kZsG * sizeof(float) + (size_t)G * sizeof(RowF);
     return (size_t)n_steps * (1 + 2 * nc_max) * sizeof(double2) + (size_t)G * sizeof(RowD);
 }
 

@@ -61,7 +61,10 @@ def test_uwb_full_grad_forward_consistent(eng, uwb_full):
     s = eng.snr(wl, P=P)
     np.testing.assert_allclose(g["eta"].cpu().numpy(), r["eta"], rtol=1e-6)
     np.testing.assert_allclose(g["snr"].cpu().numpy(), s["snr"].cpu().numpy(), rtol=1e-6)
-    assert g["T"] == pytest.approx(s["T"], rel=1e-9)
+    # the forward kernel sums small phases with the 19-moment series up to
+    # |phi| L = 6, the adjoint with 11 moments up to |phi| L = 2 and per step
+    # beyond: each form is within 5e-8 of the exact z-sum, so T agrees to ~1e-8
+    assert g["T"] == pytest.approx(s["T"], rel=1e-7)
     d = g["dT_dP"].cpu().numpy()
     assert np.all(np.isfinite(d))
 

@@ -58,7 +58,9 @@ def test_adjoint_vs_fd_of_fp64_path_tiny(eng, trx, cells):
     # the forward outputs of the gradient call equal those of isrs_gn_snr
     s = eng.snr(wl, P=P, precision=0)
     np.testing.assert_allclose(r["snr"], s["snr"], rtol=1e-6)
-    assert r["T"] == pytest.approx(s["T"], rel=1e-9)
+    # the two kernels truncate the small-phase series at different orders
+    # (19 and 11 moments), each within 5e-8 of the exact z-sum
+    assert r["T"] == pytest.approx(s["T"], rel=1e-7)
 
 
 def test_adjoint_vs_fd_of_oracle(eng, orc):

@@ -81,5 +81,5 @@ def test_case1_from_zero_dbm(eng, plan):
     T64 = eng.snr(wl, P=P, precision=1)["T"]
     assert res["T"] == pytest.approx(T64, rel=1e-5)
     rep = S.band_report(eng, wl, P, band)
-    assert rep["T"] == pytest.approx(res["T"], rel=1e-9)
+    assert rep["T"] == pytest.approx(res["T"], rel=1e-7)     # forward vs adjoint small-phase orders
     assert set(rep["bands"]) == set(W.BAND_NAMES)

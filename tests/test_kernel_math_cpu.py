@@ -88,33 +88,35 @@ def test_small_phi_centred_moment_series(orc):
     """The contracted small-phase form: about the span centre z0 = L/2,
     S e^{-j phi z0} = sum_n (j phi)^n / n! nu_n with nu_n = sum_m p_m dz_m g_n(m)
     and g_n(m) the mean of (zeta - z0)^n over step m (the step's sinc times its
-    phasor is the mean of e^{j phi zeta} over the step).  Truncated at n = 10,
-    |S|^2 = A^2 + B^2 matches the direct z-sum to 5e-8 for |phi| L <= 2, within
-    the bound 2 (phi L / 2)^11 / 11!."""
+    phasor is the mean of e^{j phi zeta} over the step).  |S|^2 = A^2 + B^2
+    matches the direct z-sum within the truncation bound 2 (phi L / 2)^{N+1} /
+    (N+1)!: to 5e-8 for N = 10 and |phi| L <= 2 (the adjoint), to 2e-8 for
+    N = 18 and |phi| L <= 6 (the forward kernels)."""
     import math
     L = 80.0
     ze = orc.zgrid(L, 0.0571, 113)
     zm, dz = 0.5 * (ze[1:] + ze[:-1]), np.diff(ze)
     lo, hi = ze[:-1] - L / 2, ze[1:] - L / 2
-    g = np.array([(hi ** (n + 1) - lo ** (n + 1)) / ((n + 1) * (hi - lo)) for n in range(11)])
-    f = np.array([(-1) ** (n // 2) / math.factorial(n) for n in range(11)])
     rng = np.random.default_rng(5)
-    worst, worst_bound = 0.0, -1.0
-    for _ in range(40):
-        a, k = rng.uniform(0.0, 0.2), rng.uniform(-0.1, 0.1)
-        p = np.exp(-a * zm + k * np.sin(zm / 7)) * rng.uniform(0.5, 2)
-        nu = f * (g @ (p * dz))
-        for x in np.concatenate([rng.uniform(-2, 2, 12), [2.0, -2.0, 1e-4]]):
-            ph = x / L
-            A = sum(nu[n] * ph ** n for n in range(0, 11, 2))
-            B = sum(nu[n] * ph ** n for n in range(1, 11, 2))
-            exact = abs(orc.zsum(zm, dz, p, ph)) ** 2
-            err = abs((A * A + B * B) / exact - 1)
-            worst = max(worst, err)
-            # within the truncation bound, up to FP64 rounding of the sums
-            worst_bound = max(worst_bound, err - 2 * (abs(x) / 2) ** 11 / math.factorial(11))
-    assert worst < 5e-8, worst
-    assert worst_bound < 1e-12, worst_bound
+    for N, T, tol in ((10, 2.0, 5e-8), (18, 6.0, 2e-8)):
+        g = np.array([(hi ** (n + 1) - lo ** (n + 1)) / ((n + 1) * (hi - lo)) for n in range(N + 1)])
+        f = np.array([(-1) ** (n // 2) / math.factorial(n) for n in range(N + 1)])
+        worst, worst_bound = 0.0, -1.0
+        for _ in range(40):
+            a, k = rng.uniform(0.0, 0.2), rng.uniform(-0.1, 0.1)
+            p = np.exp(-a * zm + k * np.sin(zm / 7)) * rng.uniform(0.5, 2)
+            nu = f * (g @ (p * dz))
+            for x in np.concatenate([rng.uniform(-T, T, 12), [T, -T, 1e-4]]):
+                ph = x / L
+                A = sum(nu[n] * ph ** n for n in range(0, N + 1, 2))
+                B = sum(nu[n] * ph ** n for n in range(1, N + 1, 2))
+                exact = abs(orc.zsum(zm, dz, p, ph)) ** 2
+                err = abs((A * A + B * B) / exact - 1)
+                worst = max(worst, err)
+                # within the truncation bound, up to FP64 rounding of the sums
+                worst_bound = max(worst_bound, err - 2 * (abs(x) / 2) ** (N + 1) / math.factorial(N + 1))
+        assert worst < tol, (N, worst)
+        assert worst_bound < 1e-12, (N, worst_bound)
 
 
 def test_chebyshev_contraction_two_offsets(orc):
