@@ -112,7 +112,11 @@ __host__ __device__ constexpr int fwd_cand_rows(int n_steps)
 {
     return n_steps <= kFwdCandSteps ? kFwdCand : 0;
 }
-__global__ void __launch_bounds__(256, 4) k_quad_f32(QuadParams qp)
+#ifndef ISRS_FWD_MIN_BLOCKS
+#define ISRS_FWD_MIN_BLOCKS 4   // resident blocks per SM the register budget is sized for
+#endif
+
+__global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParams qp)
 {
     extern __shared__ float4 smem_f4[];
     const int M = qp.n_steps, G = qp.G;
