@@ -202,3 +202,13 @@ def test_many_fc_candidates(eng, orc, prec, rtol):
     ref = _oracle_sigma(orc, wl, cuts=cuts)
     got = eng.eta(wl, cuts=cuts, precision=prec)
     np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)
+
+
+@pytest.mark.parametrize("G,n_edges", [(8, 2), (5, 3), (1, 18)])
+def test_degenerate_grids(eng, orc, G, n_edges):
+    """One z-step, two steps, and a single grid point per piece."""
+    wl = W.tiny(G=G, n_edges=n_edges, cell_set=W.CELLS_ALL)
+    ref = _oracle_sigma(orc, wl)
+    for prec, rtol in ((1, RTOL_F64), (0, RTOL_F32)):
+        got = eng.eta(wl, precision=prec)
+        np.testing.assert_allclose(got["sigma"], ref, rtol=rtol)

@@ -128,3 +128,14 @@ def test_adjoint_many_fc_candidates(eng):
     # the gradient call's forward outputs equal the forward kernel's
     s = eng.snr(wl, precision=0)
     np.testing.assert_allclose(r["snr"], s["snr"], rtol=1e-6)
+
+
+@pytest.mark.parametrize("G,n_edges", [(8, 2), (5, 3), (1, 18)])
+def test_adjoint_degenerate_grids(eng, G, n_edges):
+    """One z-step (15 of the 16 half-warp lanes hold padding steps), two
+    steps, and a single grid point per piece."""
+    wl = W.tiny(G=G, n_edges=n_edges, cell_set=W.CELLS_SCI_XCI)
+    P = wl.P_W * W.dbm_to_w(W.random_profile_dbm(5, seed=11)) / 1e-3
+    r = eng.grad(wl, P=P)
+    fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], P, range(5))
+    _check(r["dT_dP"], fd)
