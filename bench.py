@@ -319,7 +319,7 @@ def _timed(fn, dev, reps: int = 2):
 def _extras(eng, wl, P, dev):
     """Side measurements of the widened rows on the same 589-ch workload:
     the Raman-ODE power profile (SNR and gradient) and the MCI cells on their
-    own grid (SNR, and the MCI share of eta per band)."""
+    own grid (SNR, gradient, and the MCI share of eta per band)."""
     from paper_2401_18022_gb300 import workloads as W
     out = {}
     wr = W.raman(wl)
@@ -334,6 +334,8 @@ def _extras(eng, wl, P, dev):
     out["mci_G"] = g_mci
     out["mci_snr_ms"] = _timed(lambda: eng.snr(wm, P=P), dev)
     out["mci_quad_kernels_ms"] = eng.last_kernel_ms(0)
+    out["mci_grad_ms"] = _timed(lambda: eng.grad(wm, P=P), dev)
+    out["mci_grad_adjoint_kernels_ms"] = eng.last_kernel_ms(1)
     e_all = eng.eta(wm, P=P)["eta"]
     e_sx = eng.eta(wl, P=P)["eta"]
     e_all = e_all.cpu().numpy() if hasattr(e_all, "cpu") else np.asarray(e_all)

@@ -130,8 +130,8 @@ typedef struct {
     int G_mci;                  /* with ISRS_CELLS_ALL and > 0: the multi-channel-interference
                                  * cells (neither F_a nor F_b in the CUT's channel) get their own
                                  * G_mci x G_mci grid (<= 32) and are enumerated on the device
-                                 * (no piece list); closed-form profile, forward only.  0: every
-                                 * cell uses G. */
+                                 * (no piece list); closed-form profile (eta, SNR and gradient).
+                                 * 0: every cell uses G. */
 } isrs_quad;
 
 /* ------------------------------------------------------------------------ */
@@ -203,9 +203,11 @@ isrs_status isrs_gn_snr(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
 
 /* dT/dP_j [Tb/s per W] of the throughput T of isrs_gn_snr with respect to
  * every launch power, through eta (the PSD product and the ISRS profile of
- * every grid point), the ASE gain G_i and the SNR numerator.  Computed by a
+ * every grid point, including the MCI cells of a separate G_mci grid with the
+ * closed-form profile), the ASE gain G_i and the SNR numerator.  Computed by a
  * hand-written adjoint of the FP32 forward (quad->precision must be
  * ISRS_PREC_FP32).  All P_j must be > 0 and no channel may be a guard.
+ * Errors: UNSUPPORTED for G_mci > 0 with the Raman-ODE profile.
  *   dT_dP[n_ch], snr[n_ch] (nullable), eta[n_ch] (nullable),
  *   T_host (nullable, host double). */
 isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch,

@@ -54,7 +54,7 @@ struct Geom {
     // triangular cell ranges and, per output slot, their item range
     int G_mci = 0, n_mci_items = 0;
     double mci_phase_rev_max = 0.0;
-    DevBuf mci_items, slot_items2;
+    DevBuf mci_items, slot_items2, item_slot_all;   // item_slot_all: regular then MCI items
     // replayable graph of the batched launch (prep -> quadrature -> finish)
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey = 0;                 // fibre, precision and tile the graph was captured with
@@ -543,7 +543,7 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     const int chunk = (int)std::max<int64_t>(1, tile_pts / G2);
     std::vector<DevItem> items, mitems;
     std::vector<int2> slot_items, slot_items2;
-    std::vector<int> slot_cut, prof_slot_off, item_slot;
+    std::vector<int> slot_cut, prof_slot_off, item_slot, mitem_slot;
     const int mchunk = mci ? (int)std::max<int64_t>(1, tile_pts / ((int64_t)q->G_mci * q->G_mci)) : 1;
     g->n_points = 0;
     g->n_points_unfolded = 0;
@@ -574,8 +574,10 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
                 const int n2 = plans[k].n_ch - 1;
                 const int ncell = n2 * (n2 + 1) / 2;
                 const int m0 = (int)mitems.size();
-                for (int t = 0; t < ncell; t += mchunk)
+                for (int t = 0; t < ncell; t += mchunk) {
                     mitems.push_back(DevItem{p, t, std::min(t + mchunk, ncell), i});
+                    mitem_slot.push_back(slot);
+                }
                 slot_items2.push_back(make_int2(m0, (int)mitems.size()));
                 g->n_points += (int64_t)ncell * q->G_mci * q->G_mci;
                 g->n_points_unfolded += (int64_t)n2 * n2 * q->G_mci * q->G_mci;
@@ -658,6 +660,9 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     if (mci) {
         UP(mci_items, mitems);
         UP(slot_items2, slot_items2);
+        std::vector<int> slot_all(item_slot);
+        slot_all.insert(slot_all.end(), mitem_slot.begin(), mitem_slot.end());
+        UP(item_slot_all, slot_all);
     }
     if (g->profile == ISRS_PROFILE_RAMAN_ODE) {
         UP(win_lo, wlo);
@@ -677,7 +682,7 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
                           &old->ch_frel, &old->ch_B, &old->ch_alpha, &old->ch_gamma, &old->ch_nf,
                           &old->guard, &old->zs_a, &old->zs_b, &old->zs_d, &old->zs_g, &old->item_slot,
                           &old->win_lo, &old->win_hi, &old->ch_scale, &old->half_steps, &old->mci_items,
-                          &old->slot_items2};
+                          &old->slot_items2, &old->item_slot_all};
         for (DevBuf *b : bufs) release(*b);
         h->cache.pop_back();
     }
@@ -693,7 +698,8 @@ void free_geom(Geom *g)
                       &g->plan_ch_off_d, &g->plan_n_d, &g->prof_ch_off_d, &g->prof_plan_d,
                       &g->ch_frel, &g->ch_B, &g->ch_alpha, &g->ch_gamma, &g->ch_nf,
                       &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->zs_g, &g->item_slot,
-                      &g->win_lo, &g->win_hi, &g->ch_scale, &g->half_steps, &g->mci_items, &g->slot_items2};
+                      &g->win_lo, &g->win_hi, &g->ch_scale, &g->half_steps, &g->mci_items, &g->slot_items2,
+                      &g->item_slot_all};
     for (DevBuf *b : bufs) release(*b);
 }
 
@@ -793,8 +799,8 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     if (precision == ISRS_PREC_FP32 && g->mci_phase_rev_max > 536870912.0)
         return fail(h, ISRS_ERR_UNSUPPORTED, "MCI phase range %.3g revolutions exceeds the FP32 reduction range",
                     g->mci_phase_rev_max);
-    if (adjoint && g->n_mci_items > 0)
-        return fail(h, ISRS_ERR_UNSUPPORTED, "the adjoint does not cover the separate MCI grid");
+    if (adjoint && g->n_mci_items > 0 && g->profile == ISRS_PROFILE_RAMAN_ODE)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "the Raman-ODE adjoint does not cover the separate MCI grid");
     if (g->n_mci_items > 0 && (s = ensure(h, h->partial_mci, sizeof(double) * g->n_mci_items)) != ISRS_OK)
         return s;
     if ((s = ensure(h, h->pd_d, sizeof(double) * g->total_prof_ch)) != ISRS_OK) return s;
@@ -845,7 +851,9 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     const int block = h->tile_threads > 0 ? h->tile_threads : 256;
     if (adjoint) {
         const int n_ch = g->plan_n[0];
-        if ((s = ensure(h, h->gA, sizeof(double2) * (size_t)std::max(1, g->n_items) * M)) != ISRS_OK) return s;
+        if ((s = ensure(h, h->gA, sizeof(double2) * (size_t)std::max(1, g->n_items + g->n_mci_items) * M)) !=
+            ISRS_OK)
+            return s;
         if ((s = ensure(h, h->gPd, sizeof(double) * (size_t)g->n_slots * n_ch)) != ISRS_OK) return s;
         CK(cudaMemsetAsync(h->gPd.p, 0, sizeof(double) * (size_t)g->n_slots * n_ch, st));
         AdjParams ap;
@@ -859,6 +867,20 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
         if (g->n_items < grid) grid = std::max(1, g->n_items);
         if ((s = mark(h, 1, 0, st)) != ISRS_OK) return s;
         if (g->n_items > 0) CK(launch_adjoint(ap, grid, block, st));
+        if (g->n_mci_items > 0) {
+            // the MCI cells of the separate grid: further tiles of their CUTs
+            AdjParams am = ap;
+            am.q.items = (const DevItem *)g->mci_items.p;
+            am.q.n_items = g->n_mci_items;
+            am.q.G = g->G_mci;
+            am.q.partial = (double *)h->partial_mci.p;
+            am.q.counter = (int *)h->counter.p + 1;
+            am.item_R = (double2 *)h->gA.p + (size_t)g->n_items * M;
+            am.item_slot = (const int *)g->item_slot_all.p + g->n_items;
+            int mgrid = h->num_sms * adjoint_mci_blocks_per_sm(M, am.q.mci_n_max, block);
+            if (g->n_mci_items < mgrid) mgrid = g->n_mci_items;
+            CK(launch_adjoint_mci(am, mgrid, block, st));
+        }
         if ((s = mark(h, 1, 1, st)) != ISRS_OK) return s;
     } else {
         const bool tab = g->profile == ISRS_PROFILE_RAMAN_ODE;
@@ -1056,9 +1078,10 @@ ChainParams chain_params(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q
     cp.pnli = (const double *)h->o_pnli.p;
     cp.pase = (const double *)h->o_pase.p;
     cp.lnrho_L = (const double *)h->lnrho_L.p;
-    cp.item_slot = (const int *)g->item_slot.p;
+    // the MCI items of a separate grid follow the regular ones in the bucket rows
+    cp.item_slot = (const int *)(g->n_mci_items > 0 ? g->item_slot_all.p : g->item_slot.p);
     cp.slot_cut = (const int *)g->slot_cut.p;
-    cp.n_items = g->n_items;
+    cp.n_items = g->n_items + g->n_mci_items;
     cp.n_slots = g->n_slots;
     cp.n_ch = n;
     cp.n_steps = g->n_steps;
@@ -1401,8 +1424,8 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
     if (quad->precision != ISRS_PREC_FP32)
         return fail(h, ISRS_ERR_INVALID_ARG, "the gradient is the adjoint of the FP32 path");
     if (quad->n_edges - 1 > 128) return fail(h, ISRS_ERR_UNSUPPORTED, "gradient supports at most 128 z-steps");
-    if (quad->G_mci > 0)
-        return fail(h, ISRS_ERR_UNSUPPORTED, "the gradient does not cover the separate MCI grid");
+    if (quad->G_mci > 0 && fibre->profile == ISRS_PROFILE_RAMAN_ODE)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "the Raman-ODE gradient does not cover the separate MCI grid");
     if (fibre->profile == ISRS_PROFILE_RAMAN_ODE && ch->n_ch > kMaxRamanGradCh)
         return fail(h, ISRS_ERR_UNSUPPORTED, "Raman-ODE gradient supports at most %d channels", kMaxRamanGradCh);
     if (ch->guard)

@@ -138,6 +138,10 @@ size_t quad_mci_smem_bytes(int precision, int n_steps, int n_max);
 int quad_mci_blocks_per_sm(int precision, int n_steps, int n_max, int block);
 cudaError_t launch_quad_mci(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
 size_t adjoint_smem_bytes(int n_steps, int G, int block);
+// adjoint over the MCI cells of a separate grid (closed-form profile)
+size_t adjoint_mci_smem_bytes(int n_steps, int n_max, int block);
+int adjoint_mci_blocks_per_sm(int n_steps, int n_max, int block);
+cudaError_t launch_adjoint_mci(const AdjParams &ap, int grid, int block, cudaStream_t st);
 int adjoint_blocks_per_sm(int n_steps, int G, int block);
 cudaError_t launch_adjoint(const AdjParams &ap, int grid, int block, cudaStream_t st);
 cudaError_t launch_chain(const ChainParams &cp, cudaStream_t st);

@@ -84,6 +84,45 @@ def test_rejections(eng):
     with pytest.raises(IsrsError):
         eng.eta(wl.with_(cell_set=W.CELLS_ALL, G_mci=33))
     with pytest.raises(IsrsError):
-        eng.grad(wl.with_(cell_set=W.CELLS_ALL, G_mci=4))
+        eng.grad(W.raman(wl.with_(cell_set=W.CELLS_ALL, G_mci=4)))
     with pytest.raises(IsrsError):
         eng.eta(W.raman(wl.with_(cell_set=W.CELLS_ALL, G_mci=4)))
+
+
+STEP_DB = 1e-4
+
+
+def _fd(T_of_P, P, chans):
+    """dT/dP_j by central differences in dBm (1e-4 dB) of the FP64 path."""
+    g = np.zeros(len(chans))
+    for k, j in enumerate(chans):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[j] = P[j] * 10 ** (STEP_DB / 10)
+        Pm[j] = P[j] * 10 ** (-STEP_DB / 10)
+        g[k] = (T_of_P(Pp) - T_of_P(Pm)) / (2 * STEP_DB) / (P[j] * np.log(10) / 10)
+    return g
+
+
+@pytest.mark.parametrize("case", ["tiny", "oband"])
+def test_adjoint_with_mci_grid_vs_fd(eng, case):
+    """The gradient over SCI/XCI pieces plus the MCI cells of their own grid
+    against central differences of the FP64 path (same cells, same grids),
+    1e-3 relative per channel (floored at 1e-3 of the largest component)."""
+    if case == "tiny":
+        wl = W.tiny(G=32, n_edges=41, cell_set=W.CELLS_ALL).with_(G_mci=8)
+        P = wl.P_W * W.dbm_to_w(W.random_profile_dbm(5, seed=12)) / 1e-3
+        chans = list(range(5))
+    else:
+        wl = W.oband(G=12, n_edges=33, cell_set=W.CELLS_ALL).with_(G_mci=6)
+        P = wl.P_W
+        chans = [0, 9, 20, 31, 40]
+    r = eng.grad(wl, P=P)
+    fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], P, chans)
+    adj = np.asarray(r["dT_dP"].cpu() if hasattr(r["dT_dP"], "cpu") else r["dT_dP"])[chans]
+    floor = 1e-3 * np.max(np.abs(fd))
+    err = np.abs(adj - fd) / np.maximum(np.abs(fd), floor)
+    assert err.max() < 1e-3, (err.max(), adj, fd)
+    # the gradient call's forward outputs include the MCI cells
+    s = eng.snr(wl, P=P, precision=0)
+    snr_g = np.asarray(r["snr"].cpu() if hasattr(r["snr"], "cpu") else r["snr"])
+    np.testing.assert_allclose(snr_g, np.asarray(s["snr"]), rtol=1e-6)
