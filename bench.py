@@ -454,6 +454,11 @@ def profile_case(kind: str) -> int:
         from paper_2401_18022_gb300 import workloads as W
         sub = W.raman(W.subset_plan(wl, np.arange(0, wl.n_ch, 4), "uwb-148ch-every4th"))
         eng.grad(sub, P=torch.tensor(sub.P_W, dtype=torch.float64, device="cuda"))
+    elif kind == "mci256":
+        # the 148-ch subset with every cell: SCI/XCI at G = 256, the MCI cells on an 8 x 8 grid
+        from paper_2401_18022_gb300 import workloads as W
+        sub = W.subset_plan(wl, np.arange(0, wl.n_ch, 4), "uwb-148ch-every4th").with_(cell_set=W.CELLS_ALL, G_mci=8)
+        eng.grad(sub, P=torch.tensor(sub.P_W, dtype=torch.float64, device="cuda"))
     elif kind in ("adjoint256", "quad256"):
         # every 4th slot of the 589-ch grid (148 ch over the whole band) at the
         # bench's G = 256: the production per-piece shape, ~1.4e9 points
@@ -488,7 +493,7 @@ def main():
     ap.add_argument("--workload", default="uwb", choices=["uwb", "batched"],
                     help="uwb: the 589-ch system (default); batched: 512 profiles over 3 plans")
     ap.add_argument("--profile-case", default=None,
-                    choices=["quad", "quad64", "adjoint", "adjoint256", "quad256", "raman256"],
+                    choices=["quad", "quad64", "adjoint", "adjoint256", "quad256", "raman256", "mci256"],
                     help="run one small launch of a kernel (for ncu captures) and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -126,3 +126,14 @@ def test_adjoint_with_mci_grid_vs_fd(eng, case):
     s = eng.snr(wl, P=P, precision=0)
     snr_g = np.asarray(r["snr"].cpu() if hasattr(r["snr"], "cpu") else r["snr"])
     np.testing.assert_allclose(snr_g, np.asarray(s["snr"]), rtol=1e-6)
+
+
+def test_adjoint_with_mci_grid_multispan(eng):
+    """Three identical spans: the phased-array factor in the MCI cells too."""
+    wl = W.tiny(G=24, n_edges=33, cell_set=W.CELLS_ALL).with_(G_mci=6, n_spans=3)
+    r = eng.grad(wl)
+    fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], wl.P_W, range(5))
+    adj = np.asarray(r["dT_dP"].cpu() if hasattr(r["dT_dP"], "cpu") else r["dT_dP"])
+    floor = 1e-3 * np.max(np.abs(fd))
+    err = np.abs(adj - fd) / np.maximum(np.abs(fd), floor)
+    assert err.max() < 1e-3, (err.max(), adj, fd)
