@@ -235,11 +235,13 @@ def run_gpu(args):
     sfu_peak = N_SMS * SFU_PER_CLK_PER_SM * sm_max * 1e6 / 1e12       # Tops/s
     achieved = sfu_ops / (quad_ms / 1e3) / 1e12
     tot_pts = max(1, sum(paths.values()))
-    traffic = (ADJ_DRAM_CAPTURE["bytes"] * n_eval / ADJ_DRAM_CAPTURE["points"]) if use_grad else None
+    cap = ADJ_DRAM_CAPTURE if use_grad else FWD_DRAM_CAPTURE
+    traffic = cap["bytes"] * n_eval / cap["points"]
     roof = {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Tops/s (SFU: sin, cos, ex2)",
             "frac": achieved / sfu_peak, "traffic": traffic,
-            "traffic_note": ("DRAM bytes per launch, scaled by evaluated points from an ncu capture of the "
-                             "148-ch G=256 case (profiles/k_quad_adj_uwb148_every4th_G256.md)") if use_grad else None,
+            "traffic_note": "DRAM bytes per launch, scaled by evaluated points from an ncu capture of the "
+                            "148-ch G=256 case (profiles/%s)" % ("k_quad_adj_uwb148_every4th_G256.md" if use_grad
+                                                                else "k_quad_f32_uwb148_every4th_G256.md"),
             "kernel": "k_quad_adj" if use_grad else "k_quad_f32", "kernel_ms": quad_ms,
             "sfu_ops_per_launch": sfu_ops,
             "path_fraction": {k: v / tot_pts for k, v in paths.items()},
@@ -297,6 +299,7 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
 # the piece list and writes one bucket row per tile, both proportional to the
 # evaluated points at fixed G, so a full launch's traffic is scaled by points.
 ADJ_DRAM_CAPTURE = {"bytes": 4.466e6, "points": 2880700416}
+FWD_DRAM_CAPTURE = {"bytes": 4.056e6, "points": 2880700416}     # k_quad_f32, --profile-case quad256
 
 
 def _timed(fn, dev, reps: int = 2):
