@@ -212,7 +212,7 @@ def run_gpu(args):
         from paper_2401_18022_gb300 import dist as D
         t_total = D.max_over_ranks(t_total)
 
-    # grid points of the method's Riemann grid (mirror cells counted, as in the oracle)
+    # grid points of the method's Riemann grid (every piece, as the oracle counts them)
     from paper_2401_18022_gb300 import workloads as W
     import oracle  # noqa: F401  (only for the CPU baseline below)
     n_eval = info["points"]
@@ -354,10 +354,14 @@ def _extras(eng, wl, P, dev):
 
 
 def _unfolded_points(wl):
-    """Grid points of the Riemann sum as defined (every piece of every CUT,
-    mirror cells included): G^2 x (4 + 2 (N-1)) per CUT for SCI + XCI."""
+    """Grid points of the Riemann sum as defined (App. A, Eqs. q1..q4: every
+    piece of every CUT, mirror pieces included, as the oracle evaluates them).
+    With SCI + XCI cells and disjoint channels a CUT has 4 + 4 (N - 1) pieces:
+    the SCI cell's four quadrants, and two pieces (split at f1 = 0 or f2 = 0,
+    where the CUT's channel straddles the axis) for each of the cells (i, k)
+    and (k, i).  The kernels evaluate the mirror-folded half."""
     n = wl.n_ch
-    per_cut = 4 + 2 * (n - 1) if wl.cell_set == 0 else None
+    per_cut = 4 + 4 * (n - 1) if wl.cell_set == 0 else None
     if per_cut is None:
         raise ValueError("bench counts SCI+XCI grids only")
     return n * per_cut * wl.G * wl.G
