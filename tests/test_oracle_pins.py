@@ -368,3 +368,129 @@ def test_multispan_quadrature_and_ase(orc):
         snr1, pase1, _ = orc.snr_throughput(wl, np.zeros(5))
         snrn, pasen, _ = orc.snr_throughput(wl.with_(n_spans=n), np.zeros(5))
         np.testing.assert_allclose(pasen, n * pase1, rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# App. A, Eq. gain_fin: the eta prefactor, end to end
+# ---------------------------------------------------------------------------
+def _one_channel_no_dispersion(G, cell_set=0):
+    """One 96 GBaud channel, beta2 = beta3 = beta4 = 0, C_r = 0, uniform alpha."""
+    Bw, P, a, L, g = 0.096, 2e-3, 0.046, 80.0, 1.3
+    wl = W.tiny().with_(f_THz=np.array([193.4]), B_THz=np.array([Bw]), P_W=np.array([P]),
+                        alpha_per_km=np.array([a]), lambda_nm=np.array([1550.0]),
+                        aeff_um2=np.array([80.0]), nf_dB=np.array([5.0]), Cr=0.0, gamma_fixed=g,
+                        alpha_R_per_km=a, cell_set=cell_set, G=G, n_edges=113)
+    fib = np.array([L, 193.4, 0.0, 0.0, 0.0, 0.0, a])
+    return wl, fib, (Bw, P, a, L, g)
+
+
+def _eta_no_dispersion_exact(orc, a, L, g):
+    """phi = 0 at every grid point, so every point's z-sum is the same real
+    number S = sum_m e^{-alpha z_m} dz_m (Eq. slow_vary with sinc(0) = 1 and
+    p_m = e^{-alpha z_m}: the three PSD frequencies and the CUT share alpha).
+    F_a, F_b and F_c = F_a + F_b - f_i all lie in the channel on the hexagon
+    |f1|, |f2|, |f1 + f2| <= B/2, whose area is B^2 - 2 (B/2)^2 / 2 = (3/4) B^2,
+    and G_Tx = P/B there.  So the frequency integral is (P/B)^3 (3/4) B^2 S^2,
+    and Eq. gain_fin with P_NLI = G(f_i) B gives
+        eta = (16/27) gamma^2 B (P/B)^3 (3/4) B^2 S^2 / P^3 = (4/9) gamma^2 S^2,
+    the zero-dispersion limit of the GN model ((4/9) gamma^2 L_eff^2 when the
+    z-sum is replaced by its integral)."""
+    ze = _refs_zgrid(L, a, 113)
+    zm, dz = 0.5 * (ze[1:] + ze[:-1]), np.diff(ze)
+    S = float(np.sum(np.exp(-a * zm) * dz))
+    return 4.0 / 9.0 * g * g * S * S, S
+
+
+def _refs_zgrid(L, a, n):
+    """Equal power drop per step, written out here (not the oracle's routine)."""
+    t = np.arange(n) / (n - 1)
+    z = -np.log1p(-t * (1.0 - math.exp(-a * L))) / a
+    z[-1] = L
+    return z
+
+
+@pytest.mark.parametrize("cell_set", [0, 1])
+def test_eta_prefactor_single_channel_zero_dispersion(orc, cell_set):
+    """The whole chain Sigma -> eta (Eq. gain_fin, 16/27 gamma^2 B_i, P_NLI =
+    G(f_i) B_i) against the closed form (4/9) gamma^2 S^2.  The hexagon's
+    oblique edge |f1 + f2| = B/2 cuts grid cells, so the Riemann sum
+    converges to it at first order with an oscillating sign: the error must
+    shrink from G = 32 to G >= 128 and stay within 5e-4 there."""
+    errs = {}
+    for G in (32, 128, 256, 512):
+        wl, fib, (Bw, P, a, L, g) = _one_channel_no_dispersion(G, cell_set)
+        s = orc.sigma(wl, fibre=fib)
+        e, pn = orc.eta(wl, s)
+        ref, S = _eta_no_dispersion_exact(orc, a, L, g)
+        errs[G] = abs(e[0] / ref - 1)
+        assert pn[0] == pytest.approx(e[0] * P ** 3, rel=1e-14)
+    assert errs[32] > 5 * max(errs[128], errs[256], errs[512])
+    assert max(errs[128], errs[256], errs[512]) < 5e-4
+    # the continuous z-integral: S -> L_eff = (1 - e^{-alpha L})/alpha
+    assert S == pytest.approx((1 - math.exp(-a * L)) / a, rel=1e-3)
+
+
+def test_eta_prefactor_full_square_pieces(orc):
+    """The (+,-) and (-,+) quadrant pieces of the SCI cell are full squares
+    [0, B/2] x [-B/2, 0] (|f1 + f2| <= B/2 holds everywhere), so each carries
+    (P/B)^3 (B/2)^2 S^2 exactly.  The hyperbolic grid converges to it at second
+    order in the row spacing of s = ln upsilon1, whose range is ln(1/eps) = 23
+    (the eps cut-off strip itself is ~eps ln(1/eps) = 2e-9 of the area): the
+    error must fall by ~4x per doubling of G."""
+    errs = []
+    for G in (128, 256, 512):
+        wl, fib, (Bw, P, a, L, g) = _one_channel_no_dispersion(G, 0)
+        _, S = _eta_no_dispersion_exact(orc, a, L, g)
+        s, pv = orc.sigma(wl, fibre=fib, return_pieces=True)
+        pcs = orc.pieces(wl.f_THz, wl.B_THz, 0, 0)
+        mixed = [v for p, v in zip(pcs, pv) if p[2] != p[3]]
+        assert len(mixed) == 2 and mixed[0] == pytest.approx(mixed[1], rel=1e-13)
+        ref = (P / Bw) ** 3 * (Bw / 2) ** 2 * S * S
+        errs.append(abs(mixed[0] / ref - 1))
+    assert errs[2] < 2e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+@pytest.mark.parametrize("mutation", ["8/27", "drop_B", "B_squared", "gamma_not_squared"])
+def test_eta_prefactor_pin_catches_mutations(orc, mutation):
+    """Plant a slip in the oracle's eta (as a rescaling of its output): the
+    closed-form pin above must fail by far more than its 5e-4 tolerance."""
+    wl, fib, (Bw, P, a, L, g) = _one_channel_no_dispersion(256, 0)
+    s = orc.sigma(wl, fibre=fib)
+    e, _ = orc.eta(wl, s)
+    mutated = {"8/27": e[0] / 2.0, "drop_B": e[0] / Bw, "B_squared": e[0] * Bw,
+               "gamma_not_squared": e[0] / g}[mutation]
+    ref, _ = _eta_no_dispersion_exact(orc, a, L, g)
+    assert abs(mutated / ref - 1) > 100 * 5e-4
+
+
+# ---------------------------------------------------------------------------
+# Sec. IV, Eq. loss: SNR with NLI and transceiver noise
+# ---------------------------------------------------------------------------
+def test_snr_optimum_launch_power_textbook(orc):
+    """With a power-independent ASE (C_r = 0) and a fixed eta, SNR(P) =
+    P / (eta P^3 + P_ASE) peaks where the NLI power is half the ASE power,
+    P_opt = (P_ASE / (2 eta))^(1/3), at SNR = P_opt / (1.5 P_ASE): the GN
+    model's optimum launch power."""
+    wl = W.tiny(G=8, n_edges=5).with_(Cr=0.0)
+    eta = np.array([1.0e3, 2.5e3, 4.0e2, 7.0e2, 1.5e3])        # 1/W^2
+    _, pase, _ = orc.snr_throughput(wl, eta, P=np.full(5, 1e-3))
+    p_opt = (pase / (2 * eta)) ** (1.0 / 3.0)
+    snr_opt, _, _ = orc.snr_throughput(wl, eta, P=p_opt)
+    np.testing.assert_allclose(snr_opt, p_opt / (1.5 * pase), rtol=1e-12)
+    for f in (0.97, 1.03):
+        snr_f, _, _ = orc.snr_throughput(wl, eta, P=p_opt * f)
+        assert np.all(snr_f < snr_opt)
+
+
+def test_snr_transceiver_limited_and_guard(orc):
+    """No NLI and a negligible ASE (NF -300 dB): 1/SNR = 1/SNR_ASE + 1/SNR_TRX
+    leaves SNR = SNR_TRX, and T = 2 B log2(1 + SNR_TRX) over the channels that
+    are neither guards nor empty."""
+    wl = W.tiny(G=8, n_edges=5).with_(Cr=0.0, nf_dB=np.full(5, -300.0), snr_trx_dB=20.0,
+                                      guard=np.array([0, 0, 1, 0, 0], dtype=np.uint8))
+    snr, pase, T = orc.snr_throughput(wl, np.zeros(5))
+    lit = np.array([True, True, False, True, True])
+    np.testing.assert_allclose(snr[lit], 100.0, rtol=1e-12)
+    assert snr[2] == 0.0
+    assert T == pytest.approx(float(np.sum(2 * wl.B_THz[lit] * np.log2(101.0))), rel=1e-12)
