@@ -16,6 +16,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -53,14 +54,19 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, path: str = None):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        if path is None:
+            fd, path = tempfile.mkstemp(prefix=f"isrs_clocks_rank{device}_", suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            d = os.path.dirname(self.path)
+            if d:
+                os.makedirs(d, exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -186,7 +192,7 @@ def run_gpu(args):
     info = eng.last_launch_info()
     launches_per_step = info["launches"]
 
-    clk = Clocks(local)
+    clk = Clocks(local, args.clocks_csv.format(rank=local) if args.clocks_csv else None)
     clk.start()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -213,8 +219,6 @@ def run_gpu(args):
         t_total = D.max_over_ranks(t_total)
 
     # grid points of the method's Riemann grid (every piece, as the oracle counts them)
-    from paper_2401_18022_gb300 import workloads as W
-    import oracle  # noqa: F401  (only for the CPU baseline below)
     n_eval = info["points"]
     n_grid = _unfolded_points(wl)
     value = world * n_grid * args.steps / t_total
@@ -495,6 +499,8 @@ def main():
     ap.add_argument("--mode", default="grad", choices=["snr", "grad"],
                     help="grad: SNR + dT/dP (all hot-path steps); snr: forward only")
     ap.add_argument("--quick", action="store_true", help="skip e2e, FP64 and CPU legs")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="where to keep the nvidia-smi clock samples ({rank} is replaced); default: a temp file")
     ap.add_argument("--extras", action="store_true",
                     help="also time the Raman-ODE profile and the MCI cells on the same workload")
     ap.add_argument("--workload", default="uwb", choices=["uwb", "batched"],

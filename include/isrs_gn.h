@@ -24,9 +24,14 @@
  *    call only.  Channels must be sorted by frequency and disjoint.
  *  - Launch powers and per-channel outputs may be host or device pointers;
  *    the library detects which (cudaPointerGetAttributes).  Device pointers
- *    must belong to the handle's device.  With device outputs the call is
- *    asynchronous on `stream`; with any host output it synchronises `stream`
- *    before returning.
+ *    must belong to the handle's device (device memory of another GPU is
+ *    INVALID_ARG).  With device outputs the call is asynchronous on `stream`;
+ *    with any host output it synchronises `stream` before returning.
+ *  - The compute calls read the launch powers back for validation and may
+ *    synchronise `stream`, so they cannot run on a stream that is being
+ *    captured into a CUDA graph: there they return ISRS_ERR_UNSUPPORTED
+ *    before issuing any work.  isrs_gn_eta_batched captures and replays its
+ *    own graph internally.
  *  - The caller owns all input and output buffers.  The handle owns its
  *    device workspace and a cache of per-plan tables (pieces, z-grid).  A
  *    handle must not be used from two host threads at once.
@@ -272,20 +277,24 @@ isrs_status isrs_last_path_counts(isrs_handle h, int64_t *counts);
  * a memory-budgeted real-time loop, a process whose allocator is locked).
  * The paper has no counterpart; this is a deployment variant.
  *
- * All scratch (plan tables, per-profile tables, tile partials) lives in one
- * file-scope device array of 4 MiB that every GPU loading this library holds
- * until the process exits.  The first call on a device looks up that array's
- * address with the device current; make that first call before any stream
- * capture.  Every call shares the array and leaves the last call's contents
- * in it; calls whose GPU work overlaps (two streams, two host threads, two
- * devices' worth of work on one device) race on it and must be serialised by
- * the caller.
- *   P_W[n_ch], eta[n_ch]: device pointers; pnli[n_ch]: device or NULL.
- * No handle is used; the call synchronises `stream` once after uploading
- * the plan tables, then runs asynchronously.
- * Errors: INVALID_ARG (as isrs_gn_eta, or a host pointer), UNSUPPORTED
- * (the tables need more than the 4 MiB scratch: e.g. more than ~5e4 pieces,
- * or the FP32 phase range; more than one span; the Raman-ODE profile), CUDA. */
+ * All scratch (plan tables, per-profile tables, the z-grid with its step
+ * moments, tile partials) lives in one file-scope device array of 4 MiB that
+ * every GPU loading this library holds until the process exits.  The first
+ * call on a device looks up that array's address with the device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array and leaves the last call's contents in it; calls whose GPU work
+ * overlaps (two streams, two host threads, two devices' worth of work on one
+ * device) race on it and must be serialised by the caller.
+ *   P_W[n_ch], eta[n_ch]: device pointers of the current device (or managed
+ *   memory); pnli[n_ch]: the same, or NULL.
+ * No handle is used; the call reads the powers back to the host and
+ * synchronises `stream` once after uploading the plan tables, then runs
+ * asynchronously.  On a stream that is being captured it returns
+ * UNSUPPORTED before issuing any work, leaving the capture intact.
+ * Errors: INVALID_ARG (as isrs_gn_eta, a host pointer, or device memory of
+ * another GPU), UNSUPPORTED (the tables need more than the 4 MiB scratch:
+ * e.g. more than ~5e4 pieces, or the FP32 phase range; more than one span;
+ * the Raman-ODE profile; a capturing stream), CUDA. */
 isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
                                 const isrs_quad *quad, double *eta, double *pnli, void *stream);
 

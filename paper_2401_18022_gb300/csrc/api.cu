@@ -19,6 +19,7 @@
 
 #include "../../include/isrs_gn.h"
 #include "isrs_kernels.h"
+#include "ptr_class.h"
 
 using namespace isrs;
 
@@ -138,14 +139,43 @@ isrs_status upload(isrs_handle h, DevBuf &b, const std::vector<T> &v, cudaStream
     return ISRS_OK;
 }
 
-bool is_device_ptr(const void *p)
+// Where a caller's pointer lives relative to the current device (ptr_class.h).
+int where_ptr(const void *p)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return kPtrHost;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return kPtrOtherDevice;
+    }
+    return ptr_class((int)a.type, a.device, cur);
+}
+
+bool is_device_ptr(const void *p) { return where_ptr(p) == kPtrDevice; }
+
+// Rejects a device pointer of another GPU (a kernel on this device would
+// write into that GPU's memory, or fault without peer access).
+isrs_status check_ptr(isrs_handle h, const void *p, const char *name)
+{
+    if (p && where_ptr(p) == kPtrOtherDevice)
+        return fail(h, ISRS_ERR_INVALID_ARG, "%s is device memory of another GPU", name);
+    return ISRS_OK;
+}
+
+// Every call copies results to the host or synchronises `stream`, which a
+// stream capture forbids: reject a capturing stream before issuing any work,
+// so that the caller's capture stays valid.
+isrs_status reject_capture(isrs_handle h, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "the stream is being captured; this call synchronises it");
+    return ISRS_OK;
 }
 
 // Records event `pos` (0 start, 1 end) of kernel class `which` on the stream,
@@ -1319,6 +1349,10 @@ isrs_status isrs_gn_eta(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
     }
     if ((s = set_device(h)) != ISRS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((s = reject_capture(h, st)) != ISRS_OK) return s;
+    if ((s = check_ptr(h, P_W, "P_W")) != ISRS_OK || (s = check_ptr(h, eta, "eta")) != ISRS_OK ||
+        (s = check_ptr(h, pnli, "pnli")) != ISRS_OK || (s = check_ptr(h, sigma, "sigma")) != ISRS_OK)
+        return s;
     if ((s = check_powers_any(h, P_W, 0, ch->n_ch, st)) != ISRS_OK) return s;
     Geom *g = nullptr;
     std::vector<std::vector<int>> cpp{cl};
@@ -1349,6 +1383,10 @@ isrs_status isrs_gn_snr(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
     if (!P_W || !snr) return fail(h, ISRS_ERR_INVALID_ARG, "P_W or snr is NULL");
     if ((s = set_device(h)) != ISRS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((s = reject_capture(h, st)) != ISRS_OK) return s;
+    if ((s = check_ptr(h, P_W, "P_W")) != ISRS_OK || (s = check_ptr(h, snr, "snr")) != ISRS_OK ||
+        (s = check_ptr(h, eta, "eta")) != ISRS_OK)
+        return s;
     if ((s = check_powers_any(h, P_W, 0, ch->n_ch, st)) != ISRS_OK) return s;
     Geom *g = nullptr;
     std::vector<std::vector<int>> cpp{std::vector<int>()};
@@ -1393,6 +1431,8 @@ isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_pl
     }
     if ((s = set_device(h)) != ISRS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((s = reject_capture(h, st)) != ISRS_OK) return s;
+    if ((s = check_ptr(h, P_W, "P_W")) != ISRS_OK || (s = check_ptr(h, eta, "eta")) != ISRS_OK) return s;
     size_t off = 0;
     for (int p = 0; p < n_prof; ++p) {
         if ((s = check_powers_any(h, P_W, off, plans[pp[p]].n_ch, st)) != ISRS_OK) return s;
@@ -1433,6 +1473,10 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
             if (ch->guard[k]) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs every channel lit (guard %d)", k);
     if ((s = set_device(h)) != ISRS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((s = reject_capture(h, st)) != ISRS_OK) return s;
+    if ((s = check_ptr(h, P_W, "P_W")) != ISRS_OK || (s = check_ptr(h, dT_dP, "dT_dP")) != ISRS_OK ||
+        (s = check_ptr(h, snr, "snr")) != ISRS_OK || (s = check_ptr(h, eta, "eta")) != ISRS_OK)
+        return s;
     {
         std::vector<double> hp(ch->n_ch);
         if (is_device_ptr(P_W)) {
@@ -1475,9 +1519,8 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
 // Allocation-free forward entry point (isrs_gn_eta_noalloc).
 //
 // For callers that cannot allocate device memory themselves: code running
-// inside a host framework that owns the device allocator, a CUDA-graph
-// builder or a real-time loop in which a cudaMalloc would block or break the
-// memory budget.  All scratch lives in one file-scope device array of fixed
+// inside a host framework that owns the device allocator, or a real-time loop
+// in which a cudaMalloc would block or break the memory budget.  All scratch lives in one file-scope device array of fixed
 // size that every GPU loading this library holds until the process exits.
 // ============================================================================
 #include <mutex>
@@ -1535,6 +1578,17 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     if ((s = check_fibre(nullptr, fibre)) != ISRS_OK) return s;
     if ((s = check_plan(nullptr, ch)) != ISRS_OK) return s;
     if ((s = check_quad(nullptr, quad)) != ISRS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        // a capturing stream would be invalidated by the synchronisations below
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return ISRS_ERR_CUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return ISRS_ERR_UNSUPPORTED;
+    }
+    // inputs and outputs: device memory of the current device (or managed)
     if (!P_W || !eta || !is_device_ptr(P_W) || !is_device_ptr(eta) || (pnli && !is_device_ptr(pnli)))
         return ISRS_ERR_INVALID_ARG;
     if (fibre->n_spans > 1) return ISRS_ERR_UNSUPPORTED;         // single span only
@@ -1542,7 +1596,6 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     if (quad->G_mci > 0) return ISRS_ERR_UNSUPPORTED;                             // one grid for every cell
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ISRS_ERR_CUDA;
-    cudaStream_t st = (cudaStream_t)stream;
     const int n = ch->n_ch;
 
     // launch powers: validated on the host
@@ -1578,10 +1631,10 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
         av[k] = ch->alpha_per_km[k];
         gv[k] = ch->gamma_per_W_km[k];
     }
-    std::vector<float4> za, zb;
+    std::vector<float4> za, zb, zg;
     std::vector<double2> zd;
     float dz_max = 0.f;
-    zgrid_tables(fibre->L_km, fibre->alpha_R_per_km, quad->n_edges, za, zb, zd, dz_max);
+    zgrid_tables(fibre->L_km, fibre->alpha_R_per_km, quad->n_edges, za, zb, zd, dz_max, &zg);
     const int M = quad->n_edges - 1;
     if (quad->precision == ISRS_PREC_FP32) {
         const double pi = 3.14159265358979323846;
@@ -1609,6 +1662,8 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     const size_t o_alpha = L.take(sizeof(double) * n), o_gamma = L.take(sizeof(double) * n);
     const size_t o_za = L.take(sizeof(float4) * M), o_zb = L.take(sizeof(float4) * M);
     const size_t o_zd = L.take(sizeof(double2) * M);
+    const size_t o_zg = L.take(sizeof(float4) * zg.size());   // centred step moments (contracted small phase)
+    const size_t o_kapL = L.take(sizeof(double));
     const size_t o_P = L.take(sizeof(double) * n);
     const size_t o_pdd = L.take(sizeof(double) * n), o_pdf = L.take(sizeof(float) * n);
     const size_t o_lnL = L.take(sizeof(double) * n), o_ptot = L.take(sizeof(double));
@@ -1628,7 +1683,8 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
         {o_plan_n, plan_n.data(), sizeof(int)}, {o_frel, frel.data(), sizeof(double) * n},
         {o_B, Bv.data(), sizeof(double) * n}, {o_alpha, av.data(), sizeof(double) * n},
         {o_gamma, gv.data(), sizeof(double) * n}, {o_za, za.data(), sizeof(float4) * M},
-        {o_zb, zb.data(), sizeof(float4) * M}, {o_zd, zd.data(), sizeof(double2) * M}};
+        {o_zb, zb.data(), sizeof(float4) * M}, {o_zd, zd.data(), sizeof(double2) * M},
+        {o_zg, zg.data(), sizeof(float4) * zg.size()}};
     for (const Up &u : ups)
         if (u.bytes && cudaMemcpyAsync(base + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return ISRS_ERR_CUDA;
@@ -1657,6 +1713,7 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     pp.step_f = (float2 *)(base + o_stepf);
     pp.lnrho_L = (double *)(base + o_lnL);
     pp.ptot = (double *)(base + o_ptot);
+    pp.kap_L = (double *)(base + o_kapL);
     if (launch_prep(pp, 1, st) != cudaSuccess) return ISRS_ERR_CUDA;
 
     QuadParams qp;
@@ -1681,6 +1738,9 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     qp.zs_a = (const float4 *)(base + o_za);
     qp.zs_b = (const float4 *)(base + o_zb);
     qp.zs_d = pp.zs_d;
+    qp.zs_g = (const float4 *)(base + o_zg);
+    qp.kap_L = pp.kap_L;
+    qp.n_spans = 1;
     qp.dz_max = dz_max;
     qp.L = (float)fibre->L_km;
     qp.partial = (double *)(base + o_partial);

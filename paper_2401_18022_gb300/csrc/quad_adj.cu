@@ -112,7 +112,10 @@ __device__ __forceinline__ float butterfly32(const F &val, int lane)
 // The owned step tables are lane-contiguous float4 copies in shared memory
 // (conflict-free, both halves broadcast).  Lane buckets accumulate in
 // registers and are folded into per-warp FP64 shared buckets every 8 batches.
-// Every reduction has a fixed order, so results are reproducible.
+// The forward partials and the step buckets are reduced in a fixed order (bit
+// for bit reproducible); the PSD buckets V are scattered with FP64 atomics
+// across the tiles of a CUT (and FP32 shared atomics for F_c candidates past
+// the fourth), so dT/dP is reproducible to FP64 rounding, not bit for bit.
 // ---------------------------------------------------------------------------
 #ifndef ISRS_ADJ_MIN_BLOCKS
 #define ISRS_ADJ_MIN_BLOCKS 3   // resident blocks per SM the register budget is sized for

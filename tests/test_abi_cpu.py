@@ -87,3 +87,28 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_pointer_classification_rejects_other_devices(tmp_path):
+    """The rule the entry points apply to every caller pointer (csrc/ptr_class.h):
+    device memory of the current device and managed memory are used in place,
+    host memory is copied through, device memory of another GPU is rejected
+    (a kernel on this device would otherwise write into that GPU's memory)."""
+    import subprocess
+    src = tmp_path / "t.cpp"
+    src.write_text('#include "ptr_class.h"\n#include <cstdio>\nint main(){\n'
+                   'for (int t = 0; t < 4; ++t) for (int d = 0; d < 3; ++d)\n'
+                   '  std::printf("%d %d %d\\n", t, d, isrs::ptr_class(t, d, 1));\n}\n')
+    exe = tmp_path / "t"
+    subprocess.check_call(["g++", "-std=c++17", "-I", os.path.join(ROOT, "paper_2401_18022_gb300", "csrc"),
+                           str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).split("\n"):
+        if line:
+            t, d, c = map(int, line.split())
+            got[(t, d)] = c
+    HOST, DEV, OTHER = 0, 1, 2
+    for d in range(3):
+        assert got[(0, d)] == HOST and got[(1, d)] == HOST      # unregistered / pinned host
+        assert got[(3, d)] == DEV                               # managed
+        assert got[(2, d)] == (DEV if d == 1 else OTHER)        # device memory: only the current GPU

@@ -132,6 +132,34 @@ def test_invalid_arguments_write_nothing(eng):
         eng.eta(wl, cuts=[7])
 
 
+def test_calls_on_a_capturing_stream_return_unsupported(eng):
+    """Every compute call reads the powers back and may synchronise its stream,
+    which a stream capture forbids: on a capturing stream the calls return
+    UNSUPPORTED before issuing any work, and the capture stays usable."""
+    import torch
+    from paper_2401_18022_gb300._capi import IsrsError
+    wl = W.tiny(G=8, n_edges=17)
+    P = torch.tensor(wl.P_W, dtype=torch.float64, device="cuda")
+    x = torch.zeros(4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    codes = []
+    with torch.cuda.graph(graph):
+        x.add_(1.0)
+        for call in (lambda: eng.eta(wl, P=P), lambda: eng.snr(wl, P=P), lambda: eng.grad(wl, P=P)):
+            try:
+                call()
+                codes.append(0)
+            except IsrsError as e:
+                codes.append(e.status)
+        x.add_(1.0)
+    assert codes == [6, 6, 6]
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.all(x == 2.0)
+    np.testing.assert_allclose(eng.eta(wl, P=P)["eta"].cpu().numpy(), eng.eta(wl)["eta"], rtol=1e-12)
+
+
 def test_batched_equals_single_profile_launches(eng):
     """Each profile of a batched launch equals its own single-profile launch
     bit for bit: the tile partials do not depend on which block computes them

@@ -76,3 +76,32 @@ def test_noalloc_rejects_what_does_not_fit_or_host_pointers(setup):
     rc = lib.isrs_gn_eta_noalloc(ctypes.byref(fb), ctypes.byref(ch), ctypes.c_void_p(Ph.ctypes.data),
                                  ctypes.byref(q), ctypes.c_void_p(out.data_ptr()), None, None)
     assert rc == 1
+
+
+def test_noalloc_on_a_capturing_stream_returns_unsupported(setup):
+    """The call reads the powers back and synchronises its stream, which a
+    stream capture forbids: on a capturing stream it must return UNSUPPORTED
+    before issuing any work, and the caller's capture must stay usable."""
+    import torch
+    eng, lib = setup
+    wl = W.tiny(G=8, n_edges=17)
+    P = torch.tensor(wl.P_W, dtype=torch.float64, device="cuda")
+    fb, (ch, keep), q = eng.fibre(wl), eng.channels(wl), eng.quad(wl, 0)
+    eta = torch.full((wl.n_ch,), float("nan"), dtype=torch.float64, device="cuda")
+    x = torch.zeros(4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        x.add_(1.0)
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        rc = lib.isrs_gn_eta_noalloc(ctypes.byref(fb), ctypes.byref(ch), ctypes.c_void_p(P.data_ptr()),
+                                     ctypes.byref(q), ctypes.c_void_p(eta.data_ptr()), None, st)
+        x.add_(1.0)
+    assert rc == 6
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.all(x == 2.0)
+    assert torch.all(torch.isnan(eta))
+    # the entry point still works afterwards
+    rc2, e2, _ = _noalloc(eng, lib, wl, P, 0)
+    assert rc2 == 0 and np.all(np.isfinite(e2))
