@@ -174,14 +174,24 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     from paper_2401_18022_gb300 import api
     eng = api.Engine(local)
-    wl = _workload(args.G, rank)
+    split = args.split == "cuts" and world > 1
+    if args.split == "cuts" and args.mode != "grad":
+        raise SystemExit("--split cuts times the gradient (--mode grad)")
+    # weak scaling: an independent profile per rank; strong: one system split by CUT shards
+    wl = _workload(args.G, 0 if args.split == "cuts" else rank)
     dev = torch.device("cuda", local)
     P = torch.tensor(wl.P_W, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
     use_grad = args.mode == "grad"
+    from paper_2401_18022_gb300 import dist as D
+    weights = None
+    if split:
+        weights = [4 + 4 * (wl.n_ch - 1)] * wl.n_ch      # SCI+XCI: equal pieces per CUT
 
     def step():
+        if split:
+            return D.grad_split(eng, wl, P, rank, world, weights=weights)
         if use_grad:
             return eng.grad(wl, P=P)
         return eng.snr(wl, P=P)
@@ -191,6 +201,11 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     info = eng.last_launch_info()
     launches_per_step = info["launches"]
+    if split:
+        # prep + fused forward/adjoint + finish, then SNR from eta + 3 chain kernels
+        launches_per_step = 3 + 4
+        eng.grad_shard_fwd(wl, D.shard_cuts(wl.n_ch, rank, world, weights), P)
+        info = eng.last_launch_info()
 
     clk = Clocks(local, args.clocks_csv.format(rank=local) if args.clocks_csv else None)
     clk.start()
@@ -221,7 +236,8 @@ def run_gpu(args):
     # grid points of the method's Riemann grid (every piece, as the oracle counts them)
     n_eval = info["points"]
     n_grid = _unfolded_points(wl)
-    value = world * n_grid * args.steps / t_total
+    # weak: every rank evaluates a whole system; strong (split): the ranks share one
+    value = (1 if split else world) * n_grid * args.steps / t_total
 
     # roofline of the dominant kernel.  Algorithmic SFU work per point-step by
     # the z-sum form the point took: direct 3 (sin, cos, exp), telescoped 3
@@ -253,8 +269,10 @@ def run_gpu(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "uwb-589ch-80km-G256-N113-sci_xci" + ("+grad" if use_grad else ""),
+                       "parallelism": (f"cut shards x{world} (eta all-reduce gather, dT/dP all-reduce)" if split
+                                       else f"independent profile per rank x{world}"),
                        "n_ch": wl.n_ch, "G": wl.G, "n_edges": wl.n_edges, "cells": "sci_xci",
                        "profile": "R1 closed-form ISRS, flat 1 dBm/ch",
                        "l2": "flushed (256 MB write) between timed iterations",
@@ -503,6 +521,9 @@ def main():
                     help="where to keep the nvidia-smi clock samples ({rank} is replaced); default: a temp file")
     ap.add_argument("--extras", action="store_true",
                     help="also time the Raman-ODE profile and the MCI cells on the same workload")
+    ap.add_argument("--split", default="profiles", choices=["profiles", "cuts"],
+                    help="N > 1: profiles = weak scaling, an independent system per rank; cuts = one "
+                         "system's gradient split by CUT shards (strong scaling)")
     ap.add_argument("--workload", default="uwb", choices=["uwb", "batched"],
                     help="uwb: the 589-ch system (default); batched: 512 profiles over 3 plans")
     ap.add_argument("--profile-case", default=None,

@@ -219,6 +219,36 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
                          const double *P_W, const isrs_quad *quad, double *dT_dP, double *snr,
                          double *eta, double *T_host, void *stream);
 
+/* Gradient split by CUT shards, for one gradient spread over several GPUs
+ * (one process and one handle per GPU; Sec. III: every GPU takes a group of
+ * channels under test, Fig. gpu_nodes).  Every eta_i is a sum over CUT i's own
+ * grid, so the adjoint buckets of a CUT depend only on that CUT; what couples
+ * the shards is dT/deta_i, which needs the SNR of every channel.  Two phases:
+ *
+ * isrs_gn_grad_shard_fwd: the fused forward + adjoint quadrature of
+ * isrs_gn_grad over the CUTs in `cuts` only (n_cuts entries, no repeats);
+ * writes eta[n_cuts] of those CUTs (host or device) and keeps the shard's
+ * buckets in the handle.  Closed-form profile only (UNSUPPORTED otherwise);
+ * the other requirements and errors are those of isrs_gn_grad.
+ *
+ * The caller gathers eta of every channel from all shards (eta_all[n_ch]).
+ *
+ * isrs_gn_grad_shard_bwd: from eta_all, the SNR of every channel, T and
+ * dT/deta; then this shard's part of dT/dP_j (through its CUTs' PSD
+ * products and ISRS profile terms).  with_direct = 1 also adds the terms that
+ * do not pass through any eta (the ASE gain of every channel and the SNR
+ * numerator): exactly one shard sets it.  The sum of dT_dP[n_ch] over the
+ * shards is isrs_gn_grad's dT_dP.  snr[n_ch] (nullable) and T_host (nullable)
+ * are those of the whole system.  No other compute call may use the handle
+ * between the two phases (INVALID_ARG otherwise).
+ * Errors: INVALID_ARG (no preceding shard forward, eta_all not finite >= 0,
+ * NULL output), CUDA. */
+isrs_status isrs_gn_grad_shard_fwd(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch,
+                                   const double *P_W, const isrs_quad *quad, const int *cuts, int n_cuts,
+                                   double *eta, void *stream);
+isrs_status isrs_gn_grad_shard_bwd(isrs_handle h, const double *eta_all, int with_direct, double *dT_dP,
+                                   double *snr, double *T_host, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched                                                                   */
 /* ------------------------------------------------------------------------ */

@@ -72,6 +72,8 @@ def load(build_if_missing: bool = True):
                                 vp, vp, vp, vp]
     lib.isrs_gn_snr.argtypes = [vp, P(Fibre), P(Channels), vp, P(Quad), vp, vp, c_double_p, vp]
     lib.isrs_gn_grad.argtypes = [vp, P(Fibre), P(Channels), vp, P(Quad), vp, vp, vp, c_double_p, vp]
+    lib.isrs_gn_grad_shard_fwd.argtypes = [vp, P(Fibre), P(Channels), vp, P(Quad), c_int_p, ctypes.c_int, vp, vp]
+    lib.isrs_gn_grad_shard_bwd.argtypes = [vp, vp, ctypes.c_int, vp, vp, c_double_p, vp]
     lib.isrs_gn_eta_batched.argtypes = [vp, P(Fibre), ctypes.c_int, P(Channels), ctypes.c_int, c_int_p,
                                         vp, P(Quad), vp, vp]
     lib.isrs_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
@@ -82,7 +84,7 @@ def load(build_if_missing: bool = True):
     lib.isrs_last_path_counts.restype = ctypes.c_int
     lib.isrs_last_kernel_ms.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     for name in ("isrs_last_kernel_ms", "isrs_create", "isrs_destroy", "isrs_beta_from_dispersion", "isrs_gn_eta", "isrs_gn_snr",
-                 "isrs_gn_grad", "isrs_gn_eta_batched", "isrs_set_tile", "isrs_last_launch_info"):
+                 "isrs_gn_grad", "isrs_gn_grad_shard_fwd", "isrs_gn_grad_shard_bwd", "isrs_gn_eta_batched", "isrs_set_tile", "isrs_last_launch_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -177,6 +177,29 @@ class Engine:
                                     _ptr(g), _ptr(snr), _ptr(eta), ctypes.byref(T), _stream_of(P)), self.h)
         return {"dT_dP": g, "snr": snr, "eta": eta, "T": T.value}
 
+    def grad_shard_fwd(self, wl, cuts: Sequence[int], P=None):
+        """isrs_gn_grad_shard_fwd: fused forward + adjoint over the CUTs of one
+        shard; returns eta of those CUTs (the buckets stay in the handle)."""
+        P = _as_f64(wl.P_W if P is None else P)
+        fb, (ch, keep), q = self.fibre(wl), self.channels(wl), self.quad(wl, PREC_FP32)
+        cuts_arr = np.ascontiguousarray(np.asarray(cuts, dtype=np.int32))
+        eta = _empty_like(P, len(cuts_arr))
+        check(self.lib.isrs_gn_grad_shard_fwd(self.h, ctypes.byref(fb), ctypes.byref(ch), _ptr(P), ctypes.byref(q),
+                                              cuts_arr.ctypes.data_as(_capi.c_int_p), len(cuts_arr), _ptr(eta),
+                                              _stream_of(P)), self.h)
+        return eta
+
+    def grad_shard_bwd(self, eta_all, with_direct: bool):
+        """isrs_gn_grad_shard_bwd: this shard's part of dT/dP from the gathered
+        eta of every channel, with the SNR of every channel and T."""
+        eta_all = _as_f64(eta_all)
+        n = int(eta_all.shape[0])
+        g, snr = _empty_like(eta_all, n), _empty_like(eta_all, n)
+        T = ctypes.c_double()
+        check(self.lib.isrs_gn_grad_shard_bwd(self.h, _ptr(eta_all), 1 if with_direct else 0, _ptr(g), _ptr(snr),
+                                              ctypes.byref(T), _stream_of(eta_all)), self.h)
+        return {"dT_dP": g, "snr": snr, "T": T.value}
+
     def eta_batched(self, bw, P_cat=None, precision: int = PREC_FP32):
         """isrs_gn_eta_batched over a BatchedWorkload; P_cat concatenates the profiles."""
         if P_cat is None:

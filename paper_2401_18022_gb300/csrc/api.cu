@@ -79,6 +79,13 @@ struct isrs_handle_s {
     bool last_graph = false;             // the last batched call replayed a graph
     cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [quad, adjoint][start, end]
     bool ev_valid[2] = {false, false};
+    // split gradient: the shard whose buckets the last isrs_gn_grad_shard_fwd left
+    DevBuf eta_all;                      // [4 n]: gathered eta, then SNR, P_NLI, P_ASE per channel
+    bool shard_valid = false;
+    uint64_t shard_key = 0;
+    isrs_fibre shard_fibre;
+    isrs_quad shard_quad;
+    int shard_n = 0;
 };
 
 namespace {
@@ -1121,6 +1128,7 @@ ChainParams chain_params(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q
     cp.f_ref = fb->f_ref_THz;
     cp.snr_trx_lin_inv = q->snr_trx_dB > 0.0 ? std::pow(10.0, -q->snr_trx_dB / 10.0) : 0.0;
     cp.n_spans = fb->n_spans > 1 ? fb->n_spans : 1;
+    cp.with_direct = 1;
     cp.ybar = (double *)h->ybar.p;
     cp.aase = (double *)h->ybar.p + n;
     cp.dT_dP = (double *)h->dTdP.p;
@@ -1175,6 +1183,57 @@ isrs_status run_grad_tab(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q
     rap.dT_dP = (double *)h->dTdP.p;
     CK(launch_raman_adj(rap, st));
     h->last_launches += 4;   // ybar, adjoint quadrature, slope fold, ODE adjoint
+    return ISRS_OK;
+}
+
+// Argument checks shared by the gradient entry points; selects the device and
+// rejects a capturing stream.  All powers must be > 0 and no channel a guard.
+isrs_status grad_checks(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
+                        const isrs_quad *quad, cudaStream_t st)
+{
+    isrs_status s;
+    if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
+    if ((s = check_plan(h, ch)) != ISRS_OK) return s;
+    if ((s = check_quad(h, quad)) != ISRS_OK) return s;
+    if (!P_W) return fail(h, ISRS_ERR_INVALID_ARG, "P_W is NULL");
+    if (quad->precision != ISRS_PREC_FP32)
+        return fail(h, ISRS_ERR_INVALID_ARG, "the gradient is the adjoint of the FP32 path");
+    if (quad->n_edges - 1 > 128) return fail(h, ISRS_ERR_UNSUPPORTED, "gradient supports at most 128 z-steps");
+    if (quad->G_mci > 0 && fibre->profile == ISRS_PROFILE_RAMAN_ODE)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "the Raman-ODE gradient does not cover the separate MCI grid");
+    if (fibre->profile == ISRS_PROFILE_RAMAN_ODE && ch->n_ch > kMaxRamanGradCh)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "Raman-ODE gradient supports at most %d channels", kMaxRamanGradCh);
+    if (ch->guard)
+        for (int k = 0; k < ch->n_ch; ++k)
+            if (ch->guard[k]) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs every channel lit (guard %d)", k);
+    if ((s = set_device(h)) != ISRS_OK) return s;
+    if ((s = reject_capture(h, st)) != ISRS_OK) return s;
+    if ((s = check_ptr(h, P_W, "P_W")) != ISRS_OK) return s;
+    std::vector<double> hp(ch->n_ch);
+    if (is_device_ptr(P_W)) {
+        CK(cudaMemcpyAsync(hp.data(), P_W, sizeof(double) * ch->n_ch, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::memcpy(hp.data(), P_W, sizeof(double) * ch->n_ch);
+    }
+    if ((s = check_powers(h, hp.data(), ch->n_ch)) != ISRS_OK) return s;
+    for (int k = 0; k < ch->n_ch; ++k)
+        if (!(hp[k] > 0.0)) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs P[%d] > 0", k);
+    return ISRS_OK;
+}
+
+// Chain-rule constants over the buckets of the last fused forward + adjoint.
+isrs_status chain_buffers(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, int n,
+                          ChainParams &cp)
+{
+    isrs_status s;
+    if ((s = ensure(h, h->ybar, sizeof(double) * 2 * n)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->gK, sizeof(double2) * g->n_steps)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->dTdP, sizeof(double) * n)) != ISRS_OK) return s;
+    cp = chain_params(h, fb, q, g, n);
+    cp.item_R = (const double2 *)h->gA.p;
+    cp.V = (const double *)h->gPd.p;
+    cp.Rb = (double2 *)h->gK.p;
     return ISRS_OK;
 }
 
@@ -1246,7 +1305,7 @@ isrs_status isrs_destroy(isrs_handle h)
     DevBuf *bufs[] = {&h->P, &h->pd_d, &h->pd_f, &h->step_d, &h->step_f, &h->lnrho_L, &h->ptot, &h->partial,
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
                       &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP, &h->ab, &h->ode_y, &h->gAB, &h->gV,
-                      &h->gAt, &h->partial_mci};
+                      &h->gAt, &h->partial_mci, &h->eta_all};
     for (DevBuf *b : bufs) release(*b);
     release(h->paths);
     release(h->kapL);
@@ -1331,6 +1390,7 @@ isrs_status isrs_gn_eta(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
 {
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
+    h->shard_valid = false;    // the workspace is about to be overwritten
     isrs_status s;
     if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
     if ((s = check_plan(h, ch)) != ISRS_OK) return s;
@@ -1376,6 +1436,7 @@ isrs_status isrs_gn_snr(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
 {
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
+    h->shard_valid = false;    // the workspace is about to be overwritten
     isrs_status s;
     if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
     if ((s = check_plan(h, ch)) != ISRS_OK) return s;
@@ -1414,6 +1475,7 @@ isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_pl
 {
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
+    h->shard_valid = false;    // the workspace is about to be overwritten
     isrs_status s;
     if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
     if ((s = check_quad(h, quad)) != ISRS_OK) return s;
@@ -1457,60 +1519,151 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
     isrs_status s;
-    if ((s = check_fibre(h, fibre)) != ISRS_OK) return s;
-    if ((s = check_plan(h, ch)) != ISRS_OK) return s;
-    if ((s = check_quad(h, quad)) != ISRS_OK) return s;
-    if (!P_W || !dT_dP) return fail(h, ISRS_ERR_INVALID_ARG, "P_W or dT_dP is NULL");
-    if (quad->precision != ISRS_PREC_FP32)
-        return fail(h, ISRS_ERR_INVALID_ARG, "the gradient is the adjoint of the FP32 path");
-    if (quad->n_edges - 1 > 128) return fail(h, ISRS_ERR_UNSUPPORTED, "gradient supports at most 128 z-steps");
-    if (quad->G_mci > 0 && fibre->profile == ISRS_PROFILE_RAMAN_ODE)
-        return fail(h, ISRS_ERR_UNSUPPORTED, "the Raman-ODE gradient does not cover the separate MCI grid");
-    if (fibre->profile == ISRS_PROFILE_RAMAN_ODE && ch->n_ch > kMaxRamanGradCh)
-        return fail(h, ISRS_ERR_UNSUPPORTED, "Raman-ODE gradient supports at most %d channels", kMaxRamanGradCh);
-    if (ch->guard)
-        for (int k = 0; k < ch->n_ch; ++k)
-            if (ch->guard[k]) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs every channel lit (guard %d)", k);
-    if ((s = set_device(h)) != ISRS_OK) return s;
+    if (!dT_dP) return fail(h, ISRS_ERR_INVALID_ARG, "dT_dP is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    if ((s = reject_capture(h, st)) != ISRS_OK) return s;
-    if ((s = check_ptr(h, P_W, "P_W")) != ISRS_OK || (s = check_ptr(h, dT_dP, "dT_dP")) != ISRS_OK ||
-        (s = check_ptr(h, snr, "snr")) != ISRS_OK || (s = check_ptr(h, eta, "eta")) != ISRS_OK)
+    if ((s = grad_checks(h, fibre, ch, P_W, quad, st)) != ISRS_OK) return s;
+    if ((s = check_ptr(h, dT_dP, "dT_dP")) != ISRS_OK || (s = check_ptr(h, snr, "snr")) != ISRS_OK ||
+        (s = check_ptr(h, eta, "eta")) != ISRS_OK)
         return s;
-    {
-        std::vector<double> hp(ch->n_ch);
-        if (is_device_ptr(P_W)) {
-            CK(cudaMemcpyAsync(hp.data(), P_W, sizeof(double) * ch->n_ch, cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-        } else {
-            std::memcpy(hp.data(), P_W, sizeof(double) * ch->n_ch);
-        }
-        if ((s = check_powers(h, hp.data(), ch->n_ch)) != ISRS_OK) return s;
-        for (int k = 0; k < ch->n_ch; ++k)
-            if (!(hp[k] > 0.0)) return fail(h, ISRS_ERR_INVALID_ARG, "gradient needs P[%d] > 0", k);
-    }
     Geom *g = nullptr;
     std::vector<std::vector<int>> cpp{std::vector<int>()};
     std::vector<int> pp{0};
     if ((s = get_geom(h, fibre, 1, ch, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
     if ((s = load_powers(h, P_W, ch->n_ch, st)) != ISRS_OK) return s;
-    const int n = ch->n_ch, M = g->n_steps;
+    h->shard_valid = false;
+    const int n = ch->n_ch;
     if (fibre->profile == ISRS_PROFILE_RAMAN_ODE) {
         if ((s = run_grad_tab(h, fibre, quad, g, st)) != ISRS_OK) return s;
         return grad_outputs(h, n, dT_dP, snr, eta, T_host, st);
     }
     if ((s = run_forward(h, fibre, g, ISRS_PREC_FP32, st, true)) != ISRS_OK) return s;
     if ((s = run_finish(h, fibre, quad, g, true, st)) != ISRS_OK) return s;
-    if ((s = ensure(h, h->ybar, sizeof(double) * 2 * n)) != ISRS_OK) return s;
-    if ((s = ensure(h, h->gK, sizeof(double2) * M)) != ISRS_OK) return s;
-    if ((s = ensure(h, h->dTdP, sizeof(double) * n)) != ISRS_OK) return s;
-    ChainParams cp = chain_params(h, fibre, quad, g, n);
-    cp.item_R = (const double2 *)h->gA.p;
-    cp.V = (const double *)h->gPd.p;
-    cp.Rb = (double2 *)h->gK.p;
+    ChainParams cp;
+    if ((s = chain_buffers(h, fibre, quad, g, n, cp)) != ISRS_OK) return s;
     CK(launch_chain(cp, st));
     h->last_launches += 3;
     return grad_outputs(h, n, dT_dP, snr, eta, T_host, st);
+}
+
+isrs_status isrs_gn_grad_shard_fwd(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch,
+                                   const double *P_W, const isrs_quad *quad, const int *cuts, int n_cuts,
+                                   double *eta, void *stream)
+{
+    if (!h) return ISRS_ERR_INVALID_ARG;
+    h->err.clear();
+    h->shard_valid = false;
+    isrs_status s;
+    if (!eta || !cuts || n_cuts < 1) return fail(h, ISRS_ERR_INVALID_ARG, "eta, cuts or n_cuts missing");
+    if (fibre && fibre->profile == ISRS_PROFILE_RAMAN_ODE)
+        return fail(h, ISRS_ERR_UNSUPPORTED, "the split gradient covers the closed-form profile");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = grad_checks(h, fibre, ch, P_W, quad, st)) != ISRS_OK) return s;
+    if ((s = check_ptr(h, eta, "eta")) != ISRS_OK) return s;
+    std::vector<int> cl;
+    {
+        std::vector<char> seen(ch->n_ch, 0);
+        for (int k = 0; k < n_cuts; ++k) {
+            if (cuts[k] < 0 || cuts[k] >= ch->n_ch) return fail(h, ISRS_ERR_INVALID_ARG, "cut %d out of range", cuts[k]);
+            if (seen[cuts[k]]) return fail(h, ISRS_ERR_INVALID_ARG, "cut %d repeated", cuts[k]);
+            seen[cuts[k]] = 1;
+            cl.push_back(cuts[k]);
+        }
+    }
+    Geom *g = nullptr;
+    std::vector<std::vector<int>> cpp{cl};
+    std::vector<int> pp{0};
+    if ((s = get_geom(h, fibre, 1, ch, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
+    if ((s = load_powers(h, P_W, ch->n_ch, st)) != ISRS_OK) return s;
+    if ((s = run_forward(h, fibre, g, ISRS_PREC_FP32, st, true)) != ISRS_OK) return s;
+    if ((s = run_finish(h, fibre, quad, g, false, st)) != ISRS_OK) return s;
+    bool host_out = false;
+    if ((s = copy_out(h, eta, h->o_eta, g->n_slots, st, host_out)) != ISRS_OK) return s;
+    if (host_out) CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    h->shard_key = g->key;
+    h->shard_fibre = *fibre;
+    h->shard_quad = *quad;
+    h->shard_n = ch->n_ch;
+    h->shard_valid = true;
+    return ISRS_OK;
+}
+
+isrs_status isrs_gn_grad_shard_bwd(isrs_handle h, const double *eta_all, int with_direct, double *dT_dP,
+                                   double *snr, double *T_host, void *stream)
+{
+    if (!h) return ISRS_ERR_INVALID_ARG;
+    h->err.clear();
+    isrs_status s;
+    if (!h->shard_valid)
+        return fail(h, ISRS_ERR_INVALID_ARG, "no shard forward to continue (isrs_gn_grad_shard_fwd first)");
+    if (!eta_all || !dT_dP) return fail(h, ISRS_ERR_INVALID_ARG, "eta_all or dT_dP is NULL");
+    Geom *g = nullptr;
+    for (auto &c : h->cache)
+        if (c->key == h->shard_key) g = c.get();
+    if (!g) return fail(h, ISRS_ERR_INVALID_ARG, "the shard's tables were evicted by later calls");
+    if ((s = set_device(h)) != ISRS_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = reject_capture(h, st)) != ISRS_OK) return s;
+    if ((s = check_ptr(h, eta_all, "eta_all")) != ISRS_OK || (s = check_ptr(h, dT_dP, "dT_dP")) != ISRS_OK ||
+        (s = check_ptr(h, snr, "snr")) != ISRS_OK)
+        return s;
+    const int n = h->shard_n;
+    {
+        std::vector<double> he(n);
+        if (is_device_ptr(eta_all)) {
+            CK(cudaMemcpyAsync(he.data(), eta_all, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        } else {
+            std::memcpy(he.data(), eta_all, sizeof(double) * n);
+        }
+        for (int k = 0; k < n; ++k)
+            if (!(std::isfinite(he[k]) && he[k] >= 0.0))
+                return fail(h, ISRS_ERR_INVALID_ARG, "eta_all[%d] = %g is not a finite eta >= 0", k, he[k]);
+    }
+    if ((s = ensure(h, h->eta_all, sizeof(double) * 4 * n)) != ISRS_OK) return s;
+    double *e_all = (double *)h->eta_all.p;
+    CK(cudaMemcpyAsync(e_all, eta_all, sizeof(double) * n,
+                       is_device_ptr(eta_all) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if ((s = ensure(h, h->o_T, sizeof(double))) != ISRS_OK) return s;
+    SnrFromEtaParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.eta = e_all;
+    sp.P = (const double *)h->P.p;
+    sp.ch_B = (const double *)g->ch_B.p;
+    sp.ch_frel = (const double *)g->ch_frel.p;
+    sp.ch_nf = g->has_nf ? (const double *)g->ch_nf.p : nullptr;
+    sp.lnrho_L = (const double *)h->lnrho_L.p;
+    sp.f_ref = h->shard_fibre.f_ref_THz;
+    sp.snr_trx_lin_inv = h->shard_quad.snr_trx_dB > 0.0 ? std::pow(10.0, -h->shard_quad.snr_trx_dB / 10.0) : 0.0;
+    sp.n_spans = h->shard_fibre.n_spans > 1 ? h->shard_fibre.n_spans : 1;
+    sp.n = n;
+    sp.snr = e_all + n;
+    sp.pnli = e_all + 2 * n;
+    sp.pase = e_all + 3 * n;
+    sp.T = (double *)h->o_T.p;
+    CK(launch_snr_from_eta(sp, st));
+    ChainParams cp;
+    if ((s = chain_buffers(h, &h->shard_fibre, &h->shard_quad, g, n, cp)) != ISRS_OK) return s;
+    cp.snr = sp.snr;
+    cp.pnli = sp.pnli;
+    cp.pase = sp.pase;
+    cp.with_direct = with_direct ? 1 : 0;
+    CK(launch_chain(cp, st));
+    h->last_launches = 4;
+    bool host_out = false;
+    if ((s = copy_out(h, dT_dP, h->dTdP, n, st, host_out)) != ISRS_OK) return s;
+    if (snr) {
+        const bool dev = is_device_ptr(snr);
+        if (!dev) host_out = true;
+        CK(cudaMemcpyAsync(snr, sp.snr, sizeof(double) * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    if (T_host) {
+        CK(cudaMemcpyAsync(T_host, h->o_T.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (host_out) CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return ISRS_OK;
 }
 
 }  // extern "C"
@@ -1520,8 +1673,9 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
 //
 // For callers that cannot allocate device memory themselves: code running
 // inside a host framework that owns the device allocator, or a real-time loop
-// in which a cudaMalloc would block or break the memory budget.  All scratch lives in one file-scope device array of fixed
-// size that every GPU loading this library holds until the process exits.
+// in which a cudaMalloc would block or break the memory budget.  All scratch
+// lives in one file-scope device array of fixed size that every GPU loading
+// this library holds until the process exits.
 // ============================================================================
 #include <mutex>
 

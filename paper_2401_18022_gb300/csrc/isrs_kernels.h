@@ -53,22 +53,36 @@ struct AdjParams {
     int n_ch;
 };
 
-// Chain rule from the buckets to dT/dP_j (FP64, single profile).
+// Chain rule from the buckets to dT/dP_j (FP64, single profile).  The
+// buckets may cover a shard of the CUTs (n_slots output slots, slot_cut maps
+// a slot to its channel); SNR, P_NLI, P_ASE, ybar and aase are per channel.
 struct ChainParams {
     const double *P, *ch_frel, *ch_B, *ch_gamma, *ch_nf;
     const double2 *zs_d;        // {z_m, dz_m}
     const double2 *step_d;      // {lnPtot - lnN_m, kappa_m}
-    const double *snr, *pnli, *pase, *lnrho_L;
+    const double *snr, *pnli, *pase, *lnrho_L;   // [n_ch]
     const double2 *item_R;
     const double *V;
     const int *item_slot, *slot_cut;
     int n_items, n_slots, n_ch, n_steps;
+    int with_direct;            // add the terms outside the buckets (ASE gain, SNR numerator)
     double L, Cr, alpha_R, f_ref, snr_trx_lin_inv, n_spans;
-    double *ybar;               // [n_slots] dT/dSigma_i
-    double *aase;               // [n_slots] dT/dASE_i * dASE_i/d ln G_i
-    double2 *Rb;                // [n_steps] sum_i ybar_i {R_im, R'_im}
+    double *ybar;               // [n_ch] dT/dSigma_i
+    double *aase;               // [n_ch] dT/dASE_i * dASE_i/d ln G_i
+    double2 *Rb;                // [n_steps] sum over the shard's tiles of ybar_i {R_im, R'_im}
     double *dT_dP;              // [n_ch]
 };
+
+// SNR, P_NLI, P_ASE and throughput of every channel from a given eta (the
+// second phase of a gradient split by CUT shards).
+struct SnrFromEtaParams {
+    const double *eta, *P, *ch_B, *ch_frel, *ch_nf, *lnrho_L;
+    const unsigned char *guard;
+    double f_ref, snr_trx_lin_inv, n_spans;
+    int n;
+    double *snr, *pnli, *pase, *T;
+};
+cudaError_t launch_snr_from_eta(const SnrFromEtaParams &sp, cudaStream_t st);
 
 // Raman-ODE profile (one block per profile): RK4 on y = ln P through the
 // edge -> midpoint -> edge nodes of every z-step, then the tables {a, b}.

@@ -529,26 +529,25 @@ constexpr double kHPlanck = 6.62607015e-34;
 
 __global__ void __launch_bounds__(256) k_ybar(ChainParams cp)
 {
-    for (int s = threadIdx.x + blockIdx.x * blockDim.x; s < cp.n_slots; s += blockDim.x * gridDim.x) {
-        const int i = cp.slot_cut[s];
-        const double P = cp.P[i], B = cp.ch_B[i], g = cp.ch_gamma[i], snr = cp.snr[s];
+    for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < cp.n_ch; i += blockDim.x * gridDim.x) {
+        const double P = cp.P[i], B = cp.ch_B[i], g = cp.ch_gamma[i], snr = cp.snr[i];
         const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
         const double dsdN = -snr * snr / P;
         const double nf = cp.ch_nf ? pow(10.0, cp.ch_nf[i] / 10.0) : 1.0;
         const double hfb = cp.n_spans * nf * kHPlanck * ((cp.ch_frel[i] + cp.f_ref) * 1e12) * (B * 1e12);
-        cp.ybar[s] = dTds * dsdN * (16.0 / 27.0) * g * g * B;
-        cp.aase[s] = dTds * dsdN * (cp.pase[s] + hfb);    // dT/dASE * dASE/d ln G
+        cp.ybar[i] = dTds * dsdN * (16.0 / 27.0) * g * g * B;
+        cp.aase[i] = dTds * dsdN * (cp.pase[i] + hfb);    // dT/dASE * dASE/d ln G
     }
 }
 
-// Rb[m] = sum over tiles of ybar(slot of tile) * {R_m, R'_m}; one block per m.
+// Rb[m] = sum over tiles of ybar(channel of tile) * {R_m, R'_m}; one block per m.
 __global__ void __launch_bounds__(256) k_adj_reduce(ChainParams cp)
 {
     __shared__ double scratch[32];
     const int m = blockIdx.x;
     double rx = 0.0, ry = 0.0;
     for (int it = threadIdx.x; it < cp.n_items; it += blockDim.x) {
-        const double y = cp.ybar[cp.item_slot[it]];
+        const double y = cp.ybar[cp.slot_cut[cp.item_slot[it]]];
         const double2 v = cp.item_R[(size_t)it * cp.n_steps + m];
         rx += y * v.x;
         ry += y * v.y;
@@ -610,9 +609,9 @@ __global__ void __launch_bounds__(256) k_chain(ChainParams cp)
     // j-independent sums
     double a1 = 0.0, a2 = 0.0, a3 = 0.0;
     for (int m = threadIdx.x; m < M; m += blockDim.x) a1 += cp.Rb[m].y * s_Le[m];
-    for (int s = threadIdx.x; s < cp.n_slots; s += blockDim.x) {
-        a2 += cp.aase[s];
-        a3 += cp.aase[s] * (cp.ch_frel[cp.slot_cut[s]] - s_Fb[M]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a2 += cp.aase[i];
+        a3 += cp.aase[i] * (cp.ch_frel[i] - s_Fb[M]);
     }
     a1 = block_sum_d(a1, scratch);
     a2 = block_sum_d(a2, scratch);
@@ -632,15 +631,17 @@ __global__ void __launch_bounds__(256) k_chain(ChainParams cp)
             g += cp.Rb[m].x * (invPt - hN + cp.Cr * s_Le[m] * s_Fb[m]);
         }
         double v = 0.0;
-        for (int s = 0; s < cp.n_slots; ++s) v += cp.ybar[s] * cp.V[(size_t)s * n + j];
+        for (int s = 0; s < cp.n_slots; ++s) v += cp.ybar[cp.slot_cut[s]] * cp.V[(size_t)s * n + j];
         g += v / cp.P[j];
-        const double hNL = exp(-s_kap[M] * fj + log(sinhc_ad(s_kap[M] * hB)) - s_lnN[M]);
-        g += -s_const[1] * (invPt - hNL) + s_const[2];
-        // SNR numerator (slot j: the gradient call evaluates every channel)
-        const double snr = cp.snr[j], P = cp.P[j], B = cp.ch_B[j];
-        const double N = cp.pnli[j] + cp.pase[j];
-        const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
-        g += dTds * snr * snr * N / (P * P);
+        if (cp.with_direct) {
+            // through the ASE gain of every channel, and the SNR numerator
+            const double hNL = exp(-s_kap[M] * fj + log(sinhc_ad(s_kap[M] * hB)) - s_lnN[M]);
+            g += -s_const[1] * (invPt - hNL) + s_const[2];
+            const double snr = cp.snr[j], P = cp.P[j], B = cp.ch_B[j];
+            const double N = cp.pnli[j] + cp.pase[j];
+            const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
+            g += dTds * snr * snr * N / (P * P);
+        }
         cp.dT_dP[j] = g;
     }
 }

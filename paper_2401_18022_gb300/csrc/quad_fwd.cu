@@ -398,6 +398,43 @@ __global__ void __launch_bounds__(256) k_finish(FinishParams fp)
 }
 
 // ---------------------------------------------------------------------------
+// k_snr_from_eta: the Eq. loss part of k_finish for every channel, from a
+// given eta (gathered from the shards of a split gradient): P_NLI = eta P^3,
+// P_ASE, SNR and T.  One block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_snr_from_eta(SnrFromEtaParams sp)
+{
+    __shared__ double scratch[32];
+    double tpart = 0.0;
+    for (int i = threadIdx.x; i < sp.n; i += blockDim.x) {
+        const double B = sp.ch_B[i], P = sp.P[i];
+        const double pnli = sp.eta[i] * P * P * P;
+        const double nf = sp.ch_nf ? pow(10.0, sp.ch_nf[i] / 10.0) : 1.0;
+        const double f_abs = sp.ch_frel[i] + sp.f_ref;
+        const double gain = exp(-sp.lnrho_L[i]);
+        const double pase = sp.n_spans * nf * 6.62607015e-34 * (f_abs * 1e12) * (gain - 1.0) * (B * 1e12);
+        const bool off = !(P > 0.0) || (sp.guard && sp.guard[i]);
+        double snr = 0.0;
+        if (!off) {
+            snr = P / (pnli + pase);
+            if (sp.snr_trx_lin_inv > 0.0) snr = 1.0 / (1.0 / snr + sp.snr_trx_lin_inv);
+            tpart += 2.0 * B * log2(1.0 + snr);
+        }
+        sp.snr[i] = snr;
+        sp.pnli[i] = pnli;
+        sp.pase[i] = pase;
+    }
+    const double T = block_sum_d(tpart, scratch);
+    if (threadIdx.x == 0 && sp.T) sp.T[0] = T;
+}
+
+cudaError_t launch_snr_from_eta(const SnrFromEtaParams &sp, cudaStream_t st)
+{
+    k_snr_from_eta<<<1, 256, 0, st>>>(sp);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 size_t quad_smem_bytes(int precision, int n_steps, int G)

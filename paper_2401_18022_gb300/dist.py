@@ -1,13 +1,15 @@
 """Host-side multi-GPU logic (one process per GPU).
 
-Every CUT's eta is independent, and so is every launch-power profile, so the
-path shards without a data-path collective:
-  * weak scaling (the benchmark): each rank evaluates its own full system for
-    an independent seeded launch-power profile (``rank_powers``);
-  * strong scaling: the CUTs of one system are split across ranks
-    (``shard_cuts``) and the per-CUT results gathered once at the end
-    (``gather_by_cut``), which is the only exchange the method has.
-The timing reduction (max over ranks) is the only collective on the bench path.
+Every CUT's eta is independent, and so is every launch-power profile:
+  * weak scaling (the benchmark's default): each rank evaluates its own full
+    system for an independent seeded launch-power profile (``rank_powers``),
+    with no data-path collective;
+  * strong scaling (Sec. III: a group of channels under test per GPU): the
+    CUTs of one system are split across ranks (``shard_cuts``).  The forward
+    needs one exchange, the gather of eta (``gather_by_cut``); the gradient
+    (``grad_split``) adds one all-reduce of the per-channel dT/dP parts,
+    because the chain rule of a CUT reaches every launch power.
+The timing reduction (max over ranks) is the only other collective.
 """
 from __future__ import annotations
 
@@ -37,17 +39,57 @@ def shard_cuts(n_ch: int, rank: int, world: int, weights: Sequence[float] = None
     return list(range(bounds[rank], bounds[rank + 1]))
 
 
-def gather_by_cut(values: np.ndarray, cuts: Sequence[int], n_ch: int, group=None) -> np.ndarray:
-    """All-gather per-CUT values from every rank into one array of n_ch."""
+def gather_by_cut(values, cuts: Sequence[int], n_ch: int, group=None):
+    """All-gather per-CUT values from every rank into one array of n_ch.
+
+    Each rank writes its CUTs into a zero vector and one all-reduce (sum)
+    assembles them; with disjoint shards every entry has exactly one
+    contribution, so the sum is exact.  ``values`` may be a numpy array or a
+    torch tensor (CUDA tensors stay on the device for NCCL); the result has
+    the same kind."""
+    import torch
     import torch.distributed as dist
-    payload = (list(map(int, cuts)), np.asarray(values, dtype=np.float64).tolist())
-    world = dist.get_world_size(group)
-    parts = [None] * world
-    dist.all_gather_object(parts, payload, group=group)
-    out = np.full(n_ch, np.nan)
-    for c, v in parts:
-        out[np.asarray(c, dtype=int)] = v
-    return out
+    is_t = isinstance(values, torch.Tensor)
+    dev = values.device if is_t else torch.device("cpu")
+    if dist.get_backend(group) == "nccl" and dev.type != "cuda":
+        dev = torch.device("cuda", torch.cuda.current_device())
+    full = torch.zeros(n_ch, dtype=torch.float64, device=dev)
+    idx = torch.as_tensor(list(map(int, cuts)), dtype=torch.long, device=dev)
+    v = values.to(device=dev, dtype=torch.float64) if is_t else torch.as_tensor(np.asarray(values, dtype=np.float64), device=dev)
+    full[idx] = v[:len(idx)]
+    dist.all_reduce(full, op=dist.ReduceOp.SUM, group=group)
+    return full if is_t else full.cpu().numpy()
+
+
+def grad_split(eng, wl, P, rank: int, world: int, group=None, weights: Sequence[float] = None):
+    """One throughput gradient split over `world` ranks by CUT shards.
+
+    ``eng`` provides the two phases of isrs_gn_grad_shard_fwd/_bwd
+    (``grad_shard_fwd(wl, cuts, P) -> eta of the shard's CUTs`` and
+    ``grad_shard_bwd(eta_all, with_direct) -> {"dT_dP", "snr", "T"}``).
+    Steps: this rank's CUT shard (balanced by ``weights``); the fused forward +
+    adjoint over it; the gather of eta; this shard's part of dT/dP, rank 0
+    adding the terms outside every eta; one all-reduce (sum) of the parts.
+    With world == 1 no collective is issued.  Returns the full dT/dP, the
+    SNR of every channel, T, eta of every channel and this rank's CUTs."""
+    cuts = shard_cuts(wl.n_ch, rank, world, weights)
+    eta_s = eng.grad_shard_fwd(wl, cuts, P)
+    if world > 1:
+        eta_all = gather_by_cut(eta_s, cuts, wl.n_ch, group)
+    else:
+        eta_all = eta_s
+    out = eng.grad_shard_bwd(eta_all, with_direct=(rank == 0))
+    g = out["dT_dP"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        is_t = isinstance(g, torch.Tensor)
+        gt = g if is_t else torch.as_tensor(np.asarray(g, dtype=np.float64))
+        if dist.get_backend(group) == "nccl" and gt.device.type != "cuda":
+            gt = gt.cuda()
+        dist.all_reduce(gt, op=dist.ReduceOp.SUM, group=group)
+        g = gt if is_t else gt.cpu().numpy()
+    return {"dT_dP": g, "snr": out["snr"], "T": out["T"], "eta": eta_all, "cuts": cuts}
 
 
 def max_over_ranks(t: float, group=None) -> float:
