@@ -466,6 +466,50 @@ def run_batched(args) -> int:
     return 0
 
 
+def run_accuracy(args) -> int:
+    """The accuracy gate at the benchmark's size: every CUT of the 589-ch
+    workload (G = 256), the FP32 path against the plain FP64 GPU path, as the
+    per-CUT error in dB of eta and of SNR (the method's target: 0.01 dB of
+    SNR per channel).  The FP64 path runs in chunks of CUTs (~1 min each);
+    SNR_64 = P / (eta_64 P^3 + P_ASE) with the ASE of the same plan (no
+    transceiver noise in this workload).  Prints one JSON line; with --out,
+    writes the per-CUT errors there as JSON."""
+    import torch
+    from paper_2401_18022_gb300 import api, workloads as W
+    torch.cuda.set_device(0)
+    eng = api.Engine(0)
+    wl = _workload(args.G)
+    P = torch.tensor(wl.P_W, dtype=torch.float64, device="cuda")
+    r32 = eng.snr(wl, P=P, precision=0)
+    e32, s32 = r32["eta"].cpu().numpy(), r32["snr"].cpu().numpy()
+    Ph = wl.P_W
+    pase = Ph / s32 - e32 * Ph ** 3
+    e64 = np.empty(wl.n_ch)
+    t0 = time.perf_counter()
+    for chunk in np.array_split(np.arange(wl.n_ch), args.chunks):
+        e64[chunk] = eng.eta(wl, P=P, cuts=[int(c) for c in chunk], precision=1)["eta"].cpu().numpy()
+    t64 = time.perf_counter() - t0
+    s64 = Ph / (e64 * Ph ** 3 + pase)
+    de = np.abs(10 * np.log10(e32 / e64))
+    ds = np.abs(10 * np.log10(s32 / s64))
+    lam = W.nm_from_thz(wl.f_THz)
+    band = np.clip(np.searchsorted(W.BAND_EDGES_NM, lam, side="right") - 1, 0, 5)
+    line = {"accuracy_gate": "uwb-589ch-80km-G%d-N113-sci_xci FP32 vs plain FP64 GPU, all CUTs" % wl.G,
+            "n_cuts": int(wl.n_ch), "fp64_seconds": t64,
+            "eta_dB": {"max": float(de.max()), "mean": float(de.mean()), "argmax": int(de.argmax())},
+            "snr_dB": {"max": float(ds.max()), "mean": float(ds.mean()), "argmax": int(ds.argmax())},
+            "cuts_within_0.01dB_snr": int(np.sum(ds < 0.01)),
+            "snr_dB_max_by_band": {W.BAND_NAMES[b]: float(ds[band == b].max()) for b in range(6)},
+            "T_fp32_Tbps": float(r32["T"]),
+            "T_fp64_Tbps": float(np.sum(2 * wl.B_THz * np.log2(1 + s64)))}
+    print(json.dumps(line), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump({"eta_dB": de.tolist(), "snr_dB": ds.tolist(), "eta32": e32.tolist(),
+                       "eta64": e64.tolist()}, f)
+    return 0
+
+
 def profile_case(kind: str) -> int:
     """One launch for kernel captures: the 589-ch plan at the bench's G = 256
     for 16 CUTs spread over the band (1.2e9 points, ~1.2e3 work tiles, about
@@ -524,8 +568,11 @@ def main():
     ap.add_argument("--split", default="profiles", choices=["profiles", "cuts"],
                     help="N > 1: profiles = weak scaling, an independent system per rank; cuts = one "
                          "system's gradient split by CUT shards (strong scaling)")
-    ap.add_argument("--workload", default="uwb", choices=["uwb", "batched"],
-                    help="uwb: the 589-ch system (default); batched: 512 profiles over 3 plans")
+    ap.add_argument("--workload", default="uwb", choices=["uwb", "batched", "accuracy"],
+                    help="uwb: the 589-ch system (default); batched: 512 profiles over 3 plans; "
+                         "accuracy: all 589 CUTs FP32 vs the plain FP64 GPU path")
+    ap.add_argument("--chunks", type=int, default=16, help="accuracy: FP64 launches over the CUTs")
+    ap.add_argument("--out", default=None, help="accuracy: write per-CUT errors (JSON) here")
     ap.add_argument("--profile-case", default=None,
                     choices=["quad", "quad64", "adjoint", "adjoint256", "quad256", "raman256", "mci256"],
                     help="run one small launch of a kernel (for ncu captures) and exit")
@@ -536,6 +583,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "accuracy":
+        return run_accuracy(args)
     return run_gpu(args)
 
 
