@@ -239,34 +239,9 @@ def run_gpu(args):
     # weak: every rank evaluates a whole system; strong (split): the ranks share one
     value = (1 if split else world) * n_grid * args.steps / t_total
 
-    # roofline of the dominant kernel.  Algorithmic SFU work per point-step by
-    # the z-sum form the point took: direct 3 (sin, cos, exp), telescoped 3
-    # (sin, cos of the edge phasor, exp), small-phase 0 (its moments are
-    # contracted once per piece and channel: ~nc x 112 exps per 65,536 points).
-    # The fused adjoint evaluates each step term once and keeps it in registers
-    # for the bucket terms, so its algorithmic SFU work is that of its own
-    # point forms (it counts them like the forward kernel).
     quad_ms = float(np.mean(quad_ms))
     paths = eng.last_path_counts()          # z-sum forms of the last timed launch (both kernels count)
-    n_steps = wl.n_edges - 1
-    sfu_ops = n_steps * 3 * (paths["direct"] + paths["telescoped"])
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    sfu_peak = N_SMS * SFU_PER_CLK_PER_SM * sm_max * 1e6 / 1e12       # Tops/s
-    achieved = sfu_ops / (quad_ms / 1e3) / 1e12
-    tot_pts = max(1, sum(paths.values()))
-    cap = ADJ_DRAM_CAPTURE if use_grad else FWD_DRAM_CAPTURE
-    traffic = cap["bytes"] * n_eval / cap["points"]
-    roof = {"bound": "alu", "achieved": achieved, "peak": sfu_peak, "unit": "Tops/s (SFU: sin, cos, ex2)",
-            "frac": achieved / sfu_peak, "traffic": traffic,
-            "traffic_note": "DRAM bytes per launch, scaled by evaluated points from an ncu capture of the "
-                            "148-ch G=256 case (profiles/%s)" % ("k_quad_adj_uwb148_every4th_G256.md" if use_grad
-                                                                else "k_quad_f32_uwb148_every4th_G256.md"),
-            "kernel": "k_quad_adj" if use_grad else "k_quad_f32", "kernel_ms": quad_ms,
-            "sfu_ops_per_launch": sfu_ops,
-            "path_fraction": {k: v / tot_pts for k, v in paths.items()},
-            "peak_source": f"152 SMs x 16 SFU/clk x {sm_max:.0f} MHz (max SM clock)"}
-
+    roof = _roofline(eng, wl, paths, n_eval, quad_ms, use_grad, clocks)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -285,6 +260,8 @@ def run_gpu(args):
     if rank == 0 and args.extras:
         line["extras"] = _extras(eng, wl, P, dev)
     if rank == 0 and not args.quick:
+        line["batched"] = _batched_record(eng, local)
+        line["ascent"] = _ascent_record(eng, local)
         line["e2e"] = _e2e(eng, wl, args, world, n_grid)
         line["fp64_path"] = _fp64_path(eng, wl, P, args)
         line["cpu_baseline"] = cpu_baseline(args.G) if world == 1 else None
@@ -315,13 +292,130 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
             "kernel_ms": eng.last_kernel_ms(0)}
 
 
-# DRAM bytes of one k_quad_adj launch from an ncu capture of the 148-ch
-# profiling case (--profile-case adjoint256; dram__bytes.sum.per_second x
-# gpu__time_duration), and the points that launch evaluated.  The kernel reads
-# the piece list and writes one bucket row per tile, both proportional to the
-# evaluated points at fixed G, so a full launch's traffic is scaled by points.
-ADJ_DRAM_CAPTURE = {"bytes": 4.466e6, "points": 2880700416}
-FWD_DRAM_CAPTURE = {"bytes": 4.056e6, "points": 2880700416}     # k_quad_f32, --profile-case quad256
+# Per-launch counters of the dominant kernels from the ncu captures kept in
+# profiles/ (the 148-ch G = 256 profiling cases, --profile-case adjoint256 /
+# quad256): DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum), executed
+# warp instructions (smsp__inst_executed.sum) and FP32-pipe warp instructions
+# (FFMA + FADD + FMUL of sass__inst_executed_per_opcode), with the grid points
+# that launch evaluated.  The kernels' work per evaluated point is the same at
+# full size (same G, same per-piece shape), so each count is scaled to a full
+# launch by evaluated points.
+ADJ_CAPTURE = {"profile": "k_quad_adj_uwb148_every4th_G256.md", "points": 2880700416,
+               "dram_bytes": 4.466e6, "warp_inst": 1.91e11, "fp32_warp_inst": 1.104e11}
+FWD_CAPTURE = {"profile": "k_quad_f32_uwb148_every4th_G256.md", "points": 2880700416,
+               "dram_bytes": 4.056e6, "warp_inst": 8.69e10, "fp32_warp_inst": 5.76e10}
+ISSUE_PER_CLK_PER_SM = 4         # one warp instruction per clock per SM sub-partition
+
+
+def _roofline(eng, wl, paths, n_eval, kernel_ms, use_grad, clocks):
+    """Roofline of the dominant kernel (k_quad_adj for the gradient step,
+    k_quad_f32 for the SNR evaluation): plain ALU work, no tensor cores, not
+    memory-bound.  Four fractions, each with its own peak:
+      * sfu_algorithmic (the headline, `frac`): the work the method states per
+        evaluated point-step, 3 SFU operations (sin, cos, exp), over every
+        evaluated point and all N_M - 1 steps, against the SFU throughput
+        measured by isrs_probe_alu_peaks in this run.  The contracted
+        small-phase form (its z-sum from moments, exact to < 2e-8) needs none
+        of them, so this fraction can exceed 1: it measures the method's
+        rate, not pipe use;
+      * sfu_executed: the SFU operations the kernel actually issues (3 per
+        step of its direct and telescoped points, from its path counts);
+      * issue: executed warp instructions (ncu capture, scaled by evaluated
+        points) over 152 SMs x 4 per clock at the SM clock sampled during the
+        timed region: the limiter of these kernels;
+      * fp32_pipe: FP32 lane operations (FFMA, FADD, FMUL) over the measured
+        FFMA throughput."""
+    peaks = eng.probe_alu_peaks()
+    n_steps = wl.n_edges - 1
+    t = kernel_ms / 1e3
+    sfu_alg = 3.0 * n_eval * n_steps
+    sfu_exec = 3.0 * n_steps * (paths["direct"] + paths["telescoped"])
+    cap = ADJ_CAPTURE if use_grad else FWD_CAPTURE
+    scale = n_eval / cap["points"]
+    warp_inst = cap["warp_inst"] * scale
+    fp32_ops = cap["fp32_warp_inst"] * scale * 32
+    mhz = clocks.get("sm_mhz") or float(_peaks().get("sm_max_mhz", 2070.0))
+    issue_peak = N_SMS * ISSUE_PER_CLK_PER_SM * mhz * 1e6
+    sfu_peak = peaks["sfu_ops_per_s"]
+    fp32_peak = peaks["fp32_fma_per_s"]
+    tot_pts = max(1, sum(paths.values()))
+    return {"bound": "alu", "unit": "Tops/s (SFU ops of the method: 3 per evaluated point-step)",
+            "achieved": sfu_alg / t / 1e12, "peak": sfu_peak / 1e12, "frac": sfu_alg / t / sfu_peak,
+            "traffic": cap["dram_bytes"] * scale,
+            "traffic_note": "DRAM bytes per launch from the ncu capture in profiles/%s, scaled by "
+                            "evaluated points" % cap["profile"],
+            "fractions": {"sfu_algorithmic": sfu_alg / t / sfu_peak, "sfu_executed": sfu_exec / t / sfu_peak,
+                          "issue": warp_inst / t / issue_peak, "fp32_pipe": fp32_ops / t / fp32_peak},
+            "peaks": {"sfu_ops_per_s": sfu_peak, "fp32_fma_per_s": fp32_peak, "issue_warp_inst_per_s": issue_peak,
+                      "source": "SFU and FFMA: isrs_probe_alu_peaks in this run (measured); issue: 152 SMs x 4 "
+                                "x %.0f MHz (SM clock sampled during the timed region)" % mhz,
+                      "probe_ms": {"sfu": peaks["sfu_probe_ms"], "fp32": peaks["fp32_fma_probe_ms"]}},
+            "kernel": "k_quad_adj" if use_grad else "k_quad_f32", "kernel_ms": kernel_ms,
+            "sfu_ops_per_launch": {"algorithmic": sfu_alg, "executed": sfu_exec},
+            "warp_inst_per_launch": warp_inst,
+            "path_fraction": {k: v / tot_pts for k, v in paths.items()}}
+
+
+def _batched_record(eng, dev_index, reps: int = 1):
+    """C4: 512 launch-power profiles over the 589/295/147-channel plans (G = 64)
+    in one persistent launch with the autotuned tile, replayed from its
+    captured CUDA graph; one direct (capturing) call, then `reps` timed
+    replays with CUDA events on the launching stream."""
+    import torch
+    from paper_2401_18022_gb300 import api, autotune, workloads as W
+    beng = api.Engine(dev_index)
+    bw = W.batched(n_prof=512, G=64)
+    tile = autotune.tune(beng, bw)
+    dev = torch.device("cuda", dev_index)
+    P = torch.tensor(np.concatenate(bw.P_W), dtype=torch.float64, device=dev)
+    beng.eta_batched(bw, P)
+    torch.cuda.synchronize(dev)
+    st = torch.cuda.current_stream(dev)
+    ms, replays = [], []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        beng.eta_batched(bw, P)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+        replays.append(beng.last_graph_replay())
+    n_grid = sum(_unfolded_points(bw.plans[k]) for k in bw.plan_of_profile)
+    t = float(np.median(ms))
+    beng.close()
+    return {"workload": "batched-512-profiles-589/295/147ch-G64-N113-sci_xci", "ms": t,
+            "grid_pts_per_s": n_grid / (t / 1e3), "grid_points": n_grid, "graph_replayed": all(replays),
+            "tile": {k: tile[k] for k in ("points_per_item", "threads")}, "tile_cached": tile.get("cached", False)}
+
+
+def _ascent_record(eng, dev_index, iters: int = 50, G: int = 64):
+    """C5: projected gradient ascent of the throughput over the 589 launch
+    powers (dBm in [-5, 5], adjoint gradient every iteration, Armijo
+    backtracking with forward calls) at G = 64; the result checked against the
+    plain FP64 GPU path on 16 CUTs spread over the band."""
+    import torch
+    from paper_2401_18022_gb300 import optim, workloads as W
+    wl = W.uwb(G=G)
+    dev = torch.device("cuda", dev_index)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    res = optim.ascent(eng, wl, iters=iters)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    P = torch.tensor(res["P_W"], dtype=torch.float64, device=dev)
+    r32 = eng.snr(wl, P=P)
+    cuts = [int(c) for c in np.linspace(0, wl.n_ch - 1, 16)]
+    e64 = eng.eta(wl, P=P, cuts=cuts, precision=1)["eta"].cpu().numpy()
+    e32 = r32["eta"].cpu().numpy()[cuts]
+    s32 = r32["snr"].cpu().numpy()[cuts]
+    Pc = res["P_W"][cuts]
+    pase = Pc / s32 - e32 * Pc ** 3
+    s64 = Pc / (e64 * Pc ** 3 + pase)
+    return {"iters": len(res["history"]), "G": G, "seconds": dt, "iters_per_s": len(res["history"]) / dt,
+            "T_start_Tbps": res["history"][0].get("T_before", res["history"][0]["T"]), "T_final_Tbps": r32["T"],
+            "x_dbm_minmax": [float(res["x_dbm"].min()), float(res["x_dbm"].max())],
+            "fp64_check": {"cuts": cuts, "max_snr_err_dB": float(np.max(np.abs(10 * np.log10(s32 / s64)))),
+                           "max_eta_err_dB": float(np.max(np.abs(10 * np.log10(e32 / e64))))}}
 
 
 def _timed(fn, dev, reps: int = 2):
@@ -542,6 +636,9 @@ def profile_case(kind: str) -> int:
             eng.grad(sub, P=Ps)
         else:
             eng.eta(sub, P=Ps)
+    elif kind == "probe":                  # the SFU and FFMA throughput probes alone
+        print(json.dumps({"profile_case": kind, **eng.probe_alu_peaks()}))
+        return 0
     elif kind == "quad64":                 # FP64 is ~200x slower: 4 CUTs at G = 64
         eng.eta(wl.with_(G=64), P=P, cuts=cuts[::4], precision=1)
     else:
@@ -574,7 +671,7 @@ def main():
     ap.add_argument("--chunks", type=int, default=16, help="accuracy: FP64 launches over the CUTs")
     ap.add_argument("--out", default=None, help="accuracy: write per-CUT errors (JSON) here")
     ap.add_argument("--profile-case", default=None,
-                    choices=["quad", "quad64", "adjoint", "adjoint256", "quad256", "raman256", "mci256"],
+                    choices=["quad", "quad64", "adjoint", "adjoint256", "quad256", "raman256", "mci256", "probe"],
                     help="run one small launch of a kernel (for ncu captures) and exit")
     args = ap.parse_args()
     if args.profile_case:

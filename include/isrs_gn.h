@@ -272,6 +272,16 @@ isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_pl
  * Errors: INVALID_ARG (negative or not a supported block size). */
 isrs_status isrs_set_tile(isrs_handle h, int points_per_item, int threads_per_block);
 
+/* Test hook for the failure paths (no counterpart in the paper): arms one
+ * simulated failure on this handle.  kind 1: the after-th device allocation
+ * the handle makes from now on fails as if cudaMalloc had returned
+ * cudaErrorMemoryAllocation (the call returns ISRS_ERR_ALLOC); kind 2: the
+ * after-th checked CUDA runtime call fails as if it had returned an error
+ * (ISRS_ERR_CUDA).  The failure is made on the host: the simulated call is
+ * not executed and the device is untouched.  It fires once; kind 0 disarms.
+ * Errors: INVALID_ARG (NULL handle, kind outside 0..2, after < 1). */
+isrs_status isrs_debug_inject_fault(isrs_handle h, int kind, int after);
+
 /* Number of quadrature-kernel launches and grid points of the last compute
  * call (for throughput accounting).  Any argument may be NULL. */
 isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_point_steps,
@@ -296,6 +306,17 @@ isrs_status isrs_last_graph_replay(isrs_handle h, int *replayed);
  * step), counts[1] direct form, counts[2] telescoped form.  Synchronises the
  * device.  Errors: INVALID_ARG (NULL, or no launch yet), CUDA. */
 isrs_status isrs_last_path_counts(isrs_handle h, int64_t *counts);
+
+/* Measured throughput of the ALU pipes that bound the quadrature kernels
+ * (a measurement utility; the paper has no counterpart).  which = 0: the SFU
+ * (MUFU ex2.approx, the unit of the sin, cos and ex2 of every z-step of
+ * Eq. slow_vary); which = 1: the FP32 FMA pipe (one FFMA counted as one
+ * operation).  Runs one warm-up and one timed launch of independent
+ * dependency chains on `device` (~15 ms each) and writes operations per
+ * second (ops_per_s) and the timed launch's duration (ms, nullable).
+ * Allocates and frees a small output buffer.  Errors: INVALID_ARG (bad
+ * device or which, NULL ops_per_s), ALLOC, CUDA. */
+isrs_status isrs_probe_alu_peaks(int device, int which, double *ops_per_s, float *ms);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free forward                                                   */

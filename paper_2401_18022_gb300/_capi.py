@@ -77,12 +77,16 @@ def load(build_if_missing: bool = True):
     lib.isrs_gn_eta_batched.argtypes = [vp, P(Fibre), ctypes.c_int, P(Channels), ctypes.c_int, c_int_p,
                                         vp, P(Quad), vp, vp]
     lib.isrs_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.isrs_debug_inject_fault.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.isrs_debug_inject_fault.restype = ctypes.c_int
     lib.isrs_last_launch_info.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), c_int_p]
     lib.isrs_last_graph_replay.argtypes = [vp, c_int_p]
     lib.isrs_last_graph_replay.restype = ctypes.c_int
     lib.isrs_last_path_counts.argtypes = [vp, P(ctypes.c_int64)]
     lib.isrs_last_path_counts.restype = ctypes.c_int
     lib.isrs_last_kernel_ms.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
+    lib.isrs_probe_alu_peaks.argtypes = [ctypes.c_int, ctypes.c_int, c_double_p, ctypes.POINTER(ctypes.c_float)]
+    lib.isrs_probe_alu_peaks.restype = ctypes.c_int
     for name in ("isrs_last_kernel_ms", "isrs_create", "isrs_destroy", "isrs_beta_from_dispersion", "isrs_gn_eta", "isrs_gn_snr",
                  "isrs_gn_grad", "isrs_gn_grad_shard_fwd", "isrs_gn_grad_shard_bwd", "isrs_gn_eta_batched", "isrs_set_tile", "isrs_last_launch_info"):
         getattr(lib, name).restype = ctypes.c_int

@@ -111,6 +111,11 @@ class Engine:
                           float(wl.snr_trx_dB), float(getattr(wl, "ode_h_km", 0.25)),
                           int(getattr(wl, "G_mci", 0)))
 
+    def inject_fault(self, kind: int, after: int = 1):
+        """Arm one simulated failure (1: the after-th device allocation, 2: the
+        after-th checked CUDA call of this handle); 0 disarms."""
+        check(self.lib.isrs_debug_inject_fault(self.h, int(kind), int(after)), self.h)
+
     def set_tile(self, points_per_item: int = 0, threads_per_block: int = 0):
         check(self.lib.isrs_set_tile(self.h, points_per_item, threads_per_block), self.h)
 
@@ -125,6 +130,16 @@ class Engine:
         ms = ctypes.c_float()
         check(self.lib.isrs_last_kernel_ms(self.h, int(which), ctypes.byref(ms)), self.h)
         return ms.value
+
+    def probe_alu_peaks(self):
+        """Measured SFU (MUFU ex2) and FP32 FMA throughput of this device [ops/s]."""
+        out = {}
+        for which, name in ((0, "sfu_ops_per_s"), (1, "fp32_fma_per_s")):
+            v, ms = ctypes.c_double(), ctypes.c_float()
+            check(self.lib.isrs_probe_alu_peaks(int(self.device), which, ctypes.byref(v), ctypes.byref(ms)))
+            out[name] = v.value
+            out[name.replace("_per_s", "_probe_ms")] = ms.value
+        return out
 
     def last_graph_replay(self) -> bool:
         """Whether the last batched call replayed its captured CUDA graph."""

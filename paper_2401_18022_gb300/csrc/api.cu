@@ -6,6 +6,7 @@
 // Everything that depends on the launch powers runs in the kernels; the
 // plan-dependent tables built here are cached in HBM per plan signature.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -60,6 +61,7 @@ struct Geom {
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey = 0;                 // fibre, precision and tile the graph was captured with
     std::vector<void *> gptrs;         // workspace pointers baked into the graph
+    ~Geom();                           // frees whatever device tables it still holds
 };
 
 }  // namespace
@@ -79,6 +81,8 @@ struct isrs_handle_s {
     bool last_graph = false;             // the last batched call replayed a graph
     cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [quad, adjoint][start, end]
     bool ev_valid[2] = {false, false};
+    // host-side fault injection (isrs_debug_inject_fault): kind 1 allocation, 2 CUDA call
+    int inj_kind = 0, inj_countdown = 0;
     // split gradient: the shard whose buckets the last isrs_gn_grad_shard_fwd left
     DevBuf eta_all;                      // [4 n]: gathered eta, then SNR, P_NLI, P_ASE per channel
     bool shard_valid = false;
@@ -106,8 +110,27 @@ isrs_status fail(isrs_handle h, isrs_status s, const char *fmt, ...)
     return s;
 }
 
+// NVTX range over a scope (host timeline of a profiler; no cost without one).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
+// True once, when an armed injection of this kind reaches its count.
+bool inject_hit(isrs_handle h, int kind)
+{
+    if (!h || h->inj_kind != kind) return false;
+    if (--h->inj_countdown > 0) return false;
+    h->inj_kind = 0;
+    return true;
+}
+
 #define CK(call)                                                                              \
     do {                                                                                      \
+        if (inject_hit(h, 2))                                                                 \
+            return fail(h, ISRS_ERR_CUDA, "%s: injected failure (not executed)", #call);      \
         cudaError_t e_ = (call);                                                              \
         if (e_ != cudaSuccess)                                                                \
             return fail(h, e_ == cudaErrorMemoryAllocation ? ISRS_ERR_ALLOC : ISRS_ERR_CUDA,  \
@@ -121,6 +144,7 @@ isrs_status ensure(isrs_handle h, DevBuf &b, size_t bytes)
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
+    if (inject_hit(h, 1)) return fail(h, ISRS_ERR_ALLOC, "cudaMalloc(%zu) failed: injected", bytes);
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         b.p = nullptr;
@@ -711,21 +735,13 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     CK(cudaStreamSynchronize(st));   // host vectors die at return
 
     h->cache.insert(h->cache.begin(), std::move(g));
-    while (h->cache.size() > 4) {
-        Geom *old = h->cache.back().get();
-        if (old->gexec) cudaGraphExecDestroy(old->gexec);
-        DevBuf *bufs[] = {&old->pieces, &old->items, &old->slot_items, &old->slot_cut, &old->prof_slot_off,
-                          &old->plan_ch_off_d, &old->plan_n_d, &old->prof_ch_off_d, &old->prof_plan_d,
-                          &old->ch_frel, &old->ch_B, &old->ch_alpha, &old->ch_gamma, &old->ch_nf,
-                          &old->guard, &old->zs_a, &old->zs_b, &old->zs_d, &old->zs_g, &old->item_slot,
-                          &old->win_lo, &old->win_hi, &old->ch_scale, &old->half_steps, &old->mci_items,
-                          &old->slot_items2, &old->item_slot_all};
-        for (DevBuf *b : bufs) release(*b);
-        h->cache.pop_back();
-    }
+    while (h->cache.size() > 4) h->cache.pop_back();   // ~Geom frees the evicted tables and graph
     *out = h->cache[0].get();
     return ISRS_OK;
 }
+
+void free_geom(Geom *g);
+Geom::~Geom() { free_geom(this); }
 
 void free_geom(Geom *g)
 {
@@ -850,38 +866,41 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
     if ((s = ensure(h, h->partial, sizeof(double) * std::max(1, g->n_items))) != ISRS_OK) return s;
     if ((s = ensure(h, h->counter, sizeof(int) * 4)) != ISRS_OK) return s;
 
-    PrepParams pp;
-    pp.P = (const double *)h->P.p;
-    pp.ch_frel = (const double *)g->ch_frel.p;
-    pp.ch_B = (const double *)g->ch_B.p;
-    pp.ch_alpha = (const double *)g->ch_alpha.p;
-    pp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
-    pp.plan_n = (const int *)g->plan_n_d.p;
-    pp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
-    pp.prof_plan = (const int *)g->prof_plan_d.p;
-    pp.zs_d = (const double2 *)g->zs_d.p;
-    pp.n_steps = M;
-    pp.L = fb->L_km;
-    pp.Cr = fb->Cr;
-    pp.alpha_R = fb->alpha_R_per_km;
-    pp.pd_d = (double *)h->pd_d.p;
-    pp.pd_f = (float *)h->pd_f.p;
-    pp.step_d = (double2 *)h->step_d.p;
-    pp.step_f = (float2 *)h->step_f.p;
-    pp.lnrho_L = (double *)h->lnrho_L.p;
-    pp.ptot = (double *)h->ptot.p;
-    pp.kap_L = (double *)h->kapL.p;
-    CK(launch_prep(pp, g->n_prof, st));
-    if (g->profile == ISRS_PROFILE_RAMAN_ODE) {
-        // the Raman ODE overwrites ln rho(L) and fills the {a, b} tables
-        if ((s = ensure(h, h->ab, sizeof(double2) * (size_t)g->total_prof_ch * M)) != ISRS_OK) return s;
-        if (keep_nodes &&
-            (s = ensure(h, h->ode_y, sizeof(double) * (size_t)(g->n_rk + 1) * g->plan_n[0])) != ISRS_OK)
-            return s;
-        CK(launch_raman(raman_params(h, fb, g, keep_nodes), g->n_prof, g->max_plan_n, st));
+    {
+        Range r_prep("isrs prep (ISRS profile tables)");
+        PrepParams pp;
+        pp.P = (const double *)h->P.p;
+        pp.ch_frel = (const double *)g->ch_frel.p;
+        pp.ch_B = (const double *)g->ch_B.p;
+        pp.ch_alpha = (const double *)g->ch_alpha.p;
+        pp.plan_ch_off = (const int *)g->plan_ch_off_d.p;
+        pp.plan_n = (const int *)g->plan_n_d.p;
+        pp.prof_ch_off = (const int *)g->prof_ch_off_d.p;
+        pp.prof_plan = (const int *)g->prof_plan_d.p;
+        pp.zs_d = (const double2 *)g->zs_d.p;
+        pp.n_steps = M;
+        pp.L = fb->L_km;
+        pp.Cr = fb->Cr;
+        pp.alpha_R = fb->alpha_R_per_km;
+        pp.pd_d = (double *)h->pd_d.p;
+        pp.pd_f = (float *)h->pd_f.p;
+        pp.step_d = (double2 *)h->step_d.p;
+        pp.step_f = (float2 *)h->step_f.p;
+        pp.lnrho_L = (double *)h->lnrho_L.p;
+        pp.ptot = (double *)h->ptot.p;
+        pp.kap_L = (double *)h->kapL.p;
+        CK(launch_prep(pp, g->n_prof, st));
+        if (g->profile == ISRS_PROFILE_RAMAN_ODE) {
+            // the Raman ODE overwrites ln rho(L) and fills the {a, b} tables
+            if ((s = ensure(h, h->ab, sizeof(double2) * (size_t)g->total_prof_ch * M)) != ISRS_OK) return s;
+            if (keep_nodes &&
+                (s = ensure(h, h->ode_y, sizeof(double) * (size_t)(g->n_rk + 1) * g->plan_n[0])) != ISRS_OK)
+                return s;
+            CK(launch_raman(raman_params(h, fb, g, keep_nodes), g->n_prof, g->max_plan_n, st));
+        }
     }
-
     if ((s = ensure(h, h->paths, sizeof(unsigned long long) * 4)) != ISRS_OK) return s;
+    Range r_quad(adjoint ? "isrs quadrature + adjoint" : "isrs quadrature");
     QuadParams qp = quad_params(h, fb, g);
     CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
     CK(cudaMemsetAsync(h->paths.p, 0, sizeof(unsigned long long) * 4, st));
@@ -953,6 +972,7 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
 isrs_status run_finish(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, bool want_snr,
                        cudaStream_t st)
 {
+    Range r("isrs finish (eta, SNR, T)");
     isrs_status s;
     const size_t ns = (size_t)std::max(1, g->n_slots);
     if ((s = ensure(h, h->o_sigma, sizeof(double) * ns)) != ISRS_OK) return s;
@@ -1347,6 +1367,14 @@ isrs_status isrs_set_tile(isrs_handle h, int points_per_item, int threads_per_bl
     return ISRS_OK;
 }
 
+isrs_status isrs_debug_inject_fault(isrs_handle h, int kind, int after)
+{
+    if (!h || kind < 0 || kind > 2 || (kind != 0 && after < 1)) return ISRS_ERR_INVALID_ARG;
+    h->inj_kind = kind;
+    h->inj_countdown = kind ? after : 0;
+    return ISRS_OK;
+}
+
 isrs_status isrs_last_launch_info(isrs_handle h, int64_t *n_points, int64_t *n_point_steps, int *n_launches)
 {
     if (!h) return ISRS_ERR_INVALID_ARG;
@@ -1388,6 +1416,7 @@ isrs_status isrs_gn_eta(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
                         const isrs_quad *quad, const int *cuts, int n_cuts, double *eta, double *pnli,
                         double *sigma, void *stream)
 {
+    Range r_call("isrs_gn_eta");
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
     h->shard_valid = false;    // the workspace is about to be overwritten
@@ -1434,6 +1463,7 @@ isrs_status isrs_gn_eta(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
 isrs_status isrs_gn_snr(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
                         const isrs_quad *quad, double *snr, double *eta, double *T_host, void *stream)
 {
+    Range r_call("isrs_gn_snr");
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
     h->shard_valid = false;    // the workspace is about to be overwritten
@@ -1473,6 +1503,7 @@ isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_pl
                                 int n_prof, const int *plan_of_profile, const double *P_W,
                                 const isrs_quad *quad, double *eta, void *stream)
 {
+    Range r_call("isrs_gn_eta_batched");
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
     h->shard_valid = false;    // the workspace is about to be overwritten
@@ -1516,6 +1547,7 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
                          const isrs_quad *quad, double *dT_dP, double *snr, double *eta, double *T_host,
                          void *stream)
 {
+    Range r_call("isrs_gn_grad");
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
     isrs_status s;
@@ -1540,7 +1572,10 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
     if ((s = run_finish(h, fibre, quad, g, true, st)) != ISRS_OK) return s;
     ChainParams cp;
     if ((s = chain_buffers(h, fibre, quad, g, n, cp)) != ISRS_OK) return s;
-    CK(launch_chain(cp, st));
+    {
+        Range r_chain("isrs chain rule (dT/dP)");
+        CK(launch_chain(cp, st));
+    }
     h->last_launches += 3;
     return grad_outputs(h, n, dT_dP, snr, eta, T_host, st);
 }
@@ -1549,6 +1584,7 @@ isrs_status isrs_gn_grad_shard_fwd(isrs_handle h, const isrs_fibre *fibre, const
                                    const double *P_W, const isrs_quad *quad, const int *cuts, int n_cuts,
                                    double *eta, void *stream)
 {
+    Range r_call("isrs_gn_grad_shard_fwd");
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
     h->shard_valid = false;
@@ -1591,6 +1627,7 @@ isrs_status isrs_gn_grad_shard_fwd(isrs_handle h, const isrs_fibre *fibre, const
 isrs_status isrs_gn_grad_shard_bwd(isrs_handle h, const double *eta_all, int with_direct, double *dT_dP,
                                    double *snr, double *T_host, void *stream)
 {
+    Range r_call("isrs_gn_grad_shard_bwd");
     if (!h) return ISRS_ERR_INVALID_ARG;
     h->err.clear();
     isrs_status s;
@@ -1648,7 +1685,10 @@ isrs_status isrs_gn_grad_shard_bwd(isrs_handle h, const double *eta_all, int wit
     cp.pnli = sp.pnli;
     cp.pase = sp.pase;
     cp.with_direct = with_direct ? 1 : 0;
-    CK(launch_chain(cp, st));
+    {
+        Range r_chain("isrs chain rule (dT/dP)");
+        CK(launch_chain(cp, st));
+    }
     h->last_launches = 4;
     bool host_out = false;
     if ((s = copy_out(h, dT_dP, h->dTdP, n, st, host_out)) != ISRS_OK) return s;
