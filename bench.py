@@ -337,7 +337,7 @@ def _roofline(eng, wl, paths, n_eval, kernel_ms, use_grad, clocks):
     mhz = clocks.get("sm_mhz") or float(_peaks().get("sm_max_mhz", 2070.0))
     issue_peak = N_SMS * ISSUE_PER_CLK_PER_SM * mhz * 1e6
     sfu_peak = peaks["sfu_ops_per_s"]
-    fp32_peak = peaks["fp32_fma_per_s"]
+    fp32_peak = peaks["fp32_ops_per_s"]
     tot_pts = max(1, sum(paths.values()))
     return {"bound": "alu", "unit": "Tops/s (SFU ops of the method: 3 per evaluated point-step)",
             "achieved": sfu_alg / t / 1e12, "peak": sfu_peak / 1e12, "frac": sfu_alg / t / sfu_peak,
@@ -349,7 +349,7 @@ def _roofline(eng, wl, paths, n_eval, kernel_ms, use_grad, clocks):
             "peaks": {"sfu_ops_per_s": sfu_peak, "fp32_fma_per_s": fp32_peak, "issue_warp_inst_per_s": issue_peak,
                       "source": "SFU and FFMA: isrs_probe_alu_peaks in this run (measured); issue: 152 SMs x 4 "
                                 "x %.0f MHz (SM clock sampled during the timed region)" % mhz,
-                      "probe_ms": {"sfu": peaks["sfu_probe_ms"], "fp32": peaks["fp32_fma_probe_ms"]}},
+                      "probe_ms": {"sfu": peaks["sfu_probe_ms"], "fp32": peaks["fp32_probe_ms"]}},
             "kernel": "k_quad_adj" if use_grad else "k_quad_f32", "kernel_ms": kernel_ms,
             "sfu_ops_per_launch": {"algorithmic": sfu_alg, "executed": sfu_exec},
             "warp_inst_per_launch": warp_inst,

@@ -134,11 +134,11 @@ class Engine:
     def probe_alu_peaks(self):
         """Measured SFU (MUFU ex2) and FP32 FMA throughput of this device [ops/s]."""
         out = {}
-        for which, name in ((0, "sfu_ops_per_s"), (1, "fp32_fma_per_s")):
+        for which, name in ((0, "sfu"), (1, "fp32")):
             v, ms = ctypes.c_double(), ctypes.c_float()
             check(self.lib.isrs_probe_alu_peaks(int(self.device), which, ctypes.byref(v), ctypes.byref(ms)))
-            out[name] = v.value
-            out[name.replace("_per_s", "_probe_ms")] = ms.value
+            out[f"{name}_ops_per_s"] = v.value
+            out[f"{name}_probe_ms"] = ms.value
         return out
 
     def last_graph_replay(self) -> bool:

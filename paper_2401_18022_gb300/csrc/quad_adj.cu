@@ -15,13 +15,13 @@
 // k_quad_adj evaluates the forward sum and these buckets in one pass over the
 // grid, and every step term of Eq. slow_vary is evaluated once.  A warp first
 // takes 32 grid points, one per lane, for their geometry, phase and z-sum
-// form.  Small-phase points (|phi| L <= 2) whose moments come from the
-// contracted 11-moment series are finished there: their bucket terms
-// sum_n 2 (A|B) phi^n f_n w_m g_n(m) are expanded in the same Chebyshev series
-// in the point's in-channel coordinate, so per F_c candidate only 55 point
-// sums are kept (one or two warp butterflies per batch) and turned into
-// per-step terms once per piece.  The other points join one list per z-sum
-// form and
+// form.  Small-phase points (|phi| L <= 6, the forward's range) whose moments
+// come from the contracted 19-moment series are finished there: their bucket
+// terms sum_n 2 (A|B) phi^n f_n w_m g_n(m) are expanded in the same Chebyshev
+// series in the point's in-channel coordinate, so per F_c candidate at most
+// 95 point sums are kept (one to three warp butterflies per batch, as many
+// orders as the batch's largest phase needs) and turned into per-step terms
+// once per piece.  The other points join one list per z-sum form and
 // are walked two at a time on half-warps: each of the 16 lanes of a half owns
 // K = ceil(M/16) consecutive steps (112 = 16 x 7), computes their terms t_m
 // into registers, the half sums them with shuffles into S, and the same
@@ -41,14 +41,19 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClsSmall = 0, kClsDirect = 1, kClsTele = 2;
 constexpr int kListCap = 34;    // a form's list: one carried point + 32 new (+1 pad)
-constexpr int kCtr = 4;         // F_c candidates whose small-phase points are contracted
-constexpr int kCtrN = kChebMomA * 5;  // per candidate: moments nu_0..nu_10 x T_0..T_4
-constexpr int kCtrS = 64;       // slots per candidate (two 32-value butterflies)
-// A batch whose contracted points all have |phi| L <= 0.2 keeps n <= 5 in its
-// bucket sums (30 values, one butterfly): the omitted orders are below
-// (0.1)^6/6! = 1.4e-9 of the derivative.
+constexpr int kCtr = 3;         // F_c candidates whose small-phase points are contracted
+constexpr int kCtrN = kChebMom * 5;   // per candidate: moments nu_0..nu_18 x T_0..T_4
+constexpr int kCtrS = 96;       // slots per candidate (three 32-value butterflies)
+// The bucket sums of a batch keep the orders its largest contracted |phi| L
+// needs: n <= 5 up to 0.2 (30 values, one butterfly; omitted orders below
+// (0.1)^6/6! = 1.4e-9 of the derivative), n <= 10 up to 2 (55 values, two
+// butterflies; below 2 (1)^11/11! = 5e-8), n <= 18 up to 6 (95 values, three
+// butterflies; below 2 (3)^19/19! = 1.9e-8).  Rows of the grid have nearly
+// constant phi, so most batches take one form throughout.
 constexpr int kShortN = 30;
 constexpr float kShortPhiL = 0.2f;
+constexpr int kMidN = 55;
+constexpr float kMidPhiL = 2.0f;
 constexpr int kFoldBatches = 8; // batches between FP64 folds of the FP32 accumulators
 constexpr float kPadLog2 = -1000.0f;   // log2 weight of the padding steps (ex2 -> 0)
 
@@ -98,6 +103,30 @@ __device__ __forceinline__ float butterfly32(const F &val, int lane)
     return (b0 ? x2[1] : x2[0]) + __shfl_xor_sync(kFull, b0 ? x2[0] : x2[1], 1);
 }
 
+// Warp sums of the contracted bucket values of group G0 (values 32 G0 ..
+// 32 G0 + 31 of the first nv): value v = al_n T_k(x) with n = v / 5,
+// k = v mod 5, al_n = ae phi^n (n even) or ao phi^(n-1) (n odd; ao carries one
+// phi).  Only the 7 orders the group spans are formed.
+template <int G0>
+__device__ __forceinline__ float ctr_group(float ae, float ao, float p2, const float (&Tk)[5], int nv, int lane)
+{
+    constexpr int N0 = (32 * G0) / 5;          // 0, 6, 12: even
+    float pw = 1.0f;
+#pragma unroll
+    for (int i = 0; i < N0 / 2; ++i) pw *= p2;
+    float a[8];
+    a[0] = ae * pw;
+    a[1] = ao * pw;
+#pragma unroll
+    for (int j = 2; j < 8; ++j) a[j] = a[j - 2] * p2;
+    return butterfly32(
+        [&](int v) {
+            const int va = 32 * G0 + v;
+            return va < nv ? a[va / 5 - N0] * Tk[va % 5] : 0.0f;
+        },
+        lane);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -135,7 +164,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     double2 *sB = reinterpret_cast<double2 *>(sL + nw * 3 * kListCap);   // [nw][K][16] FP64 step buckets
     RowF *rows = reinterpret_cast<RowF *>(sB + nw * K * 16);             // [G]
     __shared__ PieceConst<float> kc;
-    __shared__ ChebTab ct;
+    __shared__ ChebTabN<kCtr> ct;
     __shared__ float sVc[kMaxCand];
     __shared__ double scratch[32];
     __shared__ int s_item;
@@ -160,7 +189,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     const float m4pi2 = (float)(-4.0 * kPi * kPi);
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
-    const float phi_cheb = kChebPhiLA / qp.L;
+    const float phi_cheb = kChebPhiL / qp.L;
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
     // the walks run on half-warps: lane l owns steps [K (l mod 16), K (l mod 16) + K)
@@ -215,7 +244,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
-            cheb_setup<kChebMomA>(qp, pc, item.prof, sT, M, kc, ct);
+            cheb_setup<kChebMom>(qp, pc, item.prof, sT, M, kc, ct);
             __syncthreads();
             const bool cheb = ct.ok != 0;
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2, mult = kc.mult;
@@ -259,9 +288,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                             const float aphi = fabsf(phi);
                             wwa = rw.w * W * array_factor_f(phi, qp);
                             if (cheb && ci < kCtr && aphi <= phi_cheb) {
-                                float nu[kChebMomA];
-                                cheb_moments<kChebMomA>(ct, ci, u, nu, cx);
-                                cheb_AB<kChebMomA>(nu, phi, cA, cB);
+                                float nu[kChebMom];
+                                cheb_moments<kChebMom>(ct, ci, u, nu, cx);
+                                cheb_AB<kChebMom>(nu, phi, cA, cB);
                                 ctr = true;
                                 cls = kClsSmall;
                                 fwd_add(fa, wwa * fmaf(cA, cA, cB * cB), ci, true, sVc);
@@ -279,14 +308,15 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 // phi^n f_n w_m g_n(m) with w_m = base_m sum_k b_k(a_m) T_k(x).  Their
                 // bucket terms need only, per candidate, the sums of cp 2 (A|B) phi^n
                 // T_k(x) (k <= 4 for the F_c-weighted bucket, x T_k = (T_{k+1} +
-                // T_{|k-1|})/2): 55 values, reduced over the warp in two butterflies
-                // and turned into per-step terms once per piece.
+                // T_{|k-1|})/2): 30, 55 or 95 values, reduced over the warp in one to
+                // three butterflies and turned into per-step terms once per piece.
                 unsigned cmask = __ballot_sync(kFull, ctr);
                 const unsigned cmask0 = cmask;
                 if (cmask) {
                     // positive floats order as their bit patterns
                     const unsigned phl = __reduce_max_sync(kFull, __float_as_uint(ctr ? fabsf(phi) * qp.L : 0.0f));
-                    const bool short_form = __uint_as_float(phl) <= kShortPhiL;
+                    const float phLmax = __uint_as_float(phl);
+                    const int form = phLmax <= kShortPhiL ? 0 : (phLmax <= kMidPhiL ? 1 : 2);
                     const float T2 = fmaf(2.0f * cx, cx, -1.0f);
                     const float T3 = fmaf(2.0f * cx, T2, -cx);
                     const float T4 = fmaf(2.0f * cx, T3, -T2);
@@ -294,21 +324,20 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                     while (cmask) {
                         const int cl = __shfl_sync(kFull, ci, __ffs(cmask) - 1);
                         const bool mine = ctr && ci == cl;
-                        float al[kChebMomA];
-                        al[0] = mine ? 2.0f * cpt * cA : 0.0f;
-                        al[1] = mine ? 2.0f * cpt * cB * phi : 0.0f;
-#pragma unroll
-                        for (int n = 2; n < kChebMomA; ++n) al[n] = al[n - 2] * (phi * phi);
-                        if (short_form) {
-                            const float y0 = butterfly32(
-                                [&](int v) { return v < kShortN ? al[v / 5] * Tk[v % 5] : 0.0f; }, lane);
-                            if (lane < kShortN) sYf[warp][cl][lane] += y0;
-                        } else {
-                            const auto val = [&](int v) { return v < kCtrN ? al[v / 5] * Tk[v % 5] : 0.0f; };
-                            const float y0 = butterfly32([&](int v) { return val(v); }, lane);
-                            const float y1 = butterfly32([&](int v) { return val(v + 32); }, lane);
-                            sYf[warp][cl][lane] += y0;
-                            sYf[warp][cl][lane + 32] += y1;
+                        const float ae = mine ? 2.0f * cpt * cA : 0.0f;
+                        const float ao = mine ? 2.0f * cpt * cB * phi : 0.0f;
+                        const float p2 = phi * phi;
+                        const int nv = form == 0 ? kShortN : (form == 1 ? kMidN : kCtrN);
+                        float *Yw = sYf[warp][cl];
+                        const float y0 = ctr_group<0>(ae, ao, p2, Tk, nv, lane);
+                        if (lane < nv) Yw[lane] += y0;
+                        if (form >= 1) {
+                            const float y1 = ctr_group<1>(ae, ao, p2, Tk, nv, lane);
+                            Yw[lane + 32] += y1;
+                        }
+                        if (form == 2) {
+                            const float y2 = ctr_group<2>(ae, ao, p2, Tk, nv, lane);
+                            Yw[lane + 64] += y2;
                         }
                         cmask &= ~__ballot_sync(kFull, mine);
                     }
@@ -444,8 +473,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 const int coff = qp.plan_ch_off[pc.plan];
                 for (int m = threadIdx.x; m < M; m += blockDim.x) {
                     const float4 a = sT[m];           // {A2 + log2 dz, K2, z, z^2 + dz^2/12}
-                    const float4 g0 = qp.zs_g[kZsG * m], g1 = qp.zs_g[kZsG * m + 1], g2 = qp.zs_g[kZsG * m + 2];
-                    const float gm[kChebMomA] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x, g2.y, g2.z};
+                    const float *gm = reinterpret_cast<const float *>(qp.zs_g + kZsG * m);   // g_0..g_18
                     double rx = 0.0, ry = 0.0;
                     for (int c = 0; c < ncc; ++c) {
                         const double *Y = sYt[c];
@@ -460,7 +488,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         const float b3 = 2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 / 240.0f)); // 2 I3
                         float rs = 0.0f, xs = 0.0f;
 #pragma unroll
-                        for (int n = 0; n < kChebMomA; ++n) {
+                        for (int n = 0; n < kChebMom; ++n) {
                             const double *Yn = Y + 5 * n;
                             const float y0 = (float)Yn[0], y1 = (float)Yn[1], y2 = (float)Yn[2], y3 = (float)Yn[3],
                                         y4 = (float)Yn[4];

@@ -16,10 +16,11 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// nearest integer of |t| < 2^22 on the FMA pipe (round-to-nearest-even add)
-__device__ __forceinline__ float round_magic(float t)
+// nearest integer of t (round to nearest even): one FRND instruction, exact
+// for every FP32 value; t - rint(t) is then exact (Sterbenz).
+__device__ __forceinline__ float round_nearest(float t)
 {
-    return __fadd_rn(__fadd_rn(t, 12582912.0f), -12582912.0f);
+    return rintf(t);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v)
@@ -124,7 +125,7 @@ __device__ __forceinline__ void piece_consts(const QuadParams &qp, const DevPiec
 
 __device__ __forceinline__ void sincos_rev(float t, float &sn, float &cs)
 {
-    const float fr = __fadd_rn(t, -round_magic(t));
+    const float fr = __fadd_rn(t, -round_nearest(t));
     __sincosf(fr * 6.283185307179586f, &sn, &cs);
 }
 
@@ -133,7 +134,7 @@ __device__ __forceinline__ void phasor_rev_ff(float phi, float hi, float lo, flo
     const float th = phi * hi;
     float tl = fmaf(phi, hi, -th);
     tl = fmaf(phi, lo, tl);
-    const float fr = __fadd_rn(th, -round_magic(th)) + tl;
+    const float fr = __fadd_rn(th, -round_nearest(th)) + tl;
     __sincosf(fr * 6.283185307179586f, &sn, &cs);
 }
 
@@ -185,9 +186,10 @@ __device__ __forceinline__ double array_factor_d(double phi, const QuadParams &q
 //   S e^{-j phi z0} = sum_n (j phi)^n / n! nu_n,   nu_n = sum_m w_m g_n(m),
 //   g_n(m) = mean of (zeta - z0)^n over step m,
 // exactly; |S|^2 = A^2 + B^2 with A (B) the even (odd) part, and truncating
-// at n = N leaves a relative error below 2 (phi L/2)^{N+1}/(N+1)!: the forward
-// kernels keep n <= 18 for |phi| L <= 6 (< 2e-8), the adjoint n <= 10 for
-// |phi| L <= 2 (< 5e-8; its bucket sums grow with the order).
+// at n = N leaves a relative error below 2 (phi L/2)^{N+1}/(N+1)!: the
+// closed-form kernels keep n <= 18 for |phi| L <= 6 (< 2e-8; the adjoint keeps
+// fewer orders in its bucket sums when a batch's phases allow), the
+// tabulated-profile forward n <= 10 for |phi| L <= 2 (< 5e-8).
 // The moments depend on the point only through F_c (and the candidate
 // channel's attenuation): inside channel c, F_c - f_ref = F0 + h x with
 // x in [-1, 1], and
@@ -205,12 +207,14 @@ constexpr int kChebMomA = 11;       // nu_0 .. nu_10 (adjoint)
 constexpr float kChebPhiLA = 2.0f;  // |phi| L limit of the 11-moment form: error < 5e-8
 constexpr int kZsG = 5;             // float4 per step of the centred step moments g_0..g_19 (g_19 = 0)
 
-struct ChebTab {
-    float4 c[kMaxCand][kChebMom];   // [candidate][n] = C_n0..C_n3 times (-1)^{floor(n/2)} / n!
-    float mid[kMaxCand];            // channel centre relative to the CUT
-    float invh[kMaxCand];           // 1 / (B_c / 2)
+template <int NC>
+struct ChebTabN {
+    float4 c[NC][kChebMom];         // [candidate][n] = C_n0..C_n3 times (-1)^{floor(n/2)} / n!
+    float mid[NC];                  // channel centre relative to the CUT
+    float invh[NC];                 // 1 / (B_c / 2)
     int ok;
 };
+using ChebTab = ChebTabN<kMaxCand>;
 
 // (-1)^{floor(n/2)} / n!
 __host__ __device__ constexpr double cheb_fold(int n)
@@ -273,12 +277,12 @@ __device__ __forceinline__ void cheb_sums(const QuadParams &qp, const float4 *sT
 
 // Called by every thread of the block after piece_consts; the caller syncs.
 // sT[m] = {A2d_m, K2_m, z_m, .}; qp.zs_g[kZsG m ...] = g_0..g_19 of step m.
-// One warp per candidate fills nu_0..nu_{NM-1}; the step weights are exact to
-// FP32 rounding (FP64 exponent), the sums run over the lane's steps and a
-// warp tree.
-template <int NM>
+// One warp per candidate (the first NC of the piece) fills nu_0..nu_{NM-1};
+// the step weights are exact to FP32 rounding (FP64 exponent), the sums run
+// over the lane's steps and a warp tree.
+template <int NM, int NC>
 __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece &pc, int prof,
-                                           const float4 *sT, int M, const PieceConst<float> &k, ChebTab &ct)
+                                           const float4 *sT, int M, const PieceConst<float> &k, ChebTabN<NC> &ct)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int coff = qp.plan_ch_off[pc.plan];
@@ -288,7 +292,8 @@ __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece 
     const bool ok = qp.zs_g != nullptr && kapL * hmax <= (double)kChebMaxA;
     if (threadIdx.x == 0) ct.ok = ok ? 1 : 0;
     if (!ok) return;
-    for (int c = warp; c < k.nc; c += nw) {
+    const int ncs = k.nc < NC ? k.nc : NC;
+    for (int c = warp; c < ncs; c += nw) {
         const double F0 = qp.ch_frel[coff + pc.c_lo + c];
         const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
         const double at = (double)(k.at_ab + k.hat[c]);
@@ -308,8 +313,8 @@ __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece 
 }
 
 // Folded moments nu'_n (n < NM) of a point in candidate ci at u = F_c - f_i.
-template <int NM>
-__device__ __forceinline__ void cheb_moments(const ChebTab &ct, int ci, float u, float (&nu)[NM], float &x)
+template <int NM, int NC>
+__device__ __forceinline__ void cheb_moments(const ChebTabN<NC> &ct, int ci, float u, float (&nu)[NM], float &x)
 {
     x = (u - ct.mid[ci]) * ct.invh[ci];
     const float T2 = fmaf(2.0f * x, x, -1.0f);

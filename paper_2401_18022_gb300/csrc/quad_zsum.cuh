@@ -16,8 +16,8 @@ namespace isrs {
 //
 // Exact-to-FP32 evaluations of S = sum_m p_m dz_m sinc(phi dz_m/2)
 // e^{j phi z_m} (Eq. slow_vary), chosen per grid point by |phi|:
-//  * contracted small phase (|phi| L <= 2, when the piece's Chebyshev
-//    contraction applies): the 11-moment series about the span centre
+//  * contracted small phase (|phi| L <= 6, when the piece's Chebyshev
+//    contraction applies): the 19-moment series about the span centre
 //    (quad_common.cuh), no per-step work;
 //  * small (|phi| L <= 0.02, otherwise): second-order expansion in phi,
 //      |S|^2 = M0^2 - phi^2 (M0 M2 - M1^2) + O((phi L)^4),
@@ -141,16 +141,16 @@ __device__ __forceinline__ float zsum_tele_fc(float phi, float Fc, const float4 
     return (Sr * Sr + Si * Si) / (phi * phi);
 }
 
-// As zsum_tele_f, with a phase reduction valid far beyond 2^22 revolutions:
-// the first magic-number rounding leaves an integer (or half-integer) on top
-// of the fraction once |phi z / 2pi| >= 2^22; a second one removes it.
+// As phasor_rev_ff, for phases far beyond 2^22 revolutions (the MCI cells):
+// th - rint(th) is exact at any magnitude, but tl can then exceed one
+// revolution, so the sum is reduced once more.
 __device__ __forceinline__ void phasor_rev_ff_wide(float phi, float hi, float lo, float &sn, float &cs)
 {
     const float th = phi * hi;
     float tl = fmaf(phi, hi, -th);
     tl = fmaf(phi, lo, tl);
-    float fr = __fadd_rn(th, -round_magic(th)) + tl;
-    fr = __fadd_rn(fr, -round_magic(fr));
+    float fr = __fadd_rn(th, -round_nearest(th)) + tl;
+    fr = __fadd_rn(fr, -round_nearest(fr));
     __sincosf(fr * 6.283185307179586f, &sn, &cs);
 }
 

@@ -40,3 +40,28 @@ def test_bench_grid_point_count_matches_the_oracles_pieces(orc):
         f = wl.f_THz - wl.f_ref_THz
         n_pieces = sum(len(orc.pieces(f, wl.B_THz, i, wl.cell_set)) for i in range(wl.n_ch))
         assert bench._unfolded_points(wl) == n_pieces * wl.G * wl.G, wl.name
+
+
+def test_roofline_record_with_a_stand_in_engine():
+    """The GPU line's roofline object, built from a stand-in for the engine's
+    measured peaks: keys, the four fractions and their defining formulas."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2401_18022_gb300 import workloads as W
+
+    class FakeEng:
+        def probe_alu_peaks(self):
+            return {"sfu_ops_per_s": 1.0e13, "sfu_probe_ms": 8.0, "fp32_ops_per_s": 4.0e13, "fp32_probe_ms": 16.0}
+
+    wl = W.uwb(G=4)
+    paths = {"small": 600, "direct": 100, "telescoped": 300}
+    r = bench._roofline(FakeEng(), wl, paths, 1000, 2.0, True, {"sm_mhz": 2000.0})
+    f = r["fractions"]
+    assert set(f) == {"sfu_algorithmic", "sfu_executed", "issue", "fp32_pipe"}
+    steps = wl.n_edges - 1
+    assert r["frac"] == f["sfu_algorithmic"] == 3 * 1000 * steps / 2e-3 / 1e13
+    assert f["sfu_executed"] == 3 * steps * 400 / 2e-3 / 1e13
+    cap = bench.ADJ_CAPTURE
+    assert abs(f["issue"] / (cap["warp_inst"] * 1000 / cap["points"] / 2e-3 / (152 * 4 * 2e9)) - 1) < 1e-12
+    assert r["bound"] == "alu" and r["peak"] == 10.0 and r["kernel"] == "k_quad_adj"
+    json.dumps(r)
