@@ -52,6 +52,11 @@ struct Geom {
     // steps per half z-step, largest candidate count of a piece
     int profile = 0, nc_max = 1, n_rk = 0, max_plan_n = 0;
     DevBuf win_lo, win_hi, ch_scale, half_steps;
+    // Raman-ODE gradient: per work tile the rows of the plan channels its
+    // pieces touch, per piece its local rows {a, b, CUT, first candidate},
+    // and per plan channel the (row, slot) pairs the gather sums in tile order
+    int64_t n_tab_rows = 0;
+    DevBuf tab_row_off, tab_prow, tab_gath_off, tab_gath;
     // multi-channel-interference cells on their own grid: work items over
     // triangular cell ranges and, per output slot, their item range
     int G_mci = 0, n_mci_items = 0;
@@ -72,7 +77,7 @@ struct isrs_handle_s {
     std::string err;
     DevBuf paths, kapL;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
-        o_pase, o_T, gA, gK, gPd, ybar, dTdP, ab, ode_y, gAB, gV, gAt, partial_mci;
+        o_pase, o_T, gA, gK, gPd, gVs, ybar, dTdP, ab, ode_y, gAB, gV, gAt, partial_mci, tab_rows, tab_rowsV;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
@@ -695,6 +700,45 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
             return fail(h, ISRS_ERR_UNSUPPORTED, "Raman-ODE tables of %d candidates x %d steps exceed shared memory",
                         ncm, g->n_steps);
     }
+    std::vector<int> trow_off, gath_off;
+    std::vector<int4> prow;
+    std::vector<int2> gath;
+    if (fb->profile == ISRS_PROFILE_RAMAN_ODE) {
+        // the channels of a tile: its CUT, every piece's a and b and F_c
+        // candidates (consecutive channels, so consecutive rows)
+        prow.resize(pieces.size());
+        trow_off.push_back(0);
+        std::vector<int> chs, row_ch;
+        for (const DevItem &it : items) {
+            chs.clear();
+            for (int k = it.piece0; k < it.piece1; ++k) {
+                const DevPiece &pc = pieces[k];
+                chs.push_back(pc.cut);
+                chs.push_back(pc.a);
+                chs.push_back(pc.b);
+                for (int c = pc.c_lo; c <= std::min(pc.c_hi, pc.c_lo + kMaxCand - 1); ++c) chs.push_back(c);
+            }
+            std::sort(chs.begin(), chs.end());
+            chs.erase(std::unique(chs.begin(), chs.end()), chs.end());
+            const auto local = [&](int c) { return (int)(std::lower_bound(chs.begin(), chs.end(), c) - chs.begin()); };
+            for (int k = it.piece0; k < it.piece1; ++k) {
+                const DevPiece &pc = pieces[k];
+                prow[k] = make_int4(local(pc.a), local(pc.b), local(pc.cut), local(pc.c_lo));
+            }
+            const int coff = g->plan_ch_off[prof_plan[it.prof]];
+            for (int c : chs) row_ch.push_back(coff + c);
+            trow_off.push_back(trow_off.back() + (int)chs.size());
+        }
+        g->n_tab_rows = trow_off.back();
+        // gather lists by plan-concatenated channel, rows in tile order
+        gath_off.assign(g->total_plan_ch + 1, 0);
+        for (int c : row_ch) ++gath_off[c + 1];
+        for (int c = 0; c < g->total_plan_ch; ++c) gath_off[c + 1] += gath_off[c];
+        gath.resize(row_ch.size());
+        std::vector<int> fill(gath_off.begin(), gath_off.end() - 1);
+        for (size_t t = 0; t < items.size(); ++t)
+            for (int r = trow_off[t]; r < trow_off[t + 1]; ++r) gath[fill[row_ch[r]]++] = make_int2(r, item_slot[t]);
+    }
 
     isrs_status s;
 #define UP(buf, vec) if ((s = upload(h, g->buf, vec, st)) != ISRS_OK) return s
@@ -730,6 +774,10 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
         UP(win_hi, whi);
         UP(ch_scale, scl);
         UP(half_steps, hsteps);
+        UP(tab_row_off, trow_off);
+        UP(tab_prow, prow);
+        UP(tab_gath_off, gath_off);
+        UP(tab_gath, gath);
     }
 #undef UP
     CK(cudaStreamSynchronize(st));   // host vectors die at return
@@ -752,7 +800,7 @@ void free_geom(Geom *g)
                       &g->ch_frel, &g->ch_B, &g->ch_alpha, &g->ch_gamma, &g->ch_nf,
                       &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->zs_g, &g->item_slot,
                       &g->win_lo, &g->win_hi, &g->ch_scale, &g->half_steps, &g->mci_items, &g->slot_items2,
-                      &g->item_slot_all};
+                      &g->item_slot_all, &g->tab_row_off, &g->tab_prow, &g->tab_gath_off, &g->tab_gath};
     for (DevBuf *b : bufs) release(*b);
 }
 
@@ -842,7 +890,7 @@ QuadParams quad_params(isrs_handle h, const isrs_fibre *fb, Geom *g)
 // closed-form profile also fills the step buckets and the PSD buckets (single
 // profile, FP32).  keep_nodes keeps the Raman ODE's RK4 states (profile 0).
 isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precision, cudaStream_t st,
-                        bool adjoint = false, bool keep_nodes = false)
+                        bool adjoint = false, bool keep_nodes = false, bool prep_only = false)
 {
     isrs_status s;
     const int M = g->n_steps;
@@ -900,6 +948,10 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
         }
     }
     if ((s = ensure(h, h->paths, sizeof(unsigned long long) * 4)) != ISRS_OK) return s;
+    if (prep_only) {
+        h->last_launches = g->profile == ISRS_PROFILE_RAMAN_ODE ? 2 : 1;
+        return ISRS_OK;
+    }
     Range r_quad(adjoint ? "isrs quadrature + adjoint" : "isrs quadrature");
     QuadParams qp = quad_params(h, fb, g);
     CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
@@ -910,8 +962,10 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
         if ((s = ensure(h, h->gA, sizeof(double2) * (size_t)std::max(1, g->n_items + g->n_mci_items) * M)) !=
             ISRS_OK)
             return s;
-        if ((s = ensure(h, h->gPd, sizeof(double) * (size_t)g->n_slots * n_ch)) != ISRS_OK) return s;
-        CK(cudaMemsetAsync(h->gPd.p, 0, sizeof(double) * (size_t)g->n_slots * n_ch, st));
+        // per-tile PSD buckets (regular tiles, then MCI tiles); every tile writes its whole row
+        if ((s = ensure(h, h->gPd, sizeof(double) * (size_t)std::max(1, g->n_items + g->n_mci_items) * n_ch)) !=
+            ISRS_OK)
+            return s;
         AdjParams ap;
         ap.q = qp;
         ap.item_R = (double2 *)h->gA.p;
@@ -932,6 +986,7 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
             am.q.partial = (double *)h->partial_mci.p;
             am.q.counter = (int *)h->counter.p + 1;
             am.item_R = (double2 *)h->gA.p + (size_t)g->n_items * M;
+            am.V = (double *)h->gPd.p + (size_t)g->n_items * n_ch;
             am.item_slot = (const int *)g->item_slot_all.p + g->n_items;
             int mgrid = h->num_sms * adjoint_mci_blocks_per_sm(M, am.q.mci_n_max, block);
             if (g->n_mci_items < mgrid) mgrid = g->n_mci_items;
@@ -1162,30 +1217,49 @@ isrs_status run_grad_tab(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q
 {
     isrs_status s;
     const int n = g->plan_n[0], M = g->n_steps;
-    if ((s = run_forward(h, fb, g, ISRS_PREC_FP32, st, false, true)) != ISRS_OK) return s;
-    if ((s = run_finish(h, fb, q, g, true, st)) != ISRS_OK) return s;
+    // profile tables and the RK4 states; the fused quadrature below gives Sigma
+    if ((s = run_forward(h, fb, g, ISRS_PREC_FP32, st, false, true, true)) != ISRS_OK) return s;
     if ((s = ensure(h, h->ybar, sizeof(double) * 2 * n)) != ISRS_OK) return s;
     if ((s = ensure(h, h->dTdP, sizeof(double) * n)) != ISRS_OK) return s;
     if ((s = ensure(h, h->gAB, sizeof(double2) * (size_t)n * M)) != ISRS_OK) return s;
     if ((s = ensure(h, h->gAt, sizeof(double) * (size_t)n * M)) != ISRS_OK) return s;
     if ((s = ensure(h, h->gV, sizeof(double) * n)) != ISRS_OK) return s;
-    const ChainParams cp = chain_params(h, fb, q, g, n);
-    CK(launch_ybar(cp, st));
-    CK(cudaMemsetAsync(h->gAB.p, 0, sizeof(double2) * (size_t)n * M, st));
-    CK(cudaMemsetAsync(h->gV.p, 0, sizeof(double) * n, st));
+    if ((s = ensure(h, h->tab_rows, sizeof(double2) * (size_t)std::max<int64_t>(1, g->n_tab_rows) * M)) != ISRS_OK)
+        return s;
+    if ((s = ensure(h, h->tab_rowsV, sizeof(double) * (size_t)std::max<int64_t>(1, g->n_tab_rows))) != ISRS_OK)
+        return s;
     CK(cudaMemsetAsync(h->counter.p, 0, sizeof(int) * 4, st));
     AdjTabParams ap;
     ap.q = quad_params(h, fb, g);
-    ap.ybar = cp.ybar;
-    ap.item_slot = (const int *)g->item_slot.p;
-    ap.gAB = (double2 *)h->gAB.p;
-    ap.gV = (double *)h->gV.p;
+    ap.row_off = (const int *)g->tab_row_off.p;
+    ap.prow = (const int4 *)g->tab_prow.p;
+    ap.rows = (double2 *)h->tab_rows.p;
+    ap.rowsV = (double *)h->tab_rowsV.p;
     const int block = h->tile_threads > 0 ? h->tile_threads : 256;
     int grid = h->num_sms * adjoint_tab_blocks_per_sm(M, g->G, g->nc_max, block);
     if (g->n_items < grid) grid = std::max(1, g->n_items);
-    if ((s = mark(h, 1, 0, st)) != ISRS_OK) return s;
-    if (g->n_items > 0) CK(launch_adjoint_tab(ap, grid, block, st));
-    if ((s = mark(h, 1, 1, st)) != ISRS_OK) return s;
+    {
+        Range r_adj("isrs quadrature + adjoint (tabulated profile)");
+        if ((s = mark(h, 1, 0, st)) != ISRS_OK) return s;
+        if (g->n_items > 0) CK(launch_adjoint_tab(ap, grid, block, st));
+        if ((s = mark(h, 1, 1, st)) != ISRS_OK) return s;
+    }
+    if ((s = run_finish(h, fb, q, g, true, st)) != ISRS_OK) return s;
+    const ChainParams cp = chain_params(h, fb, q, g, n);
+    Range r_chain("isrs chain rule (tabulated profile, Raman ODE)");
+    CK(launch_ybar(cp, st));
+    TabGatherParams gp;
+    gp.gath_off = (const int *)g->tab_gath_off.p;
+    gp.gath = (const int2 *)g->tab_gath.p;
+    gp.rows = ap.rows;
+    gp.rowsV = ap.rowsV;
+    gp.ybar = cp.ybar;
+    gp.slot_cut = (const int *)g->slot_cut.p;
+    gp.n_ch = n;
+    gp.n_steps = M;
+    gp.gAB = (double2 *)h->gAB.p;
+    gp.gV = (double *)h->gV.p;
+    CK(launch_tab_gather(gp, st));
     RamanAdjParams rap;
     std::memset(&rap, 0, sizeof(rap));
     rap.r = raman_params(h, fb, g, true);
@@ -1202,7 +1276,9 @@ isrs_status run_grad_tab(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q
     rap.ch_B = (const double *)g->ch_B.p;
     rap.dT_dP = (double *)h->dTdP.p;
     CK(launch_raman_adj(rap, st));
-    h->last_launches += 4;   // ybar, adjoint quadrature, slope fold, ODE adjoint
+    h->last_points = g->n_points;
+    h->last_psteps = g->n_points * (int64_t)M;
+    h->last_launches += 5;   // fused quadrature + adjoint, ybar, gather, slope fold, ODE adjoint (finish counted)
     return ISRS_OK;
 }
 
@@ -1250,9 +1326,15 @@ isrs_status chain_buffers(isrs_handle h, const isrs_fibre *fb, const isrs_quad *
     if ((s = ensure(h, h->ybar, sizeof(double) * 2 * n)) != ISRS_OK) return s;
     if ((s = ensure(h, h->gK, sizeof(double2) * g->n_steps)) != ISRS_OK) return s;
     if ((s = ensure(h, h->dTdP, sizeof(double) * n)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->gVs, sizeof(double) * (size_t)std::max(1, g->n_slots) * n)) != ISRS_OK) return s;
     cp = chain_params(h, fb, q, g, n);
     cp.item_R = (const double2 *)h->gA.p;
-    cp.V = (const double *)h->gPd.p;
+    cp.Vt = (const double *)h->gPd.p;
+    cp.Vs = (double *)h->gVs.p;
+    cp.V = cp.Vs;
+    cp.slot_items = (const int2 *)g->slot_items.p;
+    cp.slot_items2 = g->n_mci_items > 0 ? (const int2 *)g->slot_items2.p : nullptr;
+    cp.n_items_reg = g->n_items;
     cp.Rb = (double2 *)h->gK.p;
     return ISRS_OK;
 }
@@ -1325,7 +1407,7 @@ isrs_status isrs_destroy(isrs_handle h)
     DevBuf *bufs[] = {&h->P, &h->pd_d, &h->pd_f, &h->step_d, &h->step_f, &h->lnrho_L, &h->ptot, &h->partial,
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
                       &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP, &h->ab, &h->ode_y, &h->gAB, &h->gV,
-                      &h->gAt, &h->partial_mci, &h->eta_all};
+                      &h->gAt, &h->partial_mci, &h->eta_all, &h->tab_rows, &h->tab_rowsV, &h->gVs};
     for (DevBuf *b : bufs) release(*b);
     release(h->paths);
     release(h->kapL);
@@ -1576,7 +1658,7 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
         Range r_chain("isrs chain rule (dT/dP)");
         CK(launch_chain(cp, st));
     }
-    h->last_launches += 3;
+    h->last_launches += 4;   // ybar, PSD-bucket reduction, step-bucket reduction, chain rule
     return grad_outputs(h, n, dT_dP, snr, eta, T_host, st);
 }
 
@@ -1689,7 +1771,7 @@ isrs_status isrs_gn_grad_shard_bwd(isrs_handle h, const double *eta_all, int wit
         Range r_chain("isrs chain rule (dT/dP)");
         CK(launch_chain(cp, st));
     }
-    h->last_launches = 4;
+    h->last_launches = 5;    // SNR from eta, ybar, PSD-bucket reduction, step-bucket reduction, chain rule
     bool host_out = false;
     if ((s = copy_out(h, dT_dP, h->dTdP, n, st, host_out)) != ISRS_OK) return s;
     if (snr) {

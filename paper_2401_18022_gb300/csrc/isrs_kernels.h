@@ -44,11 +44,12 @@ struct FinishParams {
 };
 
 // Adjoint of the FP32 quadrature (single profile): per work tile the step
-// buckets {R_m, R'_m} and per (CUT slot, channel) the PSD buckets V.
+// buckets {R_m, R'_m} and the PSD buckets V of every channel (the tile's own
+// row, written only by its block; k_v_reduce sums a CUT's rows in tile order).
 struct AdjParams {
     QuadParams q;
     double2 *item_R;            // [n_items x n_steps]
-    double *V;                  // [n_slots x n_ch], zeroed before launch
+    double *V;                  // [n_items x n_ch]
     const int *item_slot;       // output slot of each item
     int n_ch;
 };
@@ -62,7 +63,12 @@ struct ChainParams {
     const double2 *step_d;      // {lnPtot - lnN_m, kappa_m}
     const double *snr, *pnli, *pase, *lnrho_L;   // [n_ch]
     const double2 *item_R;
-    const double *V;
+    const double *V;            // [n_slots x n_ch] PSD buckets per output slot (from Vt)
+    const double *Vt;           // [(n_items) x n_ch] PSD buckets per tile (regular, then MCI tiles)
+    double *Vs;                 // = V, written by k_v_reduce
+    const int2 *slot_items;     // per slot: regular tile range
+    const int2 *slot_items2;    // per slot: MCI tile range (nullable), offset by n_items_reg
+    int n_items_reg;
     const int *item_slot, *slot_cut;
     int n_items, n_slots, n_ch, n_steps;
     int with_direct;            // add the terms outside the buckets (ASE gain, SNR numerator)
@@ -118,16 +124,33 @@ struct RamanAdjParams {
     double *dT_dP;              // [n]
 };
 
-// Adjoint of the FP32 quadrature with the tabulated profile (single profile):
-// dT/d{a, b} per channel and step, and dT/d ln P through the PSD products,
-// given dT/dSigma of every output slot.
+// Fused forward + adjoint of the FP32 quadrature with the tabulated profile
+// (single profile): per work tile the forward partial of Sigma_i and, for
+// every plan channel the tile's pieces touch, dSigma_i/d{a, b}(m) and
+// dSigma_i/d ln P through the PSD products (unscaled: the gather applies
+// dT/dSigma_i).
 struct AdjTabParams {
     QuadParams q;
-    const double *ybar;         // [n_slots] dT/dSigma_i
-    const int *item_slot;
-    double2 *gAB;               // [n_ch x n_steps], zeroed before launch
-    double *gV;                 // [n_ch], zeroed before launch
+    const int *row_off;         // [n_items + 1] first row of each tile
+    const int4 *prow;           // [n_pieces] local rows {a, b, CUT, first F_c candidate}
+    double2 *rows;              // [n_rows x n_steps] {dSigma/da, dSigma/db}
+    double *rowsV;              // [n_rows] dSigma/d ln P
 };
+
+// dT/d{a, b} and dT/d ln P (PSD) per plan channel: the tile rows of each
+// channel times dT/dSigma of the tile's CUT, summed in tile order.
+struct TabGatherParams {
+    const int *gath_off;        // [n_ch + 1]
+    const int2 *gath;           // (row, output slot)
+    const double2 *rows;
+    const double *rowsV;
+    const double *ybar;         // [n_ch] dT/dSigma_i
+    const int *slot_cut;
+    int n_ch, n_steps;
+    double2 *gAB;               // [n_ch x n_steps]
+    double *gV;                 // [n_ch]
+};
+cudaError_t launch_tab_gather(const TabGatherParams &gp, cudaStream_t st);
 
 size_t adjoint_tab_smem_bytes(int n_steps, int G, int nc_max, int block);
 int adjoint_tab_blocks_per_sm(int n_steps, int G, int nc_max, int block);

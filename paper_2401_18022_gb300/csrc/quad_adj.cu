@@ -57,8 +57,14 @@ constexpr float kMidPhiL = 2.0f;
 constexpr int kFoldBatches = 8; // batches between FP64 folds of the FP32 accumulators
 constexpr float kPadLog2 = -1000.0f;   // log2 weight of the padding steps (ex2 -> 0)
 
-// Forward-sum bookkeeping of one walked point: lane 0 of each half adds the
-// point's value to its compensated sum and to its F_c candidate's PSD bucket.
+// Forward-sum bookkeeping of one grid point: the point's owner (every lane
+// for a contracted point, lane 0 of each half for a walked one) adds its value
+// to the compensated sum and to its F_c candidate's PSD bucket: registers for
+// the first four candidates, beyond them this half-warp's own row of sVc.  Only
+// that half's owner lane ever adds to the row, so its adds run in program
+// order (deterministic); they are issued as shared-memory reductions, which
+// hold no register across the add (a plain load-add-store here doubled the
+// kernel's spills).
 struct FwdAcc {
     float sum, comp, v0, v1, v2, v3;
 };
@@ -74,33 +80,7 @@ __device__ __forceinline__ void fwd_add(FwdAcc &a, float val, int ci, bool owner
     a.v1 += ci == 1 ? vv : 0.0f;
     a.v2 += ci == 2 ? vv : 0.0f;
     a.v3 += ci == 3 ? vv : 0.0f;
-    if (owner && ci >= 4) atomicAdd(&sVc[ci], val);
-}
-
-// Warp sum of 32 values per lane in one butterfly: each level halves the
-// values a lane carries, and lane L ends with the sum of value L.  val(i)
-// gives this lane's value i.
-template <typename F>
-__device__ __forceinline__ float butterfly32(const F &val, int lane)
-{
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
-    float x16[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-        x16[i] = (b4 ? val(i + 16) : val(i)) + __shfl_xor_sync(kFull, b4 ? val(i) : val(i + 16), 16);
-    float x8[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        x8[i] = (b3 ? x16[i + 8] : x16[i]) + __shfl_xor_sync(kFull, b3 ? x16[i] : x16[i + 8], 8);
-    float x4[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        x4[i] = (b2 ? x8[i + 4] : x8[i]) + __shfl_xor_sync(kFull, b2 ? x8[i] : x8[i + 4], 4);
-    float x2[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-        x2[i] = (b1 ? x4[i + 2] : x4[i]) + __shfl_xor_sync(kFull, b1 ? x4[i] : x4[i + 2], 2);
-    return (b0 ? x2[1] : x2[0]) + __shfl_xor_sync(kFull, b0 ? x2[0] : x2[1], 1);
+    if (owner && ci >= 4) atomicAdd(&sVc[(threadIdx.x >> 4) * kMaxCand + ci], val);
 }
 
 // Warp sums of the contracted bucket values of group G0 (values 32 G0 ..
@@ -141,10 +121,9 @@ __device__ __forceinline__ float ctr_group(float ae, float ao, float p2, const f
 // The owned step tables are lane-contiguous float4 copies in shared memory
 // (conflict-free, both halves broadcast).  Lane buckets accumulate in
 // registers and are folded into per-warp FP64 shared buckets every 8 batches.
-// The forward partials and the step buckets are reduced in a fixed order (bit
-// for bit reproducible); the PSD buckets V are scattered with FP64 atomics
-// across the tiles of a CUT (and FP32 shared atomics for F_c candidates past
-// the fourth), so dT/dP is reproducible to FP64 rounding, not bit for bit.
+// Every reduction has a fixed order (the PSD buckets go to the tile's own row,
+// summed per CUT in tile order by k_v_reduce), so results are bit for bit
+// reproducible.
 // ---------------------------------------------------------------------------
 #ifndef ISRS_ADJ_MIN_BLOCKS
 #define ISRS_ADJ_MIN_BLOCKS 3   // resident blocks per SM the register budget is sized for
@@ -165,7 +144,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     RowF *rows = reinterpret_cast<RowF *>(sB + nw * K * 16);             // [G]
     __shared__ PieceConst<float> kc;
     __shared__ ChebTabN<kCtr> ct;
-    __shared__ float sVc[kMaxCand];
+    __shared__ float sVc[16 * kMaxCand];    // PSD buckets of candidates past the fourth, per half-warp
     __shared__ double scratch[32];
     __shared__ int s_item;
     // small-phase points of contracted candidates: per-warp moment sums (FP32
@@ -181,7 +160,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     for (int t = threadIdx.x; t < 8 * kCtr * kCtrS; t += blockDim.x) (&sYf[0][0][0])[t] = 0.0f;
     for (int t = threadIdx.x; t < 128; t += blockDim.x) sC[t] = make_double2(0.0, 0.0);
     for (int t = threadIdx.x; t < nw * K * 16; t += blockDim.x) sB[t] = make_double2(0.0, 0.0);
-    if (threadIdx.x < kMaxCand) sVc[threadIdx.x] = 0.0f;
+    for (int t = threadIdx.x; t < 16 * kMaxCand; t += blockDim.x) sVc[t] = 0.0f;
 
     const float c3 = (float)(kPi * qp.beta3);
     const float c4 = (float)(2.0 * kPi * kPi / 3.0 * qp.beta4);
@@ -211,7 +190,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
         const int it = s_item;
         if (it >= qp.n_items) break;
         const DevItem item = qp.items[it];
-        const int slot = ap.item_slot[it];
+        double *Vrow = ap.V + (size_t)it * ap.n_ch;     // this tile's PSD buckets
+        for (int c = threadIdx.x; c < ap.n_ch; c += blockDim.x) Vrow[c] = 0.0;
         if (item.prof != cur_prof) {
             const float2 *st = qp.step_f + (size_t)item.prof * M;
             for (int m = threadIdx.x; m < M; m += blockDim.x) {
@@ -506,19 +486,19 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             const double t0 = block_sum_d((double)fa.v0, scratch);
             const double t1 = block_sum_d((double)fa.v1, scratch);
             const double t2 = block_sum_d((double)fa.v2, scratch);
-            const double t3 = block_sum_d((double)fa.v3, scratch);
+            const double t3 = block_sum_d((double)fa.v3, scratch);   // syncs: sVc complete
             acc += (double)mult * ptot;
-            if (threadIdx.x == 0) {
-                double *Vrow = ap.V + (size_t)slot * ap.n_ch;
-                atomicAdd(&Vrow[pc.a], (double)mult * ptot);
-                atomicAdd(&Vrow[pc.b], (double)mult * ptot);
+            if (threadIdx.x == 0) {                 // one thread, in order (the row is this tile's)
+                Vrow[pc.a] += (double)mult * ptot;
+                Vrow[pc.b] += (double)mult * ptot;
                 for (int c = 0; c < kc.nc; ++c) {
-                    const double vc = c == 0 ? t0 : c == 1 ? t1 : c == 2 ? t2 : c == 3 ? t3 : (double)sVc[c];
-                    if (vc != 0.0) atomicAdd(&Vrow[pc.c_lo + c], (double)mult * vc);
+                    double vc = c == 0 ? t0 : c == 1 ? t1 : c == 2 ? t2 : c == 3 ? t3 : 0.0;
+                    for (int hw = 0; hw < 2 * nw; ++hw) vc += (double)sVc[hw * kMaxCand + c];
+                    Vrow[pc.c_lo + c] += (double)mult * vc;
                 }
             }
             __syncthreads();
-            if (threadIdx.x < kMaxCand) sVc[threadIdx.x] = 0.0f;
+            for (int t = threadIdx.x; t < 16 * kMaxCand; t += blockDim.x) sVc[t] = 0.0f;
         }
         // tile outputs: the forward partial and the step buckets
         if (threadIdx.x == 0) qp.partial[it] = acc;
@@ -565,6 +545,21 @@ __global__ void __launch_bounds__(256) k_ybar(ChainParams cp)
         const double hfb = cp.n_spans * nf * kHPlanck * ((cp.ch_frel[i] + cp.f_ref) * 1e12) * (B * 1e12);
         cp.ybar[i] = dTds * dsdN * (16.0 / 27.0) * g * g * B;
         cp.aase[i] = dTds * dsdN * (cp.pase[i] + hfb);    // dT/dASE * dASE/d ln G
+    }
+}
+
+// V[s][j] = the PSD buckets of slot s's tiles (regular, then MCI), summed in
+// tile order; one block per slot, one thread per channel.
+__global__ void __launch_bounds__(256) k_v_reduce(ChainParams cp)
+{
+    const int s = blockIdx.x, n = cp.n_ch;
+    const int2 r1 = cp.slot_items[s];
+    const int2 r2 = cp.slot_items2 ? cp.slot_items2[s] : make_int2(0, 0);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double v = 0.0;
+        for (int t = r1.x; t < r1.y; ++t) v += cp.Vt[(size_t)t * n + j];
+        for (int t = r2.x; t < r2.y; ++t) v += cp.Vt[(size_t)(cp.n_items_reg + t) * n + j];
+        cp.Vs[(size_t)s * n + j] = v;
     }
 }
 
@@ -740,6 +735,8 @@ cudaError_t launch_chain(const ChainParams &cp, cudaStream_t st)
     k_ybar<<<1, 256, 0, st>>>(cp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    k_v_reduce<<<cp.n_slots, 256, 0, st>>>(cp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_adj_reduce<<<cp.n_steps, 256, 0, st>>>(cp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_chain<<<1, 256, 0, st>>>(cp);

@@ -119,7 +119,6 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MCI_MIN_BLOCKS) k_quad_adj_mci(A
         const int poff = qp.prof_ch_off[item.prof];
         const int n = qp.plan_n[plan];
         const int i = item.cut;
-        const int slot = ap.item_slot[it];
         if (item.prof != cur_prof) {
             // lane-contiguous owned step tables; padding steps repeat the last edge
             const float2 *st = qp.step_f + (size_t)item.prof * M;
@@ -355,11 +354,11 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MCI_MIN_BLOCKS) k_quad_adj_mci(A
         // item outputs: the forward partial, the PSD buckets and the step buckets
         const double tot = block_sum_d((double)sum - (double)comp, scratch);   // syncs the block
         if (threadIdx.x == 0) qp.partial[it] = tot;
-        double *Vrow = ap.V + (size_t)slot * ap.n_ch;
+        double *Vrow = ap.V + (size_t)it * ap.n_ch;     // this tile's own row (k_v_reduce sums them)
         for (int c = threadIdx.x; c < n; c += blockDim.x) {
             double v = 0.0;
             for (int w = 0; w < nw; ++w) v += (double)sV[w * nmax + c];
-            if (v != 0.0) atomicAdd(&Vrow[c], v);
+            Vrow[c] = v;
         }
         for (int m = threadIdx.x; m < M; m += blockDim.x) {
             const int ln = m / K, kk = m - ln * K;

@@ -16,8 +16,19 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// nearest integer of t (round to nearest even): one FRND instruction, exact
-// for every FP32 value; t - rint(t) is then exact (Sterbenz).
+// Nearest integer of t (round to nearest even), two ways:
+//  * round_magic: two adds on the FMA pipe, exact for |t| < 2^22;
+//  * round_nearest: one FRND, exact for every FP32 value, issued to the
+//    XU pipe that also runs the MUFU (sin, cos, ex2) instructions.
+// The forward kernels (3 MUFU per step, XU ~40 % busy) measured faster with
+// round_magic (FRND raised XU to ~49 % and added mio_throttle stalls); the
+// adjoint walks (XU ~25 % busy, issue-bound) with round_nearest.  Either way
+// t - round(t) is exact (Sterbenz).
+__device__ __forceinline__ float round_magic(float t)
+{
+    return __fadd_rn(__fadd_rn(t, 12582912.0f), -12582912.0f);
+}
+
 __device__ __forceinline__ float round_nearest(float t)
 {
     return rintf(t);
@@ -47,6 +58,32 @@ __device__ __forceinline__ double block_sum_d(double v, double *scratch)
     r = scratch[0];
     __syncthreads();
     return r;
+}
+
+// Warp sum of 32 values per lane in one butterfly: each level halves the
+// values a lane carries, and lane L ends with the sum of value L.  val(i)
+// gives this lane's value i.
+template <typename F>
+__device__ __forceinline__ float butterfly32(const F &val, int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+    float x16[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        x16[i] = (b4 ? val(i + 16) : val(i)) + __shfl_xor_sync(0xffffffffu, b4 ? val(i) : val(i + 16), 16);
+    float x8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        x8[i] = (b3 ? x16[i + 8] : x16[i]) + __shfl_xor_sync(0xffffffffu, b3 ? x16[i] : x16[i + 8], 8);
+    float x4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        x4[i] = (b2 ? x8[i + 4] : x8[i]) + __shfl_xor_sync(0xffffffffu, b2 ? x8[i] : x8[i + 4], 4);
+    float x2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        x2[i] = (b1 ? x4[i + 2] : x4[i]) + __shfl_xor_sync(0xffffffffu, b1 ? x4[i] : x4[i + 2], 2);
+    return (b0 ? x2[1] : x2[0]) + __shfl_xor_sync(0xffffffffu, b0 ? x2[0] : x2[1], 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -123,18 +160,23 @@ __device__ __forceinline__ void piece_consts(const QuadParams &qp, const DevPiec
     }
 }
 
+// sin and cos of 2 pi t for |t| < 2^22 revolutions (Xu: round with FRND)
+template <bool Xu = false>
 __device__ __forceinline__ void sincos_rev(float t, float &sn, float &cs)
 {
-    const float fr = __fadd_rn(t, -round_nearest(t));
+    const float fr = __fadd_rn(t, -(Xu ? round_nearest(t) : round_magic(t)));
     __sincosf(fr * 6.283185307179586f, &sn, &cs);
 }
 
+// e^{j phi z}: the phase phi (hi + lo) in revolutions as an error-free
+// float-float product, reduced to [-1/2, 1/2] (Xu: round with FRND)
+template <bool Xu = false>
 __device__ __forceinline__ void phasor_rev_ff(float phi, float hi, float lo, float &sn, float &cs)
 {
     const float th = phi * hi;
     float tl = fmaf(phi, hi, -th);
     tl = fmaf(phi, lo, tl);
-    const float fr = __fadd_rn(th, -round_nearest(th)) + tl;
+    const float fr = __fadd_rn(th, -(Xu ? round_nearest(th) : round_magic(th))) + tl;
     __sincosf(fr * 6.283185307179586f, &sn, &cs);
 }
 
@@ -232,6 +274,18 @@ __device__ __forceinline__ float exp2_split(double x)
     if (xr < -126.0) return 0.0f;
     const float sc = __int_as_float(((int)fmin(xr, 127.0) + 127) << 23);
     return ex2_approx((float)(x - xr)) * sc;
+}
+
+// The Chebyshev coefficients of e^{a x} on [-1, 1]: I0(a), 2 I1(a), 2 I2(a),
+// 2 I3(a) from their power series (|a| <= 0.05: the terms kept are exact to
+// FP32 rounding).
+__device__ __forceinline__ float4 bessel_b4(float a)
+{
+    const float t = 0.5f * a, t2 = t * t;
+    return make_float4(1.0f + t2 * (1.0f + t2 * (0.25f + t2 * (1.0f / 36.0f))),              // I0
+                       2.0f * t * (1.0f + t2 * (0.5f + t2 * (1.0f / 12.0f))),                 // 2 I1
+                       2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 * (1.0f / 48.0f))),         // 2 I2
+                       2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
 }
 
 // Moment sums of one candidate for n in [N0, N0 + NN): s[n][k] = sum_m W_k(m) g_n(m).

@@ -50,7 +50,7 @@ __device__ __forceinline__ float walk_direct(const float4 *o0s, float wq, float 
     for (int k = 0; k < K; ++k) {
         const float4 o = o0s[k * 16];
         float sn, cs;
-        sincos_rev(phr * o.z, sn, cs);
+        sincos_rev<true>(phr * o.z, sn, cs);
         float lp = fmaf(o.y, fc, o.x);
         lp = fmaf(-at, o.z, lp);
         const float amp = ex2_approx(lp) * sinc_poly(hph * o.w);
@@ -84,8 +84,8 @@ __device__ __forceinline__ float walk_tele(const float4 *o0s, const float4 *o1s,
         const float4 a = o0s[k * 16];
         const float4 b = o1s[k * 16];
         float sn, cs;
-        if (Wide) phasor_rev_ff_wide(ph, b.x, b.y, sn, cs);
-        else phasor_rev_ff(ph, b.x, b.y, sn, cs);
+        if (Wide) phasor_rev_ff_wide<true>(ph, b.x, b.y, sn, cs);
+        else phasor_rev_ff<true>(ph, b.x, b.y, sn, cs);
         float lp = fmaf(a.y, fc, b.z);
         lp = fmaf(-at, a.z, lp);
         const float pm = ex2_approx(lp);

@@ -142,15 +142,18 @@ __device__ __forceinline__ float zsum_tele_fc(float phi, float Fc, const float4 
 }
 
 // As phasor_rev_ff, for phases far beyond 2^22 revolutions (the MCI cells):
-// th - rint(th) is exact at any magnitude, but tl can then exceed one
-// revolution, so the sum is reduced once more.
+// once |phi z / 2pi| >= 2^22 the first magic-number rounding leaves an
+// integer (or half-integer) on top of the fraction, and FRND's exact
+// th - rint(th) can leave tl beyond one revolution; a second rounding of the
+// sum removes either.
+template <bool Xu = false>
 __device__ __forceinline__ void phasor_rev_ff_wide(float phi, float hi, float lo, float &sn, float &cs)
 {
     const float th = phi * hi;
     float tl = fmaf(phi, hi, -th);
     tl = fmaf(phi, lo, tl);
-    float fr = __fadd_rn(th, -round_nearest(th)) + tl;
-    fr = __fadd_rn(fr, -round_nearest(fr));
+    float fr = __fadd_rn(th, -(Xu ? round_nearest(th) : round_magic(th))) + tl;
+    fr = __fadd_rn(fr, -(Xu ? round_nearest(fr) : round_magic(fr)));
     __sincosf(fr * 6.283185307179586f, &sn, &cs);
 }
 

@@ -560,15 +560,6 @@ __device__ __forceinline__ float zsum_tele_t(float phi, float da, float db, cons
 // ---------------------------------------------------------------------------
 constexpr int kTabMom = kChebMomA;
 
-__device__ __forceinline__ float4 bessel_b4(float a)
-{
-    const float t = 0.5f * a, t2 = t * t;
-    return make_float4(1.0f + t2 * (1.0f + t2 * (0.25f + t2 * (1.0f / 36.0f))),              // I0
-                       2.0f * t * (1.0f + t2 * (0.5f + t2 * (1.0f / 12.0f))),                 // 2 I1
-                       2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 * (1.0f / 48.0f))),         // 2 I2
-                       2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
-}
-
 // Every thread calls after tab_setup_f (synced); returns whether the piece's
 // small-phase points use the contraction.  sW: [M][4] float4 scratch,
 // sG: [M][4 kZsG] moments, sC: [nc][kTabMom][4] float4, s_flag: shared int.

@@ -22,8 +22,14 @@
 // K = ceil(M/16) consecutive steps, keeps their terms t_m in registers, the
 // half sums them into S with shuffles, and the same registers give
 // d|S|^2/d ln p_m = 2 Re(conj(S) t_m).  FP32 lane buckets are folded into
-// FP64 shared buckets every 8 batches; at the end of a candidate the block
-// reduces them and scatters to the channel tables with FP64 atomics.
+// FP64 shared buckets every 8 batches.  The same pass sums the forward value
+// w W |S|^2 (the tile's partial of Sigma_i), so no separate forward runs.
+// The buckets are not yet weighted by dT/dSigma_i (unknown until every tile
+// of CUT i is done): at the end of a candidate the block adds them, in
+// order, into the rows of its own tile (one row per plan channel the tile
+// touches, owned by this block alone), and k_tab_gather applies
+// dT/dSigma_i and sums each channel's rows in tile order.  No atomics: the
+// gradient is reproducible bit for bit.
 #include <cuda_runtime.h>
 
 #include "isrs_internal.cuh"
@@ -54,6 +60,117 @@ __device__ __forceinline__ float half_sum_t(float v)
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(kFullT, v, o, 16);
     return v;
+}
+
+// ---------------------------------------------------------------------------
+// Contracted small phase (|phi| L <= 2) with the tabulated profile.  As in
+// the forward (raman.cu), S of a point in candidate c follows from 11 moments
+// about the span centre, nu_n(x, y) = sum_{k,l<=3} C_nkl T_k(x) T_l(y), with
+// x = da / h_a, y = db / h_b the offsets inside channels a and b.  Its bucket
+// terms d|S|^2/d ln p_m = w_m(x, y) sum_n fold_n g_n(m) al_n, al_n = 2 (A|B)
+// phi^n (A even, B odd orders), need w_m(x, y) = base_m e^{alpha_m x + beta_m y}
+// at the point; expanded to total degree 3 in (x, y) (|alpha|, |beta| <= 0.05:
+// truncation below (0.1)^4/4! = 4e-6 of the term), the buckets of a batch are
+// sums of cp al_n x^i y^j over its points, i + j <= 4 (the R_a, R_b buckets
+// carry one more power of x or y): 15 monomials per order, n <= 5 for a batch
+// whose phases are all |phi| L <= 0.2 (90 values, three warp butterflies),
+// n <= 10 otherwise (165 values, six).  The buckets of every step follow once
+// per candidate.
+// ---------------------------------------------------------------------------
+constexpr int kTabMom = 11;                       // nu_0 .. nu_10
+constexpr int kTabMono = 15;                      // x^i y^j, i + j <= 4
+constexpr int kTabShortN = 6 * kTabMono;          // n <= 5
+constexpr int kTabCtrN = kTabMom * kTabMono;      // n <= 10
+constexpr int kTabCtrS = 192;                     // slots (six butterflies)
+constexpr float kTabShortPhiL = 0.2f;
+
+// position of x^i y^j in the monomial list: by total degree, then by j
+__host__ __device__ constexpr int mono_idx(int i, int j) { return (i + j) * (i + j + 1) / 2 + j; }
+
+// The forward's contracted coefficients of one candidate (its table rows Q):
+// C[n][k][l] = fold_n sum_m base_m b_k(alpha_m) b_l(beta_m) g_n(m), stored as
+// sCc[n * 4 + k] = float4 over l.  sW: [M][4] float4 scratch.  Every thread
+// calls; the block is synchronised on return.
+__device__ void tab_adj_coeffs(const QuadParams &qp, const float4 *Q, float ha, float hb, float4 *sW, float4 *sCc)
+{
+    const int M = qp.n_steps;
+    const float ln2 = 0.69314718f;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float4 q = Q[m];
+        const float base = ex2_approx(q.x);
+        const float4 bk = bessel_b4(q.y * ha * ln2), bl = bessel_b4(q.z * hb * ln2);
+        const float bkv[4] = {bk.x, bk.y, bk.z, bk.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float wk = base * bkv[k];
+            sW[m * 4 + k] = make_float4(wk * bl.x, wk * bl.y, wk * bl.z, wk * bl.w);
+        }
+    }
+    __syncthreads();
+    const float *g = reinterpret_cast<const float *>(qp.zs_g);   // kZsG float4 = 20 floats per step
+    for (int t = threadIdx.x; t < kTabMom * 16; t += blockDim.x) {
+        const int n = t >> 4, k = (t >> 2) & 3, l = t & 3;
+        float sum = 0.0f, comp = 0.0f;
+        for (int m = 0; m < M; ++m) {
+            const float4 w = sW[m * 4 + k];
+            const float wl = l == 0 ? w.x : (l == 1 ? w.y : (l == 2 ? w.z : w.w));
+            const float y = wl * g[m * 4 * kZsG + n] - comp;
+            const float tt = sum + y;
+            comp = (tt - sum) - y;
+            sum = tt;
+        }
+        reinterpret_cast<float *>(sCc + n * 4 + k)[l] = sum * (float)cheb_fold(n);
+    }
+    __syncthreads();
+}
+
+// A and B (|S|^2 = A^2 + B^2) of a contracted point at offsets (x, y).
+__device__ __forceinline__ void tab_adj_AB(const float4 *sCc, float x, float y, float phi, float &A, float &B)
+{
+    const float Tx2 = fmaf(2.0f * x, x, -1.0f), Tx3 = fmaf(2.0f * x, Tx2, -x);
+    const float Ty2 = fmaf(2.0f * y, y, -1.0f), Ty3 = fmaf(2.0f * y, Ty2, -y);
+    float nu[kTabMom];
+#pragma unroll
+    for (int n = 0; n < kTabMom; ++n) {
+        float r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 c = sCc[n * 4 + k];
+            r[k] = fmaf(c.w, Ty3, fmaf(c.z, Ty2, fmaf(c.y, y, c.x)));
+        }
+        nu[n] = fmaf(r[3], Tx3, fmaf(r[2], Tx2, fmaf(r[1], x, r[0])));
+    }
+    cheb_AB<kTabMom>(nu, phi, A, B);
+}
+
+// Warp sums of the contracted bucket values of group G0 (values 32 G0 ..
+// 32 G0 + 31 of the first nv): value v = al_n mono_t with n = v / 15,
+// t = v mod 15, al_n = ae (phi^2)^{n/2} (n even) or ao (phi^2)^{(n-1)/2} (n
+// odd; ao carries one phi).  A group spans at most three orders.
+template <int G0>
+__device__ __forceinline__ float tab_ctr_group(float ae, float ao, float p2, const float (&mono)[kTabMono], int nv,
+                                               int lane)
+{
+    constexpr int N0 = (32 * G0) / kTabMono;
+    float pw = 1.0f;
+#pragma unroll
+    for (int i = 0; i < N0 / 2; ++i) pw *= p2;
+    float a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int n = N0 + j;
+        const int extra = ((N0 & 1) + j) >> 1;
+        float v = ((n & 1) ? ao : ae) * pw;
+        if (extra >= 1) v *= p2;
+        if (extra >= 2) v *= p2;
+        a[j] = v;
+    }
+    return butterfly32(
+        [&](int v) {
+            const int va = 32 * G0 + v;
+            return va < nv ? a[va / kTabMono - N0] * mono[va % kTabMono] : 0.0f;
+        },
+        lane);
 }
 
 // Per-piece table (the forward's layout): {A + log2 dz, Sa, Sb, A} in log2 units.
@@ -94,7 +211,7 @@ __device__ __forceinline__ float walk_direct_t(const float4 *oq, const float4 *o
         const float4 q = oq[k * 16];
         const float4 z = oz[k * 16];
         float sn, cs;
-        sincos_rev(phr * z.x, sn, cs);
+        sincos_rev<true>(phr * z.x, sn, cs);
         float lp = fmaf(q.y, da, q.x);
         lp = fmaf(q.z, db, lp);
         const float amp = ex2_approx(lp) * sinc_poly_t(hph * z.z);
@@ -127,7 +244,7 @@ __device__ __forceinline__ float walk_tele_t(const float4 *oq, const float4 *oe,
         const float4 q = oq[k * 16];
         const float4 e = oe[k * 16];
         float sn, cs;
-        phasor_rev_ff(ph, e.x, e.y, sn, cs);
+        phasor_rev_ff<true>(ph, e.x, e.y, sn, cs);
         float lp = fmaf(q.y, da, q.w);
         lp = fmaf(q.z, db, lp);
         const float pm = ex2_approx(lp);
@@ -226,10 +343,18 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
     float4 *sL = sOE + K * 16;                                      // [nw][3][kListCapT] {cp, phi, da, db}
     double *sB = reinterpret_cast<double *>(sL + nw * 3 * kListCapT);   // [nw][3][K][16] FP64 buckets
     RowF *rows = reinterpret_cast<RowF *>(sB + (size_t)nw * 3 * K * 16);   // [G]
+    float4 *sW = reinterpret_cast<float4 *>(rows + G);                     // [M][4] contraction scratch
     __shared__ PieceConst<float> kc;
     __shared__ float s_d0[2];
     __shared__ double scratch[32];
     __shared__ int s_item;
+    // contracted small phase: the candidate's forward coefficients, per-warp
+    // bucket sums (FP32 between folds, FP64 after) and their block totals
+    __shared__ float4 sCc[kTabMom * 4];
+    __shared__ float sYt[8][kTabCtrS];
+    __shared__ double sYd[8][kTabCtrN];
+    __shared__ double sZ[kTabCtrN];
+    __shared__ float s_amax;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int l16 = lane & 15, half = lane >> 4;
@@ -250,6 +375,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
         }
     }
     for (int t = threadIdx.x; t < nw * 3 * K * 16; t += blockDim.x) sB[t] = 0.0;
+    for (int t = threadIdx.x; t < 8 * kTabCtrS; t += blockDim.x) (&sYt[0][0])[t] = 0.0f;
+    for (int t = threadIdx.x; t < 8 * kTabCtrN; t += blockDim.x) (&sYd[0][0])[t] = 0.0;
 
     const float c3 = (float)(kPi * qp.beta3);
     const float c4 = (float)(2.0 * kPi * kPi / 3.0 * qp.beta4);
@@ -257,8 +384,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
     const float m4pi2 = (float)(-4.0 * kPi * kPi);
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
+    const float phi_cheb = kChebPhiLA / qp.L;
     const float invG = 1.0f / (float)G;
     const float4 *oq = sOQ + l16, *oz = sOZ + l16, *oe = sOE + l16;
+    float *Yw = sYt[warp];
     float4 *Ls = sL + warp * 3 * kListCapT;
     float4 *Ld = Ls + kListCapT;
     float4 *Lt = Ld + kListCapT;
@@ -272,7 +401,14 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
         const int it = s_item;
         if (it >= qp.n_items) break;
         const DevItem item = qp.items[it];
-        const float ybar = (float)ap.ybar[ap.item_slot[it]];
+        // this tile's rows start at zero
+        const int row0 = ap.row_off[it];
+        const int nrow = ap.row_off[it + 1] - row0;
+        double2 *trows = ap.rows + (size_t)row0 * M;
+        double *trowsV = ap.rowsV + row0;
+        for (int t = threadIdx.x; t < nrow * M; t += blockDim.x) trows[t] = make_double2(0.0, 0.0);
+        for (int t = threadIdx.x; t < nrow; t += blockDim.x) trowsV[t] = 0.0;
+        double acc = 0.0;           // the tile's partial of Sigma_i
         for (int kp = item.piece0; kp < item.piece1; ++kp) {
             const DevPiece pc = qp.pieces[kp];
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
@@ -285,7 +421,23 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
             }
             __syncthreads();
             tab_setup_adj(qp, pc, kc.nc, sQ);
+            // the contraction applies when the in-channel exponents are small
+            const float ha = (float)(0.5 * qp.ch_B[coff + pc.a]), hb = (float)(0.5 * qp.ch_B[coff + pc.b]);
+            if (threadIdx.x == 0) s_amax = 0.0f;
             __syncthreads();
+            {
+                float amax = 0.0f;
+                for (int t = threadIdx.x; t < kc.nc * M; t += blockDim.x) {
+                    const float4 q = sQ[t];
+                    amax = fmaxf(amax, fmaxf(fabsf(q.y * ha), fabsf(q.z * hb)) * 0.69314718f);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(kFullT, amax, o));
+                if (lane == 0) atomicMax(reinterpret_cast<unsigned *>(&s_amax), __float_as_uint(amax));
+            }
+            __syncthreads();
+            const bool cheb = qp.zs_g != nullptr && s_amax <= kChebMaxA;
+            const float invha = 1.0f / ha, invhb = 1.0f / hb;
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2, mult = kc.mult;
             const float da0 = s_d0[0], db0 = s_d0[1];
             const float three_fi2 = 3.0f * fi * fi;
@@ -297,6 +449,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                     const int k = t >> 4, l = t & 15, m = l * K + k;
                     sOQ[k * 16 + l] = m < M ? sQ[cc * M + m] : make_float4(kPadLog2T, 0.f, 0.f, kPadLog2T);
                 }
+                if (cheb) tab_adj_coeffs(qp, sQ + cc * M, ha, hb, sW, sCc);   // syncs the block
                 __syncthreads();
                 float R[K], Ra[K], Rb[K];
 #pragma unroll
@@ -309,6 +462,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                     const int q = qb + lane;
                     float cp = 0.0f, phi = 0.0f, da = 0.0f, db = 0.0f;
                     int cls = -1;
+                    bool ctr = false;            // contracted small-phase point
+                    float cA = 0.0f, cB = 0.0f, cx = 0.0f, cy = 0.0f;
                     if (q < npts) {
                         const int r = (int)(((float)q + 0.5f) * invG);
                         const int j = q - r * G;
@@ -332,10 +487,43 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                                                            three_fi2);
                                     phi = m4pi2 * f1 * f2 * br;
                                     const float aphi = fabsf(phi);
-                                    cls = aphi <= phi_small ? kClsSmallT : (aphi <= phi_direct ? kClsDirectT : kClsTeleT);
-                                    cp = mult * rw.w * W * array_factor_f(phi, qp) * ybar;
+                                    cp = mult * rw.w * W * array_factor_f(phi, qp);
+                                    if (cheb && aphi <= phi_cheb) {
+                                        cx = da * invha;
+                                        cy = db * invhb;
+                                        tab_adj_AB(sCc, cx, cy, phi, cA, cB);
+                                        vsum += cp * fmaf(cA, cA, cB * cB);
+                                        ctr = true;
+                                    } else {
+                                        cls = aphi <= phi_small ? kClsSmallT
+                                                                : (aphi <= phi_direct ? kClsDirectT : kClsTeleT);
+                                    }
                                 }
                             }
+                        }
+                    }
+                    // contracted points: their bucket sums, as many orders as the batch needs
+                    if (__ballot_sync(kFullT, ctr)) {
+                        const unsigned phl =
+                            __reduce_max_sync(kFullT, __float_as_uint(ctr ? fabsf(phi) * qp.L : 0.0f));
+                        const int nv = __uint_as_float(phl) <= kTabShortPhiL ? kTabShortN : kTabCtrN;
+                        const float xp[5] = {1.0f, cx, cx * cx, cx * cx * cx, (cx * cx) * (cx * cx)};
+                        const float yp[5] = {1.0f, cy, cy * cy, cy * cy * cy, (cy * cy) * (cy * cy)};
+                        float mono[kTabMono];
+#pragma unroll
+                        for (int d = 0; d <= 4; ++d)
+#pragma unroll
+                            for (int j = 0; j <= d; ++j) mono[mono_idx(d - j, j)] = xp[d - j] * yp[j];
+                        const float ae = ctr ? 2.0f * cp * cA : 0.0f;
+                        const float ao = ctr ? 2.0f * cp * cB * phi : 0.0f;
+                        const float p2 = phi * phi;
+                        Yw[lane] += tab_ctr_group<0>(ae, ao, p2, mono, nv, lane);
+                        Yw[lane + 32] += tab_ctr_group<1>(ae, ao, p2, mono, nv, lane);
+                        Yw[lane + 64] += tab_ctr_group<2>(ae, ao, p2, mono, nv, lane);
+                        if (nv > kTabShortN) {
+                            Yw[lane + 96] += tab_ctr_group<3>(ae, ao, p2, mono, nv, lane);
+                            Yw[lane + 128] += tab_ctr_group<4>(ae, ao, p2, mono, nv, lane);
+                            Yw[lane + 160] += tab_ctr_group<5>(ae, ao, p2, mono, nv, lane);
                         }
                     }
                     // append to the form's list
@@ -392,6 +580,10 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                             }
                             R[k] = Ra[k] = Rb[k] = 0.0f;
                         }
+                        for (int t = lane; t < kTabCtrN; t += 32) {
+                            sYd[warp][t] += (double)Yw[t];
+                            Yw[t] = 0.0f;
+                        }
                     }
                     __syncwarp();          // the next batch appends to the lists
                 }
@@ -425,10 +617,32 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                         myB[(2 * K + k) * 16 + l16] += (double)r2;
                     }
                 }
+                for (int t = lane; t < kTabCtrN; t += 32) {
+                    sYd[warp][t] += (double)Yw[t];
+                    Yw[t] = 0.0f;
+                }
                 const double vtot = block_sum_d((double)vsum, scratch);   // syncs the block
+                acc += vtot;
+                if (cheb) {
+                    // the contracted points' bucket sums of the whole block, in warp order
+                    for (int t = threadIdx.x; t < kTabCtrN; t += blockDim.x) {
+                        double z = 0.0;
+                        for (int w = 0; w < nw; ++w) {
+                            z += sYd[w][t];
+                            sYd[w][t] = 0.0;
+                        }
+                        sZ[t] = z;
+                    }
+                    __syncthreads();
+                }
                 const int c = pc.c_lo + cc;
                 const double D = (qp.ch_frel[coff + pc.a] + qp.ch_frel[coff + pc.b]) -
                                  (fi_d + qp.ch_frel[coff + c]);
+                // the tile's rows: each thread owns its steps m, so the adds are
+                // ordered (rows may coincide, e.g. a == CUT: same thread, in turn)
+                const int4 pr = ap.prow[kp];
+                double2 *ra = trows + (size_t)pr.x * M, *rb = trows + (size_t)pr.y * M;
+                double2 *ri = trows + (size_t)pr.z * M, *rc = trows + (size_t)(pr.w + cc) * M;
                 for (int m = threadIdx.x; m < M; m += blockDim.x) {
                     const int ln = m / K, kk = m - ln * K;
                     double r0 = 0.0, r1 = 0.0, r2 = 0.0;
@@ -441,26 +655,101 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                         b[(1 * K + kk) * 16 + ln] = 0.0;
                         b[(2 * K + kk) * 16 + ln] = 0.0;
                     }
-                    if (r0 == 0.0 && r1 == 0.0 && r2 == 0.0) continue;
-                    double2 *g = ap.gAB;
-                    atomicAdd(&g[(size_t)pc.a * M + m].x, 0.5 * r0);
-                    atomicAdd(&g[(size_t)pc.b * M + m].x, 0.5 * r0);
-                    atomicAdd(&g[(size_t)c * M + m].x, 0.5 * r0);
-                    atomicAdd(&g[(size_t)pc.cut * M + m].x, -0.5 * r0);
-                    atomicAdd(&g[(size_t)pc.a * M + m].y, 0.5 * r1);
-                    atomicAdd(&g[(size_t)pc.b * M + m].y, 0.5 * r2);
-                    atomicAdd(&g[(size_t)c * M + m].y, 0.5 * (D * r0 + r1 + r2));
+                    if (cheb) {
+                        // d|S|^2/d ln p_m of the contracted points: w_m(x, y) =
+                        // base e^{al x + be y} to total degree 3, so the three buckets are
+                        // base sum_n fold_n g_n(m) sum_{i+j<=3} al^i be^j / (i! j!) Z_n(x^i y^j),
+                        // with one more power of x (R_a, times h_a) or y (R_b, times h_b)
+                        const float4 q = sQ[cc * M + m];
+                        const float al = q.y * ha * 0.69314718f, be = q.z * hb * 0.69314718f;
+                        float cij[10];
+                        {
+                            const float ap[4] = {1.0f, al, al * al * 0.5f, al * al * al * (1.0f / 6.0f)};
+                            const float bp[4] = {1.0f, be, be * be * 0.5f, be * be * be * (1.0f / 6.0f)};
+#pragma unroll
+                            for (int d = 0; d <= 3; ++d)
+#pragma unroll
+                                for (int j = 0; j <= d; ++j) cij[mono_idx(d - j, j)] = ap[d - j] * bp[j];
+                        }
+                        const float *gm = reinterpret_cast<const float *>(qp.zs_g + kZsG * m);
+                        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+                        for (int n = 0; n < kTabMom; ++n) {
+                            const double *Z = sZ + n * kTabMono;
+                            float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+#pragma unroll
+                            for (int d = 0; d <= 3; ++d)
+#pragma unroll
+                                for (int j = 0; j <= d; ++j) {
+                                    const int i = d - j;
+                                    const float c = cij[mono_idx(i, j)];
+                                    t0 = fmaf(c, (float)Z[mono_idx(i, j)], t0);
+                                    t1 = fmaf(c, (float)Z[mono_idx(i + 1, j)], t1);
+                                    t2 = fmaf(c, (float)Z[mono_idx(i, j + 1)], t2);
+                                }
+                            const float gf = (float)cheb_fold(n) * gm[n];
+                            s0 = fmaf(gf, t0, s0);
+                            s1 = fmaf(gf, t1, s1);
+                            s2 = fmaf(gf, t2, s2);
+                        }
+                        const double base = (double)ex2_approx(q.x);
+                        r0 += base * (double)s0;
+                        r1 += base * (double)ha * (double)s1;
+                        r2 += base * (double)hb * (double)s2;
+                    }
+                    ra[m].x += 0.5 * r0;
+                    rb[m].x += 0.5 * r0;
+                    rc[m].x += 0.5 * r0;
+                    ri[m].x -= 0.5 * r0;
+                    ra[m].y += 0.5 * r1;
+                    rb[m].y += 0.5 * r2;
+                    rc[m].y += 0.5 * (D * r0 + r1 + r2);
                 }
-                if (threadIdx.x == 0 && vtot != 0.0) {
-                    atomicAdd(&ap.gV[pc.a], vtot);
-                    atomicAdd(&ap.gV[pc.b], vtot);
-                    atomicAdd(&ap.gV[c], vtot);
+                if (threadIdx.x == 0) {
+                    trowsV[pr.x] += vtot;
+                    trowsV[pr.y] += vtot;
+                    trowsV[pr.w + cc] += vtot;
                 }
                 __syncthreads();
             }
             __syncthreads();
         }
+        if (threadIdx.x == 0) qp.partial[it] = acc;
     }
+}
+
+// dT/d{a_c, b_c}(m) and dT/d ln P_c (PSD): the rows of channel c from every
+// tile that touches it, weighted by dT/dSigma of the tile's CUT, in tile
+// order.  One block per plan channel.
+__global__ void __launch_bounds__(128) k_tab_gather(TabGatherParams gp)
+{
+    const int c = blockIdx.x, M = gp.n_steps;
+    const int e0 = gp.gath_off[c], e1 = gp.gath_off[c + 1];
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        double ga = 0.0, gb = 0.0;
+        for (int e = e0; e < e1; ++e) {
+            const int2 rs = gp.gath[e];
+            const double y = gp.ybar[gp.slot_cut[rs.y]];
+            const double2 v = gp.rows[(size_t)rs.x * M + m];
+            ga += y * v.x;
+            gb += y * v.y;
+        }
+        gp.gAB[(size_t)c * M + m] = make_double2(ga, gb);
+    }
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int e = e0; e < e1; ++e) {
+            const int2 rs = gp.gath[e];
+            v += gp.ybar[gp.slot_cut[rs.y]] * gp.rowsV[rs.x];
+        }
+        gp.gV[c] = v;
+    }
+}
+
+cudaError_t launch_tab_gather(const TabGatherParams &gp, cudaStream_t st)
+{
+    k_tab_gather<<<gp.n_ch, 128, 0, st>>>(gp);
+    return cudaGetLastError();
 }
 
 namespace {
@@ -492,7 +781,8 @@ size_t adjoint_tab_smem_bytes(int n_steps, int G, int nc_max, int block)
 {
     const int K = (n_steps + 15) / 16, nw = block / 32;
     return ((size_t)n_steps * nc_max + 3 * K * 16 + (size_t)nw * 3 * kListCapT) * sizeof(float4) +
-           (size_t)nw * 3 * K * 16 * sizeof(double) + (size_t)G * sizeof(RowF);
+           (size_t)nw * 3 * K * 16 * sizeof(double) + (size_t)G * sizeof(RowF) +
+           (size_t)n_steps * 4 * sizeof(float4);
 }
 
 int adjoint_tab_blocks_per_sm(int n_steps, int G, int nc_max, int block)

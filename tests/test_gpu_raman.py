@@ -151,9 +151,12 @@ def test_adjoint_vs_fd_of_fp64_path(eng, trx, photon):
     r = eng.grad(wl)
     fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], wl.P_W, range(5))
     _check(r["dT_dP"], fd)
+    # the gradient call's Sigma comes from its own fused pass, which sums the
+    # small phases per step (exact to FP32) where the forward kernel truncates
+    # the 11-moment series (< 5e-8): SNR and T agree to that truncation
     s = eng.snr(wl, precision=0)
     np.testing.assert_allclose(r["snr"], s["snr"], rtol=1e-6)
-    assert r["T"] == pytest.approx(s["T"], rel=1e-9)
+    assert r["T"] == pytest.approx(s["T"], rel=1e-7)
 
 
 def test_adjoint_vs_fd_of_oracle(eng, orc):
