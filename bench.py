@@ -617,10 +617,13 @@ def profile_case(kind: str) -> int:
     if kind == "adjoint":
         eng.grad(wl.with_(G=64), P=P)          # all 589 CUTs at G = 64 (~0.6 s)
     elif kind == "raman256":
-        # the same 148-ch subset with the Raman-ODE profile: tabulated forward + its adjoint
+        # the same 148-ch subset with the Raman-ODE profile: the gradient (fused
+        # tabulated forward + adjoint), then the tabulated forward alone (SNR)
         from paper_2401_18022_gb300 import workloads as W
         sub = W.raman(W.subset_plan(wl, np.arange(0, wl.n_ch, 4), "uwb-148ch-every4th"))
-        eng.grad(sub, P=torch.tensor(sub.P_W, dtype=torch.float64, device="cuda"))
+        Ps = torch.tensor(sub.P_W, dtype=torch.float64, device="cuda")
+        eng.grad(sub, P=Ps)
+        eng.snr(sub, P=Ps)
     elif kind == "mci256":
         # the 148-ch subset with every cell: SCI/XCI at G = 256, the MCI cells on an 8 x 8 grid
         from paper_2401_18022_gb300 import workloads as W

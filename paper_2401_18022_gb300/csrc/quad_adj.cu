@@ -54,7 +54,7 @@ constexpr int kShortN = 30;
 constexpr float kShortPhiL = 0.2f;
 constexpr int kMidN = 55;
 constexpr float kMidPhiL = 2.0f;
-constexpr int kFoldBatches = 8; // batches between FP64 folds of the FP32 accumulators
+constexpr int kFoldBatches = 256; // batches between FP64 folds of the FP32 accumulators (one per piece at G = 256)
 constexpr float kPadLog2 = -1000.0f;   // log2 weight of the padding steps (ex2 -> 0)
 
 // Forward-sum bookkeeping of one grid point: the point's owner (every lane
@@ -120,7 +120,9 @@ __device__ __forceinline__ float ctr_group(float ae, float ao, float p2, const f
 //     (or, at the end of the piece, is walked beside a zero-weight copy).
 // The owned step tables are lane-contiguous float4 copies in shared memory
 // (conflict-free, both halves broadcast).  Lane buckets accumulate in
-// registers and are folded into per-warp FP64 shared buckets every 8 batches.
+// registers and are folded into per-warp FP64 shared buckets every 256 batches
+// (once per piece at G = 256: FP32 sums of at most ~512 terms, and the FP64
+// pipe, ~1/64 of the FP32 rate on this GPU, stays nearly idle).
 // Every reduction has a fixed order (the PSD buckets go to the tile's own row,
 // summed per CUT in tile order by k_v_reduce), so results are bit for bit
 // reproducible.

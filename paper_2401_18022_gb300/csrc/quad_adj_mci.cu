@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kClsSmallM = 0, kClsDirectM = 1, kClsTeleM = 2;
 constexpr int kListCapM = 34;      // a form's list: one carried point + 32 new (+1 pad)
-constexpr int kFoldBatchesM = 8;   // batches between FP64 folds of the register buckets
+constexpr int kFoldBatchesM = 256;   // batches between FP64 folds of the register buckets
 constexpr float kPadLog2M = -1000.0f;
 
 // PSD buckets of a walked pair: lane 0 (the first half's point) adds to the

@@ -22,7 +22,7 @@
 // K = ceil(M/16) consecutive steps, keeps their terms t_m in registers, the
 // half sums them into S with shuffles, and the same registers give
 // d|S|^2/d ln p_m = 2 Re(conj(S) t_m).  FP32 lane buckets are folded into
-// FP64 shared buckets every 8 batches.  The same pass sums the forward value
+// FP64 shared buckets once per piece.  The same pass sums the forward value
 // w W |S|^2 (the tile's partial of Sigma_i), so no separate forward runs.
 // The buckets are not yet weighted by dT/dSigma_i (unknown until every tile
 // of CUT i is done): at the end of a candidate the block adds them, in
@@ -44,6 +44,11 @@ constexpr unsigned kFullT = 0xffffffffu;
 constexpr int kClsSmallT = 0, kClsDirectT = 1, kClsTeleT = 2;
 constexpr int kListCapT = 34;       // a form's list: one carried point + 32 new (+1 pad)
 constexpr float kPadLog2T = -1000.0f;
+// Batches between folds of the FP32 lane buckets into the FP64 shared ones:
+// one per piece at G = 256.  A lane bucket then sums at most ~512 terms in
+// FP32 (relative rounding ~1e-6, at worst ~3e-5, against the gradient's 1e-3),
+// and the FP64 pipe, ~1/64 of the FP32 rate on this GPU, stays nearly idle.
+constexpr int kFoldBatchesT = 256;
 
 __device__ __forceinline__ float sinc_poly_t(float x)
 {
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                     nd &= 1;
                     nt &= 1;
                     ns &= 1;
-                    if (++batches == 8) {
+                    if (++batches == kFoldBatchesT) {
                         batches = 0;
 #pragma unroll
                         for (int k = 0; k < K; ++k) {

@@ -139,3 +139,22 @@ def test_adjoint_degenerate_grids(eng, G, n_edges):
     r = eng.grad(wl, P=P)
     fd = _fd(lambda Q: eng.snr(wl, P=Q, precision=1)["T"], P, range(5))
     _check(r["dT_dP"], fd)
+
+
+@pytest.mark.parametrize("case", ["uwb", "wide", "raman", "mci"])
+def test_gradient_is_bit_reproducible(eng, case):
+    """Every reduction of the adjoints has a fixed order (each tile's buckets go
+    to rows only that tile writes, summed per CUT or per channel in tile order),
+    so two gradient calls return the same bits: the 589-ch plan, a plan with six
+    F_c candidates per piece (past the four register buckets), the Raman-ODE
+    profile and the MCI cells of a separate grid."""
+    from _plans import wide_cut_plan
+    wl = {"uwb": W.uwb(G=16, n_edges=33),
+          "wide": wide_cut_plan(G=24).with_(n_edges=33),
+          "raman": W.raman(W.uwb(G=8, n_edges=33), ode_h_km=0.5),
+          "mci": W.tiny(G=16, n_edges=33).with_(G_mci=8)}[case]
+    a = eng.grad(wl)
+    b = eng.grad(wl)
+    np.testing.assert_array_equal(a["dT_dP"], b["dT_dP"])
+    np.testing.assert_array_equal(a["eta"], b["eta"])
+    assert a["T"] == b["T"]
