@@ -301,7 +301,7 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
 # full size (same G, same per-piece shape), so each count is scaled to a full
 # launch by evaluated points.
 ADJ_CAPTURE = {"profile": "k_quad_adj_uwb148_every4th_G256.md", "points": 2880700416,
-               "dram_bytes": 4.466e6, "warp_inst": 1.91e11, "fp32_warp_inst": 1.104e11}
+               "dram_bytes": 4.548e6, "warp_inst": 1.760e11, "fp32_warp_inst": 9.308e10}
 FWD_CAPTURE = {"profile": "k_quad_f32_uwb148_every4th_G256.md", "points": 2880700416,
                "dram_bytes": 4.056e6, "warp_inst": 8.69e10, "fp32_warp_inst": 5.76e10}
 ISSUE_PER_CLK_PER_SM = 4         # one warp instruction per clock per SM sub-partition
