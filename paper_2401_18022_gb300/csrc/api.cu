@@ -46,7 +46,9 @@ struct Geom {
     std::vector<int> prof_ch_off, plan_ch_off, plan_n, prof_plan;
     int total_prof_ch = 0, total_plan_ch = 0;
     DevBuf pieces, items, slot_items, slot_cut, prof_slot_off, plan_ch_off_d, plan_n_d, prof_ch_off_d,
-        prof_plan_d, ch_frel, ch_B, ch_alpha, ch_gamma, ch_nf, guard, zs_a, zs_b, zs_d, zs_g, item_slot;
+        prof_plan_d, ch_frel, ch_B, ch_alpha, ch_gamma, ch_nf, guard, zs_a, zs_b, zs_d, zs_g, item_slot, zs_gseg,
+        seg;
+    float phi_seg[3] = {0.f, 0.f, 0.f};
     bool has_nf = false, has_guard = false;
     // Raman-ODE profile: partner windows and gain scale per plan channel, RK4
     // steps per half z-step, largest candidate count of a piece
@@ -419,8 +421,66 @@ isrs_status cut_pieces(isrs_handle h, const isrs_channels *c, int plan, int i, i
 // Stored per step as FP64 {z_m, dz_m}, FP32 {z_m, dz_m} and the phase
 // positions in revolutions (z / 2 pi) as float-float pairs.
 // ----------------------------------------------------------------------------
+// Segments of the span for the segmented small-phase series: level v cuts
+// [0, L] into 2^{v+1} segments at the step edges nearest to s L / 2^{v+1}
+// (fewer where two targets share an edge).  Per segment {m0, m1, centre/2pi
+// as float-float}; per level and step the moments g_n (n <= 18) of the step
+// about its segment's centre; per level the |phi| limit 6 / (longest
+// segment), below which 19 moments truncate the series by < 2e-8.
+void segment_tables(const std::vector<double> &ze, std::vector<float4> &gseg, std::vector<int4> &seg,
+                    float *phi_seg)
+{
+    const int M = (int)ze.size() - 1;
+    const double L = ze[M];
+    gseg.assign((size_t)kSegLevels * M * 5, make_float4(0.f, 0.f, 0.f, 0.f));
+    seg.assign(kSegSlots, make_int4(0, 0, 0, 0));
+    int slot = 0;
+    for (int v = 0; v < kSegLevels; ++v) {
+        const int J = 2 << v;
+        std::vector<int> b{0};
+        for (int s = 1; s < J; ++s) {
+            int best = 0;
+            for (int e = 0; e <= M; ++e)
+                if (std::fabs(ze[e] - s * L / J) < std::fabs(ze[best] - s * L / J)) best = e;
+            if (best > b.back() && best < M) b.push_back(best);
+        }
+        b.push_back(M);
+        double lmax = 0.0;
+        const int nseg = (int)b.size() - 1;
+        for (int s = 0; s < (1 << (v + 1)); ++s, ++slot) {
+            if (s >= nseg) {                    // fewer segments than slots: an empty one
+                seg[slot] = make_int4(M, M, 0, 0);
+                continue;
+            }
+            const int m0 = b[s], m1 = b[s + 1];
+            const double c = 0.5 * (ze[m0] + ze[m1]);
+            lmax = std::max(lmax, ze[m1] - ze[m0]);
+            const double cr = c / (2.0 * 3.14159265358979323846);
+            const float hi = (float)cr, lo = (float)(cr - (double)hi);
+            int hib, lob;
+            std::memcpy(&hib, &hi, 4);
+            std::memcpy(&lob, &lo, 4);
+            seg[slot] = make_int4(m0, m1, hib, lob);
+            for (int m = m0; m < m1; ++m) {
+                const double lo2 = ze[m] - c, hi2 = ze[m + 1] - c;
+                float g[20] = {0.f};
+                double pa = lo2, pb = hi2;
+                for (int n = 0; n <= 18; ++n) {
+                    g[n] = (float)((pb - pa) / ((n + 1) * (hi2 - lo2)));
+                    pa *= lo2;
+                    pb *= hi2;
+                }
+                for (int q = 0; q < 5; ++q)
+                    gseg[((size_t)v * M + m) * 5 + q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+            }
+        }
+        phi_seg[v] = (float)(6.0 / lmax);
+    }
+}
+
 void zgrid_tables(double L, double a, int n_edges, std::vector<float4> &za, std::vector<float4> &zb,
-                  std::vector<double2> &zd, float &dz_max, std::vector<float4> *zg = nullptr)
+                  std::vector<double2> &zd, float &dz_max, std::vector<float4> *zg = nullptr,
+                  std::vector<float4> *gseg = nullptr, std::vector<int4> *seg = nullptr, float *phi_seg = nullptr)
 {
     std::vector<double> ze(n_edges);
     const double drop = a > 0.0 ? -std::expm1(-a * L) : 0.0;
@@ -462,6 +522,7 @@ void zgrid_tables(double L, double a, int n_edges, std::vector<float4> &za, std:
                 (*zg)[5 * m + q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
         }
     }
+    if (gseg && seg && phi_seg) segment_tables(ze, *gseg, *seg, phi_seg);
 }
 
 // ----------------------------------------------------------------------------
@@ -655,9 +716,10 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     g->n_slots = (int)slot_items.size();
     g->n_mci_items = (int)mitems.size();
 
-    std::vector<float4> za, zb, zg;
+    std::vector<float4> za, zb, zg, zgs;
+    std::vector<int4> segv;
     std::vector<double2> zd;
-    zgrid_tables(fb->L_km, fb->alpha_R_per_km, q->n_edges, za, zb, zd, g->dz_max, &zg);
+    zgrid_tables(fb->L_km, fb->alpha_R_per_km, q->n_edges, za, zb, zd, g->dz_max, &zg, &zgs, &segv, g->phi_seg);
 
     // Raman-ODE profile: the partners of channel i are the k != i with
     // |f_k - f_i| <= raman_max_THz, one index window of the sorted plan; the
@@ -761,6 +823,8 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     UP(zs_b, zb);
     UP(zs_d, zd);
     UP(zs_g, zg);
+    UP(zs_gseg, zgs);
+    UP(seg, segv);
     UP(item_slot, item_slot);
     if (mci) {
         UP(mci_items, mitems);
@@ -800,7 +864,8 @@ void free_geom(Geom *g)
                       &g->ch_frel, &g->ch_B, &g->ch_alpha, &g->ch_gamma, &g->ch_nf,
                       &g->guard, &g->zs_a, &g->zs_b, &g->zs_d, &g->zs_g, &g->item_slot,
                       &g->win_lo, &g->win_hi, &g->ch_scale, &g->half_steps, &g->mci_items, &g->slot_items2,
-                      &g->item_slot_all, &g->tab_row_off, &g->tab_prow, &g->tab_gath_off, &g->tab_gath};
+                      &g->item_slot_all, &g->tab_row_off, &g->tab_prow, &g->tab_gath_off, &g->tab_gath,
+                      &g->zs_gseg, &g->seg};
     for (DevBuf *b : bufs) release(*b);
 }
 
@@ -864,6 +929,9 @@ QuadParams quad_params(isrs_handle h, const isrs_fibre *fb, Geom *g)
     qp.zs_b = (const float4 *)g->zs_b.p;
     qp.zs_d = (const double2 *)g->zs_d.p;
     qp.zs_g = (const float4 *)g->zs_g.p;
+    qp.zs_gseg = (const float4 *)g->zs_gseg.p;
+    qp.seg = (const int4 *)g->seg.p;
+    for (int v = 0; v < 3; ++v) qp.phi_seg[v] = g->phi_seg[v];
     qp.dz_max = g->dz_max;
     qp.kap_L = (const double *)h->kapL.p;
     qp.L = (float)fb->L_km;
@@ -1907,10 +1975,11 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
         av[k] = ch->alpha_per_km[k];
         gv[k] = ch->gamma_per_W_km[k];
     }
-    std::vector<float4> za, zb, zg;
+    std::vector<float4> za, zb, zg, zgs;
+    std::vector<int4> segv;
     std::vector<double2> zd;
-    float dz_max = 0.f;
-    zgrid_tables(fibre->L_km, fibre->alpha_R_per_km, quad->n_edges, za, zb, zd, dz_max, &zg);
+    float dz_max = 0.f, phi_seg[3] = {0.f, 0.f, 0.f};
+    zgrid_tables(fibre->L_km, fibre->alpha_R_per_km, quad->n_edges, za, zb, zd, dz_max, &zg, &zgs, &segv, phi_seg);
     const int M = quad->n_edges - 1;
     if (quad->precision == ISRS_PREC_FP32) {
         const double pi = 3.14159265358979323846;
@@ -1939,6 +2008,8 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     const size_t o_za = L.take(sizeof(float4) * M), o_zb = L.take(sizeof(float4) * M);
     const size_t o_zd = L.take(sizeof(double2) * M);
     const size_t o_zg = L.take(sizeof(float4) * zg.size());   // centred step moments (contracted small phase)
+    const size_t o_zgs = L.take(sizeof(float4) * zgs.size());  // the same about segment centres
+    const size_t o_seg = L.take(sizeof(int4) * segv.size());
     const size_t o_kapL = L.take(sizeof(double));
     const size_t o_P = L.take(sizeof(double) * n);
     const size_t o_pdd = L.take(sizeof(double) * n), o_pdf = L.take(sizeof(float) * n);
@@ -1960,7 +2031,8 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
         {o_B, Bv.data(), sizeof(double) * n}, {o_alpha, av.data(), sizeof(double) * n},
         {o_gamma, gv.data(), sizeof(double) * n}, {o_za, za.data(), sizeof(float4) * M},
         {o_zb, zb.data(), sizeof(float4) * M}, {o_zd, zd.data(), sizeof(double2) * M},
-        {o_zg, zg.data(), sizeof(float4) * zg.size()}};
+        {o_zg, zg.data(), sizeof(float4) * zg.size()}, {o_zgs, zgs.data(), sizeof(float4) * zgs.size()},
+        {o_seg, segv.data(), sizeof(int4) * segv.size()}};
     for (const Up &u : ups)
         if (u.bytes && cudaMemcpyAsync(base + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return ISRS_ERR_CUDA;
@@ -2015,6 +2087,9 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     qp.zs_b = (const float4 *)(base + o_zb);
     qp.zs_d = pp.zs_d;
     qp.zs_g = (const float4 *)(base + o_zg);
+    qp.zs_gseg = (const float4 *)(base + o_zgs);
+    qp.seg = (const int4 *)(base + o_seg);
+    for (int v = 0; v < 3; ++v) qp.phi_seg[v] = phi_seg[v];
     qp.kap_L = pp.kap_L;
     qp.n_spans = 1;
     qp.dz_max = dz_max;

@@ -19,6 +19,8 @@ constexpr int kMaxSteps = 2048;     // max z-steps (n_edges - 1)
 constexpr int kMaxG = 4096;         // max grid points per dimension
 constexpr int kMaxRamanCh = 2048;   // max channels of a plan with the Raman-ODE profile
 constexpr int kMaxRamanGradCh = 1536;   // ... and of its gradient (shared memory of the ODE adjoint)
+constexpr int kSegLevels = 3;       // segmented small phase: 2, 4 and 8 segments ...
+constexpr int kSegSlots = 14;       // ... 14 segments in all
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kLog2e = 1.44269504088896340736;
 
@@ -71,6 +73,13 @@ struct QuadParams {
     const float4 *zs_b;         // {z_{m+1}/2pi hi, lo (float-float), z_m/2pi, 0}
     const double2 *zs_d;        // {z_m, dz_m}
     const float4 *zs_g;         // [5 per step] g_0..g_19: mean of (zeta - L/2)^n over step m (g_19 = 0)
+    // segmented small-phase series (forward FP32): the span cut at step edges
+    // into 2, 4 and 8 segments (kSegLevels levels, kSegSlots segments in all);
+    // per level and step the moments about the step's segment centre, and per
+    // segment its steps and centre in revolutions (float-float).  Null: off.
+    const float4 *zs_gseg;      // [kSegLevels][M][5]
+    const int4 *seg;            // [kSegSlots] {m0, m1, bits of centre/2pi hi, lo}
+    float phi_seg[3];           // per level: |phi| limit [rad/km] (6 / longest segment)
     const double *kap_L;        // per profile: kappa(L) [1/THz]
     float dz_max;
     float L;                    // span length [km]

@@ -288,15 +288,17 @@ __device__ __forceinline__ float4 bessel_b4(float a)
                        2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
 }
 
-// Moment sums of one candidate for n in [N0, N0 + NN): s[n][k] = sum_m W_k(m) g_n(m).
+// Moment sums of one candidate for n in [N0, N0 + NN) over the steps
+// [m0, m1): s[n][k] = sum_m W_k(m) g_n(m), with g_n(m) from gtab (kZsG float4
+// per step).
 template <int N0, int NN>
-__device__ __forceinline__ void cheb_sums(const QuadParams &qp, const float4 *sT, int M, double F0, float h,
+__device__ __forceinline__ void cheb_sums(const float4 *gtab, const float4 *sT, int m0, int m1, double F0, float h,
                                           double at, int lane, float4 *out)
 {
     float s[NN][4];
 #pragma unroll
     for (int n = 0; n < NN; ++n) s[n][0] = s[n][1] = s[n][2] = s[n][3] = 0.0f;
-    for (int m = lane; m < M; m += 32) {
+    for (int m = m0 + lane; m < m1; m += 32) {
         const float4 a = sT[m];
         const float base = exp2_split((double)a.x - at * (double)a.z + (double)a.y * F0);
         const float t = 0.5f * a.y * h * 0.69314718f, t2 = t * t;
@@ -304,7 +306,7 @@ __device__ __forceinline__ void cheb_sums(const QuadParams &qp, const float4 *sT
         const float W1 = base * (2.0f * t * (1.0f + t2 * (0.5f + t2 * (1.0f / 12.0f))));                     // 2 I1
         const float W2 = base * (2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 * (1.0f / 48.0f))));             // 2 I2
         const float W3 = base * (2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
-        const float *g = reinterpret_cast<const float *>(qp.zs_g + kZsG * m) + N0;
+        const float *g = reinterpret_cast<const float *>(gtab + kZsG * m) + N0;
 #pragma unroll
         for (int n = 0; n < NN; ++n) {
             const float gn = g[n];
@@ -335,7 +337,7 @@ __device__ __forceinline__ void cheb_sums(const QuadParams &qp, const float4 *sT
 // the step weights are exact to FP32 rounding (FP64 exponent), the sums run
 // over the lane's steps and a warp tree.
 template <int NM, int NC>
-__device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece &pc, int prof,
+__device__ __forceinline__ bool cheb_setup(const QuadParams &qp, const DevPiece &pc, int prof,
                                            const float4 *sT, int M, const PieceConst<float> &k, ChebTabN<NC> &ct)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -345,25 +347,26 @@ __device__ __forceinline__ void cheb_setup(const QuadParams &qp, const DevPiece 
     for (int c = 0; c < k.nc; ++c) hmax = fmax(hmax, 0.5 * qp.ch_B[coff + pc.c_lo + c]);
     const bool ok = qp.zs_g != nullptr && kapL * hmax <= (double)kChebMaxA;
     if (threadIdx.x == 0) ct.ok = ok ? 1 : 0;
-    if (!ok) return;
+    if (!ok) return false;
     const int ncs = k.nc < NC ? k.nc : NC;
     for (int c = warp; c < ncs; c += nw) {
         const double F0 = qp.ch_frel[coff + pc.c_lo + c];
         const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
         const double at = (double)(k.at_ab + k.hat[c]);
         static_assert(NM > 6 && NM <= kChebMom, "moment count");
-        cheb_sums<0, 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c]);
+        cheb_sums<0, 6>(qp.zs_g, sT, 0, M, F0, (float)h, at, lane, ct.c[c]);
         if constexpr (NM <= 12) {
-            cheb_sums<6, NM - 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c] + 6);
+            cheb_sums<6, NM - 6>(qp.zs_g, sT, 0, M, F0, (float)h, at, lane, ct.c[c] + 6);
         } else {
-            cheb_sums<6, 6>(qp, sT, M, F0, (float)h, at, lane, ct.c[c] + 6);
-            cheb_sums<12, NM - 12>(qp, sT, M, F0, (float)h, at, lane, ct.c[c] + 12);
+            cheb_sums<6, 6>(qp.zs_g, sT, 0, M, F0, (float)h, at, lane, ct.c[c] + 6);
+            cheb_sums<12, NM - 12>(qp.zs_g, sT, 0, M, F0, (float)h, at, lane, ct.c[c] + 12);
         }
         if (lane == 0) {
             ct.mid[c] = 0.5f * (k.lo[c] + k.hi[c]);
             ct.invh[c] = (float)(1.0 / h);
         }
     }
+    return true;
 }
 
 // Folded moments nu'_n (n < NM) of a point in candidate ci at u = F_c - f_i.
@@ -393,6 +396,77 @@ __device__ __forceinline__ void cheb_AB(const float (&nu)[NM], float phi, float 
 #pragma unroll
     for (int i = no - 2; i >= 0; --i) b = fmaf(b, p2, nu[2 * i + 1]);
     B = phi * b;
+}
+
+// ---------------------------------------------------------------------------
+// Segmented small-phase series (forward FP32).  Cut the span at step edges
+// into segments s with centres c_s; each segment's part of Eq. slow_vary is,
+// exactly as for the whole span,
+//   S_s = e^{j phi c_s} sum_n (j phi)^n / n! nu_n^s,  nu_n^s = sum_{m in s} w_m g_n^s(m),
+// g_n^s(m) the mean of (zeta - c_s)^n over step m, and S = sum_s S_s.  With
+// |phi| (segment length) <= 6 the 19-moment truncation stays below 2e-8 of
+// each part, so a point that is too fast for the whole-span series but slow
+// enough for 2, 4 or 8 segments costs 2, 4 or 8 series evaluations (and as
+// many phasors) instead of a walk over all steps.  The moments are contracted
+// in F_c as in cheb_setup, per piece, candidate and segment.
+// ---------------------------------------------------------------------------
+constexpr int kSegCand = 3;          // F_c candidates with segment tables
+
+struct SegTab {
+    float4 c[kSegCand][kSegSlots][kChebMom];   // as ChebTab.c, per segment
+    float hi[kSegSlots], lo[kSegSlots];        // segment centre / 2pi (float-float)
+};
+
+// Called by every thread after cheb_setup (ct.ok block-uniform); the caller
+// syncs.  One warp per (candidate, segment).
+__device__ __forceinline__ void seg_setup(const QuadParams &qp, const DevPiece &pc, const float4 *sT, int M,
+                                          const PieceConst<float> &k, SegTab &sg)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int coff = qp.plan_ch_off[pc.plan];
+    const int ncs = k.nc < kSegCand ? k.nc : kSegCand;
+    if (threadIdx.x < kSegSlots) {
+        const int4 si = qp.seg[threadIdx.x];
+        sg.hi[threadIdx.x] = __int_as_float(si.z);
+        sg.lo[threadIdx.x] = __int_as_float(si.w);
+    }
+    for (int t = warp; t < ncs * kSegSlots; t += nw) {
+        const int c = t / kSegSlots, sl = t - c * kSegSlots;
+        const int lv = sl < 2 ? 0 : (sl < 6 ? 1 : 2);
+        const int4 si = qp.seg[sl];
+        const float4 *gtab = qp.zs_gseg + (size_t)lv * M * kZsG;
+        const double F0 = qp.ch_frel[coff + pc.c_lo + c];
+        const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
+        const double at = (double)(k.at_ab + k.hat[c]);
+        float4 *out = sg.c[c][sl];
+        cheb_sums<0, 6>(gtab, sT, si.x, si.y, F0, (float)h, at, lane, out);
+        cheb_sums<6, 6>(gtab, sT, si.x, si.y, F0, (float)h, at, lane, out + 6);
+        cheb_sums<12, kChebMom - 12>(gtab, sT, si.x, si.y, F0, (float)h, at, lane, out + 12);
+    }
+}
+
+// |S|^2 of a point of candidate ci at in-channel coordinate x (T2, T3 its
+// Chebyshev values) from the segments [s0, s1).
+__device__ __forceinline__ float seg_s2(const SegTab &sg, int ci, int s0, int s1, float x, float T2, float T3,
+                                        float phi)
+{
+    float Sr = 0.0f, Si = 0.0f;
+    for (int s = s0; s < s1; ++s) {
+        float nu[kChebMom];
+        const float4 *C = sg.c[ci][s];
+#pragma unroll
+        for (int n = 0; n < kChebMom; ++n) {
+            const float4 c = C[n];
+            nu[n] = fmaf(c.w, T3, fmaf(c.z, T2, fmaf(c.y, x, c.x)));
+        }
+        float A, B;
+        cheb_AB<kChebMom>(nu, phi, A, B);
+        float sn, cs;
+        phasor_rev_ff(phi, sg.hi[s], sg.lo[s], sn, cs);
+        Sr = fmaf(cs, A, fmaf(-sn, B, Sr));
+        Si = fmaf(sn, A, fmaf(cs, B, Si));
+    }
+    return fmaf(Sr, Sr, Si * Si);
 }
 
 }  // namespace isrs

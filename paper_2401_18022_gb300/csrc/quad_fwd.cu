@@ -5,9 +5,12 @@
 //                of Eq. pk for the linear-slope closed-form profile.
 //  k_quad_f32    persistent quadrature: one block per work tile (a range of
 //                pieces of one CUT); G x G hyperbolic grid per piece
-//                (Eqs. q1..q4), z-sum of Eq. slow_vary per grid point in FP32
-//                with a float-float phase and mod-2pi reduction; compensated
-//                accumulation; one FP64 partial per tile.
+//                (Eqs. q1..q4), z-sum of Eq. slow_vary per grid point in FP32:
+//                the moment series about the span centre (|phi| L <= 6) or
+//                about the centres of 2, 4 or 8 segments (|phi| L up to ~42),
+//                else the direct or telescoped step sums with a float-float
+//                phase and mod-2pi reduction; compensated accumulation; one
+//                FP64 partial per tile.
 //  k_quad_f64    the same quadrature in plain FP64 (direct form of
 //                Eq. slow_vary with sinc), used as the reference GPU path.
 //  k_finish      per profile: deterministic FP64 sum of tile partials per CUT,
@@ -129,6 +132,7 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
     RowF *rows = reinterpret_cast<RowF *>(sEc + ncr * M);   // [G]
     __shared__ PieceConst<float> kc;
     __shared__ ChebTab ct;
+    __shared__ SegTab sg;
     __shared__ double scratch[32];
     __shared__ int s_item;
 
@@ -146,6 +150,7 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
     const float phi_cheb = kChebPhiL / qp.L;
+    const float phi_s0 = qp.phi_seg[0], phi_s1 = qp.phi_seg[1], phi_s2 = qp.phi_seg[2];
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
     unsigned n_small = 0, n_direct = 0, n_tele = 0;
@@ -178,7 +183,8 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
-            cheb_setup<kChebMom>(qp, pc, item.prof, sT, M, kc, ct);
+            const bool segs = cheb_setup<kChebMom>(qp, pc, item.prof, sT, M, kc, ct) && qp.zs_gseg != nullptr;
+            if (segs) seg_setup(qp, pc, sT, M, kc, sg);
             // per-candidate step rows with the candidate's attenuation folded in
             const int ncf = min(kc.nc, ncr);
             for (int t = threadIdx.x; t < ncf * M; t += blockDim.x) {
@@ -229,6 +235,15 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
                     } else {
                         S2 = zsum_small_f(phi, Fc, at, sT, M);
                     }
+                    ++n_small;
+                } else if (segs && ci < kSegCand && aphi <= phi_s2) {
+                    // the series per segment: 2, 4 or 8 segments by |phi|
+                    const int s0 = aphi <= phi_s0 ? 0 : (aphi <= phi_s1 ? 2 : 6);
+                    const int s1 = aphi <= phi_s0 ? 2 : (aphi <= phi_s1 ? 6 : kSegSlots);
+                    const float x = (u - ct.mid[ci]) * ct.invh[ci];
+                    const float T2 = fmaf(2.0f * x, x, -1.0f);
+                    const float T3 = fmaf(2.0f * x, T2, -x);
+                    S2 = seg_s2(sg, ci, s0, s1, x, T2, T3, phi);
                     ++n_small;
                 } else if (aphi <= phi_direct) {
                     S2 = ci < ncr ? zsum_direct_fc(phi, Fc, sRc + ci * M, M) : zsum_direct_f(phi, Fc, at, sR, M);
