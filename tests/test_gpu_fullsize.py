@@ -53,6 +53,16 @@ def test_uwb_full_cuts_vs_oracle(uwb_full, orc, cut):
     np.testing.assert_allclose(r["sigma"][cut], ref[0], rtol=RTOL_F32)
 
 
+def test_uwb_full_fp64_gpu_vs_oracle(eng, orc):
+    """The plain FP64 GPU path against the FP64 oracle at the benchmark's
+    G = 256, on the centre CUT of the 589-ch plan: same algorithm and
+    precision, so they agree to summation order (1e-9)."""
+    wl = W.uwb(G=256)
+    got = eng.eta(wl, cuts=[294], precision=1)["sigma"]
+    ref = orc.sigma(wl, cuts=[294], threads=os.cpu_count())
+    np.testing.assert_allclose(got, ref, rtol=1e-9)
+
+
 def test_uwb_full_vs_fp64_gpu_sampled(eng, uwb_full):
     wl, P, r = uwb_full
     cuts = [0, 1, 97, 200, 294, 401, 587, 588]

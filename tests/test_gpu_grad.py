@@ -158,3 +158,27 @@ def test_gradient_is_bit_reproducible(eng, case):
     np.testing.assert_array_equal(a["dT_dP"], b["dT_dP"])
     np.testing.assert_array_equal(a["eta"], b["eta"])
     assert a["T"] == b["T"]
+
+
+def test_adjoint_single_channel_zero_dispersion_closed_form(eng):
+    """One channel, beta2 = beta3 = beta4 = 0, C_r = 0, uniform alpha: phi = 0
+    and the profile does not depend on P, so eta is a constant and Sigma is
+    P^3 times a constant (the adjoint's PSD bucket gives dSigma/dP = 3 Sigma/P,
+    its profile buckets vanish).  With N = eta P^3 + P_ASE (P_ASE fixed,
+    G = e^{alpha L}): dT/dP = 2B / (ln 2 (1 + SNR)) (N - 3 eta P^3) / N^2."""
+    import math
+    Bw, a, L = 0.096, 0.046, 80.0
+    wl = W.tiny(G=64, n_edges=57).with_(
+        f_THz=np.array([193.4]), B_THz=np.array([Bw]), P_W=np.array([2e-3]), alpha_per_km=np.array([a]),
+        lambda_nm=np.array([1550.0]), aeff_um2=np.array([80.0]), nf_dB=np.array([5.0]), Cr=0.0,
+        gamma_fixed=1.3, alpha_R_per_km=a, D_ref=0.0, S_ref=0.0, Sdot_ref=0.0, cell_set=W.CELLS_SCI_XCI)
+    for P in (1e-3, 5e-3, 2e-2):
+        g = eng.grad(wl, P=np.array([P]))
+        eta = float(g["eta"][0])
+        pase = 10 ** 0.5 * 6.62607015e-34 * 193.4e12 * (math.exp(a * L) - 1) * Bw * 1e12
+        N = eta * P ** 3 + pase
+        snr = P / N
+        ref = 2 * Bw / (math.log(2) * (1 + snr)) * (N - 3 * eta * P ** 3) / N ** 2
+        assert float(g["snr"][0]) == pytest.approx(snr, rel=1e-9)
+        # the PSD bucket of F_c is an FP32 (uncompensated) lane sum: ~1e-6 relative
+        assert float(g["dT_dP"][0]) == pytest.approx(ref, rel=1e-5)
