@@ -303,8 +303,8 @@ isrs_status isrs_last_graph_replay(isrs_handle h, int *replayed);
 /* Grid points of the last FP32 quadrature launch (forward, or the fused
  * forward + adjoint of isrs_gn_grad) by the form its z-sum took (App. A,
  * Eq. slow_vary): counts[0] moment expansions (small phase: about the span
- * centre, contracted or per step; in the forward also about the centres of
- * 2, 4 or 8 segments of the span), counts[1] direct form, counts[2]
+ * centre, contracted or per step; in the forward at G >= 160 also about the
+ * centres of 2, 4 or 8 segments of the span), counts[1] direct form, counts[2]
  * telescoped form.  Synchronises the device.  Errors: INVALID_ARG (NULL, or
  * no launch yet), CUDA. */
 isrs_status isrs_last_path_counts(isrs_handle h, int64_t *counts);

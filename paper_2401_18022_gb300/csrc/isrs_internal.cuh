@@ -21,6 +21,8 @@ constexpr int kMaxRamanCh = 2048;   // max channels of a plan with the Raman-ODE
 constexpr int kMaxRamanGradCh = 1536;   // ... and of its gradient (shared memory of the ODE adjoint)
 constexpr int kSegLevels = 3;       // segmented small phase: 2, 4 and 8 segments ...
 constexpr int kSegSlots = 14;       // ... 14 segments in all
+constexpr int kSegMinG = 160;       // ... used from G = 160: their tables cost a fixed time per piece,
+                                    // which the few points they serve repay only on large pieces
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kLog2e = 1.44269504088896340736;
 

@@ -226,7 +226,15 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
-            cheb_setup<kChebMom>(qp, pc, item.prof, sT, M, kc, ct);
+            // step weights of the contracted candidates, once per piece, in the
+            // (empty until the points start) list space
+            int nW = 0;
+            if (cheb_applies(qp, pc, item.prof, kc) && min(kc.nc, kCtr) * M <= nw * 3 * kListCap) {
+                nW = min(kc.nc, kCtr);
+                cheb_weights(qp, pc, sT, M, kc, nW, sL);
+                __syncthreads();
+            }
+            cheb_setup<kChebMom>(qp, pc, item.prof, sT, M, kc, ct, sL, nW);
             __syncthreads();
             const bool cheb = ct.ok != 0;
             const float fi = kc.fi, s1g = kc.s1, s2g = kc.s2, mult = kc.mult;

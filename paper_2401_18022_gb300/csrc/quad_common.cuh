@@ -288,33 +288,47 @@ __device__ __forceinline__ float4 bessel_b4(float a)
                        2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
 }
 
+// The four weights of step m for a candidate (F0 its channel centre, h its
+// half-width, at its attenuation term): W_k(m) = 2^{A2d_m + K2_m F0 - at z_m}
+// times the k-th Chebyshev coefficient of e^{K2_m ln2 h x} on [-1, 1]
+// (I0, 2 I1, 2 I2, 2 I3).  The exponent is formed in FP64, so the weight is
+// exact to FP32 rounding.
+__device__ __forceinline__ float4 cheb_w4(float4 a, double F0, float h, double at)
+{
+    const float base = exp2_split((double)a.x - at * (double)a.z + (double)a.y * F0);
+    const float t = 0.5f * a.y * h * 0.69314718f, t2 = t * t;
+    return make_float4(base * (1.0f + t2 * (1.0f + t2 * (0.25f + t2 * (1.0f / 36.0f)))),                  // I0
+                       base * (2.0f * t * (1.0f + t2 * (0.5f + t2 * (1.0f / 12.0f)))),                     // 2 I1
+                       base * (2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 * (1.0f / 48.0f)))),             // 2 I2
+                       base * (2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f))))); // 2 I3
+}
+
 // Moment sums of one candidate for n in [N0, N0 + NN) over the steps
 // [m0, m1): s[n][k] = sum_m W_k(m) g_n(m), with g_n(m) from gtab (kZsG float4
-// per step).
+// per step).  The weights come from sWc (one float4 per step, cheb_w4) when
+// it is given, else they are formed here from sT.
 template <int N0, int NN>
-__device__ __forceinline__ void cheb_sums(const float4 *gtab, const float4 *sT, int m0, int m1, double F0, float h,
-                                          double at, int lane, float4 *out)
+__device__ __forceinline__ void cheb_sums(const float4 *gtab, const float4 *sT, const float4 *sWc, int m0, int m1,
+                                          double F0, float h, double at, int lane, float4 *out)
 {
     float s[NN][4];
 #pragma unroll
     for (int n = 0; n < NN; ++n) s[n][0] = s[n][1] = s[n][2] = s[n][3] = 0.0f;
-    for (int m = m0 + lane; m < m1; m += 32) {
-        const float4 a = sT[m];
-        const float base = exp2_split((double)a.x - at * (double)a.z + (double)a.y * F0);
-        const float t = 0.5f * a.y * h * 0.69314718f, t2 = t * t;
-        const float W0 = base * (1.0f + t2 * (1.0f + t2 * (0.25f + t2 * (1.0f / 36.0f))));                  // I0
-        const float W1 = base * (2.0f * t * (1.0f + t2 * (0.5f + t2 * (1.0f / 12.0f))));                     // 2 I1
-        const float W2 = base * (2.0f * t2 * (0.5f + t2 * (1.0f / 6.0f + t2 * (1.0f / 48.0f))));             // 2 I2
-        const float W3 = base * (2.0f * t2 * t * (1.0f / 6.0f + t2 * (1.0f / 24.0f + t2 * (1.0f / 240.0f)))); // 2 I3
+    auto add = [&](const float4 W, int m) {
         const float *g = reinterpret_cast<const float *>(gtab + kZsG * m) + N0;
 #pragma unroll
         for (int n = 0; n < NN; ++n) {
             const float gn = g[n];
-            s[n][0] = fmaf(W0, gn, s[n][0]);
-            s[n][1] = fmaf(W1, gn, s[n][1]);
-            s[n][2] = fmaf(W2, gn, s[n][2]);
-            s[n][3] = fmaf(W3, gn, s[n][3]);
+            s[n][0] = fmaf(W.x, gn, s[n][0]);
+            s[n][1] = fmaf(W.y, gn, s[n][1]);
+            s[n][2] = fmaf(W.z, gn, s[n][2]);
+            s[n][3] = fmaf(W.w, gn, s[n][3]);
         }
+    };
+    if (sWc) {
+        for (int m = m0 + lane; m < m1; m += 32) add(sWc[m], m);
+    } else {
+        for (int m = m0 + lane; m < m1; m += 32) add(cheb_w4(sT[m], F0, h, at), m);
     }
 #pragma unroll
     for (int n = 0; n < NN; ++n) {
@@ -331,39 +345,71 @@ __device__ __forceinline__ void cheb_sums(const float4 *gtab, const float4 *sT, 
     }
 }
 
-// Called by every thread of the block after piece_consts; the caller syncs.
-// sT[m] = {A2d_m, K2_m, z_m, .}; qp.zs_g[kZsG m ...] = g_0..g_19 of step m.
-// One warp per candidate (the first NC of the piece) fills nu_0..nu_{NM-1};
-// the step weights are exact to FP32 rounding (FP64 exponent), the sums run
-// over the lane's steps and a warp tree.
-template <int NM, int NC>
-__device__ __forceinline__ bool cheb_setup(const QuadParams &qp, const DevPiece &pc, int prof,
-                                           const float4 *sT, int M, const PieceConst<float> &k, ChebTabN<NC> &ct)
+// Whether the contracted small-phase tables apply to this piece (block
+// uniform): the centred step moments exist and every candidate channel is
+// narrow enough for the 4-term Chebyshev series of e^{kappa F_c}.
+__device__ __forceinline__ bool cheb_applies(const QuadParams &qp, const DevPiece &pc, int prof,
+                                             const PieceConst<float> &k)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int coff = qp.plan_ch_off[pc.plan];
     const double kapL = qp.kap_L ? qp.kap_L[prof] : 1e30;
     double hmax = 0.0;
     for (int c = 0; c < k.nc; ++c) hmax = fmax(hmax, 0.5 * qp.ch_B[coff + pc.c_lo + c]);
-    const bool ok = qp.zs_g != nullptr && kapL * hmax <= (double)kChebMaxA;
+    return qp.zs_g != nullptr && kapL * hmax <= (double)kChebMaxA;
+}
+
+// The step weights of the first nW candidates of the piece into sW[c M + m]
+// (all threads; the caller syncs before the tables are built from them).
+__device__ __forceinline__ void cheb_weights(const QuadParams &qp, const DevPiece &pc, const float4 *sT, int M,
+                                             const PieceConst<float> &k, int nW, float4 *sW)
+{
+    const int coff = qp.plan_ch_off[pc.plan];
+    for (int t = threadIdx.x; t < nW * M; t += blockDim.x) {
+        const int c = t / M, m = t - c * M;
+        const double F0 = qp.ch_frel[coff + pc.c_lo + c];
+        const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
+        sW[t] = cheb_w4(sT[m], F0, (float)h, (double)(k.at_ab + k.hat[c]));
+    }
+}
+
+// Called by every thread of the block after piece_consts; the caller syncs.
+// sT[m] = {A2d_m, K2_m, z_m, .}; qp.zs_g[kZsG m ...] = g_0..g_19 of step m.
+// For the first NC candidates of the piece, one warp per (candidate, group of
+// up to 6 moments) fills nu_0..nu_{NM-1}; the step weights are exact to FP32
+// rounding (FP64 exponent), read from sW for the first nW candidates
+// (cheb_weights) and formed per moment group for the rest; the sums run over
+// the lane's steps and a warp tree.
+template <int NM, int NC>
+__device__ __forceinline__ bool cheb_setup(const QuadParams &qp, const DevPiece &pc, int prof,
+                                           const float4 *sT, int M, const PieceConst<float> &k, ChebTabN<NC> &ct,
+                                           const float4 *sW = nullptr, int nW = 0)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int coff = qp.plan_ch_off[pc.plan];
+    const bool ok = cheb_applies(qp, pc, prof, k);
     if (threadIdx.x == 0) ct.ok = ok ? 1 : 0;
     if (!ok) return false;
     const int ncs = k.nc < NC ? k.nc : NC;
-    for (int c = warp; c < ncs; c += nw) {
+    static_assert(NM > 6 && NM <= kChebMom, "moment count");
+    constexpr int ng = NM <= 12 ? 2 : 3;     // moment groups of at most 6
+    // one warp per (candidate, moment group), so that small pieces do not
+    // wait on one warp per candidate
+    for (int t = warp; t < ncs * ng; t += nw) {
+        const int c = t / ng, gr = t - c * ng;
         const double F0 = qp.ch_frel[coff + pc.c_lo + c];
         const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
         const double at = (double)(k.at_ab + k.hat[c]);
-        static_assert(NM > 6 && NM <= kChebMom, "moment count");
-        cheb_sums<0, 6>(qp.zs_g, sT, 0, M, F0, (float)h, at, lane, ct.c[c]);
-        if constexpr (NM <= 12) {
-            cheb_sums<6, NM - 6>(qp.zs_g, sT, 0, M, F0, (float)h, at, lane, ct.c[c] + 6);
-        } else {
-            cheb_sums<6, 6>(qp.zs_g, sT, 0, M, F0, (float)h, at, lane, ct.c[c] + 6);
-            cheb_sums<12, NM - 12>(qp.zs_g, sT, 0, M, F0, (float)h, at, lane, ct.c[c] + 12);
-        }
-        if (lane == 0) {
-            ct.mid[c] = 0.5f * (k.lo[c] + k.hi[c]);
-            ct.invh[c] = (float)(1.0 / h);
+        const float4 *sWc = c < nW ? sW + (size_t)c * M : nullptr;
+        if (gr == 0) {
+            cheb_sums<0, 6>(qp.zs_g, sT, sWc, 0, M, F0, (float)h, at, lane, ct.c[c]);
+            if (lane == 0) {
+                ct.mid[c] = 0.5f * (k.lo[c] + k.hi[c]);
+                ct.invh[c] = (float)(1.0 / h);
+            }
+        } else if (gr == 1) {
+            cheb_sums<6, (NM <= 12 ? NM - 6 : 6)>(qp.zs_g, sT, sWc, 0, M, F0, (float)h, at, lane, ct.c[c] + 6);
+        } else if constexpr (NM > 12) {
+            cheb_sums<12, NM - 12>(qp.zs_g, sT, sWc, 0, M, F0, (float)h, at, lane, ct.c[c] + 12);
         }
     }
     return true;
@@ -418,9 +464,11 @@ struct SegTab {
 };
 
 // Called by every thread after cheb_setup (ct.ok block-uniform); the caller
-// syncs.  One warp per (candidate, segment).
+// syncs.  One warp per (candidate, segment); the step weights of the first nW
+// candidates come from sW as in cheb_setup.
 __device__ __forceinline__ void seg_setup(const QuadParams &qp, const DevPiece &pc, const float4 *sT, int M,
-                                          const PieceConst<float> &k, SegTab &sg)
+                                          const PieceConst<float> &k, SegTab &sg, const float4 *sW = nullptr,
+                                          int nW = 0)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int coff = qp.plan_ch_off[pc.plan];
@@ -439,9 +487,10 @@ __device__ __forceinline__ void seg_setup(const QuadParams &qp, const DevPiece &
         const double h = 0.5 * qp.ch_B[coff + pc.c_lo + c];
         const double at = (double)(k.at_ab + k.hat[c]);
         float4 *out = sg.c[c][sl];
-        cheb_sums<0, 6>(gtab, sT, si.x, si.y, F0, (float)h, at, lane, out);
-        cheb_sums<6, 6>(gtab, sT, si.x, si.y, F0, (float)h, at, lane, out + 6);
-        cheb_sums<12, kChebMom - 12>(gtab, sT, si.x, si.y, F0, (float)h, at, lane, out + 12);
+        const float4 *sWc = c < nW ? sW + (size_t)c * M : nullptr;
+        cheb_sums<0, 6>(gtab, sT, sWc, si.x, si.y, F0, (float)h, at, lane, out);
+        cheb_sums<6, 6>(gtab, sT, sWc, si.x, si.y, F0, (float)h, at, lane, out + 6);
+        cheb_sums<12, kChebMom - 12>(gtab, sT, sWc, si.x, si.y, F0, (float)h, at, lane, out + 12);
     }
 }
 

@@ -115,6 +115,15 @@ __host__ __device__ constexpr int fwd_cand_rows(int n_steps)
 {
     return n_steps <= kFwdCandSteps ? kFwdCand : 0;
 }
+
+// Dynamic shared memory of k_quad_f32 in float4 units: the step tables, the
+// per-candidate rows, the G row descriptors, then (G >= kSegMinG) the
+// segment tables.
+__host__ __device__ constexpr size_t fwd_seg_offset_f4(int n_steps, int G)
+{
+    return (size_t)n_steps * (3 + 2 * fwd_cand_rows(n_steps)) +
+           ((size_t)G * sizeof(RowF) + sizeof(float4) - 1) / sizeof(float4);
+}
 #ifndef ISRS_FWD_MIN_BLOCKS
 #define ISRS_FWD_MIN_BLOCKS 4   // resident blocks per SM the register budget is sized for
 #endif
@@ -130,9 +139,10 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
     float4 *sRc = sR + M;                              // [ncr][M] sR rows with - at_c z folded in
     float4 *sEc = sRc + ncr * M;                       // [ncr][M] sE rows with - at_c z folded in
     RowF *rows = reinterpret_cast<RowF *>(sEc + ncr * M);   // [G]
+    // segment tables (G >= kSegMinG only; the launch sizes the space for them)
+    SegTab *sg = reinterpret_cast<SegTab *>(smem_f4 + fwd_seg_offset_f4(M, G));
     __shared__ PieceConst<float> kc;
     __shared__ ChebTab ct;
-    __shared__ SegTab sg;
     __shared__ double scratch[32];
     __shared__ int s_item;
 
@@ -183,8 +193,18 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
-            const bool segs = cheb_setup<kChebMom>(qp, pc, item.prof, sT, M, kc, ct) && qp.zs_gseg != nullptr;
-            if (segs) seg_setup(qp, pc, sT, M, kc, sg);
+            // step weights of the contracted candidates, once per piece, in the
+            // space of the per-candidate rows (filled after the tables)
+            int nW = 0;
+            if (ncr > 0 && cheb_applies(qp, pc, item.prof, kc)) {
+                nW = min(kc.nc, 2 * ncr);
+                cheb_weights(qp, pc, sT, M, kc, nW, sRc);
+                __syncthreads();
+            }
+            const bool segs = cheb_setup<kChebMom>(qp, pc, item.prof, sT, M, kc, ct, sRc, nW) &&
+                              qp.zs_gseg != nullptr && G >= kSegMinG;
+            if (segs) seg_setup(qp, pc, sT, M, kc, *sg, sRc, nW);
+            if (nW > 0) __syncthreads();
             // per-candidate step rows with the candidate's attenuation folded in
             const int ncf = min(kc.nc, ncr);
             for (int t = threadIdx.x; t < ncf * M; t += blockDim.x) {
@@ -243,7 +263,7 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
                     const float x = (u - ct.mid[ci]) * ct.invh[ci];
                     const float T2 = fmaf(2.0f * x, x, -1.0f);
                     const float T3 = fmaf(2.0f * x, T2, -x);
-                    S2 = seg_s2(sg, ci, s0, s1, x, T2, T3, phi);
+                    S2 = seg_s2(*sg, ci, s0, s1, x, T2, T3, phi);
                     ++n_small;
                 } else if (aphi <= phi_direct) {
                     S2 = ci < ncr ? zsum_direct_fc(phi, Fc, sRc + ci * M, M) : zsum_direct_f(phi, Fc, at, sR, M);
@@ -455,7 +475,7 @@ cudaError_t launch_snr_from_eta(const SnrFromEtaParams &sp, cudaStream_t st)
 size_t quad_smem_bytes(int precision, int n_steps, int G)
 {
     if (precision == 0)
-        return (size_t)n_steps * (3 + 2 * fwd_cand_rows(n_steps)) * sizeof(float4) + (size_t)G * sizeof(RowF);
+        return fwd_seg_offset_f4(n_steps, G) * sizeof(float4) + (G >= kSegMinG ? sizeof(SegTab) : 0);
     return (size_t)n_steps * 2 * sizeof(double2) + (size_t)G * sizeof(RowD);
 }
 

@@ -67,10 +67,14 @@ def ascent(engine, wl, P0_W=None, iters: int = 50, lo_dbm: float = -5.0, hi_dbm:
            resume: bool = False, log=None) -> dict:
     """Projected gradient ascent of T in dBm with Armijo backtracking.
 
-    Every iteration: one adjoint call (T and dT/dP), then forward-only calls
-    until the Armijo condition T(x') >= T(x) + c g.(x' - x) holds.  The first
-    trial step moves the largest-gradient channel by `step_db` dB; the step
-    grows by 2 after an accepted first trial and halves on each rejection.
+    Every iteration: one adjoint call (dT/dP), then forward-only calls
+    until the Armijo condition T(x') >= T(x) + c g.(x' - x) holds.  Both
+    sides of the condition are forward-call values: the adjoint call's own T
+    can differ from the forward's in the last digits (its FP32 z-sum takes a
+    different form for some points), which near the optimum would reject
+    every trial step.  The first trial step moves the largest-gradient channel
+    by `step_db` dB; the step grows by 2 after an accepted first trial and
+    halves on each rejection.
     """
     torch = _torch()
     dev = getattr(engine, "torch_device", None) or torch.device("cuda", engine.device)
@@ -86,10 +90,13 @@ def ascent(engine, wl, P0_W=None, iters: int = 50, lo_dbm: float = -5.0, hi_dbm:
     def P_of(xd):
         return torch.tensor(1e-3 * 10.0 ** (xd / 10.0), dtype=torch.float64, device=dev)
 
+    Tf = None      # forward T at x
     for it in range(start, iters):
         P = P_of(x)
         r = engine.grad(wl, P=P)
         T0 = r["T"]
+        if Tf is None:
+            Tf = engine.snr(wl, P=P)["T"]
         gx = r["dT_dP"].cpu().numpy() * (1e-3 * 10.0 ** (x / 10.0)) * LN10_10   # dT/dx [Tb/s per dB]
         # projected direction: drop components pushing against an active bound
         free = ~(((x <= lo_dbm) & (gx < 0)) | ((x >= hi_dbm) & (gx > 0)))
@@ -105,13 +112,14 @@ def ascent(engine, wl, P0_W=None, iters: int = 50, lo_dbm: float = -5.0, hi_dbm:
             xn = np.clip(x + alpha * d, lo_dbm, hi_dbm)
             Tn = engine.snr(wl, P=P_of(xn))["T"]
             evals += 1
-            if Tn >= T0 + armijo * float(np.dot(gx, xn - x)):
+            if Tn >= Tf + armijo * float(np.dot(gx, xn - x)):
                 accepted = True
                 break
             alpha *= 0.5
         step = float(np.max(np.abs(xn - x))) if accepted else 0.0
         if accepted:
             x = xn
+            Tf = Tn
             scale = min(4.0 * step_db, 2.0 * alpha * gmax) if evals == 1 else alpha * gmax
         else:
             scale *= 0.25

@@ -67,3 +67,24 @@ def test_ascent_checkpoint_resume_matches_uninterrupted(tmp_path):
     resumed = optim.ascent(FakeEngine(), _WL(7), iters=12, ckpt=ck, resume=True)
     np.testing.assert_allclose(resumed["x_dbm"], full["x_dbm"], rtol=0, atol=1e-12)
     assert len(resumed["history"]) == 12
+
+
+class _OffsetGradEngine(FakeEngine):
+    """The adjoint call's T sits a little above the forward's (as when the two
+    FP32 kernels take different z-sum forms for some points)."""
+
+    def grad(self, wl, P):
+        r = super().grad(wl, P)
+        r["T"] *= 1.0 + 1e-9
+        return r
+
+
+def test_line_search_compares_forward_values():
+    from paper_2401_18022_gb300 import optim
+    ref = optim.ascent(FakeEngine(), _WL(7), iters=40)
+    eng = _OffsetGradEngine()
+    res = optim.ascent(eng, _WL(7), iters=40)
+    # the offset changes neither the path nor the number of forward calls
+    np.testing.assert_allclose(res["x_dbm"], ref["x_dbm"], rtol=0, atol=1e-12)
+    assert [h["evals"] for h in res["history"]] == [h["evals"] for h in ref["history"]]
+    assert eng.calls["snr"] == sum(h["evals"] for h in res["history"]) + 1
