@@ -79,7 +79,7 @@ struct isrs_handle_s {
     std::string err;
     DevBuf paths, kapL;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
-        o_pase, o_T, gA, gK, gPd, gVs, ybar, dTdP, ab, ode_y, gAB, gV, gAt, partial_mci, tab_rows, tab_rowsV;
+        o_pase, o_T, gA, gK, gPd, gVs, gY, ybar, dTdP, ab, ode_y, gAB, gV, gAt, partial_mci, tab_rows, tab_rowsV;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
@@ -1043,6 +1043,8 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
         const int per_sm = adjoint_blocks_per_sm(M, g->G, block);
         int grid = h->num_sms * per_sm;
         if (g->n_items < grid) grid = std::max(1, g->n_items);
+        if ((s = ensure(h, h->gY, adjoint_scratch_bytes(grid))) != ISRS_OK) return s;
+        ap.Yg = (double *)h->gY.p;
         if ((s = mark(h, 1, 0, st)) != ISRS_OK) return s;
         if (g->n_items > 0) CK(launch_adjoint(ap, grid, block, st));
         if (g->n_mci_items > 0) {

@@ -52,6 +52,7 @@ struct AdjParams {
     double *V;                  // [n_items x n_ch]
     const int *item_slot;       // output slot of each item
     int n_ch;
+    double *Yg;                 // per block and warp: FP64 contracted bucket sums (adjoint_scratch_bytes)
 };
 
 // Chain rule from the buckets to dT/dP_j (FP64, single profile).  The
@@ -175,6 +176,7 @@ size_t quad_mci_smem_bytes(int precision, int n_steps, int n_max);
 int quad_mci_blocks_per_sm(int precision, int n_steps, int n_max, int block);
 cudaError_t launch_quad_mci(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
 size_t adjoint_smem_bytes(int n_steps, int G, int block);
+size_t adjoint_scratch_bytes(int grid);   // AdjParams.Yg of a launch of `grid` blocks
 // adjoint over the MCI cells of a separate grid (closed-form profile)
 size_t adjoint_mci_smem_bytes(int n_steps, int n_max, int block);
 int adjoint_mci_blocks_per_sm(int n_steps, int n_max, int block);

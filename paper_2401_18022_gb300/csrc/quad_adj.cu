@@ -55,6 +55,8 @@ constexpr float kShortPhiL = 0.2f;
 constexpr int kMidN = 55;
 constexpr float kMidPhiL = 2.0f;
 constexpr int kFoldBatches = 256; // batches between FP64 folds of the FP32 accumulators (one per piece at G = 256)
+constexpr int kTeleCand = 4;      // F_c candidates with their own telescoped-walk rows (attenuation folded in)
+constexpr int kAdjWarps = 8;      // warps per block at most (launch bound 256 threads)
 constexpr float kPadLog2 = -1000.0f;   // log2 weight of the padding steps (ex2 -> 0)
 
 // Forward-sum bookkeeping of one grid point: the point's owner (every lane
@@ -141,7 +143,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     float4 *sT = smem_f4;                                     // [M] {A2 + log2 dz, K2, z, z^2 + dz^2/12}
     float4 *sO0 = sT + M;                                     // [K][16] owned {A2 + log2 dz, K2, z, dz}
     float4 *sO1 = sO0 + K * 16;                               // [K][16] owned {edge/2pi hi, lo, A2, c}
-    float4 *sL = sO1 + K * 16;                                // [nw][3][kListCap] {w W af, phi, F_c, ci}
+    float4 *sOc = sO1 + K * 16;                               // [kTeleCand][K][16] {hi, lo, A2 - at_c z, K2}
+    float4 *sL = sOc + kTeleCand * K * 16;                    // [nw][3][kListCap] {w W af, phi, F_c, ci}
     double2 *sB = reinterpret_cast<double2 *>(sL + nw * 3 * kListCap);   // [nw][K][16] FP64 step buckets
     RowF *rows = reinterpret_cast<RowF *>(sB + nw * K * 16);             // [G]
     __shared__ PieceConst<float> kc;
@@ -150,16 +153,17 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     __shared__ double scratch[32];
     __shared__ int s_item;
     // small-phase points of contracted candidates: per-warp moment sums (FP32
-    // between folds, FP64 after), their block totals, and the per-step bucket
-    // terms they give for the tile
-    __shared__ float sYf[8][kCtr][kCtrS];
-    __shared__ double sY[8][kCtr][kCtrN];
+    // between folds in shared memory, FP64 after in this block's global
+    // scratch, touched once per fold), their block totals, and the per-step
+    // bucket terms they give for the tile
+    __shared__ float sYf[kAdjWarps][kCtr][kCtrS];
+    double *gY = ap.Yg + (size_t)blockIdx.x * kAdjWarps * kCtr * kCtrN;   // [warp][c][v]
     __shared__ double sYt[kCtr][kCtrN];
     __shared__ double2 sC[128];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < 8 * kCtr * kCtrN; t += blockDim.x) (&sY[0][0][0])[t] = 0.0;
-    for (int t = threadIdx.x; t < 8 * kCtr * kCtrS; t += blockDim.x) (&sYf[0][0][0])[t] = 0.0f;
+    for (int t = threadIdx.x; t < kAdjWarps * kCtr * kCtrN; t += blockDim.x) gY[t] = 0.0;
+    for (int t = threadIdx.x; t < kAdjWarps * kCtr * kCtrS; t += blockDim.x) (&sYf[0][0][0])[t] = 0.0f;
     for (int t = threadIdx.x; t < 128; t += blockDim.x) sC[t] = make_double2(0.0, 0.0);
     for (int t = threadIdx.x; t < nw * K * 16; t += blockDim.x) sB[t] = make_double2(0.0, 0.0);
     for (int t = threadIdx.x; t < 16 * kMaxCand; t += blockDim.x) sVc[t] = 0.0f;
@@ -226,6 +230,14 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
+            // telescoped-walk rows of the first candidates (read after the setup's sync)
+            for (int t = threadIdx.x; t < kTeleCand * K * 16; t += blockDim.x) {
+                const int c = t / (K * 16), r = t - c * (K * 16);
+                if (c < kc.nc) {
+                    const float4 a = sO0[r], b = sO1[r];
+                    sOc[t] = make_float4(b.x, b.y, fmaf(-(kc.at_ab + kc.hat[c]), a.z, b.z), a.y);
+                }
+            }
             // step weights of the contracted candidates, once per piece, in the
             // (empty until the points start) list space
             int nW = 0;
@@ -364,7 +376,11 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                     const float4 st = Lt[p];
                     const int pci = __float_as_int(st.w);
                     const float at = kc.at_ab + kc.hat[pci];
-                    const float val = walk_tele<K>(o0s, o1s, l16, st.x, st.y, st.z, at, mult, R, Rp);
+                    // both halves on folded rows, or both on the shared tables
+                    const float val = __all_sync(kFull, pci < kTeleCand)
+                                          ? walk_tele<K, false, true>(o0s, sOc + pci * K * 16 + l16, l16, st.x, st.y,
+                                                                      st.z, at, mult, R, Rp)
+                                          : walk_tele<K>(o0s, o1s, l16, st.x, st.y, st.z, at, mult, R, Rp);
                     fwd_add(fa, val, pci, l16 == 0, sVc);
                 }
                 for (int p = half; p + 1 - half < ns; p += 2) {
@@ -401,7 +417,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                     }
                     for (int t = lane; t < kCtr * kCtrS; t += 32) {
                         const int c = t / kCtrS, v = t - c * kCtrS;
-                        if (v < kCtrN) sY[warp][c][v] += (double)sYf[warp][c][v];
+                        if (v < kCtrN) gY[(warp * kCtr + c) * kCtrN + v] += (double)sYf[warp][c][v];
                         sYf[warp][c][v] = 0.0f;
                     }
                 }
@@ -419,7 +435,11 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 float4 st = Lt[0];
                 const int pci = __float_as_int(st.w);
                 if (half) st.x = 0.0f;
-                const float val = walk_tele<K>(o0s, o1s, l16, st.x, st.y, st.z, kc.at_ab + kc.hat[pci], mult, R, Rp);
+                const float val = pci < kTeleCand
+                                      ? walk_tele<K, false, true>(o0s, sOc + pci * K * 16 + l16, l16, st.x, st.y,
+                                                                  st.z, 0.0f, mult, R, Rp)
+                                      : walk_tele<K>(o0s, o1s, l16, st.x, st.y, st.z, kc.at_ab + kc.hat[pci], mult,
+                                                     R, Rp);
                 fwd_add(fa, val, pci, l16 == 0, sVc);
             }
             if (ns) {
@@ -442,7 +462,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             __syncwarp();
             for (int t = lane; t < kCtr * kCtrS; t += 32) {
                 const int c = t / kCtrS, v = t - c * kCtrS;
-                if (v < kCtrN) sY[warp][c][v] += (double)sYf[warp][c][v];
+                if (v < kCtrN) gY[(warp * kCtr + c) * kCtrN + v] += (double)sYf[warp][c][v];
                 sYf[warp][c][v] = 0.0f;
             }
             // piece totals: the forward sum and the PSD buckets V_ij
@@ -454,8 +474,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                     const int c = t / kCtrN, e = t - c * kCtrN;
                     double y = 0.0;
                     for (int w = 0; w < nw; ++w) {
-                        y += sY[w][c][e];
-                        sY[w][c][e] = 0.0;
+                        double &g = gY[(w * kCtr + c) * kCtrN + e];
+                        y += g;
+                        g = 0.0;
                     }
                     sYt[c][e] = y;
                 }
@@ -685,8 +706,13 @@ __global__ void __launch_bounds__(256) k_chain(ChainParams cp)
 size_t adjoint_smem_bytes(int n_steps, int G, int block)
 {
     const int K = (n_steps + 15) / 16, nw = block / 32;
-    return (size_t)(n_steps + 2 * K * 16 + nw * 3 * kListCap) * sizeof(float4) +
+    return (size_t)(n_steps + (2 + kTeleCand) * K * 16 + nw * 3 * kListCap) * sizeof(float4) +
            (size_t)nw * K * 16 * sizeof(double2) + (size_t)G * sizeof(RowF);
+}
+
+size_t adjoint_scratch_bytes(int grid)
+{
+    return (size_t)grid * kAdjWarps * kCtr * kCtrN * sizeof(double);
 }
 
 template <int K>

@@ -34,7 +34,9 @@ __device__ __forceinline__ float half_sum(float v)
 // Half-warp walks of one grid point (state: weight w W af, phi, F_c - f_ref,
 // at).  Lane l16 owns steps [K l16, K l16 + K) with tables
 //   o0[k] = {A2 + log2 dz, K2, z, dz},  o1[k] = {edge/2pi hi, lo, A2, c}
-// (padding steps carry log2 weight -1000, so their terms vanish).  Each walk
+// (padding steps carry log2 weight -1000, so their terms vanish), and for
+// the first F_c candidates of the piece oc[k] = {edge/2pi hi, lo,
+// A2 - at_c z, K2}.  Each walk
 // adds the lane's bucket terms and returns the point's w W af |S|^2.
 // ---------------------------------------------------------------------------
 template <int K>
@@ -71,7 +73,10 @@ __device__ __forceinline__ float walk_direct(const float4 *o0s, float wq, float 
     return wq * fmaf(sr, sr, si * si);
 }
 
-template <int K, bool Wide = false>
+// Folded: o1s holds the point's candidate rows {edge/2pi hi, lo, A2 - at z, K2}
+// (attenuation folded in), so a step takes one table load and one FMA for
+// ln p; o0s and at are then unused.
+template <int K, bool Wide = false, bool Folded = false>
 __device__ __forceinline__ float walk_tele(const float4 *o0s, const float4 *o1s, int l16, float wq, float ph,
                                            float fc, float at, float mult, float (&R)[K], float (&Rp)[K])
 {
@@ -81,13 +86,18 @@ __device__ __forceinline__ float walk_tele(const float4 *o0s, const float4 *o1s,
     float Er = 1.0f, Ei = 0.0f, p0 = 0.0f, e1r = 1.0f, e1i = 0.0f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const float4 a = o0s[k * 16];
         const float4 b = o1s[k * 16];
         float sn, cs;
         if (Wide) phasor_rev_ff_wide<true>(ph, b.x, b.y, sn, cs);
         else phasor_rev_ff<true>(ph, b.x, b.y, sn, cs);
-        float lp = fmaf(a.y, fc, b.z);
-        lp = fmaf(-at, a.z, lp);
+        float lp;
+        if constexpr (Folded) {
+            lp = fmaf(b.w, fc, b.z);
+        } else {
+            const float4 a = o0s[k * 16];
+            lp = fmaf(a.y, fc, b.z);
+            lp = fmaf(-at, a.z, lp);
+        }
         const float pm = ex2_approx(lp);
         if (k == 0) {
             p0 = pm;
