@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
     const float phi_cheb = kChebPhiL / qp.L;
+    const float phi_c6 = kChebPhiL6 / qp.L, phi_c11 = kChebPhiL11 / qp.L;
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
     // the walks run on half-warps: lane l owns steps [K (l mod 16), K (l mod 16) + K)
@@ -290,9 +291,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                             const float aphi = fabsf(phi);
                             wwa = rw.w * W * array_factor_f(phi, qp);
                             if (cheb && ci < kCtr && aphi <= phi_cheb) {
-                                float nu[kChebMom];
-                                cheb_moments<kChebMom>(ct, ci, u, nu, cx);
-                                cheb_AB<kChebMom>(nu, phi, cA, cB);
+                                cheb_point(ct, ci, u, phi, aphi, phi_c6, phi_c11, cx, cA, cB);
                                 ctr = true;
                                 cls = kClsSmall;
                                 fwd_add(fa, wwa * fmaf(cA, cA, cB * cB), ci, true, sVc);

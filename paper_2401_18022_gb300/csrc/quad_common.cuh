@@ -245,6 +245,8 @@ __device__ __forceinline__ double array_factor_d(double phi, const QuadParams &q
 constexpr float kChebMaxA = 0.05f;
 constexpr int kChebMom = 19;        // nu_0 .. nu_18 (forward kernels)
 constexpr float kChebPhiL = 6.0f;   // |phi| L limit of the 19-moment form: error < 2e-8
+constexpr float kChebPhiL6 = 0.2f;  // ... of its first 6 moments: error < (0.1)^6/6! = 1.4e-9
+constexpr float kChebPhiL11 = 2.0f; // ... of its first 11 moments: error < 1/11! = 2.5e-8
 constexpr int kChebMomA = 11;       // nu_0 .. nu_10 (adjoint)
 constexpr float kChebPhiLA = 2.0f;  // |phi| L limit of the 11-moment form: error < 5e-8
 constexpr int kZsG = 5;             // float4 per step of the centred step moments g_0..g_19 (g_19 = 0)
@@ -442,6 +444,52 @@ __device__ __forceinline__ void cheb_AB(const float (&nu)[NM], float phi, float 
 #pragma unroll
     for (int i = no - 2; i >= 0; --i) b = fmaf(b, p2, nu[2 * i + 1]);
     B = phi * b;
+}
+
+// A and B of a contracted point of the 2-D series of the tabulated
+// (Raman-ODE) profile: C[4 n + k] = {c_nk0..c_nk3}, nu_n = sum_{k,l} c_nkl
+// T_k(x) T_l(y) for the point's in-channel offsets (x, y), n < NM.
+template <int NM>
+__device__ __forceinline__ void cheb2_AB(const float4 *C, float x, float y, float phi, float &A, float &B)
+{
+    const float Tx2 = fmaf(2.0f * x, x, -1.0f), Tx3 = fmaf(2.0f * x, Tx2, -x);
+    const float Ty2 = fmaf(2.0f * y, y, -1.0f), Ty3 = fmaf(2.0f * y, Ty2, -y);
+    float nu[NM];
+#pragma unroll
+    for (int n = 0; n < NM; ++n) {
+        float r[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 c = C[n * 4 + k];
+            r[k] = fmaf(c.w, Ty3, fmaf(c.z, Ty2, fmaf(c.y, y, c.x)));
+        }
+        nu[n] = fmaf(r[3], Tx3, fmaf(r[2], Tx2, fmaf(r[1], x, r[0])));
+    }
+    cheb_AB<NM>(nu, phi, A, B);
+}
+
+// A and B of a contracted point with as many moments as its phase needs:
+// the omitted orders of the centred series are below (|phi| L / 2)^n / n!
+// of the kept ones, so 6 moments serve |phi| L <= 0.2, 11 serve |phi| L <= 2
+// and 19 the rest of the contracted range (rows of the grid have nearly
+// constant phi, so a warp seldom splits between the forms).
+template <int NC>
+__device__ __forceinline__ void cheb_point(const ChebTabN<NC> &ct, int ci, float u, float phi, float aphi,
+                                           float phi6, float phi11, float &x, float &A, float &B)
+{
+    if (aphi <= phi6) {
+        float nu[6];
+        cheb_moments<6>(ct, ci, u, nu, x);
+        cheb_AB<6>(nu, phi, A, B);
+    } else if (aphi <= phi11) {
+        float nu[11];
+        cheb_moments<11>(ct, ci, u, nu, x);
+        cheb_AB<11>(nu, phi, A, B);
+    } else {
+        float nu[kChebMom];
+        cheb_moments<kChebMom>(ct, ci, u, nu, x);
+        cheb_AB<kChebMom>(nu, phi, A, B);
+    }
 }
 
 // ---------------------------------------------------------------------------

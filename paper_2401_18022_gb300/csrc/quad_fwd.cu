@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
     const float phi_cheb = kChebPhiL / qp.L;
+    const float phi_c6 = kChebPhiL6 / qp.L, phi_c11 = kChebPhiL11 / qp.L;
     const float phi_s0 = qp.phi_seg[0], phi_s1 = qp.phi_seg[1], phi_s2 = qp.phi_seg[2];
     const float log2e = (float)kLog2e;
     const float invG = 1.0f / (float)G;
@@ -248,9 +249,8 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
                 float S2;
                 if (aphi <= phi_lim) {
                     if (cheb) {
-                        float nu[kChebMom], x, A, B;
-                        cheb_moments<kChebMom>(ct, ci, u, nu, x);
-                        cheb_AB<kChebMom>(nu, phi, A, B);
+                        float x, A, B;
+                        cheb_point(ct, ci, u, phi, aphi, phi_c6, phi_c11, x, A, B);
                         S2 = fmaf(A, A, B * B);
                     } else {
                         S2 = zsum_small_f(phi, Fc, at, sT, M);

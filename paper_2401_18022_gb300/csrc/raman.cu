@@ -617,25 +617,15 @@ __device__ bool tab_cheb_setup(const QuadParams &qp, const DevPiece &pc, int nc,
     return true;
 }
 
-// |S|^2 of a small-phase point of candidate ci from the contracted series.
-__device__ __forceinline__ float tab_cheb_s2(const float4 *sC, int ci, float x, float y, float phi)
+// |S|^2 of a small-phase point of candidate ci from the contracted series
+// (6 moments serve |phi| L <= 0.2, as in cheb_point).
+__device__ __forceinline__ float tab_cheb_s2(const float4 *sC, int ci, float x, float y, float phi, float aphi,
+                                             float phi6)
 {
-    const float Tx2 = fmaf(2.0f * x, x, -1.0f), Tx3 = fmaf(2.0f * x, Tx2, -x);
-    const float Ty2 = fmaf(2.0f * y, y, -1.0f), Ty3 = fmaf(2.0f * y, Ty2, -y);
-    float nu[kTabMom];
     const float4 *C = sC + ci * kTabMom * 4;
-#pragma unroll
-    for (int n = 0; n < kTabMom; ++n) {
-        float r[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float4 c = C[n * 4 + k];
-            r[k] = fmaf(c.w, Ty3, fmaf(c.z, Ty2, fmaf(c.y, y, c.x)));
-        }
-        nu[n] = fmaf(r[3], Tx3, fmaf(r[2], Tx2, fmaf(r[1], x, r[0])));
-    }
     float A, B;
-    cheb_AB<kTabMom>(nu, phi, A, B);
+    if (aphi <= phi6) cheb2_AB<6>(C, x, y, phi, A, B);
+    else cheb2_AB<kTabMom>(C, x, y, phi, A, B);
     return fmaf(A, A, B * B);
 }
 
@@ -671,6 +661,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
     const float phi_cheb = kChebPhiLA / qp.L;
+    const float phi_c6 = kChebPhiL6 / qp.L;
     const float invG = 1.0f / (float)G;
     unsigned n_small = 0, n_direct = 0, n_tele = 0;
 
@@ -733,7 +724,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
                 const float aphi = fabsf(phi);
                 float S2;
                 if (aphi <= phi_lim) {
-                    S2 = cheb ? tab_cheb_s2(sC, ci, da * inv_ha, db * inv_hb, phi) : zsum_small_t(phi, da, db, Q, sZ, M);
+                    S2 = cheb ? tab_cheb_s2(sC, ci, da * inv_ha, db * inv_hb, phi, aphi, phi_c6) : zsum_small_t(phi, da, db, Q, sZ, M);
                     ++n_small;
                 } else if (aphi <= phi_direct) {
                     S2 = zsum_direct_t(phi, da, db, Q, sZ, M);

@@ -129,23 +129,13 @@ __device__ void tab_adj_coeffs(const QuadParams &qp, const float4 *Q, float ha, 
     __syncthreads();
 }
 
-// A and B (|S|^2 = A^2 + B^2) of a contracted point at offsets (x, y).
-__device__ __forceinline__ void tab_adj_AB(const float4 *sCc, float x, float y, float phi, float &A, float &B)
+// A and B (|S|^2 = A^2 + B^2) of a contracted point at offsets (x, y)
+// (6 moments serve |phi| L <= 0.2, as in cheb_point).
+__device__ __forceinline__ void tab_adj_AB(const float4 *sCc, float x, float y, float phi, float aphi, float phi6,
+                                           float &A, float &B)
 {
-    const float Tx2 = fmaf(2.0f * x, x, -1.0f), Tx3 = fmaf(2.0f * x, Tx2, -x);
-    const float Ty2 = fmaf(2.0f * y, y, -1.0f), Ty3 = fmaf(2.0f * y, Ty2, -y);
-    float nu[kTabMom];
-#pragma unroll
-    for (int n = 0; n < kTabMom; ++n) {
-        float r[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float4 c = sCc[n * 4 + k];
-            r[k] = fmaf(c.w, Ty3, fmaf(c.z, Ty2, fmaf(c.y, y, c.x)));
-        }
-        nu[n] = fmaf(r[3], Tx3, fmaf(r[2], Tx2, fmaf(r[1], x, r[0])));
-    }
-    cheb_AB<kTabMom>(nu, phi, A, B);
+    if (aphi <= phi6) cheb2_AB<6>(sCc, x, y, phi, A, B);
+    else cheb2_AB<kTabMom>(sCc, x, y, phi, A, B);
 }
 
 // Warp sums of the contracted bucket values of group G0 (values 32 G0 ..
@@ -390,6 +380,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
     const float phi_direct = 3.14159265f / qp.dz_max;
     const float phi_small = 0.02f / qp.L;
     const float phi_cheb = kChebPhiLA / qp.L;
+    const float phi_c6 = kChebPhiL6 / qp.L;
     const float invG = 1.0f / (float)G;
     const float4 *oq = sOQ + l16, *oz = sOZ + l16, *oe = sOE + l16;
     float *Yw = sYt[warp];
@@ -496,7 +487,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                                     if (cheb && aphi <= phi_cheb) {
                                         cx = da * invha;
                                         cy = db * invhb;
-                                        tab_adj_AB(sCc, cx, cy, phi, cA, cB);
+                                        tab_adj_AB(sCc, cx, cy, phi, aphi, phi_c6, cA, cB);
                                         vsum += cp * fmaf(cA, cA, cB * cB);
                                         ctr = true;
                                     } else {
