@@ -44,15 +44,13 @@ constexpr int kListCap = 34;    // a form's list: one carried point + 32 new (+1
 constexpr int kCtr = 3;         // F_c candidates whose small-phase points are contracted
 constexpr int kCtrN = kChebMom * 5;   // per candidate: moments nu_0..nu_18 x T_0..T_4
 constexpr int kCtrS = 96;       // slots per candidate (three 32-value butterflies)
-// The bucket sums of a batch keep the orders its largest contracted |phi| L
-// needs: n <= 5 up to 0.2 (30 values, one butterfly; omitted orders below
-// (0.1)^6/6! = 1.4e-9 of the derivative), n <= 10 up to 2 (55 values, two
-// butterflies; below 2 (1)^11/11! = 5e-8), n <= 18 up to 6 (95 values, three
-// butterflies; below 2 (3)^19/19! = 1.9e-8).  Rows of the grid have nearly
-// constant phi, so most batches take one form throughout.
-constexpr int kShortN = 30;
+// The bucket sums of a batch keep at least the orders its largest contracted
+// |phi| L needs: n <= 5 up to 0.2 (one butterfly, values 0..31; omitted
+// orders below (0.1)^6/6! = 1.4e-9 of the derivative), n <= 10 up to 2 (two,
+// values 0..63; below 2 (1)^11/11! = 5e-8), n <= 18 up to 6 (three, values
+// 0..94; below 2 (3)^19/19! = 1.9e-8).  Rows of the grid have nearly constant
+// phi, so most batches take one form throughout.
 constexpr float kShortPhiL = 0.2f;
-constexpr int kMidN = 55;
 constexpr float kMidPhiL = 2.0f;
 constexpr int kFoldBatches = 256; // batches between FP64 folds of the FP32 accumulators (one per piece at G = 256)
 constexpr int kTeleCand = 4;      // F_c candidates with their own telescoped-walk rows (attenuation folded in)
@@ -86,11 +84,13 @@ __device__ __forceinline__ void fwd_add(FwdAcc &a, float val, int ci, bool owner
 }
 
 // Warp sums of the contracted bucket values of group G0 (values 32 G0 ..
-// 32 G0 + 31 of the first nv): value v = al_n T_k(x) with n = v / 5,
-// k = v mod 5, al_n = ae phi^n (n even) or ao phi^(n-1) (n odd; ao carries one
-// phi).  Only the 7 orders the group spans are formed.
+// 32 G0 + 31): value v = al_n T_k(x) with n = v / 5, k = v mod 5, al_n = ae
+// phi^n (n even) or ao phi^(n-1) (n odd; ao carries one phi).  Only the
+// orders the group spans are formed.  A batch that needs fewer orders than
+// the group holds still sums all 32: the extra ones are further terms of the
+// same series, so they can only be kept (slots up to 94) or dropped.
 template <int G0>
-__device__ __forceinline__ float ctr_group(float ae, float ao, float p2, const float (&Tk)[5], int nv, int lane)
+__device__ __forceinline__ float ctr_group(float ae, float ao, float p2, const float (&Tk)[5], int lane)
 {
     constexpr int N0 = (32 * G0) / 5;          // 0, 6, 12: even
     float pw = 1.0f;
@@ -104,7 +104,7 @@ __device__ __forceinline__ float ctr_group(float ae, float ao, float p2, const f
     return butterfly32(
         [&](int v) {
             const int va = 32 * G0 + v;
-            return va < nv ? a[va / 5 - N0] * Tk[va % 5] : 0.0f;
+            return a[va / 5 - N0] * Tk[va % 5];
         },
         lane);
 }
@@ -328,16 +328,15 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                         const float ae = mine ? 2.0f * cpt * cA : 0.0f;
                         const float ao = mine ? 2.0f * cpt * cB * phi : 0.0f;
                         const float p2 = phi * phi;
-                        const int nv = form == 0 ? kShortN : (form == 1 ? kMidN : kCtrN);
                         float *Yw = sYf[warp][cl];
-                        const float y0 = ctr_group<0>(ae, ao, p2, Tk, nv, lane);
-                        if (lane < nv) Yw[lane] += y0;
+                        const float y0 = ctr_group<0>(ae, ao, p2, Tk, lane);
+                        Yw[lane] += y0;
                         if (form >= 1) {
-                            const float y1 = ctr_group<1>(ae, ao, p2, Tk, nv, lane);
+                            const float y1 = ctr_group<1>(ae, ao, p2, Tk, lane);
                             Yw[lane + 32] += y1;
                         }
                         if (form == 2) {
-                            const float y2 = ctr_group<2>(ae, ao, p2, Tk, nv, lane);
+                            const float y2 = ctr_group<2>(ae, ao, p2, Tk, lane);
                             Yw[lane + 64] += y2;
                         }
                         cmask &= ~__ballot_sync(kFull, mine);
