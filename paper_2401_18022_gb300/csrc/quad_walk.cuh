@@ -127,7 +127,7 @@ __device__ __forceinline__ float walk_tele(const float4 *o0s, const float4 *o1s,
     }
     ur = half_sum(ur);
     ui = half_sum(ui);
-    const float iph2 = 1.0f / (ph * ph);
+    const float iph2 = __fdividef(1.0f, ph * ph);   // MUFU reciprocal (2 ulp): phi^2 is far from the range limits
     const float c2 = 2.0f * mult * wq * iph2, c2F = c2 * fc;
 #pragma unroll
     for (int k = 0; k < K; ++k) {

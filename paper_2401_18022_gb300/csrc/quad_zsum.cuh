@@ -30,6 +30,9 @@ namespace isrs {
 //    (E_{m+1} - E_m)/(j phi) with E_e = e^{j phi z_e}, so one complex
 //    exponential per edge suffices; the phase phi z_e / 2pi (up to ~1e5
 //    revolutions) is an error-free float-float product reduced to [-1/2, 1/2].
+// The final division by phi^2 takes the MUFU reciprocal (2 ulp; phi^2 lies
+// far inside the range where it is accurate): an IEEE division there costs
+// a branch to its slow path at every point.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float zsum_small_f(float phi, float Fc, float at, const float4 *sT, int M)
 {
@@ -92,7 +95,7 @@ __device__ __forceinline__ float zsum_tele_f(float phi, float Fc, float at, cons
         Er = cs;
         Ei = sn;
     }
-    return (Sr * Sr + Si * Si) / (phi * phi);
+    return __fdividef(Sr * Sr + Si * Si, phi * phi);
 }
 
 // The same two forms with the candidate's attenuation folded into the step
@@ -138,7 +141,7 @@ __device__ __forceinline__ float zsum_tele_fc(float phi, float Fc, const float4 
         Er = cs;
         Ei = sn;
     }
-    return (Sr * Sr + Si * Si) / (phi * phi);
+    return __fdividef(Sr * Sr + Si * Si, phi * phi);
 }
 
 // As phasor_rev_ff, for phases far beyond 2^22 revolutions (the MCI cells):
@@ -175,7 +178,7 @@ __device__ __forceinline__ float zsum_tele_wide_f(float phi, float Fc, float at,
         Er = cs;
         Ei = sn;
     }
-    return (Sr * Sr + Si * Si) / (phi * phi);
+    return __fdividef(Sr * Sr + Si * Si, phi * phi);
 }
 
 }  // namespace isrs

@@ -542,7 +542,7 @@ __device__ __forceinline__ float zsum_tele_t(float phi, float da, float db, cons
         Er = cs;
         Ei = sn;
     }
-    return (Sr * Sr + Si * Si) / (phi * phi);
+    return __fdividef(Sr * Sr + Si * Si, phi * phi);
 }
 
 // ---------------------------------------------------------------------------

@@ -271,7 +271,7 @@ __device__ __forceinline__ float walk_tele_t(const float4 *oq, const float4 *oe,
     }
     ur = half_sum_t(ur);
     ui = half_sum_t(ui);
-    const float iph2 = 1.0f / (ph * ph);
+    const float iph2 = __fdividef(1.0f, ph * ph);
     const float c2 = 2.0f * cp * iph2, ca = c2 * da, cb = c2 * db;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
