@@ -301,9 +301,9 @@ def _snr_eval(eng, wl, P, dev, n_grid, reps: int = 2):
 # full size (same G, same per-piece shape), so each count is scaled to a full
 # launch by evaluated points.
 ADJ_CAPTURE = {"profile": "k_quad_adj_uwb148_every4th_G256.md", "points": 2880700416,
-               "dram_bytes": 4.548e6, "warp_inst": 1.760e11, "fp32_warp_inst": 9.308e10}
+               "dram_bytes": 4.861e6, "warp_inst": 1.587e11, "fp32_warp_inst": 8.530e10}
 FWD_CAPTURE = {"profile": "k_quad_f32_uwb148_every4th_G256.md", "points": 2880700416,
-               "dram_bytes": 4.056e6, "warp_inst": 8.69e10, "fp32_warp_inst": 5.76e10}
+               "dram_bytes": 4.126e6, "warp_inst": 7.114e10, "fp32_warp_inst": 4.469e10}
 ISSUE_PER_CLK_PER_SM = 4         # one warp instruction per clock per SM sub-partition
 
 
