@@ -202,8 +202,8 @@ def run_gpu(args):
     info = eng.last_launch_info()
     launches_per_step = info["launches"]
     if split:
-        # prep + fused forward/adjoint + finish, then SNR from eta + 4 chain kernels
-        launches_per_step = 3 + 5
+        # prep + fused forward/adjoint + finish, then SNR from eta + 6 chain kernels
+        launches_per_step = 3 + 7
         eng.grad_shard_fwd(wl, D.shard_cuts(wl.n_ch, rank, world, weights), P)
         info = eng.last_launch_info()
 

@@ -1394,7 +1394,9 @@ isrs_status chain_buffers(isrs_handle h, const isrs_fibre *fb, const isrs_quad *
 {
     isrs_status s;
     if ((s = ensure(h, h->ybar, sizeof(double) * 2 * n)) != ISRS_OK) return s;
-    if ((s = ensure(h, h->gK, sizeof(double2) * g->n_steps)) != ISRS_OK) return s;
+    if ((s = ensure(h, h->gK, sizeof(double2) * g->n_steps + sizeof(double) * (4 * (g->n_steps + 1) + 4))) !=
+        ISRS_OK)
+        return s;
     if ((s = ensure(h, h->dTdP, sizeof(double) * n)) != ISRS_OK) return s;
     if ((s = ensure(h, h->gVs, sizeof(double) * (size_t)std::max(1, g->n_slots) * n)) != ISRS_OK) return s;
     cp = chain_params(h, fb, q, g, n);
@@ -1406,6 +1408,7 @@ isrs_status chain_buffers(isrs_handle h, const isrs_fibre *fb, const isrs_quad *
     cp.slot_items2 = g->n_mci_items > 0 ? (const int2 *)g->slot_items2.p : nullptr;
     cp.n_items_reg = g->n_items;
     cp.Rb = (double2 *)h->gK.p;
+    cp.cs = (double *)((double2 *)h->gK.p + g->n_steps);
     return ISRS_OK;
 }
 
@@ -1728,7 +1731,7 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
         Range r_chain("isrs chain rule (dT/dP)");
         CK(launch_chain(cp, st));
     }
-    h->last_launches += 4;   // ybar, PSD-bucket reduction, step-bucket reduction, chain rule
+    h->last_launches += 6;   // ybar, PSD-bucket reduction, step-bucket reduction, chain rule (3)
     return grad_outputs(h, n, dT_dP, snr, eta, T_host, st);
 }
 
@@ -1841,7 +1844,7 @@ isrs_status isrs_gn_grad_shard_bwd(isrs_handle h, const double *eta_all, int wit
         Range r_chain("isrs chain rule (dT/dP)");
         CK(launch_chain(cp, st));
     }
-    h->last_launches = 5;    // SNR from eta, ybar, PSD-bucket reduction, step-bucket reduction, chain rule
+    h->last_launches = 7;    // SNR from eta, ybar, PSD-bucket reduction, step-bucket reduction, chain rule (3)
     bool host_out = false;
     if ((s = copy_out(h, dT_dP, h->dTdP, n, st, host_out)) != ISRS_OK) return s;
     if (snr) {

@@ -77,6 +77,8 @@ struct ChainParams {
     double *ybar;               // [n_ch] dT/dSigma_i
     double *aase;               // [n_ch] dT/dASE_i * dASE_i/d ln G_i
     double2 *Rb;                // [n_steps] sum over the shard's tiles of ybar_i {R_im, R'_im}
+    double *cs;                 // [4 (n_steps + 1) + 4] profile terms per step (ln N, kappa, L_eff, Fbar), then
+                                // the channel-independent sums of the chain rule
     double *dT_dP;              // [n_ch]
 };
 

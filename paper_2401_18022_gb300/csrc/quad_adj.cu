@@ -620,75 +620,111 @@ __device__ __forceinline__ double dlog_sinhc(double y)
     return fabs(y) < 1e-3 ? y / 3.0 - y * y * y / 45.0 : 1.0 / tanh(y) - 1.0 / y;
 }
 
-__global__ void __launch_bounds__(256) k_chain(ChainParams cp)
+// Block maximum (every thread gets it; scratch holds 32 values).
+__device__ __forceinline__ double block_max_d(double v, double *scratch)
 {
-    __shared__ double s_lnN[kMaxAdjSteps + 1], s_kap[kMaxAdjSteps + 1], s_Le[kMaxAdjSteps + 1],
-        s_Fb[kMaxAdjSteps + 1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double m = -1e300;
+    for (int w = 0; w < nw; ++w) m = fmax(m, scratch[w]);
+    return m;
+}
+
+// The chain rule in three launches, every sum in a fixed order:
+//  k_chain_steps  one block per z-step m (and z = L at m = M): ln N(z_m),
+//                 kappa_m, L_eff(z_m) and the tilted mean Fbar(z_m) - f_ref;
+//  k_chain_const  the channel-independent sums (one block);
+//  k_chain_ch     one warp per channel j: its lanes split the steps and the
+//                 output slots, a warp tree sums them.
+// cs = [lnN | kappa | L_eff | Fbar] (M + 1 each), then {R' term, sum of aase,
+// ASE tilt term, P_tot}.
+__global__ void __launch_bounds__(256) k_chain_steps(ChainParams cp)
+{
     __shared__ double scratch[32];
-    __shared__ double s_const[4];
-    const int n = cp.n_ch, M = cp.n_steps;
+    const int n = cp.n_ch, M = cp.n_steps, m = blockIdx.x;
     double part = 0.0;
     for (int c = threadIdx.x; c < n; c += blockDim.x) part += cp.P[c];
     const double Ptot = block_sum_d(part, scratch);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // per step m (and z = L at index M): ln N, kappa, L_eff and the tilted mean Fbar - f_ref
-    for (int m = wid; m <= M; m += nw) {
-        const double z = m < M ? cp.zs_d[m].x : cp.L;
-        const double Le = cp.alpha_R > 0.0 ? -expm1(-cp.alpha_R * z) / cp.alpha_R : z;
-        const double kap = Ptot * cp.Cr * Le;
-        double mx = -1e300;
-        for (int c = lane; c < n; c += 32)
-            mx = fmax(mx, log(cp.P[c]) - kap * cp.ch_frel[c] + log(sinhc_ad(0.5 * kap * cp.ch_B[c])));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        double s0 = 0.0, s1 = 0.0;
-        for (int c = lane; c < n; c += 32) {
-            const double a = 0.5 * cp.ch_B[c];
-            const double w = exp(log(cp.P[c]) - kap * cp.ch_frel[c] + log(sinhc_ad(kap * a)) - mx);
-            s0 += w;
-            s1 += w * (cp.ch_frel[c] - a * dlog_sinhc(kap * a));
-        }
-        s0 = warp_sum_d(s0);
-        s1 = warp_sum_d(s1);
-        if (lane == 0) {
-            s_lnN[m] = mx + log(s0);
-            s_kap[m] = kap;
-            s_Le[m] = Le;
-            s_Fb[m] = s1 / s0;
-        }
+    const double z = m < M ? cp.zs_d[m].x : cp.L;
+    const double Le = cp.alpha_R > 0.0 ? -expm1(-cp.alpha_R * z) / cp.alpha_R : z;
+    const double kap = Ptot * cp.Cr * Le;
+    double mx = -1e300;
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        mx = fmax(mx, log(cp.P[c]) - kap * cp.ch_frel[c] + log(sinhc_ad(0.5 * kap * cp.ch_B[c])));
+    mx = block_max_d(mx, scratch);
+    double s0 = 0.0, s1 = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const double a = 0.5 * cp.ch_B[c];
+        const double w = exp(log(cp.P[c]) - kap * cp.ch_frel[c] + log(sinhc_ad(kap * a)) - mx);
+        s0 += w;
+        s1 += w * (cp.ch_frel[c] - a * dlog_sinhc(kap * a));
     }
-    __syncthreads();
-    // j-independent sums
+    s0 = block_sum_d(s0, scratch);
+    s1 = block_sum_d(s1, scratch);
+    if (threadIdx.x == 0) {
+        const int st = M + 1;
+        cp.cs[m] = mx + log(s0);
+        cp.cs[st + m] = kap;
+        cp.cs[2 * st + m] = Le;
+        cp.cs[3 * st + m] = s1 / s0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_chain_const(ChainParams cp)
+{
+    __shared__ double scratch[32];
+    const int n = cp.n_ch, M = cp.n_steps, st = M + 1;
+    const double *Le = cp.cs + 2 * st, *Fb = cp.cs + 3 * st;
+    double part = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) part += cp.P[c];
+    const double Ptot = block_sum_d(part, scratch);
     double a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) a1 += cp.Rb[m].y * s_Le[m];
+    for (int m = threadIdx.x; m < M; m += blockDim.x) a1 += cp.Rb[m].y * Le[m];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         a2 += cp.aase[i];
-        a3 += cp.aase[i] * (cp.ch_frel[i] - s_Fb[M]);
+        a3 += cp.aase[i] * (cp.ch_frel[i] - Fb[M]);
     }
     a1 = block_sum_d(a1, scratch);
     a2 = block_sum_d(a2, scratch);
     a3 = block_sum_d(a3, scratch);
     if (threadIdx.x == 0) {
-        s_const[0] = -cp.Cr * a1;                     // R' term
-        s_const[1] = a2;                              // sum of aase
-        s_const[2] = cp.Cr * s_Le[M] * a3;            // ASE tilt term
+        double *k = cp.cs + 4 * st;
+        k[0] = -cp.Cr * a1;              // R' term
+        k[1] = a2;                       // sum of aase
+        k[2] = cp.Cr * Le[M] * a3;       // ASE tilt term
+        k[3] = Ptot;
     }
-    __syncthreads();
-    const double invPt = 1.0 / Ptot;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double fj = cp.ch_frel[j], hB = 0.5 * cp.ch_B[j];
-        double g = s_const[0];
-        for (int m = 0; m < M; ++m) {
-            const double hN = exp(-s_kap[m] * fj + log(sinhc_ad(s_kap[m] * hB)) - s_lnN[m]);
-            g += cp.Rb[m].x * (invPt - hN + cp.Cr * s_Le[m] * s_Fb[m]);
-        }
-        double v = 0.0;
-        for (int s = 0; s < cp.n_slots; ++s) v += cp.ybar[cp.slot_cut[s]] * cp.V[(size_t)s * n + j];
-        g += v / cp.P[j];
+}
+
+__global__ void __launch_bounds__(256) k_chain_ch(ChainParams cp)
+{
+    const int n = cp.n_ch, M = cp.n_steps, st = M + 1;
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;                  // warp-uniform
+    const double *lnN = cp.cs, *kap = cp.cs + st, *Le = cp.cs + 2 * st, *Fb = cp.cs + 3 * st;
+    const double *k = cp.cs + 4 * st;
+    const double invPt = 1.0 / k[3];
+    const double fj = cp.ch_frel[j], hB = 0.5 * cp.ch_B[j];
+    double gm = 0.0;
+    for (int m = lane; m < M; m += 32) {
+        const double hN = exp(-kap[m] * fj + log(sinhc_ad(kap[m] * hB)) - lnN[m]);
+        gm += cp.Rb[m].x * (invPt - hN + cp.Cr * Le[m] * Fb[m]);
+    }
+    double v = 0.0;
+    for (int s = lane; s < cp.n_slots; s += 32) v += cp.ybar[cp.slot_cut[s]] * cp.V[(size_t)s * n + j];
+    gm = warp_sum_d(gm);
+    v = warp_sum_d(v);
+    if (lane == 0) {
+        double g = k[0] + gm + v / cp.P[j];
         if (cp.with_direct) {
             // through the ASE gain of every channel, and the SNR numerator
-            const double hNL = exp(-s_kap[M] * fj + log(sinhc_ad(s_kap[M] * hB)) - s_lnN[M]);
-            g += -s_const[1] * (invPt - hNL) + s_const[2];
+            const double hNL = exp(-kap[M] * fj + log(sinhc_ad(kap[M] * hB)) - lnN[M]);
+            g += -k[1] * (invPt - hNL) + k[2];
             const double snr = cp.snr[j], P = cp.P[j], B = cp.ch_B[j];
             const double N = cp.pnli[j] + cp.pase[j];
             const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
@@ -773,7 +809,11 @@ cudaError_t launch_chain(const ChainParams &cp, cudaStream_t st)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_adj_reduce<<<cp.n_steps, 256, 0, st>>>(cp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_chain<<<1, 256, 0, st>>>(cp);
+    k_chain_steps<<<cp.n_steps + 1, 256, 0, st>>>(cp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_chain_const<<<1, 256, 0, st>>>(cp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_chain_ch<<<(cp.n_ch + 7) / 8, 256, 0, st>>>(cp);
     return cudaGetLastError();
 }
 

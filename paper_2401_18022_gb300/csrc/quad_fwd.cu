@@ -1,8 +1,9 @@
 // Forward kernels of the ISRS GN integral model (arXiv 2401.18022, App. A).
 //
-//  k_prep        per profile (FP64): P_tot, the ISRS normalisation ln N(z_m)
-//                by log-sum-exp over channels, and the per-step power tables
-//                of Eq. pk for the linear-slope closed-form profile.
+//  k_prep        per profile and z-step (FP64): P_tot, the ISRS
+//                normalisation ln N(z_m) by log-sum-exp over channels, and the
+//                per-step power tables of Eq. pk for the linear-slope
+//                closed-form profile.
 //  k_quad_f32    persistent quadrature: one block per work tile (a range of
 //                pieces of one CUT); G x G hyperbolic grid per piece
 //                (Eqs. q1..q4), z-sum of Eq. slow_vary per grid point in FP32:
@@ -25,13 +26,16 @@
 namespace isrs {
 
 // ---------------------------------------------------------------------------
-// k_prep: ISRS profile tables (FP64).  One block per profile.
+// k_prep: ISRS profile tables (FP64).  One block per (profile, z-step), the
+// last step index standing for z = L:
 //   rho(z,F) = e^{-alpha_c z} P_tot e^{-kappa(z)(F - f_ref)} / N(z)
 //   kappa(z) = P_tot C_r L_eff(z),  N(z) = sum_k P_k e^{-kappa f_k'} sinhc(kappa B_k/2)
 // so ln p_m (Eq. pk) = lnPtot - lnN_m - kappa_m (F_c - f_ref) - at z_m with
 // at = (alpha_a + alpha_b + alpha_c - alpha_i)/2, because F_a + F_b + F_c - f
 // = 2 F_c.  Writes, per step, {A2, K2} = log2(e) {lnPtot - lnN, -kappa} and
-// {lnPtot - lnN, kappa}; per channel P/B and ln rho(L, f_c).
+// {lnPtot - lnN, kappa}; per channel P/B (step 0's block) and ln rho(L, f_c)
+// (the z = L block).  ln N is a log-sum-exp over the channels with a block
+// maximum and a block sum in fixed order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double sinhc_d(double x)
 {
@@ -41,8 +45,7 @@ __device__ __forceinline__ double sinhc_d(double x)
 __global__ void __launch_bounds__(256) k_prep(PrepParams pp)
 {
     __shared__ double scratch[32];
-    __shared__ double s_lnN_L, s_kap_L;
-    const int p = blockIdx.x;
+    const int p = blockIdx.x, m = blockIdx.y;
     const int plan = pp.prof_plan[p];
     const int n = pp.plan_n[plan];
     const int coff = pp.plan_ch_off[plan];
@@ -50,58 +53,52 @@ __global__ void __launch_bounds__(256) k_prep(PrepParams pp)
     const double *P = pp.P + poff;
     const double *fr = pp.ch_frel + coff;
     const double *B = pp.ch_B + coff;
+    const int M = pp.n_steps;
 
     double part = 0.0;
     for (int c = threadIdx.x; c < n; c += blockDim.x) part += P[c];
     const double Ptot = block_sum_d(part, scratch);
     const double lnPtot = log(Ptot);
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        double pd = P[c] / B[c];
-        pp.pd_d[poff + c] = pd;
-        pp.pd_f[poff + c] = (float)pd;
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int M = pp.n_steps;
-    for (int m = wid; m <= M; m += nw) {
-        const double z = (m < M) ? pp.zs_d[m].x : pp.L;
-        const double leff = pp.alpha_R > 0.0 ? -expm1(-pp.alpha_R * z) / pp.alpha_R : z;
-        const double kap = Ptot * pp.Cr * leff;
-        double mx = -1e300;
-        for (int c = lane; c < n; c += 32) {
-            if (P[c] > 0.0) {
-                double e = log(P[c]) - kap * fr[c] + log(sinhc_d(0.5 * kap * B[c]));
-                mx = fmax(mx, e);
-            }
+    if (m == 0) {
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            double pd = P[c] / B[c];
+            pp.pd_d[poff + c] = pd;
+            pp.pd_f[poff + c] = (float)pd;
         }
+    }
+    const double z = (m < M) ? pp.zs_d[m].x : pp.L;
+    const double leff = pp.alpha_R > 0.0 ? -expm1(-pp.alpha_R * z) / pp.alpha_R : z;
+    const double kap = Ptot * pp.Cr * leff;
+    double mx = -1e300;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        if (P[c] > 0.0) mx = fmax(mx, log(P[c]) - kap * fr[c] + log(sinhc_d(0.5 * kap * B[c])));
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        double s = 0.0;
-        for (int c = lane; c < n; c += 32) {
-            if (P[c] > 0.0) {
-                double e = log(P[c]) - kap * fr[c] + log(sinhc_d(0.5 * kap * B[c]));
-                s += exp(e - mx);
-            }
-        }
-        s = warp_sum_d(s);
-        const double lnN = mx + log(s);
-        if (lane == 0) {
-            if (m < M) {
-                pp.step_d[(size_t)p * M + m] = make_double2(lnPtot - lnN, kap);
-                pp.step_f[(size_t)p * M + m] =
-                    make_float2((float)((lnPtot - lnN) * kLog2e), (float)(-kap * kLog2e));
-            } else {
-                s_lnN_L = lnN;
-                s_kap_L = kap;
-            }
-        }
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     __syncthreads();
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = -1e300;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, scratch[w]);
+    double sum = 0.0;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        pp.lnrho_L[poff + c] = -pp.ch_alpha[coff + c] * pp.L + lnPtot - s_lnN_L - s_kap_L * fr[c];
+        if (P[c] > 0.0) sum += exp(log(P[c]) - kap * fr[c] + log(sinhc_d(0.5 * kap * B[c])) - mx);
+    }
+    sum = block_sum_d(sum, scratch);
+    const double lnN = mx + log(sum);
+    if (m < M) {
+        if (threadIdx.x == 0) {
+            pp.step_d[(size_t)p * M + m] = make_double2(lnPtot - lnN, kap);
+            pp.step_f[(size_t)p * M + m] = make_float2((float)((lnPtot - lnN) * kLog2e), (float)(-kap * kLog2e));
+        }
+        return;
+    }
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        pp.lnrho_L[poff + c] = -pp.ch_alpha[coff + c] * pp.L + lnPtot - lnN - kap * fr[c];
     }
     if (threadIdx.x == 0) {
         pp.ptot[p] = Ptot;
-        if (pp.kap_L) pp.kap_L[p] = s_kap_L;
+        if (pp.kap_L) pp.kap_L[p] = kap;
     }
 }
 
@@ -481,7 +478,7 @@ size_t quad_smem_bytes(int precision, int n_steps, int G)
 
 cudaError_t launch_prep(const PrepParams &pp, int n_prof, cudaStream_t st)
 {
-    k_prep<<<n_prof, 256, 0, st>>>(pp);
+    k_prep<<<dim3(n_prof, pp.n_steps + 1), 256, 0, st>>>(pp);
     return cudaGetLastError();
 }
 
