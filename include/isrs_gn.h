@@ -52,7 +52,7 @@ typedef enum {
     ISRS_ERR_INVALID_ARG = 1,   /* argument outside the documented domain */
     ISRS_ERR_CUDA = 2,          /* a CUDA runtime call failed */
     ISRS_ERR_ALLOC = 3,         /* device or host allocation failed */
-    ISRS_ERR_TIMEOUT = 4,       /* a bounded device wait ran out */
+    ISRS_ERR_TIMEOUT = 4,       /* reserved: no kernel here waits on a flag, peer or grid barrier */
     ISRS_ERR_NUMERIC = 5,       /* non-finite intermediate (e.g. overflow) */
     ISRS_ERR_UNSUPPORTED = 6    /* valid but not supported by this build */
 } isrs_status;
