@@ -54,7 +54,8 @@ typedef enum {
     ISRS_ERR_ALLOC = 3,         /* device or host allocation failed */
     ISRS_ERR_TIMEOUT = 4,       /* reserved: no kernel here waits on a flag, peer or grid barrier */
     ISRS_ERR_NUMERIC = 5,       /* non-finite intermediate (e.g. overflow) */
-    ISRS_ERR_UNSUPPORTED = 6    /* valid but not supported by this build */
+    ISRS_ERR_UNSUPPORTED = 6,   /* valid but not supported by this build */
+    ISRS_ERR_CHECK = 7          /* a device bounds check of the debug build failed (see isrs_debug_build) */
 } isrs_status;
 
 typedef struct isrs_handle_s *isrs_handle;
@@ -281,6 +282,15 @@ isrs_status isrs_set_tile(isrs_handle h, int points_per_item, int threads_per_bl
  * not executed and the device is untouched.  It fires once; kind 0 disarms.
  * Errors: INVALID_ARG (NULL handle, kind outside 0..2, after < 1). */
 isrs_status isrs_debug_inject_fault(isrs_handle h, int kind, int after);
+
+/* 1 when this library is the bounds-checked debug build (compiled with
+ * ISRS_DEBUG), else 0.  In the debug build the quadrature kernels check their
+ * piece, row, candidate, list and bucket-row indices; a failed check records
+ * its code on the device, clamps the index into range (no access leaves its
+ * array and every thread still reaches every barrier), and the call then
+ * returns ISRS_ERR_CHECK with the code in isrs_last_error.  The release build
+ * compiles the checks away.  No arguments, no errors. */
+int isrs_debug_build(void);
 
 /* Number of quadrature-kernel launches and grid points of the last compute
  * call (for throughput accounting).  Any argument may be NULL. */

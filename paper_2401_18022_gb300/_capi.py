@@ -11,7 +11,7 @@ c_int_p = ctypes.POINTER(ctypes.c_int)
 
 ISRS_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "allocation failed", 4: "timeout",
-          5: "numeric error", 6: "unsupported"}
+          5: "numeric error", 6: "unsupported", 7: "debug bounds check failed"}
 CELLS_SCI_XCI, CELLS_ALL = 0, 1
 PREC_FP32, PREC_FP64 = 0, 1
 
@@ -44,16 +44,23 @@ class IsrsError(RuntimeError):
 _lib = None
 
 
+def debug_requested() -> bool:
+    """ISRS_GN_DEBUG=1 selects the bounds-checked debug build of the library."""
+    return os.environ.get("ISRS_GN_DEBUG", "0") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_requested() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load the in-tree library (building it when asked).  Raises if it cannot."""
+    """Load the in-tree library (building it when asked; the debug build when
+    ISRS_GN_DEBUG=1).  Raises if it cannot."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build_if_missing else _build.LIB
+    dbg = debug_requested()
+    path = _build.build(debug=dbg) if build_if_missing else library_path()
     if not os.path.exists(path):
         raise RuntimeError(f"ISRS GN CUDA library not built: {path}")
     lib = ctypes.CDLL(path)
@@ -65,6 +72,10 @@ def load(build_if_missing: bool = True):
     lib.isrs_status_string.restype = ctypes.c_char_p
     lib.isrs_last_error.argtypes = [vp]
     lib.isrs_last_error.restype = ctypes.c_char_p
+    lib.isrs_debug_build.argtypes = []
+    lib.isrs_debug_build.restype = ctypes.c_int
+    if bool(lib.isrs_debug_build()) != dbg:
+        raise RuntimeError(f"{path}: expected the {'debug' if dbg else 'release'} build of the library")
     lib.isrs_beta_from_dispersion.argtypes = [ctypes.c_double] * 4 + [c_double_p]
     lib.isrs_gamma_from_aeff.argtypes = [ctypes.c_double] * 3
     lib.isrs_gamma_from_aeff.restype = ctypes.c_double

@@ -58,6 +58,11 @@ class Engine:
         check(self.lib.isrs_create(ctypes.byref(self.h), int(device)))
         self.device = device
 
+    @property
+    def debug_build(self) -> bool:
+        """Whether the loaded library is the bounds-checked debug build."""
+        return bool(self.lib.isrs_debug_build())
+
     def close(self):
         if self.h:
             self.lib.isrs_destroy(self.h)

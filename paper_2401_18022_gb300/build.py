@@ -16,6 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, f"libisrs_gn_{platform.machine()}.so")
+# the bounds-checked debug build (-DISRS_DEBUG): same sources, its own objects
+LIB_DEBUG = os.path.join(BUILD, f"libisrs_gn_debug_{platform.machine()}.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
@@ -37,15 +39,20 @@ def _deps_mtime():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile every csrc/*.cu for sm_103a and link the library; debug=True
+    builds the bounds-checked variant (ISRS_DEBUG) beside the release one."""
     os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime() and not extra:
-        return LIB
+    lib = LIB_DEBUG if debug else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime() and not extra:
+        return lib
     cc = nvcc()
     objs = []
+    tag = ".debug" if debug else ""
+    extra = (*extra, "-DISRS_DEBUG") if debug else tuple(extra)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + f".{platform.machine()}.o")
+        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + f"{tag}.{platform.machine()}.o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -59,14 +66,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             objs.append(obj)
             if verbose and log:
                 print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force=True, verbose="-v" in sys.argv))
+    print(build(force=True, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -79,7 +79,7 @@ struct isrs_handle_s {
     std::string err;
     DevBuf paths, kapL;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
-        o_pase, o_T, gA, gK, gPd, gVs, gY, ybar, dTdP, ab, ode_y, gAB, gV, gAt, partial_mci, tab_rows, tab_rowsV;
+        o_pase, o_T, gA, gK, gPd, gVs, gY, dbg, ybar, dTdP, ab, ode_y, gAB, gV, gAt, partial_mci, tab_rows, tab_rowsV;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
@@ -143,6 +143,25 @@ bool inject_hit(isrs_handle h, int kind)
             return fail(h, e_ == cudaErrorMemoryAllocation ? ISRS_ERR_ALLOC : ISRS_ERR_CUDA,  \
                         "%s: %s", #call, cudaGetErrorString(e_));                             \
     } while (0)
+
+#ifdef ISRS_DEBUG
+constexpr bool kDebugBuild = true;
+#else
+constexpr bool kDebugBuild = false;
+#endif
+
+// Debug build: the first failed device bounds check since the last call
+// (its code, see isrs_debug.cuh) becomes ISRS_ERR_CHECK; the flag is cleared.
+isrs_status dbg_check(isrs_handle h, cudaStream_t st)
+{
+    if (!kDebugBuild || !h->dbg.p) return ISRS_OK;
+    unsigned code = 0;
+    CK(cudaMemcpyAsync(&code, h->dbg.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (code == 0) return ISRS_OK;
+    CK(cudaMemsetAsync(h->dbg.p, 0, sizeof(unsigned), st));
+    return fail(h, ISRS_ERR_CHECK, "device bounds check %u failed", code);
+}
 
 isrs_status ensure(isrs_handle h, DevBuf &b, size_t bytes)
 {
@@ -909,6 +928,8 @@ QuadParams quad_params(isrs_handle h, const isrs_fibre *fb, Geom *g)
     qp.pieces = (const DevPiece *)g->pieces.p;
     qp.items = (const DevItem *)g->items.p;
     qp.n_items = g->n_items;
+    qp.n_pieces = (int)g->n_pieces;
+    qp.dbg = kDebugBuild ? (unsigned *)h->dbg.p : nullptr;
     qp.G = g->G;
     qp.eps_v1 = g->eps_v1;
     qp.n_steps = g->n_steps;
@@ -1426,7 +1447,7 @@ isrs_status grad_outputs(isrs_handle h, int n, double *dT_dP, double *snr, doubl
     }
     if (host_out) CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    return ISRS_OK;
+    return dbg_check(h, st);
 }
 
 }  // namespace
@@ -1446,6 +1467,7 @@ const char *isrs_status_string(isrs_status s)
     case ISRS_ERR_TIMEOUT: return "timeout";
     case ISRS_ERR_NUMERIC: return "numeric error";
     case ISRS_ERR_UNSUPPORTED: return "unsupported";
+    case ISRS_ERR_CHECK: return "debug bounds check failed";
     }
     return "unknown status";
 }
@@ -1468,6 +1490,16 @@ isrs_status isrs_create(isrs_handle *out, int device)
         delete h;
         return ISRS_ERR_CUDA;
     }
+    if (kDebugBuild) {
+        if (cudaMalloc(&h->dbg.p, sizeof(unsigned)) != cudaSuccess ||
+            cudaMemset(h->dbg.p, 0, sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            if (h->dbg.p) cudaFree(h->dbg.p);
+            delete h;
+            return ISRS_ERR_ALLOC;
+        }
+        h->dbg.cap = sizeof(unsigned);
+    }
     *out = h;
     return ISRS_OK;
 }
@@ -1480,7 +1512,8 @@ isrs_status isrs_destroy(isrs_handle h)
     DevBuf *bufs[] = {&h->P, &h->pd_d, &h->pd_f, &h->step_d, &h->step_f, &h->lnrho_L, &h->ptot, &h->partial,
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
                       &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP, &h->ab, &h->ode_y, &h->gAB, &h->gV,
-                      &h->gAt, &h->partial_mci, &h->eta_all, &h->tab_rows, &h->tab_rowsV, &h->gVs};
+                      &h->gAt, &h->partial_mci, &h->eta_all, &h->tab_rows, &h->tab_rowsV, &h->gVs,
+                      &h->gY, &h->dbg};
     for (DevBuf *b : bufs) release(*b);
     release(h->paths);
     release(h->kapL);
@@ -1493,6 +1526,8 @@ isrs_status isrs_destroy(isrs_handle h)
 }
 
 const char *isrs_last_error(isrs_handle h) { return h ? h->err.c_str() : ""; }
+
+int isrs_debug_build(void) { return kDebugBuild ? 1 : 0; }
 
 isrs_status isrs_beta_from_dispersion(double lambda_nm, double D, double S, double Sdot, double *beta)
 {
@@ -1612,7 +1647,7 @@ isrs_status isrs_gn_eta(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
     if ((s = copy_out(h, sigma, h->o_sigma, n, st, host_out)) != ISRS_OK) return s;
     if (host_out) CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    return ISRS_OK;
+    return dbg_check(h, st);
 }
 
 isrs_status isrs_gn_snr(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
@@ -1651,7 +1686,7 @@ isrs_status isrs_gn_snr(isrs_handle h, const isrs_fibre *fibre, const isrs_chann
     }
     if (host_out) CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    return ISRS_OK;
+    return dbg_check(h, st);
 }
 
 isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_plans, const isrs_channels *plans,
@@ -1695,7 +1730,7 @@ isrs_status isrs_gn_eta_batched(isrs_handle h, const isrs_fibre *fibre, int n_pl
     if ((s = copy_out(h, eta, h->o_eta, total, st, host_out)) != ISRS_OK) return s;
     if (host_out) CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    return ISRS_OK;
+    return dbg_check(h, st);
 }
 
 isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_channels *ch, const double *P_W,
@@ -1771,6 +1806,7 @@ isrs_status isrs_gn_grad_shard_fwd(isrs_handle h, const isrs_fibre *fibre, const
     if ((s = copy_out(h, eta, h->o_eta, g->n_slots, st, host_out)) != ISRS_OK) return s;
     if (host_out) CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    if ((s = dbg_check(h, st)) != ISRS_OK) return s;
     h->shard_key = g->key;
     h->shard_fibre = *fibre;
     h->shard_quad = *quad;
@@ -1858,7 +1894,7 @@ isrs_status isrs_gn_grad_shard_bwd(isrs_handle h, const double *eta_all, int wit
     }
     if (host_out) CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    return ISRS_OK;
+    return dbg_check(h, st);
 }
 
 }  // extern "C"
@@ -2074,6 +2110,7 @@ extern "C" isrs_status isrs_gn_eta_noalloc(const isrs_fibre *fibre, const isrs_c
     qp.pieces = (const DevPiece *)(base + o_pieces);
     qp.items = (const DevItem *)(base + o_items);
     qp.n_items = (int)items.size();
+    qp.n_pieces = (int)pieces.size();
     qp.G = quad->G;
     qp.n_steps = M;
     qp.eps_v1 = quad->eps_v1;

@@ -5,12 +5,14 @@
 //   pieces        DevPiece[], plans concatenated; per CUT contiguous
 //   items         DevItem[]: work queue of (profile, piece range) tiles, ordered by
 //                 (profile, CUT) so that each CUT owns a contiguous item range
-//   z tables      per step m: float4 {A2? no: z_m, dz_m, ...} see StepZ
+//   z tables      per step m: z_m, dz_m, log2 dz_m, the centred step moments and
+//                 the edge phase z_{m+1}/2pi (float-float)
 //   profile tabs  per profile and step: float2 {A2_m, K2_m}; per profile and
 //                 channel: P/B (float, double), lnrho(L, f_c)
 //   partials      one double per item
 #pragma once
 #include <cstdint>
+#include "isrs_debug.cuh"
 
 namespace isrs {
 
@@ -52,6 +54,8 @@ struct QuadParams {
     const DevPiece *pieces;
     const DevItem *items;
     int n_items;
+    int n_pieces;
+    unsigned *dbg;              // debug build: code of the first failed bounds check (else null)
     int G;
     int n_steps;
     double eps_v1;

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
         }
         double acc = 0.0;
         for (int kp = item.piece0; kp < item.piece1; ++kp) {
-            const DevPiece pc = qp.pieces[kp];
+            const DevPiece pc = qp.pieces[dbg_clamp(kp, qp.n_pieces, kDbgPiece, qp.dbg)];
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 if (q < npts) {
                     const int r = (int)(((float)q + 0.5f) * invG);
                     const int j = q - r * G;
-                    const RowF rw = rows[r];
+                    const RowF rw = rows[dbg_clamp(r, G, kDbgRow, qp.dbg)];
                     if (rw.w != 0.0f) {
                         const float d = ((float)j + 0.5f - 0.5f * (float)G) * rw.du2;
                         const float e = expf(d);
@@ -349,9 +349,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 const unsigned bt = __ballot_sync(kFull, stage && cls == kClsTele);
                 if (stage) {
                     const float4 v = make_float4(wwa, phi, Fc, __int_as_float(ci));
-                    if (cls == kClsSmall) Ls[ns + __popc(bs & lt_mask)] = v;
-                    else if (cls == kClsDirect) Ld[nd + __popc(bd & lt_mask)] = v;
-                    else Lt[nt + __popc(bt & lt_mask)] = v;
+                    if (cls == kClsSmall) Ls[dbg_clamp(ns + __popc(bs & lt_mask), kListCap, kDbgList, qp.dbg)] = v;
+                    else if (cls == kClsDirect) Ld[dbg_clamp(nd + __popc(bd & lt_mask), kListCap, kDbgList, qp.dbg)] = v;
+                    else Lt[dbg_clamp(nt + __popc(bt & lt_mask), kListCap, kDbgList, qp.dbg)] = v;
                 }
                 if (lane == 0) {
                     n_small += __popc(bs) + __popc(cmask0);
@@ -518,12 +518,12 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
             const double t3 = block_sum_d((double)fa.v3, scratch);   // syncs: sVc complete
             acc += (double)mult * ptot;
             if (threadIdx.x == 0) {                 // one thread, in order (the row is this tile's)
-                Vrow[pc.a] += (double)mult * ptot;
-                Vrow[pc.b] += (double)mult * ptot;
+                Vrow[dbg_clamp(pc.a, ap.n_ch, kDbgVrow, qp.dbg)] += (double)mult * ptot;
+                Vrow[dbg_clamp(pc.b, ap.n_ch, kDbgVrow, qp.dbg)] += (double)mult * ptot;
                 for (int c = 0; c < kc.nc; ++c) {
                     double vc = c == 0 ? t0 : c == 1 ? t1 : c == 2 ? t2 : c == 3 ? t3 : 0.0;
                     for (int hw = 0; hw < 2 * nw; ++hw) vc += (double)sVc[hw * kMaxCand + c];
-                    Vrow[pc.c_lo + c] += (double)mult * vc;
+                    Vrow[dbg_clamp(pc.c_lo + c, ap.n_ch, kDbgVrow, qp.dbg)] += (double)mult * vc;
                 }
             }
             __syncthreads();

@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MCI_MIN_BLOCKS) k_quad_adj_mci(A
                 const int r = rem / G, j = rem - r * G;
                 int ap_, bp_;
                 tri_decode(item.piece0 + tl, n2, ap_, bp_);
-                a = ap_ + (ap_ >= i);
-                b = bp_ + (bp_ >= i);
+                a = dbg_clamp(ap_ + (ap_ >= i), n, kDbgCell, qp.dbg);
+                b = dbg_clamp(bp_ + (bp_ >= i), n, kDbgCell, qp.dbg);
                 const float mult = a == b ? 1.0f : 2.0f;
                 const float ra = rel[a], rb = rel[b];
                 const float s1 = ra > 0.0f ? 1.0f : -1.0f, s2 = rb > 0.0f ? 1.0f : -1.0f;

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
         }
         double acc = 0.0;
         for (int k = item.piece0; k < item.piece1; ++k) {
-            const DevPiece pc = qp.pieces[k];
+            const DevPiece pc = qp.pieces[dbg_clamp(k, qp.n_pieces, kDbgPiece, qp.dbg)];
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, log2e, qp.pd_f, kc);
             __syncthreads();
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
                 // row r = floor(q / G): (q + 1/2)/G is at least 1/(2G) from an integer
                 const int r = (int)(((float)q + 0.5f) * invG);
                 const int j = q - r * G;
-                const RowF rw = rows[r];
+                const RowF rw = rows[dbg_clamp(r, G, kDbgRow, qp.dbg)];
                 if (rw.w == 0.0f) continue;
                 const float d = ((float)j + 0.5f - 0.5f * (float)G) * rw.du2;
                 const float e = expf(d);
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(256, ISRS_FWD_MIN_BLOCKS) k_quad_f32(QuadParam
                     if (u >= kc.lo[c] && u < kc.hi[c]) { ci = c; break; }
                 }
                 if (ci < 0) continue;                       // F_c in a gap
+                ci = dbg_clamp(ci, kc.nc, kDbgCand, qp.dbg);
                 const float W = kc.wab * kc.pd[ci];
                 const float at = kc.at_ab + kc.hat[ci];
                 const float Fc = fi + u;                    // F_c - f_ref
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(256) k_quad_f64(QuadParams qp)
         }
         double acc = 0.0;
         for (int k = item.piece0; k < item.piece1; ++k) {
-            const DevPiece pc = qp.pieces[k];
+            const DevPiece pc = qp.pieces[dbg_clamp(k, qp.n_pieces, kDbgPiece, qp.dbg)];
             piece_rows<RowD>(pc, G, qp.eps_v1, rows);
             piece_consts<double>(qp, pc, item.prof, 1.0, qp.pd_d, kc);
             __syncthreads();
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(256) k_quad_f64(QuadParams qp)
             for (int q = threadIdx.x; q < npts; q += blockDim.x) {
                 const int r = q / G;
                 const int j = q - r * G;
-                const RowD rw = rows[r];
+                const RowD rw = rows[dbg_clamp(r, G, kDbgRow, qp.dbg)];
                 if (rw.w == 0.0) continue;
                 const double d = ((double)j + 0.5 - 0.5 * (double)G) * rw.du2;
                 const double f1 = kc.s1 * (rw.xc * exp(d));

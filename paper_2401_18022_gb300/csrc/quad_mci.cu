@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_mci_f32(QuadParams qp)
             const int tl = q / G, r = q - tl * G;
             int ap, bp;
             tri_decode(item.piece0 + tl, n2, ap, bp);
-            const int a = ap + (ap >= i), b = bp + (bp >= i);
+            const int a = dbg_clamp(ap + (ap >= i), n, kDbgCell, qp.dbg), b = dbg_clamp(bp + (bp >= i), n, kDbgCell, qp.dbg);
             const float mult = a == b ? 1.0f : 2.0f;
             const float ra = rel[a], rb = rel[b];
             const float s1 = ra > 0.0f ? 1.0f : -1.0f, s2 = rb > 0.0f ? 1.0f : -1.0f;
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_quad_mci_f64(QuadParams qp)
             const int tl = q / G, r = q - tl * G;
             int ap, bp;
             tri_decode(item.piece0 + tl, n2, ap, bp);
-            const int a = ap + (ap >= i), b = bp + (bp >= i);
+            const int a = dbg_clamp(ap + (ap >= i), n, kDbgCell, qp.dbg), b = dbg_clamp(bp + (bp >= i), n, kDbgCell, qp.dbg);
             const double mult = a == b ? 1.0 : 2.0;
             const double ra = fr[a] - fi, rb = fr[b] - fi;
             const double s1 = ra > 0.0 ? 1.0 : -1.0, s2 = rb > 0.0 ? 1.0 : -1.0;

@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
         const DevItem item = qp.items[it];
         double acc = 0.0;
         for (int k = item.piece0; k < item.piece1; ++k) {
-            const DevPiece pc = qp.pieces[k];
+            const DevPiece pc = qp.pieces[dbg_clamp(k, qp.n_pieces, kDbgPiece, qp.dbg)];
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, 0.0f, qp.pd_f, kc);
             if (threadIdx.x == 0) {
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(256, 4) k_quad_f32_tab(QuadParams qp)
             for (int q = threadIdx.x; q < npts; q += blockDim.x) {
                 const int r = (int)(((float)q + 0.5f) * invG);
                 const int j = q - r * G;
-                const RowF rw = rows[r];
+                const RowF rw = rows[dbg_clamp(r, G, kDbgRow, qp.dbg)];
                 if (rw.w == 0.0f) continue;
                 const float d = ((float)j + 0.5f - 0.5f * (float)G) * rw.du2;
                 const float e = expf(d);
@@ -786,7 +786,7 @@ __global__ void __launch_bounds__(256) k_quad_f64_tab(QuadParams qp)
         const DevItem item = qp.items[it];
         double acc = 0.0;
         for (int k = item.piece0; k < item.piece1; ++k) {
-            const DevPiece pc = qp.pieces[k];
+            const DevPiece pc = qp.pieces[dbg_clamp(k, qp.n_pieces, kDbgPiece, qp.dbg)];
             piece_rows<RowD>(pc, G, qp.eps_v1, rows);
             piece_consts<double>(qp, pc, item.prof, 0.0, qp.pd_d, kc);
             const int coff = qp.plan_ch_off[pc.plan];
@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(256) k_quad_f64_tab(QuadParams qp)
             for (int q = threadIdx.x; q < npts; q += blockDim.x) {
                 const int r = q / G;
                 const int j = q - r * G;
-                const RowD rw = rows[r];
+                const RowD rw = rows[dbg_clamp(r, G, kDbgRow, qp.dbg)];
                 if (rw.w == 0.0) continue;
                 const double d = ((double)j + 0.5 - 0.5 * (double)G) * rw.du2;
                 const double f1 = kc.s1 * (rw.xc * exp(d));

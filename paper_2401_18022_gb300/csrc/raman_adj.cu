@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
         for (int t = threadIdx.x; t < nrow; t += blockDim.x) trowsV[t] = 0.0;
         double acc = 0.0;           // the tile's partial of Sigma_i
         for (int kp = item.piece0; kp < item.piece1; ++kp) {
-            const DevPiece pc = qp.pieces[kp];
+            const DevPiece pc = qp.pieces[dbg_clamp(kp, qp.n_pieces, kDbgPiece, qp.dbg)];
             piece_rows<RowF>(pc, G, qp.eps_v1, rows);
             piece_consts<float>(qp, pc, item.prof, 0.0f, qp.pd_f, kc);
             const int coff = qp.plan_ch_off[pc.plan];
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_TAB_MIN_BLOCKS) k_quad_adj_tab(A
                     if (q < npts) {
                         const int r = (int)(((float)q + 0.5f) * invG);
                         const int j = q - r * G;
-                        const RowF rw = rows[r];
+                        const RowF rw = rows[dbg_clamp(r, G, kDbgRow, qp.dbg)];
                         if (rw.w != 0.0f) {
                             const float d = ((float)j + 0.5f - 0.5f * (float)G) * rw.du2;
                             const float e = expf(d);

@@ -16,7 +16,7 @@ def _declared():
     for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
         if f.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", f)).read()
-            names += re.findall(r"^\s*(?:isrs_status|double|const char \*)\s*\*?\s*(isrs_\w+)\s*\(", txt, re.M)
+            names += re.findall(r"^\s*(?:isrs_status|double|int|const char \*)\s*\*?\s*(isrs_\w+)\s*\(", txt, re.M)
     return sorted(set(names))
 
 
@@ -34,8 +34,23 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for s in range(7):
+    for s in range(8):
         assert lib.isrs_status_string(s)
+    assert lib.isrs_status_string(7) == b"debug bounds check failed"
+
+
+def test_debug_build_is_separate_and_reports_itself(lib):
+    """The bounds-checked variant (ISRS_DEBUG) builds from the same sources
+    into its own library; each library reports which one it is."""
+    from paper_2401_18022_gb300 import build as B
+    assert lib.isrs_debug_build() == 0
+    path = B.build(debug=True)
+    assert path == B.LIB_DEBUG and path != B.LIB
+    dbg = ctypes.CDLL(path)
+    dbg.isrs_debug_build.restype = ctypes.c_int
+    assert dbg.isrs_debug_build() == 1
+    for n in _declared():
+        assert hasattr(dbg, n), n
 
 
 def test_create_without_gpu_fails_cleanly(lib):
