@@ -16,12 +16,12 @@
 // grid, and every step term of Eq. slow_vary is evaluated once.  A warp first
 // takes 32 grid points, one per lane, for their geometry, phase and z-sum
 // form.  Small-phase points (|phi| L <= 6, the forward's range) whose moments
-// come from the contracted 19-moment series are finished there: their bucket
-// terms sum_n 2 (A|B) phi^n f_n w_m g_n(m) are expanded in the same Chebyshev
-// series in the point's in-channel coordinate, so per F_c candidate at most
-// 95 point sums are kept (one to three warp butterflies per batch, as many
-// orders as the batch's largest phase needs) and turned into per-step terms
-// once per piece.  The other points join one list per z-sum form and
+// come from the contracted centred series (6, 11 or 19 moments by phase) are
+// finished there: their bucket terms sum_n 2 (A|B) phi^n f_n w_m g_n(m) are
+// expanded in the same Chebyshev series in the point's in-channel coordinate,
+// so per F_c candidate at most 95 point sums are kept (one to three 32-value
+// warp butterflies per batch, as many orders as the batch's largest phase
+// needs) and turned into per-step terms once per piece.  The other points join one list per z-sum form and
 // are walked two at a time on half-warps: each of the 16 lanes of a half owns
 // K = ceil(M/16) consecutive steps (112 = 16 x 7), computes their terms t_m
 // into registers, the half sums them with shuffles into S, and the same
@@ -309,8 +309,9 @@ __global__ void __launch_bounds__(256, ISRS_ADJ_MIN_BLOCKS) k_quad_adj(AdjParams
                 // phi^n f_n w_m g_n(m) with w_m = base_m sum_k b_k(a_m) T_k(x).  Their
                 // bucket terms need only, per candidate, the sums of cp 2 (A|B) phi^n
                 // T_k(x) (k <= 4 for the F_c-weighted bucket, x T_k = (T_{k+1} +
-                // T_{|k-1|})/2): 30, 55 or 95 values, reduced over the warp in one to
-                // three butterflies and turned into per-step terms once per piece.
+                // T_{|k-1|})/2): 95 values, of which a batch reduces the first 32, 64
+                // or 96 over the warp (one to three butterflies) by its largest
+                // phase; they become per-step terms once per piece.
                 unsigned cmask = __ballot_sync(kFull, ctr);
                 const unsigned cmask0 = cmask;
                 if (cmask) {

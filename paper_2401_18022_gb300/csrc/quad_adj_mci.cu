@@ -6,7 +6,7 @@
 // the fused adjoint of the SCI/XCI pieces:
 //   R_im  = sum_points w W d|S|^2/d ln p_m,   R'_im = same * (F_c - f_ref),
 //   V_ij += w W |S|^2 for each of the point's channels a, b, c,
-// and the forward partial of each item, so the chain rule (k_chain) takes the
+// and the forward partial of each item, so the chain rule (k_chain_*) takes the
 // MCI items as further tiles of their CUTs.
 //
 // A warp takes 32 grid points of its item (cell, row, column decoded from the

@@ -17,8 +17,8 @@ namespace isrs {
 // Exact-to-FP32 evaluations of S = sum_m p_m dz_m sinc(phi dz_m/2)
 // e^{j phi z_m} (Eq. slow_vary), chosen per grid point by |phi|:
 //  * contracted small phase (|phi| L <= 6, when the piece's Chebyshev
-//    contraction applies): the 19-moment series about the span centre
-//    (quad_common.cuh), no per-step work;
+//    contraction applies): the centred series about the span centre with
+//    6, 11 or 19 moments by phase (quad_common.cuh), no per-step work;
 //  * small (|phi| L <= 0.02, otherwise): second-order expansion in phi,
 //      |S|^2 = M0^2 - phi^2 (M0 M2 - M1^2) + O((phi L)^4),
 //    M0 = sum p dz, M1 = sum p dz z, M2 = sum p dz (z^2 + dz^2/12); the
