@@ -3,8 +3,8 @@
 One step = one full pass of the hot path on the 589 x 96 GBaud, 1260-1675 nm,
 80 km workload (G = 256 per piece, 113 z-edges, SCI + XCI cells): ISRS
 profile tables, the hyperbolic Riemann sum for every CUT, eta, SNR and
-throughput, and (once the adjoint is built) the gradient of the throughput
-with respect to all 589 launch powers.
+throughput, and the gradient of the throughput with respect to all 589
+launch powers (the hand-written adjoint).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -26,8 +26,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "589-ch SNR eval time & grid-pts/s; SNR+gradient time vs plain FP64 at 0.01 dB"
 UNIT = "grid-pts/s"
-SFU_PER_CLK_PER_SM = 16          # MUFU (sin, cos, ex2, rcp) issue rate per SM per clock
-FP32_PER_CLK_PER_SM = 128
 N_SMS = 152
 
 

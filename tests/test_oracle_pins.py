@@ -40,7 +40,7 @@ def test_beta_reproduces_dispersion_and_its_derivatives(orc, lam, D, S, Sd):
 
 def test_gamma_textbook_values(orc):
     """Sec. II, Eq. gamma: SSMF at 1550 nm, n2 = 2.6e-20, Aeff = 80 um^2 gives
-    the textbook ~1.3 /W/km; 1310 nm with 64.2 um^2 gives ~1.94 (survey value)."""
+    the textbook ~1.3 /W/km; 1310 nm with 64.2 um^2 (the linear 60-95 um^2 Aeff model) gives ~1.94."""
     assert orc.gamma(1550.0, 2.6e-20, 80.0) == pytest.approx(1.3175, rel=2e-3)
     assert orc.gamma(1302.3, 2.6e-20, float(W.aeff_model_um2(1302.3))) == pytest.approx(2.0, rel=0.02)
 
