@@ -435,8 +435,9 @@ def _timed(fn, dev, reps: int = 2):
 
 def _extras(eng, wl, P, dev):
     """Side measurements of the widened rows on the same 589-ch workload:
-    the Raman-ODE power profile (SNR and gradient) and the MCI cells on their
-    own grid (SNR, gradient, and the MCI share of eta per band)."""
+    the Raman-ODE power profile (SNR and gradient), the MCI cells on their
+    own grid (SNR, gradient, and the MCI share of eta per band), and both
+    together (SNR and the MCI share with the Raman-ODE profile)."""
     from paper_2401_18022_gb300 import workloads as W
     out = {}
     wr = W.raman(wl)
@@ -464,6 +465,18 @@ def _extras(eng, wl, P, dev):
                                        for b in range(6)}
     n = wl.n_ch
     out["mci_cells_per_cut"] = (n - 1) * n // 2
+    # the Raman-ODE profile with the MCI cells on their own grid (forward)
+    wrm = W.raman(wm)
+    out["raman_mci_snr_ms"] = _timed(lambda: eng.snr(wrm, P=P), dev)
+    out["raman_mci_quad_kernels_ms"] = eng.last_kernel_ms(0)
+    e_rm = eng.eta(wrm, P=P)["eta"]
+    e_rs = eng.eta(wr, P=P)["eta"]
+    e_rm = e_rm.cpu().numpy() if hasattr(e_rm, "cpu") else np.asarray(e_rm)
+    e_rs = e_rs.cpu().numpy() if hasattr(e_rs, "cpu") else np.asarray(e_rs)
+    share_r = 1.0 - e_rs / e_rm
+    out["raman_mci_share_of_eta_by_band"] = {
+        W.BAND_NAMES[b]: [float(share_r[band == b].min()), float(share_r[band == b].max())] for b in range(6)}
+    out["raman_mci_T_Tbps"] = eng.snr(wrm, P=P)["T"]
     return out
 
 

@@ -136,7 +136,8 @@ typedef struct {
     int G_mci;                  /* with ISRS_CELLS_ALL and > 0: the multi-channel-interference
                                  * cells (neither F_a nor F_b in the CUT's channel) get their own
                                  * G_mci x G_mci grid (<= 32) and are enumerated on the device
-                                 * (no piece list); closed-form profile (eta, SNR and gradient).
+                                 * (no piece list); eta and SNR with either profile, the
+                                 * gradient with the closed-form profile.
                                  * 0: every cell uses G. */
 } isrs_quad;
 

@@ -79,7 +79,8 @@ struct isrs_handle_s {
     std::string err;
     DevBuf paths, kapL;
     DevBuf P, pd_d, pd_f, step_d, step_f, lnrho_L, ptot, partial, counter, o_sigma, o_pnli, o_eta, o_snr,
-        o_pase, o_T, gA, gK, gPd, gVs, gY, dbg, ybar, dTdP, ab, ode_y, gAB, gV, gAt, partial_mci, tab_rows, tab_rowsV;
+        o_pase, o_T, gA, gK, gPd, gVs, gY, dbg, ybar, dTdP, ab, ab_f, ode_y, gAB, gV, gAt, partial_mci, tab_rows,
+        tab_rowsV;
     std::vector<std::unique_ptr<Geom>> cache;   // most recent first
     int tile_points = 0, tile_threads = 0;
     int64_t last_points = 0, last_psteps = 0;
@@ -631,8 +632,6 @@ isrs_status get_geom(isrs_handle h, const isrs_fibre *fb, int n_plans, const isr
     // pieces per plan and CUT (with a separate MCI grid only the SCI and XCI
     // cells become pieces)
     const bool mci = q->cell_set == ISRS_CELLS_ALL && q->G_mci > 0;
-    if (mci && fb->profile != ISRS_PROFILE_CLOSED_FORM)
-        return fail(h, ISRS_ERR_UNSUPPORTED, "separate MCI grid needs the closed-form profile");
     const int piece_cells = mci ? ISRS_CELLS_SCI_XCI : q->cell_set;
     g->G_mci = mci ? q->G_mci : 0;
     std::vector<DevPiece> pieces;
@@ -1102,16 +1101,37 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
             qm.G = g->G_mci;
             qm.partial = (double *)h->partial_mci.p;
             qm.counter = (int *)h->counter.p + 1;
-            int mgrid = h->num_sms * quad_mci_blocks_per_sm(precision, M, qm.mci_n_max, block);
-            if (g->n_mci_items < mgrid) mgrid = g->n_mci_items;
-            CK(launch_quad_mci(qm, precision, mgrid, block, st));
+            if (tab) {
+                // the MCI cells with the tabulated profile: FP32 rows of {a, b}, cells in chunks
+                int cpc = 0;
+                if (precision == ISRS_PREC_FP32) {
+                    cpc = quad_mci_tab_cells(M, qm.mci_n_max, qm.G, block);
+                    if (cpc < 1)
+                        return fail(h, ISRS_ERR_UNSUPPORTED, "MCI step rows of %d steps exceed shared memory", M);
+                    const size_t nab = (size_t)g->total_prof_ch * M;
+                    if ((s = ensure(h, h->ab_f, sizeof(float2) * nab)) != ISRS_OK) return s;
+                    qm.ab_f = (const float2 *)h->ab_f.p;
+                    CK(launch_tab_half_log2((const double2 *)h->ab.p, (float2 *)h->ab_f.p, (int)nab, h->num_sms,
+                                            st));
+                }
+                qm.mci_cpc = cpc;
+                int mgrid = h->num_sms * quad_mci_tab_blocks_per_sm(precision, M, qm.mci_n_max, cpc, block);
+                if (g->n_mci_items < mgrid) mgrid = g->n_mci_items;
+                CK(launch_quad_mci_tab(qm, precision, mgrid, block, st));
+            } else {
+                int mgrid = h->num_sms * quad_mci_blocks_per_sm(precision, M, qm.mci_n_max, block);
+                if (g->n_mci_items < mgrid) mgrid = g->n_mci_items;
+                CK(launch_quad_mci(qm, precision, mgrid, block, st));
+            }
         }
         if ((s = mark(h, 0, 1, st)) != ISRS_OK) return s;
     }
     h->last_points = g->n_points;
     h->last_psteps = g->n_points * (int64_t)M;
     h->last_launches = (g->profile == ISRS_PROFILE_RAMAN_ODE ? 3 : 2) +   // prep (+ Raman ODE) + quadrature
-                       (g->n_mci_items > 0 ? 1 : 0);                       // + MCI cells
+                       (g->n_mci_items > 0 ? 1 : 0) +                      // + MCI cells
+                       (g->n_mci_items > 0 && g->profile == ISRS_PROFILE_RAMAN_ODE &&
+                                precision == ISRS_PREC_FP32 ? 1 : 0);      // + their FP32 profile rows
     return ISRS_OK;
 }
 
@@ -1213,7 +1233,7 @@ std::vector<void *> workspace_ptrs(isrs_handle h)
 {
     return {h->P.p, h->pd_d.p, h->pd_f.p, h->lnrho_L.p, h->step_d.p, h->step_f.p, h->ptot.p, h->partial.p,
             h->counter.p, h->paths.p, h->kapL.p, h->o_sigma.p, h->o_pnli.p, h->o_eta.p, h->o_snr.p, h->o_pase.p, h->o_T.p,
-            h->ab.p, h->partial_mci.p};
+            h->ab.p, h->ab_f.p, h->partial_mci.p};
 }
 
 isrs_status run_batched_graph(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
@@ -1513,7 +1533,7 @@ isrs_status isrs_destroy(isrs_handle h)
                       &h->counter, &h->o_sigma, &h->o_pnli, &h->o_eta, &h->o_snr, &h->o_pase, &h->o_T,
                       &h->gA, &h->gK, &h->gPd, &h->ybar, &h->dTdP, &h->ab, &h->ode_y, &h->gAB, &h->gV,
                       &h->gAt, &h->partial_mci, &h->eta_all, &h->tab_rows, &h->tab_rowsV, &h->gVs,
-                      &h->gY, &h->dbg};
+                      &h->gY, &h->dbg, &h->ab_f};
     for (DevBuf *b : bufs) release(*b);
     release(h->paths);
     release(h->kapL);

@@ -101,11 +101,13 @@ struct QuadParams {
     // ln rho(z_m, F) = a + b (F - f_c) inside channel c; index
     // (prof_ch_off[prof] + c) * n_steps + m.  Null for the closed-form profile.
     const double2 *ab;
+    const float2 *ab_f;         // MCI cells (FP32): {a, b} / 2 * log2(e), same index (k_tab_half_log2)
     int nc_max;                 // largest F_c candidate count of any piece
     // multi-channel-interference cells (k_quad_mci_*): items are cell ranges
     // of one CUT (DevItem.piece0/piece1 = triangular cell indices), G = G_mci
     const int *plan_n;          // channels per plan
     int mci_n_max;              // largest plan
+    int mci_cpc;                // tabulated profile (FP32): cells per chunk of k_quad_mci_f32_tab
 };
 
 }  // namespace isrs

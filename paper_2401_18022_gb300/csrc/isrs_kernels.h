@@ -177,6 +177,14 @@ cudaError_t launch_finish(const FinishParams &fp, int n_prof, cudaStream_t st);
 size_t quad_mci_smem_bytes(int precision, int n_steps, int n_max);
 int quad_mci_blocks_per_sm(int precision, int n_steps, int n_max, int block);
 cudaError_t launch_quad_mci(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
+// ... with the tabulated (Raman-ODE) profile: qp.ab (FP64 kernel) or qp.ab_f
+// (FP32 kernel, filled by launch_tab_half_log2) and qp.mci_cpc cells per chunk
+// (quad_mci_tab_cells; 0: the step rows do not fit shared memory)
+int quad_mci_tab_cells(int n_steps, int n_max, int G, int block);
+size_t quad_mci_tab_smem_bytes(int precision, int n_steps, int n_max, int cpc);
+int quad_mci_tab_blocks_per_sm(int precision, int n_steps, int n_max, int cpc, int block);
+cudaError_t launch_tab_half_log2(const double2 *ab, float2 *abf, int n, int n_sms, cudaStream_t st);
+cudaError_t launch_quad_mci_tab(const QuadParams &qp, int precision, int grid, int block, cudaStream_t st);
 size_t adjoint_smem_bytes(int n_steps, int G, int block);
 size_t adjoint_scratch_bytes(int grid);   // AdjParams.Yg of a launch of `grid` blocks
 // adjoint over the MCI cells of a separate grid (closed-form profile)

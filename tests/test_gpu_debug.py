@@ -3,8 +3,9 @@ on the method's workloads, and its results equal the release build's.
 
 The debug library is loaded in a child process (ISRS_GN_DEBUG=1), since one
 process loads one build.  The child evaluates SNR and the gradient on the
-tiny plan (all cells, MCI on its own grid), the Raman-ODE profile, and the
-589-channel plan at G = 16; a failed device check would surface as
+tiny plan (all cells, MCI on its own grid), the Raman-ODE profile (also with
+the MCI grid, SNR only, FP32 and FP64), and the 589-channel plan at G = 160;
+a failed device check would surface as
 ISRS_ERR_CHECK from the call.  The parent evaluates the same with the
 release library and compares."""
 import json
@@ -28,10 +29,12 @@ from paper_2401_18022_gb300 import api, workloads as W
 from _debug_cases import cases
 eng = api.Engine(0)
 out = {{"debug_build": eng.debug_build}}
-for name, wl in cases(W):
-    r = eng.grad(wl)
+for name, wl, grad in cases(W):
+    g = np.asarray(eng.grad(wl)["dT_dP"]).tolist() if grad else []
     s = eng.snr(wl)
-    out[name] = {{"dT_dP": np.asarray(r["dT_dP"]).tolist(), "eta": np.asarray(s["eta"]).tolist(), "T": s["T"]}}
+    e32 = np.asarray(s["eta"]).tolist()
+    e64 = np.asarray(eng.snr(wl, precision=1)["eta"]).tolist() if not grad else []
+    out[name] = {{"dT_dP": g, "eta": e32, "eta64": e64, "T": s["T"]}}
 json.dump(out, open(sys.argv[1], "w"))
 """
 
@@ -55,13 +58,16 @@ def test_debug_build_passes_every_check_and_matches_release(tmp_path):
 
     eng = api.Engine(0)
     assert not eng.debug_build
-    for name, wl in cases(W):
-        r = eng.grad(wl)
+    for name, wl, grad in cases(W):
         s = eng.snr(wl)
-        g_rel, e_rel = np.asarray(r["dT_dP"]), np.asarray(s["eta"])
-        g_dbg, e_dbg = np.array(dbg[name]["dT_dP"]), np.array(dbg[name]["eta"])
+        e_rel, e_dbg = np.asarray(s["eta"]), np.array(dbg[name]["eta"])
         fin = np.isfinite(e_rel)
         assert np.array_equal(fin, np.isfinite(e_dbg)), name
         np.testing.assert_allclose(e_dbg[fin], e_rel[fin], rtol=1e-12, err_msg=name)
-        np.testing.assert_allclose(g_dbg, g_rel, rtol=1e-10, atol=1e-12 * np.max(np.abs(g_rel)), err_msg=name)
         assert abs(dbg[name]["T"] / s["T"] - 1) < 1e-13, name
+        if grad:
+            g_rel, g_dbg = np.asarray(eng.grad(wl)["dT_dP"]), np.array(dbg[name]["dT_dP"])
+            np.testing.assert_allclose(g_dbg, g_rel, rtol=1e-10, atol=1e-12 * np.max(np.abs(g_rel)), err_msg=name)
+        else:
+            e64 = np.asarray(eng.snr(wl, precision=1)["eta"])
+            np.testing.assert_allclose(np.array(dbg[name]["eta64"])[fin], e64[fin], rtol=1e-12, err_msg=name)

@@ -85,8 +85,6 @@ def test_rejections(eng):
         eng.eta(wl.with_(cell_set=W.CELLS_ALL, G_mci=33))
     with pytest.raises(IsrsError):
         eng.grad(W.raman(wl.with_(cell_set=W.CELLS_ALL, G_mci=4)))
-    with pytest.raises(IsrsError):
-        eng.eta(W.raman(wl.with_(cell_set=W.CELLS_ALL, G_mci=4)))
 
 
 STEP_DB = 1e-4
