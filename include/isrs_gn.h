@@ -230,8 +230,9 @@ isrs_status isrs_gn_grad(isrs_handle h, const isrs_fibre *fibre, const isrs_chan
  * isrs_gn_grad_shard_fwd: the fused forward + adjoint quadrature of
  * isrs_gn_grad over the CUTs in `cuts` only (n_cuts entries, no repeats);
  * writes eta[n_cuts] of those CUTs (host or device) and keeps the shard's
- * buckets in the handle.  Closed-form profile only (UNSUPPORTED otherwise);
- * the other requirements and errors are those of isrs_gn_grad.
+ * buckets in the handle (with the Raman-ODE profile also the RK4 states of
+ * the profile, whose discrete adjoint is linear in the shard's bucket
+ * terms); requirements and errors are those of isrs_gn_grad.
  *
  * The caller gathers eta of every channel from all shards (eta_all[n_ch]).
  *

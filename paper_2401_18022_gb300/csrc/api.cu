@@ -1321,10 +1321,11 @@ ChainParams chain_params(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q
     return cp;
 }
 
-// Gradient with the Raman-ODE profile: forward (keeping the RK4 states),
-// dT/dSigma per CUT, the adjoint quadrature into dT/d{a, b} and the PSD
-// terms, then the discrete adjoint of the profile tables and the ODE.
-isrs_status run_grad_tab(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
+// Gradient with the Raman-ODE profile, first half: the profile tables with
+// the RK4 states kept, then the fused forward + adjoint quadrature over the
+// geometry's CUTs (Sigma into the partials, the unweighted buckets into the
+// tile rows).
+isrs_status run_grad_tab_fwd(isrs_handle h, const isrs_fibre *fb, Geom *g, cudaStream_t st)
 {
     isrs_status s;
     const int n = g->plan_n[0], M = g->n_steps;
@@ -1355,15 +1356,29 @@ isrs_status run_grad_tab(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q
         if (g->n_items > 0) CK(launch_adjoint_tab(ap, grid, block, st));
         if ((s = mark(h, 1, 1, st)) != ISRS_OK) return s;
     }
-    if ((s = run_finish(h, fb, q, g, true, st)) != ISRS_OK) return s;
-    const ChainParams cp = chain_params(h, fb, q, g, n);
+    h->last_points = g->n_points;
+    h->last_psteps = g->n_points * (int64_t)M;
+    h->last_launches += 1;   // fused quadrature + adjoint (prep and Raman ODE counted)
+    return ISRS_OK;
+}
+
+// Second half: dT/dSigma of every channel from cp.snr/pnli/pase (ybar), the
+// gather of the tile rows of the geometry's CUTs, then the discrete adjoint
+// of the profile tables and the RK4 steps.  with_direct adds the terms
+// outside every eta (the ASE gain and the SNR numerator); the parts of
+// disjoint CUT shards, one of them with_direct, sum to the full gradient,
+// since the adjoint is linear in the bucket terms.
+isrs_status run_grad_tab_bwd(isrs_handle h, const isrs_fibre *fb, Geom *g, const ChainParams &cp, bool with_direct,
+                             cudaStream_t st)
+{
+    const int n = g->plan_n[0], M = g->n_steps;
     Range r_chain("isrs chain rule (tabulated profile, Raman ODE)");
     CK(launch_ybar(cp, st));
     TabGatherParams gp;
     gp.gath_off = (const int *)g->tab_gath_off.p;
     gp.gath = (const int2 *)g->tab_gath.p;
-    gp.rows = ap.rows;
-    gp.rowsV = ap.rowsV;
+    gp.rows = (const double2 *)h->tab_rows.p;
+    gp.rowsV = (const double *)h->tab_rowsV.p;
     gp.ybar = cp.ybar;
     gp.slot_cut = (const int *)g->slot_cut.p;
     gp.n_ch = n;
@@ -1381,16 +1396,26 @@ isrs_status run_grad_tab(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q
     rap.gAt = (double *)h->gAt.p;
     rap.aase = cp.aase;
     rap.gV = (const double *)h->gV.p;
-    rap.snr = (const double *)h->o_snr.p;
-    rap.pnli = (const double *)h->o_pnli.p;
-    rap.pase = (const double *)h->o_pase.p;
+    rap.snr = cp.snr;
+    rap.pnli = cp.pnli;
+    rap.pase = cp.pase;
     rap.ch_B = (const double *)g->ch_B.p;
+    rap.with_direct = with_direct ? 1 : 0;
     rap.dT_dP = (double *)h->dTdP.p;
     CK(launch_raman_adj(rap, st));
-    h->last_points = g->n_points;
-    h->last_psteps = g->n_points * (int64_t)M;
-    h->last_launches += 5;   // fused quadrature + adjoint, ybar, gather, slope fold, ODE adjoint (finish counted)
+    h->last_launches += 4;   // ybar, gather, slope fold, ODE adjoint
     return ISRS_OK;
+}
+
+// Gradient with the Raman-ODE profile: both halves around the finish (eta,
+// SNR, T of every channel).
+isrs_status run_grad_tab(isrs_handle h, const isrs_fibre *fb, const isrs_quad *q, Geom *g, cudaStream_t st)
+{
+    isrs_status s;
+    if ((s = run_grad_tab_fwd(h, fb, g, st)) != ISRS_OK) return s;
+    if ((s = run_finish(h, fb, q, g, true, st)) != ISRS_OK) return s;
+    const ChainParams cp = chain_params(h, fb, q, g, g->plan_n[0]);
+    return run_grad_tab_bwd(h, fb, g, cp, true, st);
 }
 
 // Argument checks shared by the gradient entry points; selects the device and
@@ -1800,8 +1825,6 @@ isrs_status isrs_gn_grad_shard_fwd(isrs_handle h, const isrs_fibre *fibre, const
     h->shard_valid = false;
     isrs_status s;
     if (!eta || !cuts || n_cuts < 1) return fail(h, ISRS_ERR_INVALID_ARG, "eta, cuts or n_cuts missing");
-    if (fibre && fibre->profile == ISRS_PROFILE_RAMAN_ODE)
-        return fail(h, ISRS_ERR_UNSUPPORTED, "the split gradient covers the closed-form profile");
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = grad_checks(h, fibre, ch, P_W, quad, st)) != ISRS_OK) return s;
     if ((s = check_ptr(h, eta, "eta")) != ISRS_OK) return s;
@@ -1820,7 +1843,11 @@ isrs_status isrs_gn_grad_shard_fwd(isrs_handle h, const isrs_fibre *fibre, const
     std::vector<int> pp{0};
     if ((s = get_geom(h, fibre, 1, ch, cpp, pp, quad, st, &g)) != ISRS_OK) return s;
     if ((s = load_powers(h, P_W, ch->n_ch, st)) != ISRS_OK) return s;
-    if ((s = run_forward(h, fibre, g, ISRS_PREC_FP32, st, true)) != ISRS_OK) return s;
+    if (fibre->profile == ISRS_PROFILE_RAMAN_ODE) {
+        if ((s = run_grad_tab_fwd(h, fibre, g, st)) != ISRS_OK) return s;
+    } else if ((s = run_forward(h, fibre, g, ISRS_PREC_FP32, st, true)) != ISRS_OK) {
+        return s;
+    }
     if ((s = run_finish(h, fibre, quad, g, false, st)) != ISRS_OK) return s;
     bool host_out = false;
     if ((s = copy_out(h, eta, h->o_eta, g->n_slots, st, host_out)) != ISRS_OK) return s;
@@ -1896,11 +1923,15 @@ isrs_status isrs_gn_grad_shard_bwd(isrs_handle h, const double *eta_all, int wit
     cp.pnli = sp.pnli;
     cp.pase = sp.pase;
     cp.with_direct = with_direct ? 1 : 0;
-    {
+    if (h->shard_fibre.profile == ISRS_PROFILE_RAMAN_ODE) {
+        // the tile rows and the RK4 states of the shard's forward
+        h->last_launches = 1;   // SNR from eta
+        if ((s = run_grad_tab_bwd(h, &h->shard_fibre, g, cp, with_direct != 0, st)) != ISRS_OK) return s;
+    } else {
         Range r_chain("isrs chain rule (dT/dP)");
         CK(launch_chain(cp, st));
+        h->last_launches = 7;    // SNR from eta, ybar, PSD-bucket reduction, step-bucket reduction, chain rule (3)
     }
-    h->last_launches = 7;    // SNR from eta, ybar, PSD-bucket reduction, step-bucket reduction, chain rule (3)
     bool host_out = false;
     if ((s = copy_out(h, dT_dP, h->dTdP, n, st, host_out)) != ISRS_OK) return s;
     if (snr) {

@@ -124,6 +124,8 @@ struct RamanAdjParams {
     const double *aase;         // [n] dT/d ln G_i (G = 1/rho(L))
     const double *gV;           // [n] dT/d ln P_j through the PSD products
     const double *snr, *pnli, *pase, *ch_B;
+    int with_direct;            // add the terms outside every eta (ASE gain, SNR numerator); a CUT
+                                // shard of a split gradient leaves them to one rank
     double *dT_dP;              // [n]
 };
 

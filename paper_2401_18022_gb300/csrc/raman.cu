@@ -365,7 +365,8 @@ __global__ void __launch_bounds__(kOdeThreads) k_raman_adj(RamanAdjParams ap)
     s.x2 = s.x1 + n + 1;
     s.x3 = s.x2 + n + 1;
 
-    for (int c = threadIdx.x; c < n; c += blockDim.x) lam[c] = -ap.aase[c];      // dT/d ln rho(L)
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        lam[c] = ap.with_direct ? -ap.aase[c] : 0.0;                               // dT/d ln rho(L)
     __syncthreads();
     int node = ap.n_rk;
     for (int m = M - 1; m >= 0; --m) {
@@ -418,14 +419,16 @@ __global__ void __launch_bounds__(kOdeThreads) k_raman_adj(RamanAdjParams ap)
     }
     // a = y - y(0): every table entry also depends on y(0) directly
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double direct = ap.aase[j];                                    // - dT/d ln rho(L)
+        double direct = ap.with_direct ? ap.aase[j] : 0.0;             // - dT/d ln rho(L)
         for (int m = 0; m < M; ++m) direct -= ap.gAt[(size_t)j * M + m];
         const double P = rp.P[j];
         double g = (lam[j] + direct + ap.gV[j]) / P;
-        const double snr = ap.snr[j], B = ap.ch_B[j];
-        const double N = ap.pnli[j] + ap.pase[j];
-        const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
-        g += dTds * snr * snr * N / (P * P);
+        if (ap.with_direct) {                                          // the SNR numerator
+            const double snr = ap.snr[j], B = ap.ch_B[j];
+            const double N = ap.pnli[j] + ap.pase[j];
+            const double dTds = 2.0 * B / (0.69314718055994530942 * (1.0 + snr));
+            g += dTds * snr * snr * N / (P * P);
+        }
         ap.dT_dP[j] = g;
     }
 }

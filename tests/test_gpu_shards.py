@@ -46,17 +46,21 @@ def _np(x):
 
 
 @pytest.mark.parametrize("world", [2, 3])
-@pytest.mark.parametrize("case", ["tiny", "oband", "uwb"])
+@pytest.mark.parametrize("case", ["tiny", "oband", "uwb", "raman_tiny", "raman_uwb"])
 def test_split_gradient_shards_sum_to_one_gradient(eng, orc, world, case):
     """The gradient split by CUT shards (isrs_gn_grad_shard_fwd/_bwd), run as
     sequential ranks on one GPU with one handle each: eta gathered from the
     shards, each shard's part of dT/dP from the gathered eta, rank 0 adding
     the terms outside eta.  The parts sum to one isrs_gn_grad call; only the
-    order of the FP64 sums over tiles differs."""
+    order of the FP64 sums over tiles differs.  With the Raman-ODE profile
+    each shard runs the discrete adjoint of the RK4 steps on its own bucket
+    terms (the adjoint is linear in them)."""
     from paper_2401_18022_gb300 import api
-    wl = {"tiny": W.tiny(G=16, n_edges=33),
-          "oband": W.oband(G=12, n_edges=33),
-          "uwb": W.uwb(G=8, n_edges=33)}[case]
+    wl = {"tiny": lambda: W.tiny(G=16, n_edges=33),
+          "oband": lambda: W.oband(G=12, n_edges=33),
+          "uwb": lambda: W.uwb(G=8, n_edges=33),
+          "raman_tiny": lambda: W.raman(W.tiny(G=16, n_edges=33).with_(Cr=0.4), raman_max_THz=0.25),
+          "raman_uwb": lambda: W.raman(W.uwb(G=8, n_edges=33), ode_h_km=0.5)}[case]()
     weights = [len(orc.pieces(wl.f_THz - wl.f_ref_THz, wl.B_THz, c, wl.cell_set)) for c in range(wl.n_ch)]
     full = eng.grad(wl)
     ranks = [api.Engine(0) for _ in range(world)]
