@@ -640,6 +640,13 @@ def profile_case(kind: str) -> int:
         from paper_2401_18022_gb300 import workloads as W
         sub = W.subset_plan(wl, np.arange(0, wl.n_ch, 4), "uwb-148ch-every4th").with_(cell_set=W.CELLS_ALL, G_mci=8)
         eng.grad(sub, P=torch.tensor(sub.P_W, dtype=torch.float64, device="cuda"))
+    elif kind == "raman_mci":
+        # the Raman-ODE profile with every cell (SCI/XCI at G = 256, MCI on an
+        # 8 x 8 grid) on 48 CUTs of the 589-ch plan: 528 MCI work tiles, so the
+        # MCI kernel fills every SM as in the full run
+        from paper_2401_18022_gb300 import workloads as W
+        wr = W.raman(wl.with_(cell_set=W.CELLS_ALL, G_mci=8))
+        eng.eta(wr, P=P, cuts=[int(c) for c in np.linspace(0, wl.n_ch - 1, 48)])
     elif kind in ("adjoint256", "quad256"):
         # every 4th slot of the 589-ch grid (148 ch over the whole band) at the
         # bench's G = 256: the production per-piece shape, ~1.4e9 points
@@ -685,7 +692,8 @@ def main():
     ap.add_argument("--chunks", type=int, default=16, help="accuracy: FP64 launches over the CUTs")
     ap.add_argument("--out", default=None, help="accuracy: write per-CUT errors (JSON) here")
     ap.add_argument("--profile-case", default=None,
-                    choices=["quad", "quad64", "adjoint", "adjoint256", "quad256", "raman256", "mci256", "probe"],
+                    choices=["quad", "quad64", "adjoint", "adjoint256", "quad256", "raman256", "mci256", "raman_mci",
+                             "probe"],
                     help="run one small launch of a kernel (for ncu captures) and exit")
     args = ap.parse_args()
     if args.profile_case:
