@@ -572,8 +572,9 @@ def run_batched(args) -> int:
 
 
 def run_accuracy(args) -> int:
-    """The accuracy gate at the benchmark's size: every CUT of the 589-ch
-    workload (G = 256), the FP32 path against the plain FP64 GPU path, as the
+    """The accuracy gate: every CUT of the 589-ch workload (G = 256 unless
+    --G; --profile raman for the Raman-ODE profile, --G-mci for the MCI cells
+    on their own grid), the FP32 path against the plain FP64 GPU path, as the
     per-CUT error in dB of eta and of SNR (the method's target: 0.01 dB of
     SNR per channel).  The FP64 path runs in chunks of CUTs (~1 min each);
     SNR_64 = P / (eta_64 P^3 + P_ASE) with the ASE of the same plan (no
@@ -584,6 +585,13 @@ def run_accuracy(args) -> int:
     torch.cuda.set_device(0)
     eng = api.Engine(0)
     wl = _workload(args.G)
+    label = "uwb-589ch-80km-G%d-N113-sci_xci" % wl.G
+    if args.G_mci > 0:
+        wl = wl.with_(cell_set=W.CELLS_ALL, G_mci=args.G_mci)
+        label = "uwb-589ch-80km-G%d-N113-all_cells-Gmci%d" % (wl.G, args.G_mci)
+    if args.profile == "raman":
+        wl = W.raman(wl)
+        label += "-raman_ode"
     P = torch.tensor(wl.P_W, dtype=torch.float64, device="cuda")
     r32 = eng.snr(wl, P=P, precision=0)
     e32, s32 = r32["eta"].cpu().numpy(), r32["snr"].cpu().numpy()
@@ -599,7 +607,7 @@ def run_accuracy(args) -> int:
     ds = np.abs(10 * np.log10(s32 / s64))
     lam = W.nm_from_thz(wl.f_THz)
     band = np.clip(np.searchsorted(W.BAND_EDGES_NM, lam, side="right") - 1, 0, 5)
-    line = {"accuracy_gate": "uwb-589ch-80km-G%d-N113-sci_xci FP32 vs plain FP64 GPU, all CUTs" % wl.G,
+    line = {"accuracy_gate": label + " FP32 vs plain FP64 GPU, all CUTs",
             "n_cuts": int(wl.n_ch), "fp64_seconds": t64,
             "eta_dB": {"max": float(de.max()), "mean": float(de.mean()), "argmax": int(de.argmax())},
             "snr_dB": {"max": float(ds.max()), "mean": float(ds.mean()), "argmax": int(ds.argmax())},
@@ -691,6 +699,10 @@ def main():
                          "accuracy: all 589 CUTs FP32 vs the plain FP64 GPU path")
     ap.add_argument("--chunks", type=int, default=16, help="accuracy: FP64 launches over the CUTs")
     ap.add_argument("--out", default=None, help="accuracy: write per-CUT errors (JSON) here")
+    ap.add_argument("--profile", default="closed", choices=["closed", "raman"],
+                    help="accuracy: closed-form profile or the Raman ODEs")
+    ap.add_argument("--G-mci", dest="G_mci", type=int, default=0,
+                    help="accuracy: > 0 adds every MCI cell on its own G_mci grid")
     ap.add_argument("--profile-case", default=None,
                     choices=["quad", "quad64", "adjoint", "adjoint256", "quad256", "raman256", "mci256", "raman_mci",
                              "probe"],
