@@ -206,12 +206,15 @@ def band_report(engine, wl, P, band: np.ndarray, snr_trx_dB: float = 0.0, precis
 
 def run_stages(engine, case: int = 1, stages: Sequence[int] = (32, 64), n_edges: int = 113,
                gtol: float = 0.01, maxiter: int = 500, log: Optional[Callable] = None,
-               profile: str = "closed") -> dict:
+               profile: str = "closed", g_mci: int = 0) -> dict:
     """Case 1 (segments) or Case 2 (uniform) on the guarded 557-channel plan:
     one L-BFGS-B run per quadrature size G in `stages`, each started from the
     previous result (the first from 0 dBm).  profile "raman" uses the
     Raman-ODE power profile (15 THz gain cut-off, photon ratio, Aeff
-    scaling), "closed" the linear-slope closed form."""
+    scaling), "closed" the linear-slope closed form.  The optimisation sums
+    the SCI and XCI cells; with g_mci > 0 the optimum is also evaluated over
+    the whole band (every other cell on its own g_mci grid, App. A's integral
+    over all frequencies), reported as report_mci."""
     x = None
     out = {"case": case, "profile": profile, "stages": []}
     for G in stages:
@@ -229,6 +232,10 @@ def run_stages(engine, case: int = 1, stages: Sequence[int] = (32, 64), n_edges:
     P = obj.powers(x)
     out["report"] = band_report(engine, wl, P, band)
     out["report_trx20"] = band_report(engine, wl, P, band, snr_trx_dB=20.0)
+    if g_mci > 0:
+        wm = wl.with_(cell_set=W.CELLS_ALL, G_mci=int(g_mci))
+        out["report_mci"] = {"G_mci": int(g_mci), **band_report(engine, wm, P, band)}
+        out["report_mci_trx20"] = band_report(engine, wm, P, band, snr_trx_dB=20.0)
     out["x_ch_dBm_min_max"] = [float(param.x_ch(x).min()), float(param.x_ch(x).max())]
     return out
 
@@ -243,12 +250,14 @@ def main(argv=None):
     ap.add_argument("--gtol", type=float, default=0.01)
     ap.add_argument("--maxiter", type=int, default=500)
     ap.add_argument("--profile", default="raman", choices=("raman", "closed"))
+    ap.add_argument("--mci", type=int, default=0,
+                    help="> 0: also evaluate the optimum with every MCI cell on its own grid of this size")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     eng = api.Engine(0)
     stages = [int(s) for s in a.stages.split(",")]
     res = run_stages(eng, a.case, stages, gtol=a.gtol, maxiter=a.maxiter,
-                     log=lambda h: print(json.dumps(h), flush=True), profile=a.profile)
+                     log=lambda h: print(json.dumps(h), flush=True), profile=a.profile, g_mci=a.mci)
     print(json.dumps({k: v for k, v in res.items()}), flush=True)
     if a.out:
         json.dump(res, open(a.out, "w"), indent=1)
