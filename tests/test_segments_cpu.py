@@ -212,3 +212,37 @@ def test_band_report_with_transceiver_noise():
     assert r0["bands"]["U"]["pow_dBm"] == pytest.approx(10 * np.log10(2), abs=1e-12)
     assert sum(b["cap_Tbps"] for b in r0["bands"].values()) == pytest.approx(r0["T"], rel=1e-12)
     assert r20["T"] < r0["T"]
+
+
+class _CellsEngine(ToyEngine):
+    """ToyEngine that records the cells of every SNR call and adds 1 % more
+    noise when the MCI cells are included (whole band)."""
+
+    def __init__(self, a, c):
+        super().__init__(a, c)
+        self.seen = []
+
+    def snr(self, wl, P=None, precision=0):
+        self.seen.append((wl.cell_set, wl.G_mci))
+        a0 = self.a
+        if wl.cell_set == W.CELLS_ALL and wl.G_mci > 0:
+            self.a = a0 * 1.01
+        try:
+            return super().snr(wl, P, precision)
+        finally:
+            self.a = a0
+
+
+def test_run_stages_reports_the_optimum_over_the_whole_band():
+    """run_stages optimises over the SCI/XCI cells and, with g_mci > 0,
+    evaluates the optimum again with every MCI cell on its own grid."""
+    wl = W.uwb_guarded(G=8)
+    base = _toy_for(wl, np.full(wl.n_ch, 1.5), seed=5)
+    eng = _CellsEngine(base.a, base.c)
+    out = S.run_stages(eng, case=2, stages=(8,), g_mci=4)
+    assert out["report_mci"]["G_mci"] == 4
+    assert out["report_mci"]["T"] < out["report"]["T"]
+    assert out["report_mci_trx20"]["T"] < out["report_mci"]["T"]
+    assert (W.CELLS_ALL, 4) in eng.seen and (W.CELLS_SCI_XCI, 0) in eng.seen
+    plain = S.run_stages(_CellsEngine(base.a, base.c), case=2, stages=(8,))
+    assert "report_mci" not in plain
