@@ -110,27 +110,37 @@ class _OracleShards:
         return {"dT_dP": g, "snr": snr, "T": T}
 
 
-def _split_worker(rank, world, port, out_dir):
-    import torch.distributed as dist
-    from paper_2401_18022_gb300 import dist as D, workloads as W
-    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+def _split_wl(profile):
+    from paper_2401_18022_gb300 import workloads as W
     wl = W.tiny(G=8, n_edges=9)
+    if profile == "raman":
+        # the Raman-ODE profile: the ASE gain of every channel depends on
+        # every launch power through the ODE, one of the terms outside eta
+        wl = W.raman(wl.with_(Cr=0.4), raman_max_THz=0.25, ode_h_km=2.0)
+    return wl
+
+
+def _split_worker(rank, world, port, out_dir, profile):
+    import torch.distributed as dist
+    from paper_2401_18022_gb300 import dist as D
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    wl = _split_wl(profile)
     out = D.grad_split(_OracleShards(), wl, wl.P_W, rank, world)
     np.save(os.path.join(out_dir, f"g{rank}.npy"), np.concatenate([out["dT_dP"], out["eta"], [out["T"]]]))
     dist.barrier()
     dist.destroy_process_group()
 
 
-def test_split_gradient_world2_equals_full_gradient(tmp_path, orc):
+@pytest.mark.parametrize("profile", ["closed", "raman"])
+def test_split_gradient_world2_equals_full_gradient(tmp_path, orc, profile):
     """The split gradient's host logic (shards, eta gathered by an all-reduce,
     exactly one rank adding the terms outside eta, all-reduce of the parts),
     with the oracle standing in for each rank's GPU phases, equals the central
-    difference of the single-process oracle throughput."""
+    difference of the single-process oracle throughput, for both profiles."""
     import torch.multiprocessing as mp
-    from paper_2401_18022_gb300 import workloads as W
     port = _free_port()
-    mp.start_processes(_split_worker, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn")
-    wl = W.tiny(G=8, n_edges=9)
+    mp.start_processes(_split_worker, args=(2, port, str(tmp_path), profile), nprocs=2, start_method="spawn")
+    wl = _split_wl(profile)
     n = wl.n_ch
     r0, r1 = np.load(tmp_path / "g0.npy"), np.load(tmp_path / "g1.npy")
     np.testing.assert_array_equal(r0, r1)                     # every rank holds the full result
