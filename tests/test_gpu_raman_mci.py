@@ -123,6 +123,16 @@ def test_snr_multispan_and_batched(eng, orc):
             off += pl.n_ch
 
 
+@pytest.mark.parametrize("prec,rtol", [(1, RTOL_F64), (0, RTOL_F32)])
+def test_empty_slot_and_ragged_grids(eng, orc, prec, rtol):
+    """An empty slot (P = 0: a zero-power probe of the ODE, no PSD in any
+    cell) with odd G, G_mci and step counts."""
+    wl = _tiny_r2_all(G=13, n_edges=23, G_mci=5)
+    P = wl.P_W.copy()
+    P[1] = 0.0
+    np.testing.assert_allclose(eng.eta(wl, P=P, precision=prec)["sigma"], orc.sigma(wl, P=P), rtol=rtol)
+
+
 def test_gradient_rejected(eng):
     from paper_2401_18022_gb300._capi import IsrsError
     with pytest.raises(IsrsError):
