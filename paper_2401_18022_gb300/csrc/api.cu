@@ -1109,6 +1109,8 @@ isrs_status run_forward(isrs_handle h, const isrs_fibre *fb, Geom *g, int precis
                     if (cpc < 1)
                         return fail(h, ISRS_ERR_UNSUPPORTED, "MCI step rows of %d steps exceed shared memory", M);
                     const size_t nab = (size_t)g->total_prof_ch * M;
+                    if (nab > (size_t)INT32_MAX)
+                        return fail(h, ISRS_ERR_UNSUPPORTED, "profile tables of %zu entries exceed the MCI conversion", nab);
                     if ((s = ensure(h, h->ab_f, sizeof(float2) * nab)) != ISRS_OK) return s;
                     qm.ab_f = (const float2 *)h->ab_f.p;
                     CK(launch_tab_half_log2((const double2 *)h->ab.p, (float2 *)h->ab_f.p, (int)nab, h->num_sms,
