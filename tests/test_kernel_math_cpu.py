@@ -199,3 +199,44 @@ def test_segmented_moment_series(orc):
                 bound = 2e-8 * np.sum(p * dz) + 1e-13 * abs(exact)
                 assert abs(S - exact) < bound, (J, ph * L, abs(S - exact), bound)
         assert phmax * L > {2: 11.0, 4: 21.0, 8: 40.0}[J]
+
+
+def test_mci_cell_rows_with_tabulated_profile(orc):
+    """k_quad_mci_f32_tab forms log2 p_m of an MCI point from its cell's row
+    {A + log2 dz, S_a, S_b} (A = (a_a + a_b - a_i)/2 log2 e, S = b/2 log2 e)
+    and the FP32 row {a_c, b_c}/2 log2 e of its F_c channel:
+        log2 p_m dz_m = row.x + S_a da + S_b db + T_c.x + T_c.y dc,
+    da, db, dc the point's offsets from the channel centres.  This equals
+    log2 of p_m dz_m from the oracle's ln rho (Eq. pk with the Raman-ODE
+    tables) to FP32 rounding (measured 8.7e-7 in log2 units on the 589-ch
+    plan, a 6e-7 relative error of p; bound 4e-6)."""
+    from paper_2401_18022_gb300 import workloads as W
+    wl = W.raman(W.uwb(G=8, n_edges=57), ode_h_km=1.0)
+    a, b, _ = orc.raman_profile(wl)
+    f = wl.f_THz
+    ze = orc.zgrid(wl.L_km, wl.alpha_R_per_km, wl.n_edges)
+    dz = np.diff(ze)
+    l2e = 1.0 / np.log(2.0)
+    af = (0.5 * l2e * a).astype(np.float32)
+    bf = (0.5 * l2e * b).astype(np.float32)
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for _ in range(200):
+        i, ca, cb = rng.integers(0, wl.n_ch, 3)
+        Fa = f[ca] + rng.uniform(-0.048, 0.048)
+        Fb = f[cb] + rng.uniform(-0.048, 0.048)
+        Fc = Fa + Fb - f[i]
+        cc = int(np.argmin(np.abs(f - Fc)))
+        if abs(Fc - f[cc]) > 0.048:
+            continue
+        # the oracle's definition, FP64
+        lnp = 0.5 * ((a[ca] + b[ca] * (Fa - f[ca])) + (a[cb] + b[cb] * (Fb - f[cb]))
+                     + (a[cc] + b[cc] * (Fc - f[cc])) - a[i])
+        ref = lnp * l2e + np.log2(dz)
+        # the kernel's rows and FP32 arithmetic
+        A = (af[ca] + af[cb]) - af[i]
+        rowx = A + np.log2(dz).astype(np.float32)
+        da, db, dc = np.float32(Fa - f[ca]), np.float32(Fb - f[cb]), np.float32(Fc - f[cc])
+        got = rowx + bf[ca] * da + bf[cb] * db + bf[cc] * dc + af[cc]
+        worst = max(worst, float(np.max(np.abs(got.astype(np.float64) - ref))))
+    assert worst < 4e-6, worst
